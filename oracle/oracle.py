@@ -1,0 +1,234 @@
+"""ctypes front end of the FP64 CPU oracle (oracle.c).
+
+TEST INFRASTRUCTURE ONLY: the slow, plain definition of the multistep BSDE
+scheme (Kapllani & Teng, arXiv:1909.13560, Eq. 20-21, Tables 1-2) that the
+CUDA path is checked against.  Only the test suite, the smoke check and the
+CPU-baseline leg of the benchmark import this module.  It shares no code with
+the product package and never imports it.
+
+Problems are plain dicts (see ``paper_1909_13560_gb300.workloads``); this
+module marshals them into its own C struct.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+DRIVERS = {"LIN_SIN": 0, "BS": 1, "LB": 2, "EX1": 3, "EX2": 4}
+TERMINALS = {"SIN": 0, "CALL_LOG": 1, "LOGISTIC": 2, "LNSIN": 3}
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [
+        ("driver", ctypes.c_int), ("terminal", ctypes.c_int),
+        ("smoothing", ctypes.c_int), ("picard_max", ctypes.c_int),
+        ("T", ctypes.c_double), ("x_min", ctypes.c_double),
+        ("x_max", ctypes.c_double), ("x0", ctypes.c_double),
+        ("a_x", ctypes.c_double), ("b_x", ctypes.c_double),
+        ("r", ctypes.c_double), ("mu", ctypes.c_double),
+        ("sigma", ctypes.c_double), ("R", ctypes.c_double),
+        ("delta", ctypes.c_double), ("lb_sign", ctypes.c_double),
+        ("strike", ctypes.c_double), ("picard_tol", ctypes.c_double),
+        ("Nx", ctypes.c_longlong), ("N", ctypes.c_int), ("k", ctypes.c_int),
+        ("L", ctypes.c_int),
+    ]
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [
+        ("y0", ctypes.c_double), ("z0", ctypes.c_double),
+        ("picard_resid_max", ctypes.c_double), ("levels_done", ctypes.c_longlong),
+        ("status", ctypes.c_int), ("picard_iters_max", ctypes.c_int),
+    ]
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so next to it (plain C, FP64, no FMA
+    contraction, OpenMP over grid points)."""
+    with _lock:
+        if (not force and os.path.exists(_LIB)
+                and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+            return _LIB
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+               "-fno-fast-math", "-fopenmp", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+        return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        P = ctypes.POINTER
+        d = ctypes.c_double
+        lib.orc_gauss_hermite.argtypes = [ctypes.c_int, P(d), P(d)]
+        lib.orc_gamma.argtypes = [ctypes.c_int, P(d), P(d)]
+        lib.orc_spline.argtypes = [ctypes.c_longlong, d, P(d), P(d)]
+        lib.orc_interp.argtypes = [ctypes.c_longlong, d, d, P(d), P(d), d]
+        lib.orc_interp.restype = d
+        lib.orc_driver.argtypes = [P(_Problem), d, d, d]
+        lib.orc_driver.restype = d
+        lib.orc_exact.argtypes = [P(_Problem), d, d, P(d), P(d)]
+        lib.orc_init_levels.argtypes = [P(_Problem), P(d), P(d)]
+        lib.orc_expectations.argtypes = [P(_Problem), ctypes.c_int, P(d), P(d),
+                                         P(ctypes.c_longlong), ctypes.c_longlong, P(d)]
+        lib.orc_solve.argtypes = [P(_Problem), P(d), P(d), ctypes.c_longlong,
+                                  P(d), P(d), P(_Result), ctypes.c_int]
+        lib.orc_max_threads.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _problem(p: dict) -> _Problem:
+    s = _Problem()
+    s.driver = DRIVERS[p["driver"]]
+    s.terminal = TERMINALS[p["terminal"]]
+    s.smoothing = int(p.get("smoothing", 0))
+    s.picard_max = int(p.get("picard_max", 30))
+    for f in ("T", "x_min", "x_max", "x0", "a_x", "b_x"):
+        setattr(s, f, float(p[f]))
+    for f in ("r", "mu", "sigma", "R", "delta", "strike"):
+        setattr(s, f, float(p.get(f, 0.0)))
+    s.lb_sign = float(p.get("lb_sign", 1.0))
+    if s.sigma == 0.0:
+        s.sigma = 1.0
+    s.picard_tol = float(p.get("picard_tol", 1e-12))
+    s.Nx = int(p["Nx"])
+    s.N = int(p["N"])
+    s.k = int(p["k"])
+    s.L = int(p["L"])
+    return s
+
+
+def gauss_hermite(L: int):
+    lib = _load()
+    a = np.zeros(L)
+    w = np.zeros(L)
+    if lib.orc_gauss_hermite(L, _dptr(a), _dptr(w)) != 0:
+        raise ValueError("bad L")
+    return a, w
+
+
+def gamma(K: int):
+    lib = _load()
+    gy = np.zeros(K + 1)
+    gz = np.zeros(K + 1)
+    if lib.orc_gamma(K, _dptr(gy), _dptr(gz)) != 0:
+        raise ValueError("K out of the tables' range 1..6")
+    return gy, gz
+
+
+def spline(v: np.ndarray, dx: float) -> np.ndarray:
+    lib = _load()
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    M = np.zeros_like(v)
+    if lib.orc_spline(len(v), dx, _dptr(v), _dptr(M)) != 0:
+        raise ValueError("spline needs at least 2 points")
+    return M
+
+
+def interp(v: np.ndarray, M: np.ndarray, x_min: float, dx: float, X: float) -> float:
+    lib = _load()
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    M = np.ascontiguousarray(M, dtype=np.float64)
+    return lib.orc_interp(len(v), x_min, dx, _dptr(v), _dptr(M), float(X))
+
+
+def driver(p: dict, t: float, y: float, z: float) -> float:
+    lib = _load()
+    s = _problem(p)
+    return lib.orc_driver(ctypes.byref(s), t, y, z)
+
+
+def exact(p: dict, t: float, x: float):
+    lib = _load()
+    s = _problem(p)
+    u = ctypes.c_double()
+    z = ctypes.c_double()
+    if lib.orc_exact(ctypes.byref(s), t, x, ctypes.byref(u), ctypes.byref(z)) != 0:
+        raise ValueError("no closed form for this terminal id")
+    return u.value, z.value
+
+
+def init_levels(p: dict):
+    lib = _load()
+    s = _problem(p)
+    iy = np.zeros((s.k, s.Nx))
+    iz = np.zeros((s.k, s.Nx))
+    if lib.orc_init_levels(ctypes.byref(s), _dptr(iy), _dptr(iz)) != 0:
+        raise ValueError("no closed form for this problem")
+    return iy, iz
+
+
+def expectations(p: dict, n: int, levels_y: np.ndarray, levels_z: np.ndarray,
+                 idx) -> np.ndarray:
+    """E_j[z^], E_j[f], E_j[f dW], E_j[y^], E_j[y^ dW] (j = 1..k) at grid
+    points idx for level n; row j-1 of levels_* is level n+j.
+    Returns an array of shape (len(idx), k, 5)."""
+    lib = _load()
+    s = _problem(p)
+    ly = np.ascontiguousarray(levels_y, dtype=np.float64)
+    lz = np.ascontiguousarray(levels_z, dtype=np.float64)
+    ix = np.ascontiguousarray(np.asarray(idx, dtype=np.int64))
+    out = np.zeros((len(ix), s.k, 5))
+    rc = lib.orc_expectations(ctypes.byref(s), int(n), _dptr(ly), _dptr(lz),
+                              ix.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)),
+                              len(ix), _dptr(out))
+    if rc != 0:
+        raise ValueError("bad problem")
+    return out
+
+
+def solve(p: dict, init_y=None, init_z=None, levels: int = 0, threads: int = 1,
+          want_level: bool = False) -> dict:
+    """Run the backward loop.  Returns y0, z0 (readout at x0 of the last
+    computed level), Picard statistics and, if asked, that level's arrays."""
+    lib = _load()
+    s = _problem(p)
+    res = _Result()
+    iy = iz = None
+    if init_y is not None:
+        iy = np.ascontiguousarray(init_y, dtype=np.float64)
+        iz = np.ascontiguousarray(init_z, dtype=np.float64)
+        if iy.shape != (s.k, s.Nx) or iz.shape != (s.k, s.Nx):
+            raise ValueError("initial levels must have shape (k, Nx)")
+    oy = np.zeros(s.Nx) if want_level else None
+    oz = np.zeros(s.Nx) if want_level else None
+    rc = lib.orc_solve(ctypes.byref(s),
+                       _dptr(iy) if iy is not None else None,
+                       _dptr(iz) if iz is not None else None,
+                       int(levels),
+                       _dptr(oy) if oy is not None else None,
+                       _dptr(oz) if oz is not None else None,
+                       ctypes.byref(res), int(threads))
+    if rc != 0:
+        raise ValueError(f"oracle rejected the problem (rc={rc})")
+    out = {"y0": res.y0, "z0": res.z0, "status": res.status,
+           "picard_iters_max": res.picard_iters_max,
+           "picard_resid_max": res.picard_resid_max,
+           "levels_done": res.levels_done}
+    if want_level:
+        out["y"] = oy
+        out["z"] = oz
+    return out
+
+
+def max_threads() -> int:
+    return int(_load().orc_max_threads())

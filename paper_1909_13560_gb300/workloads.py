@@ -1,0 +1,132 @@
+"""Seeded synthetic workloads: problem parameters only.
+
+These generators describe *what* is solved (drivers, terminal conditions,
+domains, grid sizes, seeded parameter draws); they contain none of the
+scheme's arithmetic.  Both the CUDA path and the CPU oracle consume the same
+dicts.  No dataset is involved anywhere: the paper's examples are analytic
+BSDEs (Section 5) and every workload here is defined by closed-form data.
+
+Problem dict keys
+-----------------
+driver      "LIN_SIN" | "BS" | "LB" | "EX1" | "EX2"
+terminal    "SIN" | "CALL_LOG" | "LOGISTIC" | "LNSIN"
+T, x_min, x_max, x0        time horizon, uniform grid [x_min, x_max], readout point
+a_x, b_x    forward process dX = a_x dt + b_x dW (X = W: 0, 1;
+            log price, Eq. 33: mu - sigma^2/2, sigma)
+r, mu, sigma, R, delta, lb_sign, strike   driver / payoff parameters
+Nx, N, k, L                 grid points, time steps, steps of the scheme, GH nodes
+picard_tol, picard_max, smoothing
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+def sin_problem(Nx: int = 2001, N: int = 64, k: int = 2, L: int = 8,
+                x_lim: float = 8.0, T: float = 1.0) -> dict:
+    """1-D linear BSDE f = y/2 - z, g(x) = sin(x + T), X = W; exact
+    y = sin(W_t + t), z = cos(W_t + t), so (y_0, z_0) = (0, 1)."""
+    return dict(driver="LIN_SIN", terminal="SIN", T=T, x_min=-x_lim, x_max=x_lim,
+                x0=0.0, a_x=0.0, b_x=1.0, Nx=Nx, N=N, k=k, L=L,
+                picard_tol=1e-12, picard_max=30, smoothing=0)
+
+
+def call_problem(S0: float = 100.0, strike: float = 100.0, r: float = 0.03,
+                 mu: float = 0.05, sigma: float = 0.2, T: float = 1.0,
+                 delta: float = 0.0, Nx: int = 65536, N: int = 256, k: int = 6,
+                 L: int = 16, width_sd: float = 6.0, smoothing: int = 1,
+                 driver: str = "BS", R: float = 0.0, lb_sign: float = 1.0) -> dict:
+    """European call as a linear (BS) or lending/borrowing-rate (LB) BSDE in
+    log price X = ln S (Eq. 30, Eq. 33); grid ln S0 +- width_sd*sigma*sqrt(T)."""
+    x0 = math.log(S0)
+    half = width_sd * sigma * math.sqrt(T)
+    return dict(driver=driver, terminal="CALL_LOG", T=T, x_min=x0 - half,
+                x_max=x0 + half, x0=x0, a_x=mu - 0.5 * sigma * sigma, b_x=sigma,
+                r=r, mu=mu, sigma=sigma, R=R, delta=delta, lb_sign=lb_sign,
+                strike=strike, Nx=Nx, N=N, k=k, L=L, picard_tol=1e-12,
+                picard_max=30, smoothing=smoothing)
+
+
+def ex1_problem(Nx: int = 4097, N: int = 128, k: int = 3, L: int = 32,
+                x_lim: float = 16.0) -> dict:
+    """Example 1 (Eq. 22-23): exact (y_0, z_0) = (1/2, 1/4)."""
+    return dict(driver="EX1", terminal="LOGISTIC", T=1.0, x_min=-x_lim, x_max=x_lim,
+                x0=0.0, a_x=0.0, b_x=1.0, Nx=Nx, N=N, k=k, L=L,
+                picard_tol=1e-12, picard_max=30, smoothing=0)
+
+
+def ex2_problem(Nx: int = 4097, N: int = 128, k: int = 3, L: int = 32,
+                x_lim: float = 16.0) -> dict:
+    """Example 2 (Eq. 24-25): exact (y_0, z_0) = (ln 3, 1/3)."""
+    return dict(driver="EX2", terminal="LNSIN", T=1.0, x_min=-x_lim, x_max=x_lim,
+                x0=0.0, a_x=0.0, b_x=1.0, Nx=Nx, N=N, k=k, L=L,
+                picard_tol=1e-12, picard_max=30, smoothing=0)
+
+
+# --- the five benchmark configurations -------------------------------------
+
+def config1() -> dict:
+    """sin driver, x in [-8, 8], Nx = 2001, N = 64, k = 2, L = 8, FP64."""
+    return sin_problem()
+
+
+def config2(k: int = 6) -> dict:
+    """Black-Scholes call in log price, S0 = K = 100, r = .03, mu = .05,
+    sigma = .2, T = 1, domain +-6 sigma sqrt(T), Nx = 65536, N = 256, L = 16."""
+    return call_problem(k=k)
+
+
+def config3(Nx: int = 1 << 20, N: int = 1024, k: int = 4) -> dict:
+    """Call with different lending/borrowing rates r = .04, R = .06,
+    mu = .06, sigma = .2, T = .5, K = 100, Nx = 2^20, N = 1024, k = 4, L = 16."""
+    return call_problem(r=0.04, R=0.06, mu=0.06, sigma=0.2, T=0.5, Nx=Nx, N=N,
+                        k=k, driver="LB", lb_sign=1.0)
+
+
+def config4(count: int = 4096, seed: int = 13560) -> list:
+    """Batch of Black-Scholes calls: K ~ U[70,130], sigma ~ U[.1,.5],
+    T ~ U[.25,2], r ~ U[0,.05], Nx in {2^10..2^14}, N in {32,64,128,256},
+    k ~ U{1..6}, L = 16, S0 = 100, mu = .05."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        out.append(call_problem(
+            strike=float(rng.uniform(70, 130)), sigma=float(rng.uniform(0.1, 0.5)),
+            T=float(rng.uniform(0.25, 2.0)), r=float(rng.uniform(0.0, 0.05)),
+            Nx=int(1 << int(rng.integers(10, 15))),
+            N=int(32 << int(rng.integers(0, 4))),
+            k=int(rng.integers(1, 7)), L=16))
+    return out
+
+
+def config5_arrivals(rate: float = 2000.0, duration: float = 10.0,
+                     seed: int = 1909) -> list:
+    """Poisson arrivals of pricing solves: 70% Black-Scholes (Nx = 2^12,
+    N = 64, k = 3), 30% lending/borrowing calls (Nx = 2^16, N = 256, k = 4),
+    L = 16, parameters drawn as in config4.  Returns (t_arrival, problem)."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    while True:
+        t += float(rng.exponential(1.0 / rate))
+        if t >= duration:
+            break
+        strike = float(rng.uniform(70, 130))
+        sigma = float(rng.uniform(0.1, 0.5))
+        T = float(rng.uniform(0.25, 2.0))
+        r = float(rng.uniform(0.0, 0.05))
+        if rng.uniform() < 0.7:
+            p = call_problem(strike=strike, sigma=sigma, T=T, r=r, Nx=1 << 12, N=64,
+                             k=3, L=16)
+        else:
+            p = call_problem(strike=strike, sigma=sigma, T=T, r=r, R=r + 0.02,
+                             mu=0.06, Nx=1 << 16, N=256, k=4, L=16, driver="LB")
+        out.append((t, p))
+    return out
+
+
+def gp_steps(p: dict) -> int:
+    """Grid-point time steps of one solve: Nx * (N - k + 1) levels computed."""
+    return int(p["Nx"]) * (int(p["N"]) - int(p["k"]) + 1)
