@@ -1,0 +1,376 @@
+#!/usr/bin/env python
+"""Benchmark of the multistep BSDE solve: grid-point time steps per second.
+
+One step = the Black-Scholes call workload (log price, S0 = K = 100,
+r = .03, mu = .05, sigma = .2, T = 1, Nx = 65536, N = 256, L = 16) solved
+once for every k = 1..6: sum_k Nx (N - k + 1) grid-point time steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32c|fp64]
+  python bench.py --impl reference ...   (the FP64 CPU oracle on the host cores)
+
+Prints one JSON line (rank 0).  Under torchrun each rank solves its own copy
+of the workload (independent instances, weak scaling, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "grid-point·steps/s at max|err|≤tol vs FP64 oracle; served solves/s + p99 ms"
+UNIT = "grid-point·steps/s"
+KS = (1, 2, 3, 4, 5, 6)
+# Algorithmic FP operations per grid-point time step of the Black-Scholes
+# driver: per Gauss-Hermite node two spline values (7 each: 4 products, 3
+# sums), the linear driver (3) and three quadrature sums (2 each), plus E[y]
+# at j = k; then the z and y combinations (4 per j) and ~3 Picard iterations.
+FLOP_NODE = 7 + 7 + 3 + 6
+
+
+def flops_per_gp_step(k: int, L: int) -> float:
+    return k * L * FLOP_NODE + 2 * L + 4 * k + 12
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+def _alu_peak_tflops(precision: str, sm_mhz: float) -> float:
+    """FP32: 152 SMs x 128 lanes x 2 flop per FMA; FP64: 152 SMs x 2 FMA units
+    x 2 (GB300 unit counts), at the given SM clock."""
+    lanes = 128 if precision == "fp32c" else 2
+    return 152 * lanes * 2 * sm_mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        cmd = ["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.uuid:
+            cmd.insert(1, f"--id={self.uuid}")
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return self
+
+        def pump():
+            for line in self.proc.stdout:
+                self.rows.append([c.strip() for c in line.split(",")])
+        self.thread = threading.Thread(target=pump, daemon=True)
+        self.thread.start()
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, r[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _golden():
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "config2_oracle.json")) as fh:
+            return {r["k"]: r for r in json.load(fh)["rows"]}
+    except OSError:
+        return {}
+
+
+def _dist_init(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        return dist
+    return None
+
+
+def _max_over_ranks(dist, v: float) -> float:
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def cpu_baseline(levels: int, threads: int) -> dict:
+    """The FP64 oracle as it stands, on a bounded sample: every k = 1..6 of
+    the workload, first `levels` backward levels each, `threads` host threads."""
+    from oracle import oracle as O
+    from paper_1909_13560_gb300 import workloads as W
+    t0 = time.perf_counter()
+    units = 0
+    for k in KS:
+        p = W.config2(k=k)
+        r = O.solve(p, levels=levels, threads=threads)
+        units += int(p["Nx"]) * int(r["levels_done"])
+    dt = time.perf_counter() - t0
+    return {"value": units / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"config2 k=1..6, first {levels} backward levels of each, "
+                      f"{threads} host threads; {units} grid-point steps in {dt:.2f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    threads = os.cpu_count() or 1
+    levels = args.ref_levels
+    for _ in range(args.warmup):
+        cpu_baseline(levels, threads)
+    t0 = time.perf_counter()
+    tot = 0.0
+    for _ in range(args.steps):
+        r = cpu_baseline(levels, threads)
+        tot += r["value"]
+    wall = time.perf_counter() - t0
+    value = tot / args.steps
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * wall / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "config2: Black-Scholes call in log price, Nx=65536, "
+                                   "N=256, k=1..6, L=16", "Nx": 65536, "N": 256, "k": list(KS),
+                       "L": 16, "sample_levels_per_k": levels},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": r["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    from paper_1909_13560_gb300 import bsde as B
+    from paper_1909_13560_gb300 import workloads as W
+
+    dist = _dist_init(world)
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    probs = [W.config2(k=k) for k in KS]
+    solvers = [B.Solver(p, args.precision, device=dev) for p in probs]
+    units_per_step = sum(W.gp_steps(p) for p in probs)
+    launches_per_step = sum(s.launches for s in solvers)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def one_step():
+        for s in solvers:
+            B.bsde_solve(s.plan, sp, want_result=False)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        one_step()
+    torch.cuda.synchronize(dev)
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        if not uuid.startswith("GPU-"):
+            uuid = "GPU-" + uuid
+    except Exception:
+        uuid = None
+    _barrier(dist)
+    torch.cuda.synchronize(dev)
+    with ClockSampler(uuid) as clk:
+        w0 = time.perf_counter()
+        for i in range(args.steps):
+            flush.zero_()  # L2 flush between steps, outside the events
+            starts[i].record(stream)
+            one_step()
+            ends[i].record(stream)
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - w0
+    _barrier(dist)
+    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    ms_max = _max_over_ranks(dist, ms)
+    value = world * units_per_step * args.steps / (ms_max / 1000.0)
+
+    # results of the last step and their gate against the stored oracle values
+    gold = _golden()
+    rows = []
+    ok = True
+    for k, s in zip(KS, solvers):
+        r = B.bsde_result_fetch(s.plan, sp)
+        g = gold.get(k)
+        row = {"k": k, "y0": r.y0, "z0": r.z0, "picard_iters_max": r.picard_iters_max}
+        if g:
+            row["err_y0_vs_oracle"] = abs(r.y0 - g["y0"])
+            row["err_y0_vs_exact"] = abs(r.y0 - g["exact_y0"])
+            tol = (1e-12 if args.precision == "fp64" else 1e-6) * max(1.0, abs(g["y0"]))
+            row["within_tol"] = row["err_y0_vs_oracle"] <= tol
+            ok = ok and row["within_tol"]
+        rows.append(row)
+
+    # dominant kernel: the step kernel, timed launch by launch on the same
+    # stream (re-running level 0 of each plan, whose inputs levels 1..k are
+    # resident after the solve)
+    reps = 20
+    kern_ms, kern_flops = 0.0, 0.0
+    for k, p, s in zip(KS, probs, solvers):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        B.bsde_enqueue_level(s.plan, sp, 0, 1)
+        e0.record(stream)
+        for _ in range(reps):
+            B.bsde_enqueue_level(s.plan, sp, 0, 1)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        avg = e0.elapsed_time(e1) / reps
+        nlev = p["N"] - k + 1
+        kern_ms += avg * nlev
+        kern_flops += flops_per_gp_step(k, p["L"]) * p["Nx"] * nlev
+    peaks = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = _alu_peak_tflops(args.precision, sm_max)
+    achieved = kern_flops / (kern_ms / 1000.0) / 1e12
+
+    # end to end through the C ABI with host buffers: initial levels copied in
+    # from pinned memory, level 0 and the result read back, every step
+    host_in, host_out = [], []
+    h2d = d2h = 0
+    for p in probs:
+        iy, iz = W.initial_levels(p)
+        ty = torch.from_numpy(iy).pin_memory()
+        tz = torch.from_numpy(iz).pin_memory()
+        oy = torch.empty(p["Nx"], dtype=torch.float64).pin_memory()
+        oz = torch.empty(p["Nx"], dtype=torch.float64).pin_memory()
+        host_in.append((ty, tz))
+        host_out.append((oy, oz))
+        h2d += ty.numel() * 8 + tz.numel() * 8
+        d2h += oy.numel() * 8 + oz.numel() * 8 + 40
+    for s, (ty, tz), (oy, oz) in zip(solvers, host_in, host_out):
+        B.bsde_solve(s.plan, sp, ty.data_ptr(), tz.data_ptr(), True, oy.data_ptr(), oz.data_ptr(), True)
+    _barrier(dist)
+    torch.cuda.synchronize(dev)
+    e_t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for s, (ty, tz), (oy, oz) in zip(solvers, host_in, host_out):
+            B.bsde_solve(s.plan, sp, ty.data_ptr(), tz.data_ptr(), True, oy.data_ptr(), oz.data_ptr(), True)
+    torch.cuda.synchronize(dev)
+    e_dt = _max_over_ranks(dist, time.perf_counter() - e_t0)
+    e2e_value = world * units_per_step * args.steps / e_dt
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.cpu_levels, os.cpu_count() or 1)
+
+    if rank == 0:
+        kname = "k_step32" if args.precision == "fp32c" else "k_step64"
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "fp32c" else "f64",
+            "data": "synthetic",
+            "config": {"workload": "config2: Black-Scholes call in log price (S0=K=100, "
+                                   "r=.03, mu=.05, sigma=.2, T=1, x in ln100 +- 6 sigma), "
+                                   "Nx=65536, N=256, k=1..6 (one solve each per step), L=16",
+                       "Nx": 65536, "N": 256, "k": list(KS), "L": 16,
+                       "precision": args.precision,
+                       "l2": "flushed between steps (256 MiB write, outside the timed events); "
+                             "within a solve the level ring (<= 15 MB) is L2-resident by design",
+                       "parallelism": f"{world} independent replica(s)"},
+            "accuracy": {"gate": "y0 vs stored FP64 oracle", "all_within_tol": ok, "rows": rows},
+            "roofline": {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "peak_source": f"derived: 152 SMs x {'128 FP32 lanes' if args.precision == 'fp32c' else '2 FP64 FMA units'} x 2 flop x {sm_max:.0f} MHz",
+                         "flop_per_gp_step": {str(k): flops_per_gp_step(k, 16) for k in KS},
+                         "avg_launch_ms": kern_ms / sum(p['N'] - p['k'] + 1 for p in probs)},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk.summary(),
+            "wall_s_timed_region": wall,
+        }
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    for s in solvers:
+        s.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp32c", "fp64"], default="fp32c")
+    ap.add_argument("--cpu-levels", type=int, default=64)
+    ap.add_argument("--ref-levels", type=int, default=12)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    local_rank = _env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,184 @@
+/*
+ * bsde.h -- C ABI of the GB300 (sm_103a) solver for the multistep BSDE scheme
+ * of Kapllani & Teng, "Multistep schemes for solving backward stochastic
+ * differential equations on GPU" (arXiv:1909.13560).
+ *
+ * What is solved (Section 2.2, Eq. 20-21; Section 3.1):
+ *   the decoupled FBSDE  dX = a_x dt + b_x dW,  -dy = f(t, y, z) dt - z dW,
+ *   y_T = g(X_T), on a uniform grid x_i = x_min + i*dx (i = 0..Nx-1),
+ *   dx = (x_max - x_min)/(Nx-1), with N time steps dt = T/N.  Going backward
+ *   from the k initial levels N, N-1, ..., N-k+1, every level n = N-k..0 is
+ *   computed at every grid point from the k later levels:
+ *     - Gauss-Hermite estimates (Eq. 21, L nodes) of E[z^], E[f], E[f dW],
+ *       E[y^], E[y^ dW] over the off-grid points
+ *       x_i + a_x j dt + b_x sqrt(2 j dt) a_l, j = 1..k, l = 1..L, where y^
+ *       and z^ are natural cubic splines of the level values (Section 3.3),
+ *       constant outside [x_min, x_max] (Section 3.2);
+ *     - z^n explicitly from the second line of Eq. 20;
+ *     - y^n from the first line of Eq. 20 by Picard iteration on the implicit
+ *       term f(t_n, y^n, z^n) (Section 3.1 step 3).
+ *   gamma coefficients: Tables 1 and 2 (K_y = K_z = k <= 6).
+ *
+ * Memory model: the caller owns every device buffer (one workspace per
+ * plan, sized by bsde_workspace_bytes) and every stream.  A plan owns host
+ * metadata, CUDA graphs and a small pinned host buffer only; bsde_free never
+ * frees caller memory.  Pointers passed as "host" must stay valid until the
+ * call returns (calls that take host pointers synchronise the stream).
+ * Streams are passed as void* (a cudaStream_t; NULL = the legacy default
+ * stream).
+ *
+ * Errors: every int-returning call returns BSDE_OK (0), a positive warning
+ * or a negative error; bsde_strerror() describes a code and bsde_last_error()
+ * gives the detail of the last failure on the calling thread.
+ */
+#ifndef BSDE_H
+#define BSDE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define BSDE_API __attribute__((visibility("default")))
+#else
+#define BSDE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* driver ids: f(t, y, z) */
+enum {
+  BSDE_DRIVER_LIN_SIN = 0, /* f = y/2 - z (1-D analogue of Example 4, Eq. 34)     */
+  BSDE_DRIVER_BS = 1,      /* f = -(r y + (mu - r + delta) z / sigma)   (Eq. 29)     */
+  BSDE_DRIVER_LB = 2,      /* f = -(r y + (mu - r) z / sigma)
+                              + lb_sign (R - r) min(y - z/sigma, 0): borrowing rate */
+  BSDE_DRIVER_EX1 = 3,     /* f = -y^3 + 5/2 y^2 - 3/2 y                (Eq. 22)     */
+  BSDE_DRIVER_EX2 = 4      /* f = (e^{t^2} - 4ty - 3e^{t^2 - y e^{-t^2}}
+                              + z^2 e^{-t^2}) / 2                       (Eq. 24)     */
+};
+
+/* terminal ids: g and, for the closed-form start, the exact solution u(t, x)
+ * with z = b_x u_x */
+enum {
+  BSDE_TERMINAL_SIN = 0,      /* g = sin(x + T); u = sin(x + t)             (Eq. 35) */
+  BSDE_TERMINAL_CALL_LOG = 1, /* g = (e^x - strike)^+, x = ln S; u = Black-Scholes
+                                 call with dividend yield delta (Eq. 31; for LB
+                                 the rate r - lb_sign (R - r), no dividend)          */
+  BSDE_TERMINAL_LOGISTIC = 2, /* g = e^{x+T}/(e^{x+T}+1)                    (Eq. 23) */
+  BSDE_TERMINAL_LNSIN = 3     /* g = ln(sin x + 3) e^{T^2}                  (Eq. 25) */
+};
+
+/* arithmetic of the bulk (interpolation, driver at the nodes, quadrature) */
+enum {
+  BSDE_FP64 = 0,  /* everything in IEEE double                                     */
+  BSDE_FP32C = 1  /* levels as float (hi, lo) pairs, FP32 interpolation and driver,
+                     compensated (error-free product and sum) accumulation of the
+                     y and z expectations, double for the final combination of
+                     y^n and z^n and the Picard convergence test; spline second
+                     derivatives from exact float differences of the pairs       */
+};
+
+/* return codes */
+enum {
+  BSDE_OK = 0,
+  BSDE_WARN_NOCONV = 1, /* Picard stopped at picard_max somewhere; results written */
+  BSDE_EINVAL = -1,     /* bad problem: k outside 1..min(6, N), Nx < 4, L outside
+                           1..64, x0 outside [x_min, x_max], unknown id, T <= 0    */
+  BSDE_ENOSPC = -2,     /* workspace smaller than bsde_workspace_bytes()          */
+  BSDE_ECUDA = -3,      /* a CUDA call failed (detail in bsde_last_error())       */
+  BSDE_ENOMEM = -4,     /* host allocation failed                                 */
+  BSDE_ETIMEOUT = -5    /* a bounded device-side wait expired                     */
+};
+
+/* Problem description (all fields read by bsde_plan; nothing is kept by
+ * reference).  Initial levels: unless the caller passes them to bsde_solve,
+ * the closed form of the terminal id is evaluated at t_N, ..., t_{N-k+1}
+ * (Section 3.1 step 2, read as the exact start); when smoothing = 1 and the terminal is CALL_LOG, level N holds the
+ * cell averages of the payoff and of b_x times its derivative over
+ * [x_i - dx/2, x_i + dx/2] (Section 5, Example 3).  Callers may instead pass
+ * their own k initial levels to bsde_solve. */
+typedef struct bsde_problem {
+  int32_t driver, terminal, precision, smoothing;
+  int32_t picard_max; /* Picard iteration cap (paper: 30)                     */
+  int32_t N, k, L;    /* time steps, steps of the scheme (K_y = K_z), GH nodes */
+  int64_t Nx;         /* grid points                                          */
+  double T, x_min, x_max, x0; /* horizon, grid ends, readout point            */
+  double a_x, b_x;    /* forward process dX = a_x dt + b_x dW                 */
+  double r, mu, sigma, R, delta, lb_sign, strike; /* driver/payoff parameters */
+  double picard_tol;  /* stop when |y^(p+1) - y^(p)| <= picard_tol            */
+} bsde_problem;
+
+typedef struct bsde_result {
+  double y0, z0;           /* spline values of y^0, z^0 at x0 (Section 3.1 step 3) */
+  double picard_resid_max; /* max over points and levels of the last |dy|          */
+  int32_t status;          /* BSDE_OK or BSDE_WARN_NOCONV                          */
+  int32_t picard_iters_max;
+  int64_t levels_done;     /* N - k + 1                                            */
+} bsde_result;
+
+typedef struct bsde_plan_s bsde_plan_t;
+
+/* Device workspace a plan for *p needs, in bytes (ring of k+1 levels, the
+ * spline scratch, node tables, output staging).  Used for admission by
+ * footprint.  Returns BSDE_EINVAL for a bad problem. */
+BSDE_API int bsde_workspace_bytes(const bsde_problem *p, size_t *bytes);
+
+/* Validate *p, compute the plan constants on the host (Gauss-Hermite rule,
+ * gamma tables, per-(j, l) cell shift and spline weights), copy the node
+ * table into dev_workspace (device memory of at least bsde_workspace_bytes
+ * bytes, 256-byte aligned, owned by the caller and reserved for this plan
+ * until bsde_free) and return the plan in *out.  The plan records the
+ * current CUDA device.  Solves on one plan must be ordered (one stream, or
+ * synchronised streams): they share the workspace. */
+BSDE_API int bsde_plan(const bsde_problem *p, void *dev_workspace, size_t bytes,
+              bsde_plan_t **out);
+
+/* Run the whole backward loop on `stream`.
+ *   init_y, init_z: NULL (closed-form start) or k*Nx doubles each, row m
+ *                   holding level N-m; host memory if init_on_host != 0,
+ *                   device memory otherwise.
+ *   out_y, out_z:   NULL or Nx doubles each, receiving level 0; host memory
+ *                   if out_on_host != 0, device memory otherwise.
+ *   result:         NULL or host struct receiving y0, z0 and the Picard
+ *                   statistics; when non-NULL, or when any pointer is a host
+ *                   pointer, the call waits for the stream.
+ * Without host pointers and with result == NULL the call only enqueues work;
+ * bsde_result_fetch() then reads the result.  Returns BSDE_OK,
+ * BSDE_WARN_NOCONV (only when result is non-NULL) or an error. */
+BSDE_API int bsde_solve(bsde_plan_t *plan, void *stream, const double *init_y,
+               const double *init_z, int init_on_host, double *out_y,
+               double *out_z, int out_on_host, bsde_result *result);
+
+/* Copy the result of the last bsde_solve on this plan to the host, waiting
+ * for `stream`. */
+BSDE_API int bsde_result_fetch(bsde_plan_t *plan, void *stream, bsde_result *result);
+
+/* Enqueue on `stream`, outside the captured graph, the kernels of backward
+ * level n (0 <= n <= N-k): parts & 1 = the step kernel (Gauss-Hermite
+ * expectations, z^n, Picard y^n), parts & 2 = the two spline sweeps of level
+ * n.  The ring must hold levels n+1..n+k for meaningful values (after a
+ * completed bsde_solve it does for n = 0, and re-running level 0 then
+ * rewrites the same values); every index stays inside the workspace either
+ * way.  Used to time the kernels one by one. */
+BSDE_API int bsde_enqueue_level(bsde_plan_t *plan, void *stream, int n, int parts);
+
+/* Release the plan's host resources and graphs (not the workspace). */
+BSDE_API void bsde_free(bsde_plan_t *plan);
+
+/* Number of kernel launches one bsde_solve issues (for launch accounting). */
+BSDE_API int64_t bsde_plan_launches(const bsde_plan_t *plan);
+
+BSDE_API const char *bsde_strerror(int code);
+BSDE_API const char *bsde_last_error(void);
+
+/* Host-side plan constants, exposed for inspection and tests: the Gauss-
+ * Hermite rule used by the kernels (nodes ascending, weights for exp(-a^2)),
+ * and the gamma tables (Table 1 into gy[0..k], Table 2 into gz[0..k]). */
+BSDE_API int bsde_gauss_hermite(int L, double *nodes, double *weights);
+BSDE_API int bsde_gamma(int k, double *gy, double *gz);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BSDE_H */

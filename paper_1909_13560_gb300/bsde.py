@@ -1,0 +1,282 @@
+"""Python binding of the C ABI in include/bsde.h (argument marshalling only).
+
+Every step of the solve runs in the CUDA kernels of libbsde.so; PyTorch is
+used for device memory (the workspace) and streams.  Importing this module
+does not touch the GPU; the first call loads the library and raises if it is
+missing -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbsde.so")
+
+BSDE_DRIVER = {"LIN_SIN": 0, "BS": 1, "LB": 2, "EX1": 3, "EX2": 4}
+BSDE_TERMINAL = {"SIN": 0, "CALL_LOG": 1, "LOGISTIC": 2, "LNSIN": 3}
+BSDE_PRECISION = {"fp64": 0, "fp32c": 1}
+
+BSDE_OK = 0
+BSDE_WARN_NOCONV = 1
+BSDE_EINVAL = -1
+BSDE_ENOSPC = -2
+BSDE_ECUDA = -3
+BSDE_ENOMEM = -4
+BSDE_ETIMEOUT = -5
+
+
+class bsde_problem(ctypes.Structure):
+    _fields_ = [
+        ("driver", ctypes.c_int32), ("terminal", ctypes.c_int32),
+        ("precision", ctypes.c_int32), ("smoothing", ctypes.c_int32),
+        ("picard_max", ctypes.c_int32), ("N", ctypes.c_int32),
+        ("k", ctypes.c_int32), ("L", ctypes.c_int32),
+        ("Nx", ctypes.c_int64),
+        ("T", ctypes.c_double), ("x_min", ctypes.c_double),
+        ("x_max", ctypes.c_double), ("x0", ctypes.c_double),
+        ("a_x", ctypes.c_double), ("b_x", ctypes.c_double),
+        ("r", ctypes.c_double), ("mu", ctypes.c_double),
+        ("sigma", ctypes.c_double), ("R", ctypes.c_double),
+        ("delta", ctypes.c_double), ("lb_sign", ctypes.c_double),
+        ("strike", ctypes.c_double), ("picard_tol", ctypes.c_double),
+    ]
+
+
+class bsde_result(ctypes.Structure):
+    _fields_ = [
+        ("y0", ctypes.c_double), ("z0", ctypes.c_double),
+        ("picard_resid_max", ctypes.c_double),
+        ("status", ctypes.c_int32), ("picard_iters_max", ctypes.c_int32),
+        ("levels_done", ctypes.c_int64),
+    ]
+
+
+_lib = None
+_SYMBOLS = ("bsde_workspace_bytes", "bsde_plan", "bsde_solve", "bsde_result_fetch",
+            "bsde_enqueue_level", "bsde_free", "bsde_plan_launches", "bsde_strerror",
+            "bsde_last_error", "bsde_gauss_hermite", "bsde_gamma")
+
+
+def load(path: str = LIB_PATH):
+    """Load libbsde.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    from . import build as _build
+    if _build._stale():
+        _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is missing and could not be built")
+    lib = ctypes.CDLL(path)
+    P, vp = ctypes.POINTER, ctypes.c_void_p
+    d = ctypes.c_double
+    lib.bsde_workspace_bytes.argtypes = [P(bsde_problem), P(ctypes.c_size_t)]
+    lib.bsde_plan.argtypes = [P(bsde_problem), vp, ctypes.c_size_t, P(vp)]
+    lib.bsde_solve.argtypes = [vp, vp, vp, vp, ctypes.c_int, vp, vp, ctypes.c_int,
+                               P(bsde_result)]
+    lib.bsde_result_fetch.argtypes = [vp, vp, P(bsde_result)]
+    lib.bsde_enqueue_level.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int]
+    lib.bsde_free.argtypes = [vp]
+    lib.bsde_free.restype = None
+    lib.bsde_plan_launches.argtypes = [vp]
+    lib.bsde_plan_launches.restype = ctypes.c_int64
+    lib.bsde_strerror.argtypes = [ctypes.c_int]
+    lib.bsde_strerror.restype = ctypes.c_char_p
+    lib.bsde_last_error.restype = ctypes.c_char_p
+    lib.bsde_gauss_hermite.argtypes = [ctypes.c_int, P(d), P(d)]
+    lib.bsde_gamma.argtypes = [ctypes.c_int, P(d), P(d)]
+    _lib = lib
+    return lib
+
+
+class BsdeError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        lib = load()
+        msg = f"{what}: {lib.bsde_strerror(code).decode()} ({code})"
+        detail = lib.bsde_last_error().decode()
+        if detail:
+            msg += f": {detail}"
+        super().__init__(msg)
+        self.code = code
+
+
+def _check(code: int, what: str) -> int:
+    if code < 0:
+        raise BsdeError(code, what)
+    return code
+
+
+def make_problem(p: dict, precision: str = "fp64") -> bsde_problem:
+    s = bsde_problem()
+    s.driver = BSDE_DRIVER[p["driver"]]
+    s.terminal = BSDE_TERMINAL[p["terminal"]]
+    s.precision = BSDE_PRECISION[precision]
+    s.smoothing = int(p.get("smoothing", 0))
+    s.picard_max = int(p.get("picard_max", 30))
+    s.N, s.k, s.L, s.Nx = int(p["N"]), int(p["k"]), int(p["L"]), int(p["Nx"])
+    for f in ("T", "x_min", "x_max", "x0", "a_x", "b_x"):
+        setattr(s, f, float(p[f]))
+    for f in ("r", "mu", "sigma", "R", "delta", "strike"):
+        setattr(s, f, float(p.get(f, 0.0)))
+    s.lb_sign = float(p.get("lb_sign", 1.0))
+    if s.sigma == 0.0:
+        s.sigma = 1.0
+    s.picard_tol = float(p.get("picard_tol", 1e-12))
+    return s
+
+
+# --- thin wrappers with the C names ----------------------------------------
+
+def bsde_workspace_bytes(prob: bsde_problem) -> int:
+    n = ctypes.c_size_t()
+    _check(load().bsde_workspace_bytes(ctypes.byref(prob), ctypes.byref(n)),
+           "bsde_workspace_bytes")
+    return int(n.value)
+
+
+def bsde_plan(prob: bsde_problem, dev_ptr: int, nbytes: int) -> int:
+    h = ctypes.c_void_p()
+    _check(load().bsde_plan(ctypes.byref(prob), ctypes.c_void_p(dev_ptr), nbytes,
+                            ctypes.byref(h)), "bsde_plan")
+    return h.value
+
+
+def bsde_solve(plan: int, stream: int, init_y: int = 0, init_z: int = 0,
+               init_on_host: bool = False, out_y: int = 0, out_z: int = 0,
+               out_on_host: bool = False, want_result: bool = True):
+    res = bsde_result()
+    rc = load().bsde_solve(ctypes.c_void_p(plan), ctypes.c_void_p(stream),
+                           ctypes.c_void_p(init_y or None), ctypes.c_void_p(init_z or None),
+                           int(init_on_host), ctypes.c_void_p(out_y or None),
+                           ctypes.c_void_p(out_z or None), int(out_on_host),
+                           ctypes.byref(res) if want_result else None)
+    _check(rc, "bsde_solve")
+    return res if want_result else None
+
+
+def bsde_result_fetch(plan: int, stream: int) -> bsde_result:
+    res = bsde_result()
+    _check(load().bsde_result_fetch(ctypes.c_void_p(plan), ctypes.c_void_p(stream),
+                                    ctypes.byref(res)), "bsde_result_fetch")
+    return res
+
+
+def bsde_enqueue_level(plan: int, stream: int, n: int, parts: int = 1) -> None:
+    _check(load().bsde_enqueue_level(ctypes.c_void_p(plan), ctypes.c_void_p(stream),
+                                     int(n), int(parts)), "bsde_enqueue_level")
+
+
+def bsde_free(plan: int) -> None:
+    if plan:
+        load().bsde_free(ctypes.c_void_p(plan))
+
+
+def bsde_plan_launches(plan: int) -> int:
+    return int(load().bsde_plan_launches(ctypes.c_void_p(plan)))
+
+
+def bsde_gauss_hermite(L: int):
+    a = np.zeros(L)
+    w = np.zeros(L)
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(load().bsde_gauss_hermite(L, a.ctypes.data_as(dp), w.ctypes.data_as(dp)),
+           "bsde_gauss_hermite")
+    return a, w
+
+
+def bsde_gamma(k: int):
+    gy = np.zeros(k + 1)
+    gz = np.zeros(k + 1)
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(load().bsde_gamma(k, gy.ctypes.data_as(dp), gz.ctypes.data_as(dp)), "bsde_gamma")
+    return gy, gz
+
+
+# --- convenience: a plan bound to a torch-allocated workspace ---------------
+
+def _result_dict(r: bsde_result) -> dict:
+    return {"y0": r.y0, "z0": r.z0, "status": r.status,
+            "picard_iters_max": r.picard_iters_max,
+            "picard_resid_max": r.picard_resid_max, "levels_done": r.levels_done}
+
+
+class Solver:
+    """One problem, one device workspace (a torch uint8 tensor), one plan."""
+
+    def __init__(self, problem: dict, precision: str = "fp64", device=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("the BSDE solver needs a CUDA device (no CPU fallback)")
+        self.problem = dict(problem)
+        self.precision = precision
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self._prob = make_problem(problem, precision)
+        self.ws_bytes = bsde_workspace_bytes(self._prob)
+        with torch.cuda.device(self.device):
+            self.workspace = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=self.device)
+            base = self.workspace.data_ptr()
+            self._base = (base + 255) // 256 * 256
+            self.plan = bsde_plan(self._prob, self._base, self.ws_bytes)
+
+    @property
+    def launches(self) -> int:
+        return bsde_plan_launches(self.plan)
+
+    def solve(self, init=None, want_level: bool = False, stream=None) -> dict:
+        """init: None (closed-form start) or (init_y, init_z), each (k, Nx)
+        float64 host arrays or device tensors (row m = level N - m)."""
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        sp = stream.cuda_stream
+        iy = iz = 0
+        on_host = False
+        keep = []
+        if init is not None:
+            y, z = init
+            if isinstance(y, torch.Tensor) and y.is_cuda:
+                y = y.contiguous().to(torch.float64)
+                z = z.contiguous().to(torch.float64)
+                keep += [y, z]
+                iy, iz = y.data_ptr(), z.data_ptr()
+            else:
+                y = np.ascontiguousarray(y, dtype=np.float64)
+                z = np.ascontiguousarray(z, dtype=np.float64)
+                keep += [y, z]
+                iy, iz = y.ctypes.data, z.ctypes.data
+                on_host = True
+        oy = oz = None
+        if want_level:
+            oy = np.zeros(int(self.problem["Nx"]))
+            oz = np.zeros(int(self.problem["Nx"]))
+        res = bsde_solve(self.plan, sp, iy, iz, on_host,
+                         oy.ctypes.data if want_level else 0,
+                         oz.ctypes.data if want_level else 0, True, True)
+        out = _result_dict(res)
+        if want_level:
+            out["y"] = oy
+            out["z"] = oz
+        return out
+
+    def close(self) -> None:
+        if getattr(self, "plan", None):
+            bsde_free(self.plan)
+            self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve(problem: dict, precision: str = "fp64", init=None, want_level: bool = False) -> dict:
+    s = Solver(problem, precision)
+    try:
+        return s.solve(init=init, want_level=want_level)
+    finally:
+        s.close()

@@ -1,0 +1,227 @@
+// Host-side plan constants for the multistep BSDE solver: validation, the
+// Gauss-Hermite rule, the multistep coefficients and the per-(j, l) node
+// tables (Section 2.2, Eq. 20-21; Section 3.2 remarks on the uniform grid).
+#include <cmath>
+#include <cstring>
+
+#include "bsde_internal.h"
+
+namespace bsde {
+
+int validate(const bsde_problem &p) {
+  if (p.k < 1 || p.k > kMaxK || p.k > p.N || p.N < 1) return BSDE_EINVAL;
+  if (p.Nx < 4 || p.Nx > (int64_t(1) << 31)) return BSDE_EINVAL;
+  if (p.L < 1 || p.L > kMaxL) return BSDE_EINVAL;
+  if (!(p.T > 0.0) || !(p.x_max > p.x_min)) return BSDE_EINVAL;
+  if (!(p.x0 >= p.x_min && p.x0 <= p.x_max)) return BSDE_EINVAL;
+  if (p.driver < BSDE_DRIVER_LIN_SIN || p.driver > BSDE_DRIVER_EX2) return BSDE_EINVAL;
+  if (p.terminal < BSDE_TERMINAL_SIN || p.terminal > BSDE_TERMINAL_LNSIN) return BSDE_EINVAL;
+  if (p.precision != BSDE_FP64 && p.precision != BSDE_FP32C) return BSDE_EINVAL;
+  if (p.picard_max < 1 || !(p.picard_tol >= 0.0)) return BSDE_EINVAL;
+  if ((p.driver == BSDE_DRIVER_BS || p.driver == BSDE_DRIVER_LB) && p.sigma == 0.0) return BSDE_EINVAL;
+  return BSDE_OK;
+}
+
+// ---- Gauss-Hermite rule for the weight exp(-a^2) (Eq. 21) -----------------
+// Nodes: eigenvalues of the symmetric tridiagonal Jacobi matrix of the Hermite
+// recurrence (zero diagonal, off-diagonal sqrt(m/2)), isolated one by one by
+// bisection on the Sturm sequence count, then polished by Newton steps on the
+// scaled Hermite polynomial h_m = H_m / sqrt(2^m m!),
+//   h_{m+1} = sqrt(2/(m+1)) a h_m - sqrt(m/(m+1)) h_{m-1},  h'_L = sqrt(2L) h_{L-1}.
+// Weights: w = sqrt(pi) / (L h_{L-1}(a)^2), the classical formula
+// 2^{L-1} L! sqrt(pi) / (L^2 H_{L-1}(a)^2) rewritten in the scaled basis.
+static int sturm_count_below(int L, double lam) {
+  // number of eigenvalues < lam of tridiag(beta, 0, beta)
+  int cnt = 0;
+  double q = -lam;
+  if (q < 0) ++cnt;
+  for (int m = 1; m < L; ++m) {
+    double b2 = 0.5 * m;
+    if (q == 0.0) q = 1e-300;
+    q = -lam - b2 / q;
+    if (q < 0) ++cnt;
+  }
+  return cnt;
+}
+
+static void scaled_hermite(long double a, int L, long double &hL, long double &hLm1) {
+  long double h0 = 1.0L, h1 = std::sqrt(2.0L) * a;
+  if (L == 0) { hL = h0; hLm1 = 0; return; }
+  if (L == 1) { hL = h1; hLm1 = h0; return; }
+  for (int m = 1; m < L; ++m) {
+    long double h2 = std::sqrt(2.0L / (m + 1)) * a * h1 - std::sqrt((long double)m / (m + 1)) * h0;
+    h0 = h1;
+    h1 = h2;
+  }
+  hL = h1;
+  hLm1 = h0;
+}
+
+int gauss_hermite(int L, double *nodes, double *weights) {
+  if (L < 1 || L > 128) return BSDE_EINVAL;
+  const double bound = std::sqrt(2.0 * L + 1.0) + 1.0;
+  for (int m = 0; m < L; ++m) {
+    // the m-th smallest eigenvalue: count(lo) <= m < count(hi)
+    double lo = -bound, hi = bound;
+    for (int it = 0; it < 200 && hi - lo > 1e-15 * (1.0 + std::fabs(lo)); ++it) {
+      double mid = 0.5 * (lo + hi);
+      if (sturm_count_below(L, mid) > m) hi = mid; else lo = mid;
+    }
+    long double a = 0.5L * ((long double)lo + (long double)hi);
+    for (int it = 0; it < 6; ++it) {
+      long double hL, hLm1;
+      scaled_hermite(a, L, hL, hLm1);
+      long double d = std::sqrt(2.0L * L) * hLm1;
+      if (d == 0.0L) break;
+      a -= hL / d;
+    }
+    long double hL, hLm1;
+    scaled_hermite(a, L, hL, hLm1);
+    nodes[m] = (double)a;
+    weights[m] = (double)(std::sqrt((long double)M_PI) / ((long double)L * hLm1 * hLm1));
+  }
+  if (L % 2 == 1) nodes[L / 2] = 0.0;
+  return BSDE_OK;
+}
+
+// ---- multistep coefficients (Table 1: gamma^k_{k,j}; Table 2: gamma^1_{k,j}) --
+struct Frac { int num, den; };
+static const Frac kTable1[6][7] = {
+    {{1, 2}, {1, 2}},
+    {{1, 6}, {2, 3}, {1, 6}},
+    {{1, 8}, {3, 8}, {3, 8}, {1, 8}},
+    {{1, 12}, {1, 3}, {1, 6}, {1, 3}, {1, 12}},
+    {{41, 600}, {19, 75}, {107, 600}, {107, 600}, {19, 75}, {41, 600}},
+    {{19, 336}, {3, 14}, {15, 112}, {4, 21}, {15, 112}, {3, 14}, {19, 336}}};
+static const Frac kTable2[6][7] = {
+    {{1, 2}, {1, 2}},
+    {{5, 12}, {2, 3}, {-1, 12}},
+    {{3, 8}, {19, 24}, {-5, 24}, {1, 24}},
+    {{35, 96}, {5, 6}, {-13, 48}, {1, 12}, {-1, 96}},
+    {{131, 360}, {151, 180}, {-103, 360}, {37, 360}, {-1, 45}, {1, 360}},
+    {{163, 448}, {47, 56}, {-129, 448}, {3, 28}, {-37, 1344}, {1, 168}, {-1, 1344}}};
+
+int gamma_tables(int k, double *gy, double *gz) {
+  if (k < 1 || k > kMaxK) return BSDE_EINVAL;
+  for (int j = 0; j <= k; ++j) {
+    gy[j] = double(kTable1[k - 1][j].num) / double(kTable1[k - 1][j].den);
+    gz[j] = double(kTable2[k - 1][j].num) / double(kTable2[k - 1][j].den);
+  }
+  return BSDE_OK;
+}
+
+int fill_params(const bsde_problem &p, Params &P) {
+  int rc = validate(p);
+  if (rc) return rc;
+  std::memset(&P, 0, sizeof(P));
+  P.Nx = p.Nx;
+  P.N = p.N;
+  P.k = p.k;
+  P.L = p.L;
+  P.driver = p.driver;
+  P.terminal = p.terminal;
+  P.precision = p.precision;
+  P.smoothing = p.smoothing;
+  P.picard_max = p.picard_max;
+  P.nslot = p.k + 1;
+  P.T = p.T;
+  P.dt = p.T / p.N;
+  P.dx = (p.x_max - p.x_min) / double(p.Nx - 1);
+  P.x_min = p.x_min;
+  P.x_max = p.x_max;
+  P.x0 = p.x0;
+  P.a_x = p.a_x;
+  P.b_x = p.b_x;
+  P.r = p.r;
+  P.mu = p.mu;
+  P.sigma = p.sigma;
+  P.R = p.R;
+  P.delta = p.delta;
+  P.lb_sign = p.lb_sign;
+  P.strike = p.strike;
+  P.picard_tol = p.picard_tol;
+  gamma_tables(p.k, P.gy, P.gz);
+  P.h = p.k * P.dt;
+  P.hg0 = P.h * P.gy[0];
+  P.inv_gz0 = 1.0 / P.gz[0];
+  P.inv_dx2_6 = 6.0 / (P.dx * P.dx);
+  // LU pivots of tridiag(1, 4, 1): d_0 = 4, d_m = 4 - 1/d_{m-1}; they reach
+  // 2 + sqrt(3) to double precision long before m = 64.
+  double d = 4.0;
+  for (int m = 0; m < kInvPivots; ++m) {
+    P.invd[m] = 1.0 / d;
+    d = 4.0 - 1.0 / d;
+  }
+  return BSDE_OK;
+}
+
+Layout layout_for(const bsde_problem &p) {
+  auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
+  Layout L{};
+  const size_t nx = size_t(p.Nx), ns = size_t(p.k + 1);
+  size_t off = 0;
+  if (p.precision == BSDE_FP64) {
+    L.ring64 = off; off = up(off + ns * nx * 32);
+  } else {
+    L.ringA = off; off = up(off + ns * nx * 16);
+    L.ringB = off; off = up(off + ns * nx * 8);
+  }
+  L.gscr = off; off = up(off + 2 * nx * (p.precision == BSDE_FP64 ? 8 : 4));
+  L.table = off; off = up(off + size_t(p.k) * p.L * (p.precision == BSDE_FP64 ? sizeof(NodeF64) : sizeof(NodeF32)));
+  L.stage = off; off = up(off + 2 * size_t(p.k) * nx * 8);
+  L.stats = off; off = up(off + sizeof(Stats));
+  L.total = off;
+  return L;
+}
+
+// Node tables.  On the uniform grid with a constant-coefficient forward
+// process the off-grid point of (j, l) is x_i + o_jl dx with the same o_jl for
+// every i (Section 3.2, third remark: the cell index is found without a
+// search); its cell is i + floor(o_jl) and its position inside the cell
+// theta = o_jl - floor(o_jl).
+void build_tables(const Params &P, NodeF64 *t64, NodeF32 *t32) {
+  double a[kMaxL], w[kMaxL];
+  gauss_hermite(P.L, a, w);
+  const double rpi = 1.0 / std::sqrt(M_PI);
+  const double c6 = P.dx * P.dx / 6.0;
+  for (int j = 1; j <= P.k; ++j) {
+    const double sq = std::sqrt(2.0 * j * P.dt);
+    for (int l = 0; l < P.L; ++l) {
+      const double dW = sq * a[l];
+      const double o = (P.a_x * j * P.dt + P.b_x * dW) / P.dx;
+      const double s = std::floor(o);
+      const double th = o - s;
+      const double om = 1.0 - th;
+      const double wt = w[l] * rpi;
+      NodeF64 e{};
+      e.shift = (int64_t)s;
+      e.w0 = om;
+      e.w1 = th;
+      e.w2 = c6 * (om * om * om - om);
+      e.w3 = c6 * (th * th * th - th);
+      e.wt = wt;
+      e.wdw = wt * dW;
+      const int idx = (j - 1) * P.L + l;
+      if (t64) t64[idx] = e;
+      if (t32) {
+        NodeF32 f{};
+        f.shift = (int32_t)s;
+        f.w0 = (float)e.w0;
+        f.w1 = (float)e.w1;
+        f.w2 = (float)e.w2;
+        f.w3 = (float)e.w3;
+        const double cz = wt * ((j == 1 ? 1.0 : 0.0) - P.gz[j]) * P.inv_gz0;
+        f.czh = (float)cz;
+        f.czl = (float)(cz - (double)f.czh);
+        f.cfz = (float)(P.gz[j] * e.wdw * P.inv_gz0);
+        f.cfy = (float)(P.h * P.gy[j] * wt);
+        const double cy = (j == P.k) ? wt : 0.0;
+        f.cyh = (float)cy;
+        f.cyl = (float)(cy - (double)f.cyh);
+        t32[idx] = f;
+      }
+    }
+  }
+}
+
+}  // namespace bsde

@@ -1,0 +1,84 @@
+// Internal definitions shared by the host planning code (bsde_host.cpp) and
+// the CUDA kernels (bsde_cuda.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/bsde.h"
+
+namespace bsde {
+
+constexpr int kMaxK = 6;
+constexpr int kMaxL = 64;
+constexpr int kInvPivots = 64;   // exact 1/d_m of the spline LU for m < 64
+constexpr int kSplineChunk = 64; // unknowns per thread in the spline passes
+constexpr int kSplineWarm = 32;  // warm-up length: (2 - sqrt 3)^33 < 2^-62
+
+// Per (j, l) entry of the FP64 node table: the off-grid point
+// x_i + a_x j dt + b_x sqrt(2 j dt) a_l sits in cell i + shift at relative
+// position theta; w0..w3 are the spline weights of y_c, y_{c+1}, M_c,
+// M_{c+1}; wt = omega_l / sqrt(pi) (Eq. 21) and wdw = wt * DeltaW_{jl}.
+struct NodeF64 {
+  int64_t shift;
+  double w0, w1, w2, w3, wt, wdw, pad;
+};
+
+// FP32C node table entry.  The y and z expectations of Eq. 20 are folded
+// into per-node coefficients so that the kernel keeps four accumulators:
+//   z^n     = sum_jl cz_jl z^_jl + sum_jl cfz_jl F_jl
+//   A (y^n) = sum_l  cy_l  y^_kl + sum_jl cfy_jl F_jl
+// with cz = wt (delta_{j1} - gz_j) / gz_0, cfz = gz_j wdw / gz_0,
+// cy = wt (j = k only), cfy = k dt gy_j wt.  cz and cy are split into
+// float hi + lo parts for the compensated sums.
+struct NodeF32 {
+  int32_t shift;
+  float w0, w1, w2, w3;
+  float czh, czl, cfz, cfy, cyh, cyl;
+  float pad;
+};
+
+// Everything a kernel needs to know about one problem.
+struct Params {
+  int64_t Nx;
+  int32_t N, k, L, driver, terminal, precision, smoothing, picard_max, nslot;
+  double T, dt, dx, x_min, x_max, x0, a_x, b_x;
+  double r, mu, sigma, R, delta, lb_sign, strike;
+  double picard_tol;
+  double gy[kMaxK + 1], gz[kMaxK + 1];
+  double h;       // k dt
+  double hg0;     // k dt gy_0 (weight of the implicit term)
+  double inv_gz0; // 1 / gz_0
+  double inv_dx2_6; // 6 / dx^2
+  double invd[kInvPivots];
+};
+
+// Device workspace layout (byte offsets from the workspace base).
+struct Layout {
+  size_t ring64;   // FP64: double4 (y, M_y, z, M_z) x nslot x Nx
+  size_t ringA;    // FP32C: float4 (y_hi, y_lo, z_hi, z_lo) x nslot x Nx
+  size_t ringB;    // FP32C: float2 (M_y, M_z) x nslot x Nx
+  size_t gscr;     // spline forward-sweep scratch: 2 x Nx values
+  size_t table;    // node table (k L entries)
+  size_t stage;    // 2 x k x Nx doubles: imported initial levels / exported level 0
+  size_t stats;    // Stats
+  size_t total;
+};
+
+struct Stats {
+  double y0, z0;
+  unsigned long long resid_bits; // max |dy| as the bits of a non-negative double
+  int32_t iters_max;
+  int32_t nonconv;
+  int32_t pad[2];
+};
+
+// Host-side planning (bsde_host.cpp).
+int validate(const bsde_problem &p);
+int fill_params(const bsde_problem &p, Params &P);
+Layout layout_for(const bsde_problem &p);
+int gauss_hermite(int L, double *nodes, double *weights);
+int gamma_tables(int k, double *gy, double *gz);
+void build_tables(const Params &P, NodeF64 *t64, NodeF32 *t32);
+
+}  // namespace bsde

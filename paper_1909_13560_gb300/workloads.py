@@ -1,8 +1,8 @@
-"""Seeded synthetic workloads: problem parameters only.
+"""Seeded synthetic workloads: problem parameters and closed-form input data.
 
 These generators describe *what* is solved (drivers, terminal conditions,
-domains, grid sizes, seeded parameter draws); they contain none of the
-scheme's arithmetic.  Both the CUDA path and the CPU oracle consume the same
+domains, grid sizes, seeded parameter draws, the exact initial levels as host
+input); they contain none of the scheme's arithmetic.  Both the CUDA path and the CPU oracle consume the same
 dicts.  No dataset is involved anywhere: the paper's examples are analytic
 BSDEs (Section 5) and every workload here is defined by closed-form data.
 
@@ -130,3 +130,50 @@ def config5_arrivals(rate: float = 2000.0, duration: float = 10.0,
 def gp_steps(p: dict) -> int:
     """Grid-point time steps of one solve: Nx * (N - k + 1) levels computed."""
     return int(p["Nx"]) * (int(p["N"]) - int(p["k"]) + 1)
+
+
+def initial_levels(p: dict):
+    """Host arrays (k, Nx) of the k initial levels N, N-1, ..., N-k+1 from the
+    closed-form solution of the problem (the exact start), with the level-N
+    call payoff replaced by its cell average when smoothing is on.  This is
+    input data for callers that pass their own levels through host memory."""
+    from scipy.special import ndtr
+    k, Nx, N = int(p["k"]), int(p["Nx"]), int(p["N"])
+    dx = (p["x_max"] - p["x_min"]) / (Nx - 1)
+    x = p["x_min"] + dx * np.arange(Nx)
+    dt = p["T"] / N
+    ys, zs = np.zeros((k, Nx)), np.zeros((k, Nx))
+    for m in range(k):
+        t = (N - m) * dt
+        term = p["terminal"]
+        if term == "SIN":
+            u, ux = np.sin(x + t), np.cos(x + t)
+        elif term == "LOGISTIC":
+            e = np.exp(x + t)
+            u, ux = e / (e + 1), e / (e + 1) ** 2
+        elif term == "LNSIN":
+            e = math.exp(t * t)
+            u, ux = np.log(np.sin(x) + 3) * e, e * np.cos(x) / (np.sin(x) + 3)
+        else:
+            K = p["strike"]
+            if m == 0 and p.get("smoothing", 0):
+                a, b, kap = x - dx / 2, x + dx / 2, math.log(K)
+                ea = np.exp(a) * np.expm1(b - a) / dx
+                d = np.clip(b - kap, 0.0, None)
+                mid = K * (np.expm1(d) - d) / dx
+                u = np.where(b <= kap, 0.0, np.where(a >= kap, ea - K, mid))
+                ux = np.where(b <= kap, 0.0, np.where(a >= kap, ea, K * np.expm1(d) / dx))
+            else:
+                r, dl = p.get("r", 0.0), p.get("delta", 0.0)
+                if p["driver"] == "LB":
+                    r, dl = r - p.get("lb_sign", 1.0) * (p["R"] - r), 0.0
+                S, tau, sig = np.exp(x), p["T"] - t, p["sigma"]
+                if tau <= 0:
+                    u, ux = np.maximum(S - K, 0.0), np.where(S > K, S, 0.0)
+                else:
+                    sq = sig * math.sqrt(tau)
+                    d1 = (np.log(S / K) + (r - dl + 0.5 * sig * sig) * tau) / sq
+                    a = S * math.exp(-dl * tau) * ndtr(d1)
+                    u, ux = a - K * math.exp(-r * tau) * ndtr(d1 - sq), a
+        ys[m], zs[m] = u, p["b_x"] * ux
+    return ys, zs

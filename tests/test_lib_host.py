@@ -1,0 +1,114 @@
+"""Host-side checks of the CUDA library: it builds, loads without a GPU,
+exports every entry point include/bsde.h declares, and its host-computed plan
+constants are right.  No kernel is launched here."""
+import ctypes
+import math
+import os
+import re
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from paper_1909_13560_gb300 import bsde as B
+from paper_1909_13560_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            names += re.findall(r"BSDE_API\s+[\w\s\*]+?\b(\w+)\s*\(", text)
+    return names
+
+
+def test_header_declares_the_abi():
+    names = _declared()
+    for n in ("bsde_plan", "bsde_solve", "bsde_free", "bsde_workspace_bytes"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = B.load()
+    for name in _declared():
+        assert hasattr(lib, name), name
+        assert getattr(lib, name) is not None
+
+
+def test_binding_structs_match_header_layout(tmp_path):
+    """Compile a probe against include/bsde.h with the host C compiler and
+    compare sizes and offsets with the ctypes mirror."""
+    import subprocess
+    src = tmp_path / "probe.c"
+    fields_p = [f for f, _ in B.bsde_problem._fields_]
+    fields_r = [f for f, _ in B.bsde_result._fields_]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "bsde.h"', 'int main(void){',
+             'printf("%zu %zu\\n", sizeof(bsde_problem), sizeof(bsde_result));']
+    lines += [f'printf("%zu\\n", offsetof(bsde_problem, {f}));' for f in fields_p]
+    lines += [f'printf("%zu\\n", offsetof(bsde_result, {f}));' for f in fields_r]
+    lines += ['return 0;}']
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "probe"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    vals = [int(v) for v in out]
+    assert vals[0] == ctypes.sizeof(B.bsde_problem)
+    assert vals[1] == ctypes.sizeof(B.bsde_result)
+    offs = vals[2:]
+    for f, o in zip(fields_p, offs[:len(fields_p)]):
+        assert getattr(B.bsde_problem, f).offset == o, f
+    for f, o in zip(fields_r, offs[len(fields_p):]):
+        assert getattr(B.bsde_result, f).offset == o, f
+
+
+@pytest.mark.parametrize("L", [1, 2, 5, 8, 16, 32, 64])
+def test_device_plan_gauss_hermite(L):
+    a, w = B.bsde_gauss_hermite(L)
+    ra, rw = np.polynomial.hermite.hermgauss(L)
+    assert np.max(np.abs(a - ra)) <= 1e-13 * max(1.0, np.abs(ra).max())
+    assert np.max(np.abs(w - rw) / rw) <= 2e-12
+    for p in range(0, 2 * L, 2):
+        assert float(np.sum(w * a ** p)) == pytest.approx(math.gamma((p + 1) / 2), rel=1e-12)
+
+
+@pytest.mark.parametrize("k", range(1, 7))
+def test_device_plan_gamma_tables(k):
+    gy, gz = B.bsde_gamma(k)
+    # exact sums and the closed forms of the small cases (trapezoid, Simpson,
+    # Simpson 3/8, Adams-Moulton in Table 2)
+    assert sum(Fraction(x).limit_denominator(2000) for x in gy) == 1
+    assert sum(Fraction(x).limit_denominator(2000) for x in gz) == 1
+    known_y = {1: [1 / 2, 1 / 2], 2: [1 / 6, 2 / 3, 1 / 6], 3: [1 / 8, 3 / 8, 3 / 8, 1 / 8]}
+    known_z = {1: [1 / 2, 1 / 2], 2: [5 / 12, 8 / 12, -1 / 12],
+               3: [9 / 24, 19 / 24, -5 / 24, 1 / 24]}
+    if k in known_y:
+        assert np.allclose(gy, known_y[k], rtol=0, atol=1e-16)
+        assert np.allclose(gz, known_z[k], rtol=0, atol=1e-16)
+
+
+def test_gamma_rejects_k_beyond_tables():
+    with pytest.raises(B.BsdeError):
+        B.bsde_gamma(7)
+
+
+@pytest.mark.parametrize("bad", [dict(k=7), dict(k=5, N=4), dict(Nx=3), dict(L=0),
+                                 dict(L=65), dict(x0=9.0), dict(T=0.0),
+                                 dict(picard_max=0)])
+def test_invalid_problems_rejected(bad):
+    p = W.sin_problem()
+    p.update(bad)
+    with pytest.raises(B.BsdeError) as ei:
+        B.bsde_workspace_bytes(B.make_problem(p))
+    assert ei.value.code == B.BSDE_EINVAL
+
+
+def test_workspace_bytes_scale_with_ring():
+    p = W.config2(k=6)
+    b64 = B.bsde_workspace_bytes(B.make_problem(p, "fp64"))
+    b32 = B.bsde_workspace_bytes(B.make_problem(p, "fp32c"))
+    nx, ns = p["Nx"], p["k"] + 1
+    assert b64 >= ns * nx * 32 and b32 >= ns * nx * 24
+    assert b32 < b64
