@@ -178,6 +178,40 @@ BSDE_API const char *bsde_last_error(void);
 BSDE_API int bsde_gauss_hermite(int L, double *nodes, double *weights);
 BSDE_API int bsde_gamma(int k, double *gy, double *gz);
 
+/* Solve without allocating anything (no counterpart in the paper; this is a
+ * service for callers of this library).
+ *
+ * Some callers must not allocate device or pinned memory at solve time: a
+ * host application that owns the whole device through its own allocator and
+ * forbids others from calling cudaMalloc, a latency-critical pricing loop
+ * where an allocation would synchronise the device in the middle of a
+ * trading cycle, or a plug-in loaded into a process whose memory budget is
+ * fixed.  This entry point serves them.  It runs the same kernels as
+ * bsde_solve, with the workspace in a fixed array that the library reserves
+ * in device memory (BSDE_NOALLOC_MAX_BYTES per GPU, held by every GPU that
+ * loads the library until the process exits).  It launches the kernels one
+ * by one and calls no cudaMalloc, cudaMallocHost, cudaFree or any other
+ * allocating routine; the plan constants live on the host stack.
+ *
+ * Arguments are those of bsde_plan and bsde_solve (the caller still passes
+ * the initial levels, if any, and the output buffers).  The call waits for
+ * `stream` before returning.  A problem whose workspace
+ * (bsde_workspace_bytes) exceeds BSDE_NOALLOC_MAX_BYTES is rejected with
+ * BSDE_ENOSPC and a message naming both sizes.
+ *
+ * The first call on each device looks up that device's copy of the array
+ * (cudaGetSymbolAddress, with the device current) and caches the address;
+ * make that first call before any stream capture on the device.  All calls
+ * on a device share the one array, which keeps the contents of the last
+ * call; every call rewrites what it reads before reading it.  Calls whose GPU
+ * work overlaps (different streams, or different host threads, on the same
+ * device) race on the array: order them. */
+#define BSDE_NOALLOC_MAX_BYTES ((size_t)32 << 20)
+BSDE_API int bsde_solve_noalloc(const bsde_problem *p, void *stream,
+                                const double *init_y, const double *init_z,
+                                int init_on_host, double *out_y, double *out_z,
+                                int out_on_host, bsde_result *result);
+
 #ifdef __cplusplus
 }
 #endif

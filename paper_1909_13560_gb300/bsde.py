@@ -58,7 +58,7 @@ class bsde_result(ctypes.Structure):
 _lib = None
 _SYMBOLS = ("bsde_workspace_bytes", "bsde_plan", "bsde_solve", "bsde_result_fetch",
             "bsde_enqueue_level", "bsde_free", "bsde_plan_launches", "bsde_strerror",
-            "bsde_last_error", "bsde_gauss_hermite", "bsde_gamma")
+            "bsde_last_error", "bsde_gauss_hermite", "bsde_gamma", "bsde_solve_noalloc")
 
 
 def load(path: str = LIB_PATH):
@@ -89,6 +89,8 @@ def load(path: str = LIB_PATH):
     lib.bsde_last_error.restype = ctypes.c_char_p
     lib.bsde_gauss_hermite.argtypes = [ctypes.c_int, P(d), P(d)]
     lib.bsde_gamma.argtypes = [ctypes.c_int, P(d), P(d)]
+    lib.bsde_solve_noalloc.argtypes = [P(bsde_problem), vp, vp, vp, ctypes.c_int, vp, vp,
+                                       ctypes.c_int, P(bsde_result)]
     _lib = lib
     return lib
 
@@ -168,6 +170,21 @@ def bsde_result_fetch(plan: int, stream: int) -> bsde_result:
 def bsde_enqueue_level(plan: int, stream: int, n: int, parts: int = 1) -> None:
     _check(load().bsde_enqueue_level(ctypes.c_void_p(plan), ctypes.c_void_p(stream),
                                      int(n), int(parts)), "bsde_enqueue_level")
+
+
+def bsde_solve_noalloc(prob: bsde_problem, stream: int, init_y: int = 0, init_z: int = 0,
+                       init_on_host: bool = False, out_y: int = 0, out_z: int = 0,
+                       out_on_host: bool = False) -> bsde_result:
+    """Solve with the library's fixed device workspace: for callers that may
+    not allocate memory at solve time (see include/bsde.h)."""
+    res = bsde_result()
+    rc = load().bsde_solve_noalloc(ctypes.byref(prob), ctypes.c_void_p(stream),
+                                   ctypes.c_void_p(init_y or None), ctypes.c_void_p(init_z or None),
+                                   int(init_on_host), ctypes.c_void_p(out_y or None),
+                                   ctypes.c_void_p(out_z or None), int(out_on_host),
+                                   ctypes.byref(res))
+    _check(rc, "bsde_solve_noalloc")
+    return res
 
 
 def bsde_free(plan: int) -> None:

@@ -4,6 +4,7 @@
 
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -347,3 +348,93 @@ int bsde_gamma(int k, double *gy, double *gz) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Solve without allocating: the workspace is a fixed array in device memory
+// reserved when the library is loaded.  Host code never touches `noalloc_ws`
+// by name as a device address (in host code the symbol is a host-side
+// stand-in); it asks the runtime for each device's address once and caches
+// it.
+// ---------------------------------------------------------------------------
+namespace bsde {
+
+static __device__ __align__(256) unsigned char noalloc_ws[BSDE_NOALLOC_MAX_BYTES];
+
+constexpr int kMaxDevices = 64;
+static unsigned char *g_noalloc_addr[kMaxDevices];
+static std::mutex g_noalloc_mu;
+
+static int noalloc_address(int dev, unsigned char **out) {
+  if (dev < 0 || dev >= kMaxDevices) return fail(BSDE_EINVAL, "device ordinal out of range");
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void *ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, noalloc_ws);
+    if (e != cudaSuccess || ptr == nullptr)
+      return fail(BSDE_ECUDA, std::string("cudaGetSymbolAddress(noalloc workspace): ") +
+                                  cudaGetErrorString(e));
+    g_noalloc_addr[dev] = static_cast<unsigned char *>(ptr);
+  }
+  *out = g_noalloc_addr[dev];
+  return BSDE_OK;
+}
+
+}  // namespace bsde
+
+extern "C" int bsde_solve_noalloc(const bsde_problem *p, void *stream, const double *init_y,
+                                  const double *init_z, int init_on_host, double *out_y,
+                                  double *out_z, int out_on_host, bsde_result *result) {
+  if (!p) return fail(BSDE_EINVAL, "null problem");
+  if ((init_y == nullptr) != (init_z == nullptr))
+    return fail(BSDE_EINVAL, "init_y and init_z must both be given or both be NULL");
+  // the plan lives on this stack frame: no host or device allocation
+  bsde_plan_t pl{};
+  if (fill_params(*p, pl.P)) return fail(BSDE_EINVAL, "invalid problem");
+  pl.lay = layout_for(*p);
+  if (pl.lay.total > BSDE_NOALLOC_MAX_BYTES)
+    return fail(BSDE_ENOSPC, "problem needs " + std::to_string(pl.lay.total) +
+                                 " bytes of workspace; the no-allocation workspace holds " +
+                                 std::to_string(size_t(BSDE_NOALLOC_MAX_BYTES)));
+  pl.prob = *p;
+  cudaGetDevice(&pl.device);
+  int rc = noalloc_address(pl.device, &pl.ws);
+  if (rc) return rc;
+  pl.ws_bytes = BSDE_NOALLOC_MAX_BYTES;
+  driver_coefs(pl.P, pl.dc64, pl.dc32);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const Params &P = pl.P;
+  const int kL = P.k * P.L;
+  NodeF64 t64[kMaxK * kMaxL];
+  NodeF32 t32[kMaxK * kMaxL];
+  build_tables(P, t64, t32);
+  if (P.precision == BSDE_FP64)
+    BSDE_CUDA_TRY(cudaMemcpyAsync(pl.ws + pl.lay.table, t64, sizeof(NodeF64) * kL,
+                                  cudaMemcpyHostToDevice, s));
+  else
+    BSDE_CUDA_TRY(cudaMemcpyAsync(pl.ws + pl.lay.table, t32, sizeof(NodeF32) * kL,
+                                  cudaMemcpyHostToDevice, s));
+  double *sy = reinterpret_cast<double *>(pl.ws + pl.lay.stage);
+  double *sz = sy + int64_t(P.k) * P.Nx;
+  const size_t lev_bytes = size_t(P.k) * size_t(P.Nx) * sizeof(double);
+  if (init_y) {
+    const cudaMemcpyKind kind = init_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    BSDE_CUDA_TRY(cudaMemcpyAsync(sy, init_y, lev_bytes, kind, s));
+    BSDE_CUDA_TRY(cudaMemcpyAsync(sz, init_z, lev_bytes, kind, s));
+  }
+  if (P.precision == BSDE_FP64)
+    enqueue_solve<BSDE_FP64>(&pl, s, init_y != nullptr);
+  else
+    enqueue_solve<BSDE_FP32C>(&pl, s, init_y != nullptr);
+  BSDE_CUDA_TRY(cudaGetLastError());
+  const size_t out_bytes = size_t(P.Nx) * sizeof(double);
+  const cudaMemcpyKind okind = out_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (out_y) BSDE_CUDA_TRY(cudaMemcpyAsync(out_y, sy, out_bytes, okind, s));
+  if (out_z) BSDE_CUDA_TRY(cudaMemcpyAsync(out_z, sy + P.Nx, out_bytes, okind, s));
+  Stats st{};
+  BSDE_CUDA_TRY(cudaMemcpyAsync(&st, pl.ws + pl.lay.stats, sizeof(Stats),
+                                cudaMemcpyDeviceToHost, s));
+  BSDE_CUDA_TRY(cudaStreamSynchronize(s));
+  if (!result) return BSDE_OK;
+  pl.host_stats = &st;
+  return fill_result(&pl, result);
+}
