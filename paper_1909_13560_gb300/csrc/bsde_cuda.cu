@@ -79,18 +79,19 @@ static void driver_coefs(const Params &P, DrvC<double> &c64, DrvC<float> &c32) {
 template <int PREC, int DRV>
 static void launch_step(bsde_plan_t *pl, cudaStream_t s, int n) {
   const Params &P = pl->P;
-  const int threads = 128;
-  const unsigned blocks = unsigned((P.Nx + threads - 1) / threads);
+  const int threads = kStepTP * P.G;
+  const unsigned blocks = unsigned((P.Nx + kStepTP - 1) / kStepTP);
+  const int kL = P.k * P.L;
   Stats *st = reinterpret_cast<Stats *>(pl->ws + pl->lay.stats);
   if (PREC == BSDE_FP64) {
-    const size_t sm = size_t(P.k) * P.L * sizeof(NodeF64);
+    const size_t sm = sizeof(NodeF64) * kL + sizeof(double) * 2 * P.G * kStepTP;
     k_step64<DRV><<<blocks, threads, sm, s>>>(
         P, pl->dc64, reinterpret_cast<double4_32a *>(pl->ws + pl->lay.ring64),
         reinterpret_cast<const NodeF64 *>(pl->ws + pl->lay.table), n, st);
   } else {
-    const size_t sm = size_t(P.k) * P.L * sizeof(NodeF32);
+    const size_t sm = sizeof(NodeF32) * kL + sizeof(float) * 6 * P.G * kStepTP;
     k_step32<DRV><<<blocks, threads, sm, s>>>(
-        P, pl->dc32, pl->dc64, reinterpret_cast<float4 *>(pl->ws + pl->lay.ringA),
+        P, pl->dc32, reinterpret_cast<float4 *>(pl->ws + pl->lay.ringA),
         reinterpret_cast<const float2 *>(pl->ws + pl->lay.ringB),
         reinterpret_cast<const NodeF32 *>(pl->ws + pl->lay.table), n, st);
   }
@@ -113,12 +114,9 @@ static int64_t enqueue_spline(bsde_plan_t *pl, cudaStream_t s, int slot) {
   Ring64 r64{reinterpret_cast<double4_32a *>(pl->ws + pl->lay.ring64)};
   Ring32 r32{reinterpret_cast<float4 *>(pl->ws + pl->lay.ringA),
              reinterpret_cast<float2 *>(pl->ws + pl->lay.ringB)};
-  void *g = pl->ws + pl->lay.gscr;
-  const int64_t chunks = (P.Nx - 2 + kSplineChunk - 1) / kSplineChunk;
-  const unsigned blocks = unsigned((chunks + 127) / 128);
-  k_spline_fwd<PREC><<<blocks, 128, 0, s>>>(P, r64, r32, g, slot);
-  k_spline_bwd<PREC><<<blocks, 128, 0, s>>>(P, r64, r32, g, slot);
-  return 2;
+  const unsigned blocks = unsigned((P.Nx - 2 + kSplineTile - 1) / kSplineTile);
+  k_spline<PREC><<<blocks, kSplineTile / kSplineChunk, 0, s>>>(P, r64, r32, slot);
+  return 1;
 }
 
 // The whole solve as one stream-ordered sequence (captured into a graph).
@@ -216,7 +214,7 @@ int bsde_plan(const bsde_problem *p, void *dev_workspace, size_t bytes, bsde_pla
     delete pl;
     return fail(BSDE_ENOMEM, "table allocation");
   }
-  build_tables(P, t64, t32);
+  build_tables(pl->P, t64, t32);
   cudaError_t e;
   if (P.precision == BSDE_FP64)
     e = cudaMemcpy(pl->ws + lay.table, t64, sizeof(NodeF64) * kL, cudaMemcpyHostToDevice);
@@ -319,7 +317,7 @@ int64_t bsde_plan_launches(const bsde_plan_t *pl) {
   if (!pl) return 0;
   // kernels in one solve (identical for both starts)
   const Params &P = pl->P;
-  return 1 + int64_t(P.k) * 3 + int64_t(P.N - P.k + 1) * 3 + 2;
+  return 1 + int64_t(P.k) * 2 + int64_t(P.N - P.k + 1) * 2 + 2;
 }
 
 const char *bsde_strerror(int code) {
@@ -406,7 +404,7 @@ extern "C" int bsde_solve_noalloc(const bsde_problem *p, void *stream, const dou
   const int kL = P.k * P.L;
   NodeF64 t64[kMaxK * kMaxL];
   NodeF32 t32[kMaxK * kMaxL];
-  build_tables(P, t64, t32);
+  build_tables(pl.P, t64, t32);
   if (P.precision == BSDE_FP64)
     BSDE_CUDA_TRY(cudaMemcpyAsync(pl.ws + pl.lay.table, t64, sizeof(NodeF64) * kL,
                                   cudaMemcpyHostToDevice, s));

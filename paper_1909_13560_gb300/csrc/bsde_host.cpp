@@ -10,7 +10,7 @@ namespace bsde {
 
 int validate(const bsde_problem &p) {
   if (p.k < 1 || p.k > kMaxK || p.k > p.N || p.N < 1) return BSDE_EINVAL;
-  if (p.Nx < 4 || p.Nx > (int64_t(1) << 31)) return BSDE_EINVAL;
+  if (p.Nx < 4 || p.Nx > (int64_t(1) << 30)) return BSDE_EINVAL;
   if (p.L < 1 || p.L > kMaxL) return BSDE_EINVAL;
   if (!(p.T > 0.0) || !(p.x_max > p.x_min)) return BSDE_EINVAL;
   if (!(p.x0 >= p.x_min && p.x0 <= p.x_max)) return BSDE_EINVAL;
@@ -166,7 +166,6 @@ Layout layout_for(const bsde_problem &p) {
     L.ringA = off; off = up(off + ns * nx * 16);
     L.ringB = off; off = up(off + ns * nx * 8);
   }
-  L.gscr = off; off = up(off + 2 * nx * (p.precision == BSDE_FP64 ? 8 : 4));
   L.table = off; off = up(off + size_t(p.k) * p.L * (p.precision == BSDE_FP64 ? sizeof(NodeF64) : sizeof(NodeF32)));
   L.stage = off; off = up(off + 2 * size_t(p.k) * nx * 8);
   L.stats = off; off = up(off + sizeof(Stats));
@@ -174,53 +173,73 @@ Layout layout_for(const bsde_problem &p) {
   return L;
 }
 
+// Work split of the step kernels: enough (j, l-chunk) groups per point that a
+// level of a modest grid still fills the GPU (at least four groups).
+static void work_split(Params &P) {
+  int S = (4 + P.k - 1) / P.k;
+  if (S > P.L) S = P.L;
+  if (S < 1) S = 1;
+  P.S = S;
+  P.Lg = (P.L + S - 1) / S;
+  P.G = P.k * S;
+}
+
 // Node tables.  On the uniform grid with a constant-coefficient forward
 // process the off-grid point of (j, l) is x_i + o_jl dx with the same o_jl for
 // every i (Section 3.2, third remark: the cell index is found without a
 // search); its cell is i + floor(o_jl) and its position inside the cell
 // theta = o_jl - floor(o_jl).
-void build_tables(const Params &P, NodeF64 *t64, NodeF32 *t32) {
+void build_tables(Params &P, NodeF64 *t64, NodeF32 *t32) {
+  work_split(P);
   double a[kMaxL], w[kMaxL];
   gauss_hermite(P.L, a, w);
   const double rpi = 1.0 / std::sqrt(M_PI);
   const double c6 = P.dx * P.dx / 6.0;
   for (int j = 1; j <= P.k; ++j) {
     const double sq = std::sqrt(2.0 * j * P.dt);
+    int smin = 0x7fffffff, smax = -0x7fffffff;
     for (int l = 0; l < P.L; ++l) {
       const double dW = sq * a[l];
       const double o = (P.a_x * j * P.dt + P.b_x * dW) / P.dx;
-      const double s = std::floor(o);
-      const double th = o - s;
+      // a shift beyond the grid only ever clamps: keep |shift| <= Nx + 1 so
+      // that i + shift stays in 32-bit range
+      const double lim = double(P.Nx + 1);
+      const double s = std::fmin(std::fmax(std::floor(o), -lim), lim);
+      const double th = o - std::floor(o);
       const double om = 1.0 - th;
       const double wt = w[l] * rpi;
       NodeF64 e{};
-      e.shift = (int64_t)s;
+      e.shift = (int32_t)s;
       e.w0 = om;
       e.w1 = th;
       e.w2 = c6 * (om * om * om - om);
       e.w3 = c6 * (th * th * th - th);
-      e.wt = wt;
-      e.wdw = wt * dW;
+      e.cz = wt * ((j == 1 ? 1.0 : 0.0) - P.gz[j]) * P.inv_gz0;
+      e.cfz = P.gz[j] * wt * dW * P.inv_gz0;
+      e.cfy = P.h * P.gy[j] * wt;
+      e.cy = (j == P.k) ? wt : 0.0;
+      if (e.shift < smin) smin = e.shift;
+      if (e.shift > smax) smax = e.shift;
       const int idx = (j - 1) * P.L + l;
       if (t64) t64[idx] = e;
       if (t32) {
         NodeF32 f{};
-        f.shift = (int32_t)s;
+        f.shift = e.shift;
         f.w0 = (float)e.w0;
         f.w1 = (float)e.w1;
         f.w2 = (float)e.w2;
         f.w3 = (float)e.w3;
-        const double cz = wt * ((j == 1 ? 1.0 : 0.0) - P.gz[j]) * P.inv_gz0;
-        f.czh = (float)cz;
-        f.czl = (float)(cz - (double)f.czh);
-        f.cfz = (float)(P.gz[j] * e.wdw * P.inv_gz0);
-        f.cfy = (float)(P.h * P.gy[j] * wt);
-        const double cy = (j == P.k) ? wt : 0.0;
-        f.cyh = (float)cy;
-        f.cyl = (float)(cy - (double)f.cyh);
+        f.czh = (float)e.cz;
+        f.czl = (float)(e.cz - (double)f.czh);
+        f.cfz = (float)e.cfz;
+        f.cfy = (float)e.cfy;
+        f.cyh = (float)e.cy;
+        f.cyl = (float)(e.cy - (double)f.cyh);
         t32[idx] = f;
       }
     }
+    P.smin[j - 1] = smin;
+    P.smax[j - 1] = smax;
   }
 }
 

@@ -12,25 +12,28 @@ namespace bsde {
 constexpr int kMaxK = 6;
 constexpr int kMaxL = 64;
 constexpr int kInvPivots = 64;   // exact 1/d_m of the spline LU for m < 64
-constexpr int kSplineChunk = 64; // unknowns per thread in the spline passes
-constexpr int kSplineWarm = 32;  // warm-up length: (2 - sqrt 3)^33 < 2^-62
+constexpr int kStepTP = 64;      // grid points per CTA in the step kernels
+constexpr int kMaxGroups = 8;    // (j, l-chunk) groups per point
+constexpr int kSplineTile = 512;  // unknowns per CTA in the spline kernel
+constexpr int kSplineChunk = 4;   // unknowns per thread (serial recurrence)
 
-// Per (j, l) entry of the FP64 node table: the off-grid point
+// Per (j, l) entry of the node tables.  The off-grid point
 // x_i + a_x j dt + b_x sqrt(2 j dt) a_l sits in cell i + shift at relative
-// position theta; w0..w3 are the spline weights of y_c, y_{c+1}, M_c,
-// M_{c+1}; wt = omega_l / sqrt(pi) (Eq. 21) and wdw = wt * DeltaW_{jl}.
+// position theta; w0..w3 are the spline weights of v_c, v_{c+1}, M_c, M_{c+1}.
+// The expectations of Eq. 20 are folded into per-node coefficients, so that
+// a thread keeps two sums per point:
+//   z^n = sum_jl cz_jl z^_jl + sum_jl cfz_jl F_jl
+//   A   = sum_l  cy_l  y^_kl + sum_jl cfy_jl F_jl      (y^n = A + k dt gy_0 f(t_n, y^n, z^n))
+// with wt = omega_l / sqrt(pi) (Eq. 21), DeltaW_jl = sqrt(2 j dt) a_l,
+// cz = wt (delta_{j1} - gz_j) / gz_0, cfz = gz_j wt DeltaW_jl / gz_0,
+// cy = wt (j = k only), cfy = k dt gy_j wt.
 struct NodeF64 {
-  int64_t shift;
-  double w0, w1, w2, w3, wt, wdw, pad;
+  int32_t shift, pad;
+  double w0, w1, w2, w3, cz, cfz, cfy, cy;
 };
 
-// FP32C node table entry.  The y and z expectations of Eq. 20 are folded
-// into per-node coefficients so that the kernel keeps four accumulators:
-//   z^n     = sum_jl cz_jl z^_jl + sum_jl cfz_jl F_jl
-//   A (y^n) = sum_l  cy_l  y^_kl + sum_jl cfy_jl F_jl
-// with cz = wt (delta_{j1} - gz_j) / gz_0, cfz = gz_j wdw / gz_0,
-// cy = wt (j = k only), cfy = k dt gy_j wt.  cz and cy are split into
-// float hi + lo parts for the compensated sums.
+// FP32C entry: the same coefficients, with cz and cy split into float
+// hi + lo parts for the compensated sums.
 struct NodeF32 {
   int32_t shift;
   float w0, w1, w2, w3;
@@ -51,6 +54,10 @@ struct Params {
   double inv_gz0; // 1 / gz_0
   double inv_dx2_6; // 6 / dx^2
   double invd[kInvPivots];
+  // work split of the step kernels: S l-chunks of Lg nodes per j, G = k S
+  // groups per point; shift range per j (for the clamp-free fast path)
+  int32_t S, Lg, G, pad0;
+  int32_t smin[kMaxK], smax[kMaxK];
 };
 
 // Device workspace layout (byte offsets from the workspace base).
@@ -58,7 +65,6 @@ struct Layout {
   size_t ring64;   // FP64: double4 (y, M_y, z, M_z) x nslot x Nx
   size_t ringA;    // FP32C: float4 (y_hi, y_lo, z_hi, z_lo) x nslot x Nx
   size_t ringB;    // FP32C: float2 (M_y, M_z) x nslot x Nx
-  size_t gscr;     // spline forward-sweep scratch: 2 x Nx values
   size_t table;    // node table (k L entries)
   size_t stage;    // 2 x k x Nx doubles: imported initial levels / exported level 0
   size_t stats;    // Stats
@@ -79,6 +85,6 @@ int fill_params(const bsde_problem &p, Params &P);
 Layout layout_for(const bsde_problem &p);
 int gauss_hermite(int L, double *nodes, double *weights);
 int gamma_tables(int k, double *gy, double *gz);
-void build_tables(const Params &P, NodeF64 *t64, NodeF32 *t32);
+void build_tables(Params &P, NodeF64 *t64, NodeF32 *t32);
 
 }  // namespace bsde

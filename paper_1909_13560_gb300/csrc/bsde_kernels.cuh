@@ -183,91 +183,116 @@ __global__ void k_export(const Params P, Ring64 r64, Ring32 r32, double *sy, dou
 
 // ---------------------------------------------------------------------------
 // S2: natural cubic spline second derivatives of the level in `slot`
-// (Section 3.3; the paper solves the tridiagonal system iteratively, here it is
-// solved exactly).  Unknowns u_m = M_{m+1}, m = 0..Nx-3:
-//   u_{m-1} + 4 u_m + u_{m+1} = 6 (v_m - 2 v_{m+1} + v_{m+2}) / dx^2.
-// LU of tridiag(1, 4, 1): forward g_m = r_m - g_{m-1}/d_{m-1}, backward
-// u_m = (g_m - u_{m+1})/d_m.  Both recurrences contract by 2 - sqrt(3) per
-// step, so a chunk of kSplineChunk unknowns starts kSplineWarm steps early
-// from zero and is exact to rounding ((2 - sqrt 3)^33 ~ 1.4e-19).
+// (Section 3.3; the paper solves the tridiagonal system iteratively, here it
+// is solved exactly).  Unknowns u_m = M_{m+1}, m = 0..Nx-3:
+//   u_{m-1} + 4 u_m + u_{m+1} = r_m = 6 (v_m - 2 v_{m+1} + v_{m+2}) / dx^2,
+// M_0 = M_{Nx-1} = 0.  LU of tridiag(1, 4, 1): forward g_m = r_m - g_{m-1}/d_{m-1},
+// backward u_m = (g_m - u_{m+1})/d_m.  Both recurrences contract by 2 - sqrt 3
+// per step, so a chunk of unknowns started W steps early from zero is exact
+// to (2 - sqrt 3)^{W+1}: W = 32 (1.4e-19) in FP64, W = 16 (1.9e-10, far below
+// what M contributes at weight dx^2/6) in FP32C.
+// One CTA owns a tile of kSplineTile unknowns: it stages the level values of
+// the tile and its halo in shared memory, forms r, runs the forward sweep of
+// each thread's chunk (warm-up from the left), then the backward sweep
+// (warm-up from the right over the neighbouring chunks' g), all on chip.
 // ---------------------------------------------------------------------------
-// FP64: right-hand side from double values
-__device__ __forceinline__ void rhs64(const Params &P, const double4_32a *lev, int64_t m,
-                                      double &ry, double &rz) {
-  const double4_32a a = lev[m], b = lev[m + 1], c = lev[m + 2];
-  ry = P.inv_dx2_6 * (a.x - 2.0 * b.x + c.x);
-  rz = P.inv_dx2_6 * (a.z - 2.0 * b.z + c.z);
-}
-
-// FP32C: right-hand side from (hi, lo) pairs.  Neighbouring hi values are
-// within a factor two of each other away from sign changes, so their
-// difference is exact (Sterbenz); the second difference then carries the
-// full precision of the pair.
-__device__ __forceinline__ void rhs32(const Params &P, float inv6, const float4 *lev,
-                                      int64_t m, float &ry, float &rz) {
-  const float4 a = lev[m], b = lev[m + 1], c = lev[m + 2];
-  const float d1y = __fadd_rn(__fsub_rn(b.x, a.x), __fsub_rn(b.y, a.y));
-  const float d2y = __fadd_rn(__fsub_rn(c.x, b.x), __fsub_rn(c.y, b.y));
-  const float d1z = __fadd_rn(__fsub_rn(b.z, a.z), __fsub_rn(b.w, a.w));
-  const float d2z = __fadd_rn(__fsub_rn(c.z, b.z), __fsub_rn(c.w, b.w));
-  ry = inv6 * __fsub_rn(d2y, d1y);
-  rz = inv6 * __fsub_rn(d2z, d1z);
-}
+template <int PREC>
+struct SplineT;
+template <>
+struct SplineT<BSDE_FP64> {
+  using T = double;
+  static constexpr int W = 32;
+};
+template <>
+struct SplineT<BSDE_FP32C> {
+  using T = float;
+  static constexpr int W = 16;
+};
 
 template <int PREC>
-__global__ void __launch_bounds__(128) k_spline_fwd(const Params P, Ring64 r64, Ring32 r32,
-                                                    void *gscr, int slot) {
-  const int64_t u = P.Nx - 2;
-  const int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  const int64_t m0 = q * kSplineChunk;
-  if (m0 >= u) return;
-  const int64_t m1 = m0 + kSplineChunk < u ? m0 + kSplineChunk : u;
-  const int64_t start = m0 - kSplineWarm > 0 ? m0 - kSplineWarm : 0;
+__global__ void __launch_bounds__(kSplineTile / kSplineChunk)
+    k_spline(const Params P, Ring64 r64, Ring32 r32, int slot) {
+  using T = typename SplineT<PREC>::T;
+  constexpr int W = SplineT<PREC>::W;
+  constexpr int TS = kSplineTile, C = kSplineChunk;
+  // r and g over the unknowns [a - W, b + W), stored at index m - (a - W)
+  __shared__ T sr[2][TS + 2 * W];
+  __shared__ T sg[2][TS + 2 * W];
+  __shared__ T sid[kInvPivots];
+  const int u = int(P.Nx - 2);
+  const int a = blockIdx.x * TS;
+  const int b = a + TS < u ? a + TS : u;
+  const int ra = a - W > 0 ? a - W : 0;
+  const int rb = b + W < u ? b + W : u;
+  const int base = a - W;
   const int64_t off = int64_t(slot) * P.Nx;
-  if (PREC == BSDE_FP64) {
-    const double4_32a *lev = r64.ring + off;
-    double *gy = static_cast<double *>(gscr), *gz = gy + P.Nx;
-    double py = 0.0, pz = 0.0;
-    for (int64_t m = start; m < m1; ++m) {
-      double ry, rz;
-      rhs64(P, lev, m, ry, rz);
-      const double id = m > 0 ? P.invd[m - 1 < kInvPivots ? m - 1 : kInvPivots - 1] : 0.0;
-      py = ry - py * id;
-      pz = rz - pz * id;
-      if (m >= m0) {
-        gy[m] = py;
-        gz[m] = pz;
-      }
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid < kInvPivots) sid[tid] = T(P.invd[tid]);
+
+  // right-hand sides
+  for (int m = ra + tid; m < rb; m += nt) {
+    T ry, rz;
+    if constexpr (PREC == BSDE_FP64) {
+      const double4_32a v0 = r64.ring[off + m], v1 = r64.ring[off + m + 1],
+                        v2 = r64.ring[off + m + 2];
+      ry = P.inv_dx2_6 * (v0.x - 2.0 * v1.x + v2.x);
+      rz = P.inv_dx2_6 * (v0.z - 2.0 * v1.z + v2.z);
+    } else {
+      // (hi, lo) pairs: neighbouring hi values differ exactly (Sterbenz) away
+      // from sign changes, so the second difference keeps the pair precision
+      const float4 v0 = r32.A[off + m], v1 = r32.A[off + m + 1], v2 = r32.A[off + m + 2];
+      const float inv6 = float(P.inv_dx2_6);
+      const float d1y = __fadd_rn(__fsub_rn(v1.x, v0.x), __fsub_rn(v1.y, v0.y));
+      const float d2y = __fadd_rn(__fsub_rn(v2.x, v1.x), __fsub_rn(v2.y, v1.y));
+      const float d1z = __fadd_rn(__fsub_rn(v1.z, v0.z), __fsub_rn(v1.w, v0.w));
+      const float d2z = __fadd_rn(__fsub_rn(v2.z, v1.z), __fsub_rn(v2.w, v1.w));
+      ry = inv6 * __fsub_rn(d2y, d1y);
+      rz = inv6 * __fsub_rn(d2z, d1z);
     }
-  } else {
-    const float4 *lev = r32.A + off;
-    float *gy = static_cast<float *>(gscr), *gz = gy + P.Nx;
-    const float inv6 = float(P.inv_dx2_6);
-    float py = 0.f, pz = 0.f;
-    for (int64_t m = start; m < m1; ++m) {
-      float ry, rz;
-      rhs32(P, inv6, lev, m, ry, rz);
-      const float id = m > 0 ? float(P.invd[m - 1 < kInvPivots ? m - 1 : kInvPivots - 1]) : 0.f;
-      py = ry - py * id;
-      pz = rz - pz * id;
-      if (m >= m0) {
-        gy[m] = py;
-        gz[m] = pz;
+    sr[0][m - base] = ry;
+    sr[1][m - base] = rz;
+  }
+  __syncthreads();
+
+  // forward sweep over the chunks of [a, rb): the tile and its right halo
+  for (int s0 = a + tid * C; s0 < rb; s0 += nt * C) {
+    const int e = s0 + C < rb ? s0 + C : rb;
+    const int st = s0 - W > 0 ? s0 - W : 0;
+    T gy = T(0), gz = T(0);
+    for (int m = st; m < e; ++m) {
+      const T id = m > 0 ? sid[m - 1 < kInvPivots ? m - 1 : kInvPivots - 1] : T(0);
+      gy = sr[0][m - base] - gy * id;
+      gz = sr[1][m - base] - gz * id;
+      if (m >= s0) {
+        sg[0][m - base] = gy;
+        sg[1][m - base] = gz;
       }
     }
   }
-}
+  __syncthreads();
 
-template <int PREC>
-__global__ void __launch_bounds__(128) k_spline_bwd(const Params P, Ring64 r64, Ring32 r32,
-                                                    const void *gscr, int slot) {
-  const int64_t u = P.Nx - 2;
-  const int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  const int64_t m0 = q * kSplineChunk;
-  const int64_t off = int64_t(slot) * P.Nx;
-  if (q == 0) {
+  // backward sweep over the chunks of the tile, warm-up from the right
+  for (int s0 = a + tid * C; s0 < b; s0 += nt * C) {
+    const int e = s0 + C < b ? s0 + C : b;
+    const int top = e + W < u ? e + W : u;
+    T my = T(0), mz = T(0);
+    for (int m = top - 1; m >= s0; --m) {
+      const T id = sid[m < kInvPivots ? m : kInvPivots - 1];
+      my = (sg[0][m - base] - my) * id;
+      mz = (sg[1][m - base] - mz) * id;
+      if (m < e) {
+        if constexpr (PREC == BSDE_FP64) {
+          r64.ring[off + m + 1].y = my;
+          r64.ring[off + m + 1].w = mz;
+        } else {
+          r32.B[off + m + 1] = make_float2(my, mz);
+        }
+      }
+    }
+  }
+  if (blockIdx.x == 0 && tid == 0) {
     // natural end conditions M_0 = M_{Nx-1} = 0
-    if (PREC == BSDE_FP64) {
+    if constexpr (PREC == BSDE_FP64) {
       r64.ring[off].y = 0.0;
       r64.ring[off].w = 0.0;
       r64.ring[off + P.Nx - 1].y = 0.0;
@@ -275,31 +300,6 @@ __global__ void __launch_bounds__(128) k_spline_bwd(const Params P, Ring64 r64, 
     } else {
       r32.B[off] = make_float2(0.f, 0.f);
       r32.B[off + P.Nx - 1] = make_float2(0.f, 0.f);
-    }
-  }
-  if (m0 >= u) return;
-  const int64_t m1 = m0 + kSplineChunk < u ? m0 + kSplineChunk : u;
-  const int64_t end = m1 + kSplineWarm < u ? m1 + kSplineWarm : u;
-  if (PREC == BSDE_FP64) {
-    const double *gy = static_cast<const double *>(gscr), *gz = gy + P.Nx;
-    double ny = 0.0, nz = 0.0;
-    for (int64_t m = end - 1; m >= m0; --m) {
-      const double id = P.invd[m < kInvPivots ? m : kInvPivots - 1];
-      ny = (gy[m] - ny) * id;
-      nz = (gz[m] - nz) * id;
-      if (m < m1) {
-        r64.ring[off + m + 1].y = ny;
-        r64.ring[off + m + 1].w = nz;
-      }
-    }
-  } else {
-    const float *gy = static_cast<const float *>(gscr), *gz = gy + P.Nx;
-    float ny = 0.f, nz = 0.f;
-    for (int64_t m = end - 1; m >= m0; --m) {
-      const float id = float(P.invd[m < kInvPivots ? m : kInvPivots - 1]);
-      ny = (gy[m] - ny) * id;
-      nz = (gz[m] - nz) * id;
-      if (m < m1) r32.B[off + m + 1] = make_float2(ny, nz);
     }
   }
 }
@@ -325,67 +325,102 @@ __device__ __forceinline__ void record_picard(Stats *st, bool active, int it, do
 }
 
 // ---------------------------------------------------------------------------
-// S3, FP64: one thread per grid point.  For j = 1..k and l = 1..L, the spline
-// values of y^{n+j}, z^{n+j} at the off-grid node (cell i + shift_jl, constant
-// per (j, l) on the uniform grid), the driver there, and the Gauss-Hermite
-// sums of Eq. 21; then z^n from the second line of Eq. 20 and y^n by Picard
-// on its first line.
+// S3: the step kernels.  A CTA owns kStepTP consecutive grid points and runs
+// G = k S groups of threads over them; group g takes j = g / S + 1 and the
+// l-chunk g % S of the Gauss-Hermite nodes (Eq. 21).  For every node a thread
+// forms the spline values of y^{n+j} and z^{n+j} at the off-grid point (cell
+// i + shift_jl, the same for every i on the uniform grid), evaluates the
+// driver there and accumulates the folded sums of Eq. 20 (see NodeF64).  The
+// groups' partial sums meet in shared memory; the first group then forms
+// z^n, runs the Picard iteration for y^n and writes the new level.
+// A warp covers 32 consecutive points of one group, so every node load is a
+// coalesced window.  CTAs whose points keep all their nodes of level n+j
+// inside [0, Nx-1] skip the boundary clamping (Section 3.2 first remark).
 // ---------------------------------------------------------------------------
+template <bool CLAMP, typename W4>
+__device__ __forceinline__ void node_cells(int ii, int shift, int last, int &c0, int &c1,
+                                           W4 &w0, W4 &w1, W4 &w2, W4 &w3) {
+  c0 = ii + shift;
+  c1 = c0 + 1;
+  if (CLAMP) {
+    const bool cl = c0 < 0, ch = c0 >= last;
+    if (cl | ch) {
+      c0 = cl ? 0 : last;
+      c1 = c0;
+      w0 = W4(1);
+      w1 = W4(0);
+      w2 = W4(0);
+      w3 = W4(0);
+    }
+  }
+}
+
+template <int DRV, bool CLAMP>
+__device__ __forceinline__ void nodes64(const DrvC<double> &dc, const double4_32a *__restrict__ lev,
+                                        const NodeF64 *row, int l0, int l1, int ii, int last,
+                                        double tj, double et, double emt, bool lastj, double &Zs,
+                                        double &Ys) {
+#pragma unroll 4
+  for (int l = l0; l < l1; ++l) {
+    const NodeF64 &e = row[l];
+    double w0 = e.w0, w1 = e.w1, w2 = e.w2, w3 = e.w3;
+    int c0, c1;
+    node_cells<CLAMP>(ii, e.shift, last, c0, c1, w0, w1, w2, w3);
+    const double4_32a a = lev[c0], b = lev[c1];
+    const double yh = w0 * a.x + w1 * b.x + w2 * a.y + w3 * b.y;
+    const double zh = w0 * a.z + w1 * b.z + w2 * a.w + w3 * b.w;
+    const double F = driver<DRV>(dc, tj, et, emt, yh, zh);
+    Zs += e.cz * zh + e.cfz * F;
+    Ys += e.cfy * F;
+    if (lastj) Ys += e.cy * yh;
+  }
+}
+
 template <int DRV>
-__global__ void __launch_bounds__(128) k_step64(const Params P, const DrvC<double> dc,
-                                                double4_32a *__restrict__ ring,
-                                                const NodeF64 *__restrict__ table, int n,
-                                                Stats *st) {
+__global__ void __launch_bounds__(kStepTP * kMaxGroups)
+    k_step64(const Params P, const DrvC<double> dc, double4_32a *__restrict__ ring,
+             const NodeF64 *__restrict__ table, int n, Stats *st) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  NodeF64 *tab = reinterpret_cast<NodeF64 *>(smem_raw);
   const int kL = P.k * P.L;
+  NodeF64 *tab = reinterpret_cast<NodeF64 *>(smem_raw);
+  double *part = reinterpret_cast<double *>(smem_raw + sizeof(NodeF64) * kL);  // [2][G][TP]
   for (int t = threadIdx.x; t < kL; t += blockDim.x) tab[t] = table[t];
   __syncthreads();
 
-  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  const bool active = i < P.Nx;
+  const int tp = threadIdx.x % kStepTP, g = threadIdx.x / kStepTP;
+  const int j = g / P.S + 1, lc = g % P.S;
+  const int l0 = lc * P.Lg, l1 = l0 + P.Lg < P.L ? l0 + P.Lg : P.L;
+  const int i0 = blockIdx.x * kStepTP, ii = i0 + tp;
+  const int last = int(P.Nx - 1);
+  double Zs = 0.0, Ys = 0.0;
+  if (ii <= last) {
+    const double4_32a *lev = ring + int64_t((n + j) % P.nslot) * P.Nx;
+    const double tj = (n + j) * P.dt;
+    const double et = exp(tj * tj), emt = exp(-tj * tj);
+    const NodeF64 *row = tab + (j - 1) * P.L;
+    const bool interior = i0 + P.smin[j - 1] >= 0 && i0 + kStepTP + P.smax[j - 1] <= last;
+    if (interior)
+      nodes64<DRV, false>(dc, lev, row, l0, l1, ii, last, tj, et, emt, j == P.k, Zs, Ys);
+    else
+      nodes64<DRV, true>(dc, lev, row, l0, l1, ii, last, tj, et, emt, j == P.k, Zs, Ys);
+  }
+  part[(0 * P.G + g) * kStepTP + tp] = Zs;
+  part[(1 * P.G + g) * kStepTP + tp] = Ys;
+  __syncthreads();
+  if (g != 0) return;
+
+  const bool active = ii <= last;
   int it = 0;
   double d = 0.0;
   if (active) {
-    const int64_t last = P.Nx - 1;
-    double e1z = 0.0, ekY = 0.0, sfw = 0.0, sz = 0.0, sf = 0.0;
-    for (int j = 1; j <= P.k; ++j) {
-      const double4_32a *lev = ring + int64_t((n + j) % P.nslot) * P.Nx;
-      const double tj = (n + j) * P.dt;
-      const double et = exp(tj * tj), emt = exp(-tj * tj);
-      double ez = 0.0, ef = 0.0, efw = 0.0, ey = 0.0;
-      const NodeF64 *row = tab + (j - 1) * P.L;
-      for (int l = 0; l < P.L; ++l) {
-        const NodeF64 e = row[l];
-        int64_t c0 = i + e.shift, c1 = c0 + 1;
-        double w0 = e.w0, w1 = e.w1, w2 = e.w2, w3 = e.w3;
-        if (c0 < 0) {
-          c0 = c1 = 0;
-          w0 = 1.0; w1 = 0.0; w2 = 0.0; w3 = 0.0;
-        } else if (c0 >= last) {
-          c0 = c1 = last;
-          w0 = 1.0; w1 = 0.0; w2 = 0.0; w3 = 0.0;
-        }
-        const double4_32a a = lev[c0], b = lev[c1];
-        const double yh = w0 * a.x + w1 * b.x + w2 * a.y + w3 * b.y;
-        const double zh = w0 * a.z + w1 * b.z + w2 * a.w + w3 * b.w;
-        const double F = driver<DRV>(dc, tj, et, emt, yh, zh);
-        ez += e.wt * zh;
-        ef += e.wt * F;
-        efw += e.wdw * F;
-        ey += e.wt * yh;
-      }
-      sfw += P.gz[j] * efw;
-      sz += P.gz[j] * ez;
-      sf += P.gy[j] * ef;
-      if (j == 1) e1z = ez;
-      if (j == P.k) ekY = ey;
+    double z = 0.0, A = 0.0;
+    for (int q = 0; q < P.G; ++q) {
+      z += part[(0 * P.G + q) * kStepTP + tp];
+      A += part[(1 * P.G + q) * kStepTP + tp];
     }
-    const double z = (e1z + sfw - sz) * P.inv_gz0;
-    const double A = ekY + P.h * sf;
     const double tn = n * P.dt;
     const double etn = exp(tn * tn), emtn = exp(-tn * tn);
-    double y = ring[int64_t((n + 1) % P.nslot) * P.Nx + i].x;
+    double y = ring[int64_t((n + 1) % P.nslot) * P.Nx + ii].x;
     while (it < P.picard_max) {
       const double y1 = A + P.hg0 * driver<DRV>(dc, tn, etn, emtn, y, z);
       d = fabs(y1 - y);
@@ -393,20 +428,22 @@ __global__ void __launch_bounds__(128) k_step64(const Params P, const DrvC<doubl
       ++it;
       if (d <= P.picard_tol) break;
     }
-    ring[int64_t(n % P.nslot) * P.Nx + i] = make_double4_32a(y, 0.0, z, 0.0);
+    ring[int64_t(n % P.nslot) * P.Nx + ii] = make_double4_32a(y, 0.0, z, 0.0);
   }
   record_picard(st, active, it, d, P.picard_tol);
 }
 
 // ---------------------------------------------------------------------------
-// S3, FP32C: same scheme, bulk in FP32.  The spline value at a node is kept as
-// the unevaluated sum hi_c + del, del = theta (hi_{c+1} - hi_c) + (spline
-// corrections and lo parts) computed in FP32 (its magnitude is ~dx |y'|, so
-// its rounding is far below that of y).  The y and z expectations are summed
-// with error-free products (FMA) and TwoSum into (S, C) pairs; the driver
-// terms, already scaled by dt, are summed in plain FP32.  z, the Picard
-// iteration and its convergence test are in FP64.
+// FP32C: the spline value at a node is kept as the unevaluated sum hi_c + del,
+// del = theta (hi_{c+1} - hi_c) + (lo and spline-curvature parts), computed in
+// FP32 (|del| ~ dx |y'|, so its rounding is far below that of y).  The z and
+// y sums take the exact product of the coefficient's hi part with hi_c (FMA)
+// and add it by TwoSum into an (S, C) pair; the driver terms, which carry a
+// dt-sized or sqrt(dt)-sized weight, are summed in plain FP32.  The final
+// combination of z^n and A, the Picard iteration and its test run in FP64.
 // ---------------------------------------------------------------------------
+// S += ch*hi exactly (error-free product by FMA, TwoSum), C += the rounding
+// errors plus the small terms ch*del + cl*hi.
 __device__ __forceinline__ void comp_acc(float &S, float &C, float ch, float cl, float hi,
                                          float del) {
   const float p = __fmul_rn(ch, hi);
@@ -415,80 +452,173 @@ __device__ __forceinline__ void comp_acc(float &S, float &C, float ch, float cl,
   const float bp = __fsub_rn(s, S);
   const float err = __fadd_rn(__fsub_rn(S, __fsub_rn(s, bp)), __fsub_rn(p, bp));
   S = s;
-  C = __fadd_rn(C, __fadd_rn(__fadd_rn(err, e), __fmaf_rn(cl, hi, __fmul_rn(ch, del))));
+  C = __fadd_rn(C, __fadd_rn(err, __fmaf_rn(ch, del, __fmaf_rn(cl, hi, e))));
+}
+
+__device__ __forceinline__ void two_sum_into(float &S, float &C, float x) {
+  const float s = __fadd_rn(S, x);
+  const float bp = __fsub_rn(s, S);
+  C = __fadd_rn(C, __fadd_rn(__fsub_rn(S, __fsub_rn(s, bp)), __fsub_rn(x, bp)));
+  S = s;
+}
+
+// One group's nodes.  Table entry as three float4: (shift, w0, w1, w2),
+// (w3, czh, czl, cfz), (cfy, cyh, cyl, -).  With theta = w1 the spline value
+// is hi_c + del, del = theta (dhi + dlo) + lo_c + w2 M_c + w3 M_{c+1}; where
+// y only feeds the FP32 driver (j < k) its lo part is left out.
+template <int DRV, bool CLAMP, bool LASTJ>
+__device__ __forceinline__ void nodes32(const DrvC<float> &dc, const float4 *__restrict__ A,
+                                        const float2 *__restrict__ B, const NodeF32 *row, int l0,
+                                        int l1, int ii, int last, float tj, float et, float emt,
+                                        float &Sz, float &Cz, float &Fz, float &Fy, float &Sy,
+                                        float &Cy) {
+#pragma unroll 4
+  for (int l = l0; l < l1; ++l) {
+    const float4 *te = reinterpret_cast<const float4 *>(row + l);
+    const float4 e0 = te[0], e1 = te[1], e2 = te[2];
+    float w1 = e0.z, w2 = e0.w, w3 = e1.x;
+    int c0 = ii + __float_as_int(e0.x), c1 = c0 + 1;
+    if (CLAMP) {
+      const bool cl = c0 < 0, ch = c0 >= last;
+      if (cl | ch) {
+        c0 = cl ? 0 : last;
+        c1 = c0;
+        w1 = 0.f;
+        w2 = 0.f;
+        w3 = 0.f;
+      }
+    }
+    const float4 a = A[c0], b = A[c1];
+    const float2 ma = B[c0], mb = B[c1];
+    const float mz = __fmaf_rn(w2, ma.y, w3 * mb.y);
+    const float zdel = __fadd_rn(
+        __fmaf_rn(w1, __fadd_rn(__fsub_rn(b.z, a.z), __fsub_rn(b.w, a.w)), a.w), mz);
+    const float my = __fmaf_rn(w2, ma.x, w3 * mb.x);
+    float yf, ydel = 0.f;
+    if (LASTJ) {
+      ydel = __fadd_rn(__fmaf_rn(w1, __fadd_rn(__fsub_rn(b.x, a.x), __fsub_rn(b.y, a.y)), a.y), my);
+      yf = a.x + ydel;
+    } else {
+      yf = a.x + __fmaf_rn(w1, __fsub_rn(b.x, a.x), my);
+    }
+    const float zf = a.z + zdel;
+    const float F = driver<DRV>(dc, tj, et, emt, yf, zf);
+    Fz = __fmaf_rn(e1.w, F, Fz);
+    Fy = __fmaf_rn(e2.x, F, Fy);
+    comp_acc(Sz, Cz, e1.y, e1.z, a.z, zdel);
+    if (LASTJ) comp_acc(Sy, Cy, e2.y, e2.z, a.x, ydel);
+  }
+}
+
+template <int DRV, bool LASTJ>
+__device__ __forceinline__ void nodes32_any(bool interior, const DrvC<float> &dc,
+                                            const float4 *__restrict__ A,
+                                            const float2 *__restrict__ B, const NodeF32 *row,
+                                            int l0, int l1, int ii, int last, float tj, float et,
+                                            float emt, float &Sz, float &Cz, float &Fz, float &Fy,
+                                            float &Sy, float &Cy) {
+  if (interior)
+    nodes32<DRV, false, LASTJ>(dc, A, B, row, l0, l1, ii, last, tj, et, emt, Sz, Cz, Fz, Fy, Sy, Cy);
+  else
+    nodes32<DRV, true, LASTJ>(dc, A, B, row, l0, l1, ii, last, tj, et, emt, Sz, Cz, Fz, Fy, Sy, Cy);
 }
 
 template <int DRV>
-__global__ void __launch_bounds__(128) k_step32(const Params P, const DrvC<float> dc,
-                                                const DrvC<double> dc64,
-                                                float4 *__restrict__ ringA,
-                                                const float2 *__restrict__ ringB,
-                                                const NodeF32 *__restrict__ table, int n,
-                                                Stats *st) {
+__global__ void __launch_bounds__(kStepTP * kMaxGroups)
+    k_step32(const Params P, const DrvC<float> dc, float4 *__restrict__ ringA,
+             const float2 *__restrict__ ringB, const NodeF32 *__restrict__ table, int n,
+             Stats *st) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  NodeF32 *tab = reinterpret_cast<NodeF32 *>(smem_raw);
   const int kL = P.k * P.L;
-  for (int t = threadIdx.x; t < kL; t += blockDim.x) tab[t] = table[t];
+  NodeF32 *tab = reinterpret_cast<NodeF32 *>(smem_raw);
+  float *part = reinterpret_cast<float *>(smem_raw + sizeof(NodeF32) * kL);  // [6][G][TP]
+  {
+    const float4 *src = reinterpret_cast<const float4 *>(table);
+    float4 *dst = reinterpret_cast<float4 *>(tab);
+    for (int t = threadIdx.x; t < kL * 3; t += blockDim.x) dst[t] = src[t];
+  }
   __syncthreads();
 
-  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  const bool active = i < P.Nx;
+  const int tp = threadIdx.x % kStepTP, g = threadIdx.x / kStepTP;
+  const int j = g / P.S + 1, lc = g % P.S;
+  const int l0 = lc * P.Lg, l1 = l0 + P.Lg < P.L ? l0 + P.Lg : P.L;
+  const int i0 = blockIdx.x * kStepTP, ii = i0 + tp;
+  const int last = int(P.Nx - 1);
+  float Sz = 0.f, Cz = 0.f, Fz = 0.f, Fy = 0.f, Sy = 0.f, Cy = 0.f;
+  if (ii <= last) {
+    const int64_t off = int64_t((n + j) % P.nslot) * P.Nx;
+    const double tjd = (n + j) * P.dt;
+    const float tj = float(tjd);
+    float et = 0.f, emt = 0.f;
+    if constexpr (DRV == BSDE_DRIVER_EX2) {
+      et = float(exp(tjd * tjd));
+      emt = float(exp(-tjd * tjd));
+    }
+    const NodeF32 *row = tab + (j - 1) * P.L;
+    const bool interior = i0 + P.smin[j - 1] >= 0 && i0 + kStepTP + P.smax[j - 1] <= last;
+    if (j == P.k)
+      nodes32_any<DRV, true>(interior, dc, ringA + off, ringB + off, row, l0, l1, ii, last, tj,
+                             et, emt, Sz, Cz, Fz, Fy, Sy, Cy);
+    else
+      nodes32_any<DRV, false>(interior, dc, ringA + off, ringB + off, row, l0, l1, ii, last, tj,
+                              et, emt, Sz, Cz, Fz, Fy, Sy, Cy);
+  }
+  const int G = P.G;
+  part[(0 * G + g) * kStepTP + tp] = Sz;
+  part[(1 * G + g) * kStepTP + tp] = Cz;
+  part[(2 * G + g) * kStepTP + tp] = Fz;
+  part[(3 * G + g) * kStepTP + tp] = Fy;
+  part[(4 * G + g) * kStepTP + tp] = Sy;
+  part[(5 * G + g) * kStepTP + tp] = Cy;
+  __syncthreads();
+  if (g != 0) return;
+
+  const bool active = ii <= last;
   int it = 0;
   double d = 0.0;
   if (active) {
-    const int64_t last = P.Nx - 1;
-    float Sz = 0.f, Cz = 0.f, Sy = 0.f, Cy = 0.f, Fz = 0.f, Fy = 0.f;
-    for (int j = 1; j <= P.k; ++j) {
-      const int64_t off = int64_t((n + j) % P.nslot) * P.Nx;
-      const float4 *A = ringA + off;
-      const float2 *B = ringB + off;
-      const double tjd = (n + j) * P.dt;
-      const float tj = float(tjd);
-      const float et = float(exp(tjd * tjd)), emt = float(exp(-tjd * tjd));
-      const NodeF32 *row = tab + (j - 1) * P.L;
-      const bool lastj = (j == P.k);
-      for (int l = 0; l < P.L; ++l) {
-        const NodeF32 e = row[l];
-        int64_t c0 = i + e.shift, c1 = c0 + 1;
-        float w0 = e.w0, w1 = e.w1, w2 = e.w2, w3 = e.w3;
-        if (c0 < 0) {
-          c0 = c1 = 0;
-          w0 = 1.f; w1 = 0.f; w2 = 0.f; w3 = 0.f;
-        } else if (c0 >= last) {
-          c0 = c1 = last;
-          w0 = 1.f; w1 = 0.f; w2 = 0.f; w3 = 0.f;
-        }
-        const float4 a = A[c0], b = A[c1];
-        const float2 ma = B[c0], mb = B[c1];
-        const float ydel = __fadd_rn(__fmaf_rn(w1, __fsub_rn(b.x, a.x), __fmaf_rn(w0, a.y, w1 * b.y)),
-                                     __fmaf_rn(w2, ma.x, w3 * mb.x));
-        const float zdel = __fadd_rn(__fmaf_rn(w1, __fsub_rn(b.z, a.z), __fmaf_rn(w0, a.w, w1 * b.w)),
-                                     __fmaf_rn(w2, ma.y, w3 * mb.y));
-        const float yf = a.x + ydel, zf = a.z + zdel;
-        const float F = driver<DRV>(dc, tj, et, emt, yf, zf);
-        Fz = __fmaf_rn(e.cfz, F, Fz);
-        Fy = __fmaf_rn(e.cfy, F, Fy);
-        comp_acc(Sz, Cz, e.czh, e.czl, a.z, zdel);
-        if (lastj) comp_acc(Sy, Cy, e.cyh, e.cyl, a.x, ydel);
-      }
+    float zS = 0.f, zC = 0.f, yS = 0.f, yC = 0.f, fz = 0.f, fy = 0.f;
+    for (int q = 0; q < G; ++q) {
+      two_sum_into(zS, zC, part[(0 * G + q) * kStepTP + tp]);
+      zC = __fadd_rn(zC, part[(1 * G + q) * kStepTP + tp]);
+      fz = __fadd_rn(fz, part[(2 * G + q) * kStepTP + tp]);
+      fy = __fadd_rn(fy, part[(3 * G + q) * kStepTP + tp]);
+      two_sum_into(yS, yC, part[(4 * G + q) * kStepTP + tp]);
+      yC = __fadd_rn(yC, part[(5 * G + q) * kStepTP + tp]);
     }
-    const double z = (double(Sz) + double(Cz)) + double(Fz);
-    const double Ay = (double(Sy) + double(Cy)) + double(Fy);
+    // combination of z^n and of the explicit part A of y^n in FP64
+    const double z = double(zS) + (double(zC) + double(fz));
+    const double Ay = double(yS) + (double(yC) + double(fy));
     const double tnd = n * P.dt;
     const float tn = float(tnd);
-    const float etn = float(exp(tnd * tnd)), emtn = float(exp(-tnd * tnd));
+    float etn = 0.f, emtn = 0.f;
+    if constexpr (DRV == BSDE_DRIVER_EX2) {
+      etn = float(exp(tnd * tnd));
+      emtn = float(exp(-tnd * tnd));
+    }
     const float zf = __double2float_rn(z);
-    const float4 prev = ringA[int64_t((n + 1) % P.nslot) * P.Nx + i];
-    double y = double(prev.x) + double(prev.y);
+    const float Ayf = __double2float_rn(Ay);
+    const float hg0 = float(P.hg0);
+    // Picard on the increment delta = y^n - A = k dt gy_0 f(t_n, A + delta, z^n).
+    // The driver sees y in FP32, so the iteration runs in FP32; the test
+    // |delta^(p+1) - delta^(p)| <= tol is exact (near convergence the two
+    // increments are within a factor two, so their float difference carries
+    // no rounding).  A two-cycle across a rounding boundary of the FP32
+    // argument is as far as the FP32 driver can resolve, and ends it too.
+    const float4 prev = ringA[int64_t((n + 1) % P.nslot) * P.Nx + ii];
+    float dl = __fsub_rn(prev.x, Ayf), dpp = __int_as_float(0x7fc00000);
     while (it < P.picard_max) {
-      const float fv = driver<DRV>(dc, tn, etn, emtn, __double2float_rn(y), zf);
-      const double y1 = Ay + P.hg0 * double(fv);
-      d = fabs(y1 - y);
-      y = y1;
+      const float dn = hg0 * driver<DRV>(dc, tn, etn, emtn, Ayf + dl, zf);
       ++it;
+      d = double(fabsf(__fsub_rn(dn, dl)));
+      const bool cyc = dn == dpp;
+      dpp = dl;
+      dl = dn;
+      if (cyc) d = 0.0;
       if (d <= P.picard_tol) break;
     }
-    split_store(ringA + int64_t(n % P.nslot) * P.Nx, i, y, z);
+    const double y = Ay + double(dl);
+    split_store(ringA + int64_t(n % P.nslot) * P.Nx, ii, y, z);
   }
   record_picard(st, active, it, d, P.picard_tol);
 }
