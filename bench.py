@@ -350,6 +350,178 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def run_batch(args, rank, world, local_rank):
+    """config4: 4096 Black-Scholes problems of uneven Nx, N, k, one persistent
+    launch per step (FP32C)."""
+    import torch
+    from paper_1909_13560_gb300 import bsde as B
+    from paper_1909_13560_gb300 import workloads as W
+
+    dist = _dist_init(world)
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    probs = W.config4()
+    units_per_step = sum(W.gp_steps(p) for p in probs)
+    flops_per_step = sum(flops_per_gp_step(p["k"], p["L"]) * W.gp_steps(p) for p in probs)
+    t0 = time.perf_counter()
+    bs = B.BatchSolver(probs, device=dev)
+    plan_s = time.perf_counter() - t0
+    cfg = bs.autotune() if args.autotune else (bs.set_config(1, 4) or bs.config())
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        flush.zero_()
+        bs.solve(want_results=False)
+    torch.cuda.synchronize(dev)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        if not uuid.startswith("GPU-"):
+            uuid = "GPU-" + uuid
+    except Exception:
+        uuid = None
+    _barrier(dist)
+    torch.cuda.synchronize(dev)
+    with ClockSampler(uuid) as clk:
+        for i in range(args.steps):
+            flush.zero_()
+            starts[i].record(stream)
+            bs.solve(want_results=False)
+            ends[i].record(stream)
+        torch.cuda.synchronize(dev)
+    _barrier(dist)
+    ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+    ms_max = _max_over_ranks(dist, ms)
+    value = world * units_per_step * args.steps / (ms_max / 1000.0)
+    res = bs.solve()
+    exact = []
+    from scipy.special import ndtr
+    for p in probs:
+        sq = p["sigma"] * math.sqrt(p["T"])
+        d1 = (math.log(100.0 / p["strike"]) + (p["r"] + 0.5 * p["sigma"] ** 2) * p["T"]) / sq
+        exact.append(100.0 * ndtr(d1) - p["strike"] * math.exp(-p["r"] * p["T"]) * ndtr(d1 - sq))
+    errs = sorted(abs(r["y0"] - e) for r, e in zip(res, exact))
+    # end to end: plan the batch from host problem descriptions (tables and
+    # descriptors copied in), solve, read every result back
+    e_t0 = time.perf_counter()
+    for _ in range(args.steps):
+        bs.close()
+        bs = B.BatchSolver(probs, device=dev)
+        bs.set_config(cfg["cluster"], cfg["target_groups"])
+        bs.solve()
+    torch.cuda.synchronize(dev)
+    e_dt = _max_over_ranks(dist, time.perf_counter() - e_t0)
+    h2d = sum(1024 + 64 * p["k"] * ((p["L"] + 1) // 2) for p in probs) + 4 * len(probs)
+    d2h = 32 * len(probs)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import oracle as O
+        threads = os.cpu_count() or 1
+        c0 = time.perf_counter()
+        cu = 0
+        for p in probs[:: max(1, len(probs) // 24)]:
+            r = O.solve(p, threads=threads)
+            cu += W.gp_steps(p)
+        cdt = time.perf_counter() - c0
+        cpu = {"value": cu / cdt, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"every {max(1, len(probs) // 24)}th problem of config4 "
+                         f"({cu} grid-point steps, {cdt:.1f} s)"}
+    if rank == 0:
+        peaks = _peaks()
+        sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+        peak = _alu_peak_tflops("fp32c", sm_max)
+        achieved = flops_per_step / (ms_max / args.steps / 1000.0) / 1e12
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "config4: 4096 Black-Scholes calls, seed 13560, K~U[70,130], "
+                                   "sigma~U[.1,.5], T~U[.25,2], r~U[0,.05], Nx in 2^10..2^14, "
+                                   "N in 32..256, k~U{1..6}, L=16; one persistent launch",
+                       "instances": len(probs), "batch_config": cfg, "plan_s": plan_s,
+                       "l2": "flushed between steps (256 MiB write)",
+                       "parallelism": f"{world} independent replica(s)"},
+            "accuracy": {"gate": "|y0 - Black-Scholes closed form| over the batch",
+                         "median": errs[len(errs) // 2], "p90": errs[int(0.9 * len(errs))],
+                         "max": errs[-1]},
+            "roofline": {"kernel": "k_batch32", "bound": "alu", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz"},
+            "e2e": {"value": world * units_per_step * args.steps / e_dt, "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": 2 * args.steps,
+            "clocks": clk.summary(),
+        }
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    bs.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_serving(args, rank, world, local_rank):
+    """config5: Poisson arrivals of pricing requests served by the persistent
+    continuous-batching kernel; one step = the whole arrival sequence."""
+    import torch
+    from paper_1909_13560_gb300 import bsde as B
+    from paper_1909_13560_gb300 import serve
+    from paper_1909_13560_gb300 import workloads as W
+
+    dist = _dist_init(world)
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    arrivals = W.config5_arrivals(rate=args.rate, duration=args.duration)
+    units = sum(W.gp_steps(p) for _, p in arrivals)
+    srv = B.Server(slots=1024, pool_bytes=8 << 30, device=dev)
+    srv.start(cluster=1, idle_ms=60000)
+    try:
+        # warm-up: a short burst through the same server
+        serve.serve(srv, [(0.0, p) for _, p in arrivals[:64]])
+        uuid = None
+        try:
+            uuid = str(torch.cuda.get_device_properties(dev).uuid)
+            if not uuid.startswith("GPU-"):
+                uuid = "GPU-" + uuid
+        except Exception:
+            uuid = None
+        _barrier(dist)
+        with ClockSampler(uuid) as clk:
+            records, summary = serve.serve(srv, arrivals)
+        _barrier(dist)
+    finally:
+        srv.stop()
+        srv.close()
+    t = _max_over_ranks(dist, summary["duration_s"])
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": world * summary["requests"] / t, "unit": "solves/s",
+            "n_gpus": world, "steps": 1, "warmup": 1, "ms_per_step": 1000.0 * t,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"config5: Poisson arrivals at {args.rate:g}/s for "
+                                   f"{args.duration:g} s (seed 1909), 70% Black-Scholes "
+                                   "(Nx=2^12, N=64, k=3), 30% lending/borrowing calls "
+                                   "(Nx=2^16, N=256, k=4), L=16; admission by device memory "
+                                   "(8 GiB pool, 1024 slots); persistent continuous-batching kernel",
+                       "requests": summary["requests"]},
+            "serving": {"p50_ms": summary["p50_ms"], "p99_ms": summary["p99_ms"],
+                        "max_inflight": summary["max_inflight"],
+                        "admit_wait_p99_ms": summary["admit_wait_p99_ms"],
+                        "grid_point_steps_per_s": world * units / t},
+            "e2e": {"value": world * summary["requests"] / t, "unit": "solves/s",
+                    "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 40 * summary["requests"]},
+            "gpu_launches": 1,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -357,9 +529,17 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp32c", "fp64"], default="fp32c")
+    ap.add_argument("--workload", choices=["config2", "config4", "config5"], default="config2",
+                    help="config2: the Black-Scholes solves k = 1..6 (default); "
+                         "config4: the 4096-instance batch in one persistent launch; "
+                         "config5: the serving run (Poisson arrivals, continuous batching)")
+    ap.add_argument("--duration", type=float, default=10.0, help="config5: seconds of arrivals")
+    ap.add_argument("--rate", type=float, default=2000.0, help="config5: arrivals per second")
     ap.add_argument("--cpu-levels", type=int, default=64)
     ap.add_argument("--ref-levels", type=int, default=12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--autotune", action="store_true",
+                    help="config4: pick the batch configuration by timing (else cluster 1, 4 groups)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -368,6 +548,10 @@ def main():
     local_rank = _env_int("LOCAL_RANK", 0)
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "config4":
+        run_batch(args, rank, world, local_rank)
+    elif args.workload == "config5":
+        run_serving(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

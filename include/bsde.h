@@ -83,6 +83,7 @@ enum {
 enum {
   BSDE_OK = 0,
   BSDE_WARN_NOCONV = 1, /* Picard stopped at picard_max somewhere; results written */
+  BSDE_BUSY = 2,        /* server: no free slot or pool memory now; try again later */
   BSDE_EINVAL = -1,     /* bad problem: k outside 1..min(6, N), Nx < 4, L outside
                            1..64, x0 outside [x_min, x_max], unknown id, T <= 0    */
   BSDE_ENOSPC = -2,     /* workspace smaller than bsde_workspace_bytes()          */
@@ -177,6 +178,90 @@ BSDE_API const char *bsde_last_error(void);
  * and the gamma tables (Table 1 into gy[0..k], Table 2 into gz[0..k]). */
 BSDE_API int bsde_gauss_hermite(int L, double *nodes, double *weights);
 BSDE_API int bsde_gamma(int k, double *gy, double *gz);
+
+/* ---- batched solves ------------------------------------------------------
+ * Many independent problems (uneven Nx, N, k, driver, parameters; all
+ * precision BSDE_FP32C, closed-form start) solved by one persistent launch:
+ * a cluster of CTAs takes the next problem from a device queue (largest work
+ * first) and shares its levels; the launch and its queue reset are one CUDA
+ * graph.  Results are those of one bsde_solve per problem (same kernels per
+ * tile, same order of operations), whatever the composition of the batch. */
+typedef struct bsde_batch_s bsde_batch_t;
+
+typedef struct bsde_batch_config {
+  int32_t cluster;       /* CTAs that share one problem: 1, 2, 4 or 8            */
+  int32_t target_groups; /* thread groups per grid point in the step tiles, 1..6 */
+  int32_t reserved[6];
+} bsde_batch_config;
+
+/* Workspace for the n problems ps[0..n-1] (rings, tables, descriptors,
+ * queue, per-problem statistics).  BSDE_EINVAL if any problem is invalid or
+ * not BSDE_FP32C. */
+BSDE_API int bsde_batch_workspace_bytes(int n, const bsde_problem *ps, size_t *bytes);
+
+/* Plan the batch on dev_workspace (caller-owned, >= bsde_batch_workspace_bytes,
+ * 256-byte aligned): host constants per problem, descriptors and tables copied
+ * to the device.  The default configuration is cluster 2, 4 target groups. */
+BSDE_API int bsde_plan_batch(int n, const bsde_problem *ps, void *dev_workspace,
+                             size_t bytes, bsde_batch_t **out);
+
+BSDE_API int bsde_batch_set_config(bsde_batch_t *b, const bsde_batch_config *cfg);
+BSDE_API int bsde_batch_get_config(const bsde_batch_t *b, bsde_batch_config *cfg);
+
+/* Time every candidate configuration (cluster in {1, 2, 4, 8} x target
+ * groups in {2, 4, 6}) on this batch with CUDA events on `stream`, keep the
+ * fastest and return it in *best (may be NULL).  Solves the batch 2 x 12
+ * times; waits for the stream. */
+BSDE_API int bsde_batch_autotune(bsde_batch_t *b, void *stream, bsde_batch_config *best);
+
+/* Solve all problems; results (NULL or n host structs, in the order of ps)
+ * receive y0, z0 and the Picard statistics of each.  Waits for the stream
+ * when results is non-NULL. */
+BSDE_API int bsde_solve_batch(bsde_batch_t *b, void *stream, bsde_result *results);
+
+BSDE_API void bsde_batch_free(bsde_batch_t *b);
+
+/* ---- continuous-batching server ---------------------------------------------
+ * A persistent kernel solves pricing requests as they are submitted: each
+ * request is admitted when a slot and enough of the device pool for its
+ * level ring are free (admission by footprint), runs on the next free
+ * cluster while others are in flight, and frees its slot and memory when
+ * polled.  Problems must be BSDE_FP32C with the closed-form start.  A request
+ * gives the same result alone and in any mix (same kernels per tile, same
+ * order of operations).  The server's waits for new requests are bounded: a
+ * cluster that finds no request for idle_ms milliseconds leaves and the
+ * server reports BSDE_ETIMEOUT at bsde_server_stop. */
+typedef struct bsde_server_s bsde_server_t;
+
+/* Device bytes a request for *p occupies in the pool (its level ring). */
+BSDE_API int bsde_request_bytes(const bsde_problem *p, size_t *bytes);
+
+/* Workspace for a server with `slots` request slots and a pool of
+ * pool_bytes for level rings. */
+BSDE_API int bsde_server_workspace_bytes(int slots, size_t pool_bytes, size_t *bytes);
+
+/* Bind a server to dev_workspace (caller-owned device memory); allocates its
+ * host-mapped control block and slots (pinned). */
+BSDE_API int bsde_server_create(void *dev_workspace, size_t bytes, int slots,
+                                size_t pool_bytes, bsde_server_t **out);
+
+/* Launch the persistent kernel on `stream` (clusters of `cluster` CTAs, as
+ * many as fit on the GPU at once). */
+BSDE_API int bsde_server_start(bsde_server_t *s, void *stream, int cluster, int idle_ms);
+
+/* Admit a request: BSDE_OK with *slot set, BSDE_BUSY when no slot or pool
+ * memory is free now, BSDE_EINVAL for a bad problem.  Non-blocking. */
+BSDE_API int bsde_server_submit(bsde_server_t *s, const bsde_problem *p, int *slot);
+
+/* Collect up to max finished requests: their slots and results; frees their
+ * slots and pool memory.  Returns the number collected (>= 0) or an error. */
+BSDE_API int bsde_server_poll(bsde_server_t *s, int max, int *slots, bsde_result *results);
+
+/* Ask the kernel to finish (requests already published are still solved)
+ * and wait for it.  BSDE_ETIMEOUT if a cluster gave up waiting. */
+BSDE_API int bsde_server_stop(bsde_server_t *s);
+
+BSDE_API void bsde_server_free(bsde_server_t *s);
 
 /* Solve without allocating anything (no counterpart in the paper; this is a
  * service for callers of this library).

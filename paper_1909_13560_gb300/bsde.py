@@ -22,6 +22,7 @@ BSDE_PRECISION = {"fp64": 0, "fp32c": 1}
 
 BSDE_OK = 0
 BSDE_WARN_NOCONV = 1
+BSDE_BUSY = 2
 BSDE_EINVAL = -1
 BSDE_ENOSPC = -2
 BSDE_ECUDA = -3
@@ -46,6 +47,11 @@ class bsde_problem(ctypes.Structure):
     ]
 
 
+class bsde_batch_config(ctypes.Structure):
+    _fields_ = [("cluster", ctypes.c_int32), ("target_groups", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
+
+
 class bsde_result(ctypes.Structure):
     _fields_ = [
         ("y0", ctypes.c_double), ("z0", ctypes.c_double),
@@ -58,7 +64,12 @@ class bsde_result(ctypes.Structure):
 _lib = None
 _SYMBOLS = ("bsde_workspace_bytes", "bsde_plan", "bsde_solve", "bsde_result_fetch",
             "bsde_enqueue_level", "bsde_free", "bsde_plan_launches", "bsde_strerror",
-            "bsde_last_error", "bsde_gauss_hermite", "bsde_gamma", "bsde_solve_noalloc")
+            "bsde_last_error", "bsde_gauss_hermite", "bsde_gamma", "bsde_solve_noalloc",
+            "bsde_batch_workspace_bytes", "bsde_plan_batch", "bsde_batch_set_config",
+            "bsde_batch_get_config", "bsde_batch_autotune", "bsde_solve_batch", "bsde_batch_free",
+            "bsde_request_bytes", "bsde_server_workspace_bytes", "bsde_server_create",
+            "bsde_server_start", "bsde_server_submit", "bsde_server_poll", "bsde_server_stop",
+            "bsde_server_free")
 
 
 def load(path: str = LIB_PATH):
@@ -91,6 +102,23 @@ def load(path: str = LIB_PATH):
     lib.bsde_gamma.argtypes = [ctypes.c_int, P(d), P(d)]
     lib.bsde_solve_noalloc.argtypes = [P(bsde_problem), vp, vp, vp, ctypes.c_int, vp, vp,
                                        ctypes.c_int, P(bsde_result)]
+    lib.bsde_batch_workspace_bytes.argtypes = [ctypes.c_int, P(bsde_problem), P(ctypes.c_size_t)]
+    lib.bsde_plan_batch.argtypes = [ctypes.c_int, P(bsde_problem), vp, ctypes.c_size_t, P(vp)]
+    lib.bsde_batch_set_config.argtypes = [vp, P(bsde_batch_config)]
+    lib.bsde_batch_get_config.argtypes = [vp, P(bsde_batch_config)]
+    lib.bsde_batch_autotune.argtypes = [vp, vp, P(bsde_batch_config)]
+    lib.bsde_solve_batch.argtypes = [vp, vp, P(bsde_result)]
+    lib.bsde_batch_free.argtypes = [vp]
+    lib.bsde_batch_free.restype = None
+    lib.bsde_request_bytes.argtypes = [P(bsde_problem), P(ctypes.c_size_t)]
+    lib.bsde_server_workspace_bytes.argtypes = [ctypes.c_int, ctypes.c_size_t, P(ctypes.c_size_t)]
+    lib.bsde_server_create.argtypes = [vp, ctypes.c_size_t, ctypes.c_int, ctypes.c_size_t, P(vp)]
+    lib.bsde_server_start.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int]
+    lib.bsde_server_submit.argtypes = [vp, P(bsde_problem), P(ctypes.c_int)]
+    lib.bsde_server_poll.argtypes = [vp, ctypes.c_int, P(ctypes.c_int), P(bsde_result)]
+    lib.bsde_server_stop.argtypes = [vp]
+    lib.bsde_server_free.argtypes = [vp]
+    lib.bsde_server_free.restype = None
     _lib = lib
     return lib
 
@@ -297,3 +325,158 @@ def solve(problem: dict, precision: str = "fp64", init=None, want_level: bool = 
         return s.solve(init=init, want_level=want_level)
     finally:
         s.close()
+
+
+# --- batched solves ---------------------------------------------------------
+
+def _problem_array(problems, precision):
+    arr = (bsde_problem * len(problems))()
+    for i, p in enumerate(problems):
+        arr[i] = make_problem(p, precision)
+    return arr
+
+
+def bsde_batch_workspace_bytes(problems, precision: str = "fp32c") -> int:
+    arr = _problem_array(problems, precision)
+    n = ctypes.c_size_t()
+    _check(load().bsde_batch_workspace_bytes(len(problems), arr, ctypes.byref(n)),
+           "bsde_batch_workspace_bytes")
+    return int(n.value)
+
+
+class BatchSolver:
+    """Many problems, one workspace, one persistent launch per solve."""
+
+    def __init__(self, problems, precision: str = "fp32c", device=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("the BSDE solver needs a CUDA device (no CPU fallback)")
+        self.problems = [dict(p) for p in problems]
+        self.n = len(problems)
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self._arr = _problem_array(problems, precision)
+        need = ctypes.c_size_t()
+        _check(load().bsde_batch_workspace_bytes(self.n, self._arr, ctypes.byref(need)),
+               "bsde_batch_workspace_bytes")
+        self.ws_bytes = int(need.value)
+        with torch.cuda.device(self.device):
+            self.workspace = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=self.device)
+            base = (self.workspace.data_ptr() + 255) // 256 * 256
+            h = ctypes.c_void_p()
+            _check(load().bsde_plan_batch(self.n, self._arr, ctypes.c_void_p(base), self.ws_bytes,
+                                          ctypes.byref(h)), "bsde_plan_batch")
+            self.batch = h.value
+
+    def config(self) -> dict:
+        c = bsde_batch_config()
+        _check(load().bsde_batch_get_config(ctypes.c_void_p(self.batch), ctypes.byref(c)),
+               "bsde_batch_get_config")
+        return {"cluster": c.cluster, "target_groups": c.target_groups}
+
+    def set_config(self, cluster: int, target_groups: int) -> None:
+        c = bsde_batch_config()
+        c.cluster, c.target_groups = cluster, target_groups
+        _check(load().bsde_batch_set_config(ctypes.c_void_p(self.batch), ctypes.byref(c)),
+               "bsde_batch_set_config")
+
+    def autotune(self, stream=None) -> dict:
+        import torch
+        s = stream or torch.cuda.current_stream(self.device)
+        c = bsde_batch_config()
+        _check(load().bsde_batch_autotune(ctypes.c_void_p(self.batch), ctypes.c_void_p(s.cuda_stream),
+                                          ctypes.byref(c)), "bsde_batch_autotune")
+        return {"cluster": c.cluster, "target_groups": c.target_groups}
+
+    def solve(self, stream=None, want_results: bool = True):
+        import torch
+        s = stream or torch.cuda.current_stream(self.device)
+        if not want_results:
+            _check(load().bsde_solve_batch(ctypes.c_void_p(self.batch), ctypes.c_void_p(s.cuda_stream),
+                                           None), "bsde_solve_batch")
+            return None
+        res = (bsde_result * self.n)()
+        _check(load().bsde_solve_batch(ctypes.c_void_p(self.batch), ctypes.c_void_p(s.cuda_stream),
+                                       res), "bsde_solve_batch")
+        return [_result_dict(r) for r in res]
+
+    def close(self) -> None:
+        if getattr(self, "batch", None):
+            load().bsde_batch_free(ctypes.c_void_p(self.batch))
+            self.batch = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# --- continuous-batching server ---------------------------------------------
+
+def bsde_request_bytes(problem: dict) -> int:
+    n = ctypes.c_size_t()
+    _check(load().bsde_request_bytes(ctypes.byref(make_problem(problem, "fp32c")), ctypes.byref(n)),
+           "bsde_request_bytes")
+    return int(n.value)
+
+
+class Server:
+    """A persistent device kernel solving requests as they are submitted.
+    Device memory: one torch tensor (slot statistics + the request pool)."""
+
+    def __init__(self, slots: int = 512, pool_bytes: int = 4 << 30, device=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("the BSDE server needs a CUDA device (no CPU fallback)")
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.slots = slots
+        need = ctypes.c_size_t()
+        _check(load().bsde_server_workspace_bytes(slots, pool_bytes, ctypes.byref(need)),
+               "bsde_server_workspace_bytes")
+        with torch.cuda.device(self.device):
+            self.workspace = torch.empty(int(need.value) + 256, dtype=torch.uint8, device=self.device)
+            base = (self.workspace.data_ptr() + 255) // 256 * 256
+            h = ctypes.c_void_p()
+            _check(load().bsde_server_create(ctypes.c_void_p(base), int(need.value), slots, pool_bytes,
+                                             ctypes.byref(h)), "bsde_server_create")
+        self.handle = h.value
+        self.stream = None
+        self._slot_buf = (ctypes.c_int * slots)()
+        self._res_buf = (bsde_result * slots)()
+
+    def start(self, cluster: int = 1, idle_ms: int = 30000):
+        import torch
+        # a stream of its own: the persistent kernel occupies it until stop()
+        self.stream = torch.cuda.Stream(self.device)
+        _check(load().bsde_server_start(ctypes.c_void_p(self.handle),
+                                        ctypes.c_void_p(self.stream.cuda_stream), cluster, idle_ms),
+               "bsde_server_start")
+
+    def submit(self, problem: dict):
+        """Slot index, or None when no slot or pool memory is free now."""
+        sl = ctypes.c_int(-1)
+        rc = load().bsde_server_submit(ctypes.c_void_p(self.handle),
+                                       ctypes.byref(make_problem(problem, "fp32c")), ctypes.byref(sl))
+        if rc == BSDE_BUSY:
+            return None
+        _check(rc, "bsde_server_submit")
+        return sl.value
+
+    def poll(self):
+        n = _check(load().bsde_server_poll(ctypes.c_void_p(self.handle), self.slots,
+                                           self._slot_buf, self._res_buf), "bsde_server_poll")
+        return [(self._slot_buf[i], _result_dict(self._res_buf[i])) for i in range(n)]
+
+    def stop(self):
+        _check(load().bsde_server_stop(ctypes.c_void_p(self.handle)), "bsde_server_stop")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().bsde_server_free(ctypes.c_void_p(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -9,7 +9,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libbsde.so")
 SOURCES = ["bsde_cuda.cu", "bsde_host.cpp"]
-HEADERS = ["bsde_internal.h", "bsde_kernels.cuh"]
+HEADERS = ["bsde_internal.h", "bsde_kernels.cuh", "bsde_batch.cuh", "bsde_server.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

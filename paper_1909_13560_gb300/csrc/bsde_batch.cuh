@@ -1,0 +1,140 @@
+// Batched solves: many independent problems of uneven Nx, N, k and driver in
+// one persistent launch (FP32C).  Included once, by bsde_cuda.cu.
+//
+// A thread-block cluster takes the next problem from a device queue (problems
+// ordered by decreasing work, so the longest start first) and its CTAs share
+// the problem level by level: the step tiles and spline tiles of a level are
+// dealt round-robin over the cluster's CTAs, with a cluster barrier (a
+// hardware barrier: no spin loop) between the step phase and the spline phase
+// and between levels.  Clusters never wait for one another, so the launch
+// needs no co-residency guarantee; the grid is sized to the clusters that fit
+// on the GPU at once and they drain the queue.
+#pragma once
+
+#include <cooperative_groups.h>
+
+namespace bsde {
+
+namespace cg = cooperative_groups;
+
+// Per-problem descriptor in the batch workspace.
+struct alignas(16) InstDesc {
+  Params P;
+  DrvC<float> dc32;
+  int64_t ringA, ringB, ptable;  // byte offsets in the batch workspace
+  int64_t pad;
+};
+
+constexpr int kBatchThreads = kStepTP * 6;          // up to six groups per point
+constexpr int kBatchSplineTile = kBatchThreads * kSplineChunk;  // 1536 unknowns
+
+struct alignas(16) BatchSmem {
+  InstDesc D;
+  PairF32 tab[kMaxK * (kMaxL / 2)];
+  float part[6 * 6 * kStepTP];
+  float sr[2][kBatchSplineTile + 2 * SplineT<BSDE_FP32C>::W];
+  float sg[2][kBatchSplineTile + 2 * SplineT<BSDE_FP32C>::W];
+  float sid[kInvPivots];
+  int inst;
+};
+
+__global__ void k_batch_reset(int *queue, Stats *stats, int count) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) *queue = 0;
+  if (i < count) {
+    stats[i].y0 = 0.0;
+    stats[i].z0 = 0.0;
+    stats[i].resid_bits = 0ull;
+    stats[i].iters_max = 0;
+    stats[i].nonconv = 0;
+    stats[i].timeout = 0;
+  }
+}
+
+template <int DRV>
+__device__ void batch_instance(BatchSmem &sm, unsigned char *ws, Stats *st,
+                               cg::cluster_group &cl) {
+  const Params &P = sm.D.P;
+  const int crank = int(cl.block_rank()), csize = int(cl.num_blocks());
+  const int tid = threadIdx.x, nt = blockDim.x;
+  float4 *ringA = reinterpret_cast<float4 *>(ws + sm.D.ringA);
+  float2 *ringB = reinterpret_cast<float2 *>(ws + sm.D.ringB);
+  Ring64 r64{nullptr};
+  Ring32 r32{ringA, ringB};
+
+  // the k initial levels and their splines
+  for (int m = 0; m < P.k; ++m)
+    for (int64_t i = int64_t(crank) * nt + tid; i < P.Nx; i += int64_t(csize) * nt)
+      init_point<BSDE_FP32C>(P, r64, r32, m, i);
+  cl.sync();
+  const int nst = int((P.Nx - 2 + kBatchSplineTile - 1) / kBatchSplineTile);
+  for (int m = 0; m < P.k; ++m) {
+    for (int t = crank; t < nst; t += csize) {
+      spline_tile<BSDE_FP32C, kBatchSplineTile, true>(P, r64, r32, (P.N - m) % P.nslot, t, nt, sm.sr,
+                                                sm.sg, sm.sid);
+      __syncthreads();
+    }
+  }
+  cl.sync();
+
+  // the backward loop: step tiles, barrier, spline tiles, barrier
+  const int ntiles = int((P.Nx + kStepTP - 1) / kStepTP);
+  for (int n = P.N - P.k; n >= 0; --n) {
+    for (int t = crank; t < ntiles; t += csize) {
+      step_tile32<DRV, false, true>(P, sm.D.dc32, ringA, ringB, sm.tab, sm.part, n, t * kStepTP, st);
+      __syncthreads();
+    }
+    cl.sync();
+    for (int t = crank; t < nst; t += csize) {
+      spline_tile<BSDE_FP32C, kBatchSplineTile, true>(P, r64, r32, n % P.nslot, t, nt, sm.sr, sm.sg,
+                                                sm.sid);
+      __syncthreads();
+    }
+    cl.sync();
+  }
+  if (crank == 0 && tid == 0) {
+    double ay, az;
+    readout_values<BSDE_FP32C, true>(P, r64, r32, 0, ay, az);
+    st->y0 = ay;
+    st->z0 = az;
+  }
+}
+
+__global__ void __launch_bounds__(kBatchThreads, 2)
+    k_batch32(const InstDesc *__restrict__ descs, const int *__restrict__ order, int count,
+              int *queue, unsigned char *ws, Stats *stats) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  BatchSmem &sm = *reinterpret_cast<BatchSmem *>(smem_raw);
+  cg::cluster_group cl = cg::this_cluster();
+  while (true) {
+    if (cl.block_rank() == 0 && threadIdx.x == 0) sm.inst = atomicAdd(queue, 1);
+    cl.sync();
+    const int q = *cl.map_shared_rank(&sm.inst, 0);
+    cl.sync();  // every CTA has read rank 0's value before it changes
+    if (q >= count) break;
+    const int id = order[q];
+    {
+      const int4 *src = reinterpret_cast<const int4 *>(descs + id);
+      int4 *dst = reinterpret_cast<int4 *>(&sm.D);
+      for (int t = threadIdx.x; t < int(sizeof(InstDesc) / 16); t += blockDim.x) dst[t] = src[t];
+    }
+    __syncthreads();
+    {
+      const float4 *src = reinterpret_cast<const float4 *>(ws + sm.D.ptable);
+      float4 *dst = reinterpret_cast<float4 *>(sm.tab);
+      const int n4 = sm.D.P.k * sm.D.P.Lp * 4;
+      for (int t = threadIdx.x; t < n4; t += blockDim.x) dst[t] = src[t];
+      if (threadIdx.x < kInvPivots) sm.sid[threadIdx.x] = float(sm.D.P.invd[threadIdx.x]);
+    }
+    __syncthreads();
+    switch (sm.D.P.driver) {
+      case BSDE_DRIVER_LIN_SIN: batch_instance<BSDE_DRIVER_LIN_SIN>(sm, ws, stats + id, cl); break;
+      case BSDE_DRIVER_BS: batch_instance<BSDE_DRIVER_BS>(sm, ws, stats + id, cl); break;
+      case BSDE_DRIVER_LB: batch_instance<BSDE_DRIVER_LB>(sm, ws, stats + id, cl); break;
+      case BSDE_DRIVER_EX1: batch_instance<BSDE_DRIVER_EX1>(sm, ws, stats + id, cl); break;
+      default: batch_instance<BSDE_DRIVER_EX2>(sm, ws, stats + id, cl); break;
+    }
+  }
+}
+
+}  // namespace bsde

@@ -4,12 +4,19 @@
 
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
+#include <atomic>
+#include <map>
 #include <mutex>
 #include <new>
+#include <numeric>
 #include <string>
+#include <vector>
 
 #include "bsde_internal.h"
 #include "bsde_kernels.cuh"
+#include "bsde_batch.cuh"
+#include "bsde_server.cuh"
 
 namespace bsde {
 
@@ -89,11 +96,17 @@ static void launch_step(bsde_plan_t *pl, cudaStream_t s, int n) {
         P, pl->dc64, reinterpret_cast<double4_32a *>(pl->ws + pl->lay.ring64),
         reinterpret_cast<const NodeF64 *>(pl->ws + pl->lay.table), n, st);
   } else {
-    const size_t sm = sizeof(NodeF32) * kL + sizeof(float) * 6 * P.G * kStepTP;
+    const size_t sm = step32_smem(P.G, P.k * P.Lp);
+    static bool attr_set = false;  // per driver instantiation
+    if (!attr_set) {
+      cudaFuncSetAttribute(k_step32<DRV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           int(step32_smem(kMaxGroups, kMaxK * kMaxL / 2)));
+      attr_set = true;
+    }
     k_step32<DRV><<<blocks, threads, sm, s>>>(
         P, pl->dc32, reinterpret_cast<float4 *>(pl->ws + pl->lay.ringA),
         reinterpret_cast<const float2 *>(pl->ws + pl->lay.ringB),
-        reinterpret_cast<const NodeF32 *>(pl->ws + pl->lay.table), n, st);
+        reinterpret_cast<const PairF32 *>(pl->ws + pl->lay.ptable), n, st);
   }
 }
 
@@ -208,20 +221,27 @@ int bsde_plan(const bsde_problem *p, void *dev_workspace, size_t bytes, bsde_pla
   const int kL = P.k * P.L;
   NodeF64 *t64 = new (std::nothrow) NodeF64[kL];
   NodeF32 *t32 = new (std::nothrow) NodeF32[kL];
-  if (!t64 || !t32) {
+  PairF32 *tp = new (std::nothrow) PairF32[kL];
+  if (!t64 || !t32 || !tp) {
     delete[] t64;
     delete[] t32;
+    delete[] tp;
     delete pl;
     return fail(BSDE_ENOMEM, "table allocation");
   }
-  build_tables(pl->P, t64, t32);
+  build_tables(pl->P, t64, t32, tp);
   cudaError_t e;
-  if (P.precision == BSDE_FP64)
+  if (P.precision == BSDE_FP64) {
     e = cudaMemcpy(pl->ws + lay.table, t64, sizeof(NodeF64) * kL, cudaMemcpyHostToDevice);
-  else
+  } else {
     e = cudaMemcpy(pl->ws + lay.table, t32, sizeof(NodeF32) * kL, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(pl->ws + lay.ptable, tp, sizeof(PairF32) * P.k * pl->P.Lp,
+                     cudaMemcpyHostToDevice);
+  }
   delete[] t64;
   delete[] t32;
+  delete[] tp;
   if (e == cudaSuccess) e = cudaMallocHost(&pl->host_stats, sizeof(Stats));
   if (e != cudaSuccess) {
     delete pl;
@@ -242,6 +262,10 @@ static int fill_result(bsde_plan_t *pl, bsde_result *r) {
   r->picard_iters_max = s.iters_max;
   r->levels_done = pl->P.N - pl->P.k + 1;
   r->status = s.nonconv ? BSDE_WARN_NOCONV : BSDE_OK;
+  if (s.timeout) {
+    r->status = BSDE_ETIMEOUT;
+    return fail(BSDE_ETIMEOUT, "a bulk-copy wait in the step kernel gave up");
+  }
   return r->status;
 }
 
@@ -404,13 +428,19 @@ extern "C" int bsde_solve_noalloc(const bsde_problem *p, void *stream, const dou
   const int kL = P.k * P.L;
   NodeF64 t64[kMaxK * kMaxL];
   NodeF32 t32[kMaxK * kMaxL];
-  build_tables(pl.P, t64, t32);
-  if (P.precision == BSDE_FP64)
+  PairF32 tpr[kMaxK * kMaxL];
+  build_tables(pl.P, t64, t32, tpr);
+  if (P.precision == BSDE_FP64) {
     BSDE_CUDA_TRY(cudaMemcpyAsync(pl.ws + pl.lay.table, t64, sizeof(NodeF64) * kL,
                                   cudaMemcpyHostToDevice, s));
-  else
+  } else {
     BSDE_CUDA_TRY(cudaMemcpyAsync(pl.ws + pl.lay.table, t32, sizeof(NodeF32) * kL,
                                   cudaMemcpyHostToDevice, s));
+    BSDE_CUDA_TRY(cudaMemcpyAsync(pl.ws + pl.lay.ptable, tpr, sizeof(PairF32) * P.k * P.Lp,
+                                  cudaMemcpyHostToDevice, s));
+  }
+  // the host tables live on this stack frame: wait for the copies
+  BSDE_CUDA_TRY(cudaStreamSynchronize(s));
   double *sy = reinterpret_cast<double *>(pl.ws + pl.lay.stage);
   double *sz = sy + int64_t(P.k) * P.Nx;
   const size_t lev_bytes = size_t(P.k) * size_t(P.Nx) * sizeof(double);
@@ -436,3 +466,543 @@ extern "C" int bsde_solve_noalloc(const bsde_problem *p, void *stream, const dou
   pl.host_stats = &st;
   return fill_result(&pl, result);
 }
+
+// ---------------------------------------------------------------------------
+// Batched solves: host side
+// ---------------------------------------------------------------------------
+struct bsde_batch_s {
+  int n = 0, device = 0;
+  unsigned char *ws = nullptr;
+  size_t ws_bytes = 0;
+  size_t off_desc = 0, off_order = 0, off_queue = 0, off_stats = 0;
+  std::vector<bsde_problem> probs;
+  std::vector<size_t> off_ptable, off_ringA, off_ringB;
+  bsde_batch_config cfg{};
+  int desc_groups = 0;  // target_groups the device descriptors were built with
+  cudaGraphExec_t graph = nullptr;
+  int graph_cluster = 0, graph_groups = 0;
+  Stats *host_stats = nullptr;
+};
+
+namespace bsde {
+
+struct BatchLayout {
+  size_t off_desc, off_order, off_queue, off_stats, total;
+  std::vector<size_t> ptable, ringA, ringB;
+};
+
+static int batch_layout(int n, const bsde_problem *ps, BatchLayout &L) {
+  auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
+  size_t off = 0;
+  L.off_desc = off; off = up(off + size_t(n) * sizeof(InstDesc));
+  L.off_order = off; off = up(off + size_t(n) * sizeof(int));
+  L.off_queue = off; off = up(off + 16);
+  L.off_stats = off; off = up(off + size_t(n) * sizeof(Stats));
+  L.ptable.resize(n);
+  L.ringA.resize(n);
+  L.ringB.resize(n);
+  for (int i = 0; i < n; ++i) {
+    const bsde_problem &p = ps[i];
+    if (validate(p) || p.precision != BSDE_FP32C) return BSDE_EINVAL;
+    const size_t nx = size_t(p.Nx), ns = size_t(p.k + 1);
+    L.ptable[i] = off; off = up(off + size_t(p.k) * ((p.L + 1) / 2) * sizeof(PairF32));
+    L.ringA[i] = off; off = up(off + ns * nx * 16);
+    L.ringB[i] = off; off = up(off + ns * nx * 8 + 64);
+  }
+  L.total = off;
+  return BSDE_OK;
+}
+
+// Descriptors, pair tables and the largest-first order, copied to the device.
+static int batch_upload(bsde_batch_t *b, int target_groups) {
+  const int n = b->n;
+  std::vector<InstDesc> descs(n);
+  std::vector<double> work(n);
+  std::vector<NodeF32> t32(kMaxK * kMaxL);
+  std::vector<PairF32> tp(kMaxK * kMaxL);
+  for (int i = 0; i < n; ++i) {
+    InstDesc &D = descs[i];
+    std::memset(&D, 0, sizeof(D));
+    fill_params(b->probs[i], D.P);
+    build_tables(D.P, nullptr, t32.data(), tp.data(), target_groups, 6);
+    DrvC<double> c64;
+    driver_coefs(D.P, c64, D.dc32);
+    D.ringA = int64_t(b->off_ringA[i]);
+    D.ringB = int64_t(b->off_ringB[i]);
+    D.ptable = int64_t(b->off_ptable[i]);
+    BSDE_CUDA_TRY(cudaMemcpy(b->ws + b->off_ptable[i], tp.data(),
+                             sizeof(PairF32) * D.P.k * D.P.Lp, cudaMemcpyHostToDevice));
+    work[i] = double(D.P.Nx) * double(D.P.N - D.P.k + 1) * double(D.P.k) * double(D.P.L);
+  }
+  std::vector<int> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return work[a] > work[c]; });
+  BSDE_CUDA_TRY(cudaMemcpy(b->ws + b->off_desc, descs.data(), sizeof(InstDesc) * n,
+                           cudaMemcpyHostToDevice));
+  BSDE_CUDA_TRY(cudaMemcpy(b->ws + b->off_order, order.data(), sizeof(int) * n,
+                           cudaMemcpyHostToDevice));
+  b->desc_groups = target_groups;
+  return BSDE_OK;
+}
+
+static int batch_enqueue(bsde_batch_t *b, cudaStream_t s) {
+  const int n = b->n;
+  int *queue = reinterpret_cast<int *>(b->ws + b->off_queue);
+  Stats *stats = reinterpret_cast<Stats *>(b->ws + b->off_stats);
+  k_batch_reset<<<(n + 255) / 256, 256, 0, s>>>(queue, stats, n);
+  const size_t smem = sizeof(BatchSmem);
+  BSDE_CUDA_TRY(cudaFuncSetAttribute(k_batch32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     int(smem)));
+  const int cl = b->cfg.cluster;
+  cudaLaunchConfig_t lc{};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = unsigned(cl);
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  lc.blockDim = dim3(kBatchThreads, 1, 1);
+  lc.dynamicSmemBytes = smem;
+  lc.stream = s;
+  lc.attrs = attr;
+  lc.numAttrs = 1;
+  lc.gridDim = dim3(unsigned(cl), 1, 1);
+  int active = 0;
+  BSDE_CUDA_TRY(cudaOccupancyMaxActiveClusters(&active, k_batch32, &lc));
+  if (active < 1) return fail(BSDE_ECUDA, "batch kernel: no cluster fits on the device");
+  const int clusters = std::min(active, n);
+  lc.gridDim = dim3(unsigned(clusters * cl), 1, 1);
+  const InstDesc *descs = reinterpret_cast<const InstDesc *>(b->ws + b->off_desc);
+  const int *order = reinterpret_cast<const int *>(b->ws + b->off_order);
+  BSDE_CUDA_TRY(cudaLaunchKernelEx(&lc, k_batch32, descs, order, n, queue, b->ws, stats));
+  return BSDE_OK;
+}
+
+static int batch_graph(bsde_batch_t *b) {
+  if (b->graph && b->graph_cluster == b->cfg.cluster && b->graph_groups == b->cfg.target_groups)
+    return BSDE_OK;
+  if (b->desc_groups != b->cfg.target_groups) {
+    int rc = batch_upload(b, b->cfg.target_groups);
+    if (rc) return rc;
+  }
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  cudaStream_t cs;
+  BSDE_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  int rc = BSDE_OK;
+  if (e == cudaSuccess) {
+    rc = batch_enqueue(b, cs);
+    cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+    if (e == cudaSuccess) e = e2;
+  }
+  cudaStreamDestroy(cs);
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return fail(BSDE_ECUDA, std::string("batch capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&b->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess)
+    return fail(BSDE_ECUDA, std::string("batch graph: ") + cudaGetErrorString(e));
+  b->graph_cluster = b->cfg.cluster;
+  b->graph_groups = b->cfg.target_groups;
+  return BSDE_OK;
+}
+
+static bool valid_config(const bsde_batch_config &c) {
+  return (c.cluster == 1 || c.cluster == 2 || c.cluster == 4 || c.cluster == 8) &&
+         c.target_groups >= 1 && c.target_groups <= 6;
+}
+
+}  // namespace bsde
+
+extern "C" {
+
+int bsde_batch_workspace_bytes(int n, const bsde_problem *ps, size_t *bytes) {
+  if (n < 1 || !ps || !bytes) return fail(BSDE_EINVAL, "bad batch arguments");
+  BatchLayout L;
+  if (batch_layout(n, ps, L)) return fail(BSDE_EINVAL, "invalid problem in batch (FP32C only)");
+  *bytes = L.total;
+  return BSDE_OK;
+}
+
+int bsde_plan_batch(int n, const bsde_problem *ps, void *dev_workspace, size_t bytes,
+                    bsde_batch_t **out) {
+  if (!out) return fail(BSDE_EINVAL, "null argument");
+  *out = nullptr;
+  if (n < 1 || !ps) return fail(BSDE_EINVAL, "bad batch arguments");
+  BatchLayout L;
+  if (batch_layout(n, ps, L)) return fail(BSDE_EINVAL, "invalid problem in batch (FP32C only)");
+  if (!dev_workspace || bytes < L.total)
+    return fail(BSDE_ENOSPC, "workspace smaller than bsde_batch_workspace_bytes()");
+  if (reinterpret_cast<uintptr_t>(dev_workspace) % 256)
+    return fail(BSDE_EINVAL, "workspace must be 256-byte aligned");
+  bsde_batch_t *b = new (std::nothrow) bsde_batch_t();
+  if (!b) return fail(BSDE_ENOMEM, "batch allocation");
+  b->n = n;
+  cudaGetDevice(&b->device);
+  b->ws = static_cast<unsigned char *>(dev_workspace);
+  b->ws_bytes = bytes;
+  b->off_desc = L.off_desc;
+  b->off_order = L.off_order;
+  b->off_queue = L.off_queue;
+  b->off_stats = L.off_stats;
+  b->off_ptable = L.ptable;
+  b->off_ringA = L.ringA;
+  b->off_ringB = L.ringB;
+  b->probs.assign(ps, ps + n);
+  b->cfg.cluster = 2;
+  b->cfg.target_groups = 4;
+  int rc = batch_upload(b, b->cfg.target_groups);
+  if (rc == BSDE_OK && cudaMallocHost(&b->host_stats, sizeof(Stats) * size_t(n)) != cudaSuccess)
+    rc = fail(BSDE_ECUDA, "pinned result buffer");
+  if (rc) {
+    delete b;
+    return rc;
+  }
+  *out = b;
+  return BSDE_OK;
+}
+
+int bsde_batch_set_config(bsde_batch_t *b, const bsde_batch_config *cfg) {
+  if (!b || !cfg || !valid_config(*cfg)) return fail(BSDE_EINVAL, "bad batch configuration");
+  b->cfg = *cfg;
+  return BSDE_OK;
+}
+
+int bsde_batch_get_config(const bsde_batch_t *b, bsde_batch_config *cfg) {
+  if (!b || !cfg) return fail(BSDE_EINVAL, "null argument");
+  *cfg = b->cfg;
+  return BSDE_OK;
+}
+
+int bsde_solve_batch(bsde_batch_t *b, void *stream, bsde_result *results) {
+  if (!b) return fail(BSDE_EINVAL, "null batch");
+  DeviceGuard guard(b->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int rc = batch_graph(b);
+  if (rc) return rc;
+  BSDE_CUDA_TRY(cudaGraphLaunch(b->graph, s));
+  if (!results) return BSDE_OK;
+  BSDE_CUDA_TRY(cudaMemcpyAsync(b->host_stats, b->ws + b->off_stats, sizeof(Stats) * b->n,
+                                cudaMemcpyDeviceToHost, s));
+  BSDE_CUDA_TRY(cudaStreamSynchronize(s));
+  int worst = BSDE_OK;
+  for (int i = 0; i < b->n; ++i) {
+    const Stats &st = b->host_stats[i];
+    bsde_result &r = results[i];
+    r.y0 = st.y0;
+    r.z0 = st.z0;
+    double d;
+    unsigned long long bits = st.resid_bits;
+    std::memcpy(&d, &bits, sizeof(d));
+    r.picard_resid_max = d;
+    r.picard_iters_max = st.iters_max;
+    r.levels_done = b->probs[i].N - b->probs[i].k + 1;
+    r.status = st.nonconv ? BSDE_WARN_NOCONV : BSDE_OK;
+    if (r.status != BSDE_OK) worst = r.status;
+  }
+  return worst;
+}
+
+int bsde_batch_autotune(bsde_batch_t *b, void *stream, bsde_batch_config *best) {
+  if (!b) return fail(BSDE_EINVAL, "null batch");
+  DeviceGuard guard(b->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bsde_batch_config keep = b->cfg;
+  bsde_batch_config win = keep;
+  float win_ms = -1.f;
+  cudaEvent_t e0, e1;
+  BSDE_CUDA_TRY(cudaEventCreate(&e0));
+  BSDE_CUDA_TRY(cudaEventCreate(&e1));
+  const int clusters[4] = {1, 2, 4, 8};
+  const int groups[3] = {2, 4, 6};
+  int rc = BSDE_OK;
+  for (int gi = 0; gi < 3 && rc == BSDE_OK; ++gi) {
+    for (int ci = 0; ci < 4 && rc == BSDE_OK; ++ci) {
+      b->cfg.cluster = clusters[ci];
+      b->cfg.target_groups = groups[gi];
+      rc = batch_graph(b);
+      if (rc) break;
+      if (cudaGraphLaunch(b->graph, s) != cudaSuccess) { rc = fail(BSDE_ECUDA, "autotune launch"); break; }
+      cudaEventRecord(e0, s);
+      cudaGraphLaunch(b->graph, s);
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) { rc = fail(BSDE_ECUDA, "autotune timing"); break; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (win_ms < 0.f || ms < win_ms) {
+        win_ms = ms;
+        win = b->cfg;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->cfg = rc ? keep : win;
+  if (rc) return rc;
+  if (best) *best = win;
+  return BSDE_OK;
+}
+
+void bsde_batch_free(bsde_batch_t *b) {
+  if (!b) return;
+  DeviceGuard guard(b->device);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->host_stats) cudaFreeHost(b->host_stats);
+  delete b;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Continuous-batching server: host side
+// ---------------------------------------------------------------------------
+struct bsde_server_s {
+  int device = 0, nslots = 0;
+  unsigned char *ws = nullptr;
+  size_t ws_bytes = 0, off_dev = 0, off_stats = 0, off_pool = 0, pool_bytes = 0;
+  ServerCtl *ctl = nullptr;   // host view of the mapped control block
+  ServerCtl *ctl_d = nullptr; // device view
+  ServerSlot *slots = nullptr, *slots_d = nullptr;
+  std::vector<int> free_slots;
+  std::vector<size_t> slot_off, slot_size;
+  std::vector<char> busy;
+  std::map<size_t, size_t> free_blocks;  // pool offset -> bytes
+  uint32_t tail = 0;
+  bool running = false;
+  cudaStream_t stream = nullptr;
+};
+
+namespace bsde {
+
+static size_t request_bytes(const bsde_problem &p) {
+  auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
+  const size_t nx = size_t(p.Nx), ns = size_t(p.k + 1);
+  return up(ns * nx * 16) + up(ns * nx * 8 + 64);
+}
+
+static bool pool_alloc(bsde_server_t *s, size_t bytes, size_t &off) {
+  for (auto it = s->free_blocks.begin(); it != s->free_blocks.end(); ++it) {
+    if (it->second >= bytes) {
+      off = it->first;
+      const size_t rest = it->second - bytes;
+      s->free_blocks.erase(it);
+      if (rest) s->free_blocks[off + bytes] = rest;
+      return true;
+    }
+  }
+  return false;
+}
+
+static void pool_free(bsde_server_t *s, size_t off, size_t bytes) {
+  auto it = s->free_blocks.emplace(off, bytes).first;
+  auto nx = std::next(it);
+  if (nx != s->free_blocks.end() && it->first + it->second == nx->first) {
+    it->second += nx->second;
+    s->free_blocks.erase(nx);
+  }
+  if (it != s->free_blocks.begin()) {
+    auto pv = std::prev(it);
+    if (pv->first + pv->second == it->first) {
+      pv->second += it->second;
+      s->free_blocks.erase(it);
+    }
+  }
+}
+
+}  // namespace bsde
+
+extern "C" {
+
+int bsde_request_bytes(const bsde_problem *p, size_t *bytes) {
+  if (!p || !bytes) return fail(BSDE_EINVAL, "null argument");
+  if (validate(*p) || p->precision != BSDE_FP32C) return fail(BSDE_EINVAL, "invalid request");
+  *bytes = request_bytes(*p);
+  return BSDE_OK;
+}
+
+int bsde_server_workspace_bytes(int slots, size_t pool_bytes, size_t *bytes) {
+  if (slots < 1 || !bytes) return fail(BSDE_EINVAL, "bad server arguments");
+  auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
+  *bytes = up(sizeof(ServerDev)) + up(sizeof(Stats) * size_t(slots)) + up(pool_bytes);
+  return BSDE_OK;
+}
+
+int bsde_server_create(void *dev_workspace, size_t bytes, int slots, size_t pool_bytes,
+                       bsde_server_t **out) {
+  if (!out) return fail(BSDE_EINVAL, "null argument");
+  *out = nullptr;
+  size_t need = 0;
+  int rc = bsde_server_workspace_bytes(slots, pool_bytes, &need);
+  if (rc) return rc;
+  if (!dev_workspace || bytes < need) return fail(BSDE_ENOSPC, "server workspace too small");
+  if (reinterpret_cast<uintptr_t>(dev_workspace) % 256)
+    return fail(BSDE_EINVAL, "workspace must be 256-byte aligned");
+  bsde_server_t *s = new (std::nothrow) bsde_server_t();
+  if (!s) return fail(BSDE_ENOMEM, "server allocation");
+  auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
+  cudaGetDevice(&s->device);
+  s->nslots = slots;
+  s->ws = static_cast<unsigned char *>(dev_workspace);
+  s->ws_bytes = bytes;
+  s->off_dev = 0;
+  s->off_stats = up(sizeof(ServerDev));
+  s->off_pool = s->off_stats + up(sizeof(Stats) * size_t(slots));
+  s->pool_bytes = pool_bytes;
+  cudaError_t e = cudaHostAlloc(&s->ctl, sizeof(ServerCtl), cudaHostAllocMapped);
+  if (e == cudaSuccess)
+    e = cudaHostAlloc(&s->slots, sizeof(ServerSlot) * size_t(slots), cudaHostAllocMapped);
+  if (e == cudaSuccess) e = cudaHostGetDevicePointer(&s->ctl_d, s->ctl, 0);
+  if (e == cudaSuccess) e = cudaHostGetDevicePointer(&s->slots_d, s->slots, 0);
+  if (e != cudaSuccess) {
+    if (s->ctl) cudaFreeHost(s->ctl);
+    if (s->slots) cudaFreeHost(s->slots);
+    delete s;
+    return fail(BSDE_ECUDA, std::string("server host memory: ") + cudaGetErrorString(e));
+  }
+  std::memset(s->ctl, 0, sizeof(ServerCtl));
+  std::memset(s->slots, 0, sizeof(ServerSlot) * size_t(slots));
+  s->free_slots.resize(slots);
+  for (int i = 0; i < slots; ++i) s->free_slots[i] = slots - 1 - i;
+  s->slot_off.assign(slots, 0);
+  s->slot_size.assign(slots, 0);
+  s->busy.assign(slots, 0);
+  if (pool_bytes) s->free_blocks[0] = pool_bytes;
+  *out = s;
+  return BSDE_OK;
+}
+
+int bsde_server_start(bsde_server_t *s, void *stream, int cluster, int idle_ms) {
+  if (!s || s->running) return fail(BSDE_EINVAL, "server missing or already running");
+  if (!(cluster == 1 || cluster == 2 || cluster == 4 || cluster == 8) || idle_ms < 1)
+    return fail(BSDE_EINVAL, "bad server launch arguments");
+  DeviceGuard guard(s->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  s->ctl->shutdown = 0;
+  BSDE_CUDA_TRY(cudaMemsetAsync(s->ws + s->off_dev, 0, sizeof(ServerDev), st));
+  const size_t smem = sizeof(BatchSmem);
+  BSDE_CUDA_TRY(cudaFuncSetAttribute(k_server32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     int(smem)));
+  cudaLaunchConfig_t lc{};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = unsigned(cluster);
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  lc.blockDim = dim3(kBatchThreads, 1, 1);
+  lc.dynamicSmemBytes = smem;
+  lc.stream = st;
+  lc.attrs = attr;
+  lc.numAttrs = 1;
+  lc.gridDim = dim3(unsigned(cluster), 1, 1);
+  int active = 0;
+  BSDE_CUDA_TRY(cudaOccupancyMaxActiveClusters(&active, k_server32, &lc));
+  if (active < 1) return fail(BSDE_ECUDA, "server kernel: no cluster fits on the device");
+  lc.gridDim = dim3(unsigned(active * cluster), 1, 1);
+  BSDE_CUDA_TRY(cudaLaunchKernelEx(&lc, k_server32, s->ctl_d, s->slots_d,
+                                   reinterpret_cast<ServerDev *>(s->ws + s->off_dev),
+                                   reinterpret_cast<Stats *>(s->ws + s->off_stats),
+                                   s->ws + s->off_pool,
+                                   (unsigned long long)idle_ms * 1000000ull));
+  s->running = true;
+  s->stream = st;
+  return BSDE_OK;
+}
+
+int bsde_server_submit(bsde_server_t *s, const bsde_problem *p, int *slot) {
+  if (!s || !p || !slot) return fail(BSDE_EINVAL, "null argument");
+  if (!s->running) return fail(BSDE_EINVAL, "server not running");
+  if (validate(*p) || p->precision != BSDE_FP32C) return fail(BSDE_EINVAL, "invalid request");
+  if (s->free_slots.empty()) return BSDE_BUSY;
+  const size_t need = request_bytes(*p);
+  size_t off = 0;
+  if (!pool_alloc(s, need, off)) return BSDE_BUSY;
+  const int sl = s->free_slots.back();
+  s->free_slots.pop_back();
+  ServerSlot &S = s->slots[sl];
+  InstDesc D;
+  std::memset(&D, 0, sizeof(D));
+  fill_params(*p, D.P);
+  {
+    NodeF32 t32[kMaxK * kMaxL];
+    PairF32 tp[kMaxK * kMaxL];
+    build_tables(D.P, nullptr, t32, tp, 4, 6);
+    std::memcpy(S.tab, tp, sizeof(PairF32) * size_t(D.P.k) * size_t(D.P.Lp));
+  }
+  DrvC<double> c64;
+  driver_coefs(D.P, c64, D.dc32);
+  auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
+  const size_t nx = size_t(p->Nx), ns = size_t(p->k + 1);
+  D.ringA = int64_t(off);
+  D.ringB = int64_t(off + up(ns * nx * 16));
+  D.ptable = 0;
+  S.D = D;
+  S.done = 0;
+  s->slot_off[sl] = off;
+  s->slot_size[sl] = need;
+  s->busy[sl] = 1;
+  // publish: slot data before the ring entry before the tail
+  s->ctl->req_slot[s->tail % kServerRing] = sl;
+  std::atomic_thread_fence(std::memory_order_release);
+  __atomic_store_n(&s->ctl->req_tail, s->tail + 1, __ATOMIC_RELEASE);
+  ++s->tail;
+  *slot = sl;
+  return BSDE_OK;
+}
+
+int bsde_server_poll(bsde_server_t *s, int max, int *slots, bsde_result *results) {
+  if (!s || max < 0) return fail(BSDE_EINVAL, "bad poll arguments");
+  int got = 0;
+  for (int sl = 0; sl < s->nslots && got < max; ++sl) {
+    if (!s->busy[sl]) continue;
+    if (__atomic_load_n(&s->slots[sl].done, __ATOMIC_ACQUIRE) != 1u) continue;
+    const Stats st = s->slots[sl].result;
+    if (results) {
+      bsde_result &r = results[got];
+      r.y0 = st.y0;
+      r.z0 = st.z0;
+      double d;
+      unsigned long long bits = st.resid_bits;
+      std::memcpy(&d, &bits, sizeof(d));
+      r.picard_resid_max = d;
+      r.picard_iters_max = st.iters_max;
+      r.levels_done = s->slots[sl].D.P.N - s->slots[sl].D.P.k + 1;
+      r.status = st.timeout ? BSDE_ETIMEOUT : (st.nonconv ? BSDE_WARN_NOCONV : BSDE_OK);
+    }
+    if (slots) slots[got] = sl;
+    ++got;
+    s->busy[sl] = 0;
+    pool_free(s, s->slot_off[sl], s->slot_size[sl]);
+    s->free_slots.push_back(sl);
+  }
+  return got;
+}
+
+int bsde_server_stop(bsde_server_t *s) {
+  if (!s) return fail(BSDE_EINVAL, "null server");
+  if (!s->running) return BSDE_OK;
+  DeviceGuard guard(s->device);
+  __atomic_store_n(&s->ctl->shutdown, 1u, __ATOMIC_RELEASE);
+  BSDE_CUDA_TRY(cudaStreamSynchronize(s->stream));
+  s->running = false;
+  ServerDev dev{};
+  BSDE_CUDA_TRY(cudaMemcpy(&dev, s->ws + s->off_dev, sizeof(dev), cudaMemcpyDeviceToHost));
+  if (dev.error) return fail(BSDE_ETIMEOUT, "a server cluster waited longer than idle_ms");
+  return BSDE_OK;
+}
+
+void bsde_server_free(bsde_server_t *s) {
+  if (!s) return;
+  DeviceGuard guard(s->device);
+  if (s->running) bsde_server_stop(s);
+  if (s->ctl) cudaFreeHost(s->ctl);
+  if (s->slots) cudaFreeHost(s->slots);
+  delete s;
+}
+
+}  // extern "C"

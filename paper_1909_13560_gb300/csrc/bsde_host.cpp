@@ -3,6 +3,7 @@
 // tables (Section 2.2, Eq. 20-21; Section 3.2 remarks on the uniform grid).
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "bsde_internal.h"
 
@@ -79,6 +80,16 @@ int gauss_hermite(int L, double *nodes, double *weights) {
     scaled_hermite(a, L, hL, hLm1);
     nodes[m] = (double)a;
     weights[m] = (double)(std::sqrt((long double)M_PI) / ((long double)L * hLm1 * hLm1));
+  }
+  // the rule is symmetric: make it so to the last bit (a_{L-1-l} = -a_l,
+  // equal weights), which the pairwise kernels rely on
+  for (int m = 0; m < L / 2; ++m) {
+    const double a = 0.5 * (nodes[L - 1 - m] - nodes[m]);
+    const double w = 0.5 * (weights[m] + weights[L - 1 - m]);
+    nodes[m] = -a;
+    nodes[L - 1 - m] = a;
+    weights[m] = w;
+    weights[L - 1 - m] = w;
   }
   if (L % 2 == 1) nodes[L / 2] = 0.0;
   return BSDE_OK;
@@ -164,9 +175,10 @@ Layout layout_for(const bsde_problem &p) {
     L.ring64 = off; off = up(off + ns * nx * 32);
   } else {
     L.ringA = off; off = up(off + ns * nx * 16);
-    L.ringB = off; off = up(off + ns * nx * 8);
+    L.ringB = off; off = up(off + ns * nx * 8 + 64);  // bulk copies may read 8 B past a level
   }
   L.table = off; off = up(off + size_t(p.k) * p.L * (p.precision == BSDE_FP64 ? sizeof(NodeF64) : sizeof(NodeF32)));
+  L.ptable = off; off = up(off + size_t(p.k) * ((p.L + 1) / 2) * sizeof(PairF32));
   L.stage = off; off = up(off + 2 * size_t(p.k) * nx * 8);
   L.stats = off; off = up(off + sizeof(Stats));
   L.total = off;
@@ -175,12 +187,16 @@ Layout layout_for(const bsde_problem &p) {
 
 // Work split of the step kernels: enough (j, l-chunk) groups per point that a
 // level of a modest grid still fills the GPU (at least four groups).
-static void work_split(Params &P) {
-  int S = (4 + P.k - 1) / P.k;
-  if (S > P.L) S = P.L;
+static void work_split(Params &P, int target_groups, int max_groups) {
+  // FP64 splits the L nodes, FP32C the ceil(L/2) symmetric pairs
+  P.Lp = (P.L + 1) / 2;
+  const int units = P.precision == BSDE_FP64 ? P.L : P.Lp;
+  int S = (target_groups + P.k - 1) / P.k;
+  if (S * P.k > max_groups) S = max_groups / P.k;
+  if (S > units) S = units;
   if (S < 1) S = 1;
   P.S = S;
-  P.Lg = (P.L + S - 1) / S;
+  P.Lg = (units + S - 1) / S;
   P.G = P.k * S;
 }
 
@@ -189,10 +205,25 @@ static void work_split(Params &P) {
 // every i (Section 3.2, third remark: the cell index is found without a
 // search); its cell is i + floor(o_jl) and its position inside the cell
 // theta = o_jl - floor(o_jl).
-void build_tables(Params &P, NodeF64 *t64, NodeF32 *t32) {
-  work_split(P);
+// The Gauss-Hermite rule depends on L only: computed once per L and kept.
+static void cached_rule(int L, double *a, double *w) {
+  static std::mutex mu;
+  static bool have[kMaxL + 1];
+  static double na[kMaxL + 1][kMaxL], nw[kMaxL + 1][kMaxL];
+  std::lock_guard<std::mutex> lk(mu);
+  if (!have[L]) {
+    gauss_hermite(L, na[L], nw[L]);
+    have[L] = true;
+  }
+  std::memcpy(a, na[L], sizeof(double) * L);
+  std::memcpy(w, nw[L], sizeof(double) * L);
+}
+
+void build_tables(Params &P, NodeF64 *t64, NodeF32 *t32, PairF32 *tp, int target_groups,
+                  int max_groups) {
+  work_split(P, target_groups, max_groups);
   double a[kMaxL], w[kMaxL];
-  gauss_hermite(P.L, a, w);
+  cached_rule(P.L, a, w);
   const double rpi = 1.0 / std::sqrt(M_PI);
   const double c6 = P.dx * P.dx / 6.0;
   for (int j = 1; j <= P.k; ++j) {
@@ -240,6 +271,30 @@ void build_tables(Params &P, NodeF64 *t64, NodeF32 *t32) {
     }
     P.smin[j - 1] = smin;
     P.smax[j - 1] = smax;
+    if (tp && t32) {
+      for (int q = 0; q < P.Lp; ++q) {
+        const NodeF32 &na = t32[(j - 1) * P.L + q];
+        const NodeF32 &nb = t32[(j - 1) * P.L + (P.L - 1 - q)];
+        const bool single = (q == P.L - 1 - q);
+        const float half = single ? 0.5f : 1.0f;  // exact in binary
+        PairF32 pr{};
+        pr.shift_a = na.shift;
+        pr.shift_b = nb.shift;
+        pr.w1a = na.w1;
+        pr.w1b = nb.w1;
+        pr.w2a = na.w2;
+        pr.w3a = na.w3;
+        pr.w2b = nb.w2;
+        pr.w3b = nb.w3;
+        pr.czh = na.czh * half;
+        pr.czl = na.czl * half;
+        pr.cfz = na.cfz;  // zero for the middle node (DeltaW = 0)
+        pr.cfy = na.cfy * half;
+        pr.cyh = na.cyh * half;
+        pr.cyl = na.cyl * half;
+        tp[(j - 1) * P.Lp + q] = pr;
+      }
+    }
   }
 }
 

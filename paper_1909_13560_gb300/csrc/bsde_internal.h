@@ -16,6 +16,11 @@ constexpr int kStepTP = 64;      // grid points per CTA in the step kernels
 constexpr int kMaxGroups = 8;    // (j, l-chunk) groups per point
 constexpr int kSplineTile = 512;  // unknowns per CTA in the spline kernel
 constexpr int kSplineChunk = 4;   // unknowns per thread (serial recurrence)
+constexpr int kTmaStages = 3;     // pipeline depth of the bulk-copy step path
+// one stage: the A windows (65 float4) and B windows (66 float2) of a node pair
+constexpr int kWinA = (kStepTP + 1) * 16, kWinB = (kStepTP + 2) * 8;
+constexpr int kStageBytes = 2 * kWinA + 2 * kWinB;
+constexpr unsigned kWaitLimit = 1u << 26;  // polls of a bulk-copy barrier before giving up
 
 // Per (j, l) entry of the node tables.  The off-grid point
 // x_i + a_x j dt + b_x sqrt(2 j dt) a_l sits in cell i + shift at relative
@@ -41,6 +46,20 @@ struct NodeF32 {
   float pad;
 };
 
+// FP32C pair entry: Gauss-Hermite nodes l and L-1-l (a_{L-1-l} = -a_l) share
+// |DeltaW| and the weight, so cz, cy and cfy are equal for the pair and cfz
+// is opposite.  A pair is processed together: the two spline values are
+// added exactly (TwoSum) before one compensated product, and the driver
+// terms enter as cfz (F_a - F_b) and cfy (F_a + F_b).  For odd L the middle
+// node (a = 0, DeltaW = 0) is a pair with itself and halved coefficients.
+// Layout as four float4: (shift_a, shift_b, w1a, w1b), (w2a, w3a, w2b, w3b),
+// (czh, czl, cfz, cfy), (cyh, cyl, -, -); w1 = theta, w0 = 1 - theta.
+struct PairF32 {
+  int32_t shift_a, shift_b;
+  float w1a, w1b, w2a, w3a, w2b, w3b;
+  float czh, czl, cfz, cfy, cyh, cyl, pad0, pad1;
+};
+
 // Everything a kernel needs to know about one problem.
 struct Params {
   int64_t Nx;
@@ -56,7 +75,7 @@ struct Params {
   double invd[kInvPivots];
   // work split of the step kernels: S l-chunks of Lg nodes per j, G = k S
   // groups per point; shift range per j (for the clamp-free fast path)
-  int32_t S, Lg, G, pad0;
+  int32_t S, Lg, G, Lp;  // Lp = ceil(L/2) pairs; in FP32C the chunks hold Lg pairs
   int32_t smin[kMaxK], smax[kMaxK];
 };
 
@@ -66,6 +85,7 @@ struct Layout {
   size_t ringA;    // FP32C: float4 (y_hi, y_lo, z_hi, z_lo) x nslot x Nx
   size_t ringB;    // FP32C: float2 (M_y, M_z) x nslot x Nx
   size_t table;    // node table (k L entries)
+  size_t ptable;   // FP32C pair table (k ceil(L/2) entries)
   size_t stage;    // 2 x k x Nx doubles: imported initial levels / exported level 0
   size_t stats;    // Stats
   size_t total;
@@ -76,7 +96,8 @@ struct Stats {
   unsigned long long resid_bits; // max |dy| as the bits of a non-negative double
   int32_t iters_max;
   int32_t nonconv;
-  int32_t pad[2];
+  int32_t timeout;  // a bounded device-side wait gave up
+  int32_t pad;
 };
 
 // Host-side planning (bsde_host.cpp).
@@ -85,6 +106,7 @@ int fill_params(const bsde_problem &p, Params &P);
 Layout layout_for(const bsde_problem &p);
 int gauss_hermite(int L, double *nodes, double *weights);
 int gamma_tables(int k, double *gy, double *gz);
-void build_tables(Params &P, NodeF64 *t64, NodeF32 *t32);
+void build_tables(Params &P, NodeF64 *t64, NodeF32 *t32, PairF32 *tp = nullptr,
+                  int target_groups = 4, int max_groups = kMaxGroups);
 
 }  // namespace bsde

@@ -18,21 +18,37 @@ struct DrvC {
   T ca, cb, cc, cis;
 };
 
+// Every product and sum is spelled out with an explicit rounding intrinsic,
+// so no kernel that inlines a driver can contract it differently from
+// another: the single-problem, batched and served solves give bitwise equal
+// results.
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float rsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float rfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double rsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double rfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 template <int DRV, typename T>
 __device__ __forceinline__ T driver(const DrvC<T> &c, T t, T et, T emt, T y, T z) {
   // et = exp(t^2), emt = exp(-t^2): per-level constants of Example 2
   if constexpr (DRV == BSDE_DRIVER_LIN_SIN) {
-    return T(0.5) * y - z;
+    return rsub(rmul(T(0.5), y), z);
   } else if constexpr (DRV == BSDE_DRIVER_BS) {
-    return -(c.ca * y + c.cb * z);
+    return -rfma(c.ca, y, rmul(c.cb, z));
   } else if constexpr (DRV == BSDE_DRIVER_LB) {
-    T m = y - z * c.cis;
+    T m = rsub(y, rmul(z, c.cis));
     m = m < T(0) ? m : T(0);
-    return -(c.ca * y + c.cb * z) + c.cc * m;
+    return rfma(c.cc, m, -rfma(c.ca, y, rmul(c.cb, z)));
   } else if constexpr (DRV == BSDE_DRIVER_EX1) {
-    return -y * y * y + T(2.5) * y * y - T(1.5) * y;
+    const T y2 = rmul(y, y);
+    return rfma(T(-1.5), y, rfma(T(2.5), y2, -rmul(y2, y)));
   } else {
-    return T(0.5) * (et - T(4) * t * y - T(3) * exp(t * t - y * emt) + z * z * emt);
+    const T e = exp(rsub(rmul(t, t), rmul(y, emt)));
+    const T s = rfma(rmul(z, z), emt, rsub(et, rfma(T(3), e, rmul(rmul(T(4), t), y))));
+    return rmul(T(0.5), s);
   }
 }
 
@@ -107,6 +123,18 @@ __device__ __forceinline__ void split_store(float4 *A, int64_t i, double y, doub
   A[i] = make_float4(yh, yl, zh, zl);
 }
 
+// Level loads.  Within one launch of the per-level kernels the levels they
+// read are constant, so any cache path is fine; the persistent batch kernel
+// rewrites ring slots between levels from other SMs, so there (COH = true)
+// the loads go to L2 (ld.global.cg), which the cluster barrier makes current.
+template <bool COH, typename T>
+__device__ __forceinline__ T ldl(const T *p) {
+  if constexpr (COH)
+    return __ldcg(p);
+  else
+    return *p;
+}
+
 struct Ring64 {
   double4_32a *ring;
 };
@@ -122,27 +150,34 @@ __global__ void k_reset_stats(Stats *s) {
     s->resid_bits = 0ull;
     s->iters_max = 0;
     s->nonconv = 0;
+    s->timeout = 0;
   }
 }
 
 // initial level N - m from the closed form
+// point i of initial level N - m from the closed form
 template <int PREC>
-__global__ void k_init_closed(const Params P, Ring64 r64, Ring32 r32, int m) {
+__device__ __forceinline__ void init_point(const Params &P, Ring64 r64, Ring32 r32, int m,
+                                           int64_t i) {
   const int level = P.N - m;
   const int64_t off = int64_t(level % P.nslot) * P.Nx;
   const double t = level * P.dt;
   const bool smooth = (m == 0) && P.smoothing && P.terminal == BSDE_TERMINAL_CALL_LOG;
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < P.Nx;
-       i += int64_t(gridDim.x) * blockDim.x) {
-    const double x = P.x_min + double(i) * P.dx;
-    double u, z;
-    closed_form(P, t, x, smooth, u, z);
-    if (PREC == BSDE_FP64) {
-      r64.ring[off + i] = make_double4_32a(u, 0.0, z, 0.0);
-    } else {
-      split_store(r32.A + off, i, u, z);
-    }
+  const double x = P.x_min + double(i) * P.dx;
+  double u, z;
+  closed_form(P, t, x, smooth, u, z);
+  if (PREC == BSDE_FP64) {
+    r64.ring[off + i] = make_double4_32a(u, 0.0, z, 0.0);
+  } else {
+    split_store(r32.A + off, i, u, z);
   }
+}
+
+template <int PREC>
+__global__ void k_init_closed(const Params P, Ring64 r64, Ring32 r32, int m) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < P.Nx;
+       i += int64_t(gridDim.x) * blockDim.x)
+    init_point<PREC>(P, r64, r32, m, i);
 }
 
 // initial level N - m imported from the staging area (row m of y, row m of z)
@@ -209,38 +244,42 @@ struct SplineT<BSDE_FP32C> {
   static constexpr int W = 16;
 };
 
-template <int PREC>
-__global__ void __launch_bounds__(kSplineTile / kSplineChunk)
-    k_spline(const Params P, Ring64 r64, Ring32 r32, int slot) {
+// One tile of TS unknowns of the level in `slot`, by the threads tid < nt of
+// the CTA (all threads of the CTA must call it: it holds barriers).
+// sr, sg: [2][TS + 2W] and sid: [kInvPivots] in shared memory; sid must hold
+// the pivots 1/d_m in T before the call.
+template <int PREC, int TS, bool COH = false>
+__device__ __forceinline__ void spline_tile(const Params &P, Ring64 r64, Ring32 r32, int slot,
+                                            int tile, int nt,
+                                            typename SplineT<PREC>::T (*sr)[TS + 2 * SplineT<PREC>::W],
+                                            typename SplineT<PREC>::T (*sg)[TS + 2 * SplineT<PREC>::W],
+                                            const typename SplineT<PREC>::T *sid) {
   using T = typename SplineT<PREC>::T;
   constexpr int W = SplineT<PREC>::W;
-  constexpr int TS = kSplineTile, C = kSplineChunk;
-  // r and g over the unknowns [a - W, b + W), stored at index m - (a - W)
-  __shared__ T sr[2][TS + 2 * W];
-  __shared__ T sg[2][TS + 2 * W];
-  __shared__ T sid[kInvPivots];
+  constexpr int C = kSplineChunk;
   const int u = int(P.Nx - 2);
-  const int a = blockIdx.x * TS;
+  const int a = tile * TS;
   const int b = a + TS < u ? a + TS : u;
   const int ra = a - W > 0 ? a - W : 0;
   const int rb = b + W < u ? b + W : u;
   const int base = a - W;
   const int64_t off = int64_t(slot) * P.Nx;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  if (tid < kInvPivots) sid[tid] = T(P.invd[tid]);
+  const int tid = threadIdx.x;
+  if (a >= u) return;  // uniform over the CTA
 
   // right-hand sides
-  for (int m = ra + tid; m < rb; m += nt) {
+  for (int m = ra + tid; m < rb && tid < nt; m += nt) {
     T ry, rz;
     if constexpr (PREC == BSDE_FP64) {
-      const double4_32a v0 = r64.ring[off + m], v1 = r64.ring[off + m + 1],
-                        v2 = r64.ring[off + m + 2];
+      const double4_32a v0 = ldl<COH>(r64.ring + off + m), v1 = ldl<COH>(r64.ring + off + m + 1),
+                        v2 = ldl<COH>(r64.ring + off + m + 2);
       ry = P.inv_dx2_6 * (v0.x - 2.0 * v1.x + v2.x);
       rz = P.inv_dx2_6 * (v0.z - 2.0 * v1.z + v2.z);
     } else {
       // (hi, lo) pairs: neighbouring hi values differ exactly (Sterbenz) away
       // from sign changes, so the second difference keeps the pair precision
-      const float4 v0 = r32.A[off + m], v1 = r32.A[off + m + 1], v2 = r32.A[off + m + 2];
+      const float4 v0 = ldl<COH>(r32.A + off + m), v1 = ldl<COH>(r32.A + off + m + 1),
+                   v2 = ldl<COH>(r32.A + off + m + 2);
       const float inv6 = float(P.inv_dx2_6);
       const float d1y = __fadd_rn(__fsub_rn(v1.x, v0.x), __fsub_rn(v1.y, v0.y));
       const float d2y = __fadd_rn(__fsub_rn(v2.x, v1.x), __fsub_rn(v2.y, v1.y));
@@ -255,7 +294,7 @@ __global__ void __launch_bounds__(kSplineTile / kSplineChunk)
   __syncthreads();
 
   // forward sweep over the chunks of [a, rb): the tile and its right halo
-  for (int s0 = a + tid * C; s0 < rb; s0 += nt * C) {
+  for (int s0 = a + tid * C; s0 < rb && tid < nt; s0 += nt * C) {
     const int e = s0 + C < rb ? s0 + C : rb;
     const int st = s0 - W > 0 ? s0 - W : 0;
     T gy = T(0), gz = T(0);
@@ -272,7 +311,7 @@ __global__ void __launch_bounds__(kSplineTile / kSplineChunk)
   __syncthreads();
 
   // backward sweep over the chunks of the tile, warm-up from the right
-  for (int s0 = a + tid * C; s0 < b; s0 += nt * C) {
+  for (int s0 = a + tid * C; s0 < b && tid < nt; s0 += nt * C) {
     const int e = s0 + C < b ? s0 + C : b;
     const int top = e + W < u ? e + W : u;
     T my = T(0), mz = T(0);
@@ -290,7 +329,7 @@ __global__ void __launch_bounds__(kSplineTile / kSplineChunk)
       }
     }
   }
-  if (blockIdx.x == 0 && tid == 0) {
+  if (tile == 0 && tid == 0) {
     // natural end conditions M_0 = M_{Nx-1} = 0
     if constexpr (PREC == BSDE_FP64) {
       r64.ring[off].y = 0.0;
@@ -302,6 +341,19 @@ __global__ void __launch_bounds__(kSplineTile / kSplineChunk)
       r32.B[off + P.Nx - 1] = make_float2(0.f, 0.f);
     }
   }
+}
+
+
+template <int PREC>
+__global__ void __launch_bounds__(kSplineTile / kSplineChunk)
+    k_spline(const Params P, Ring64 r64, Ring32 r32, int slot) {
+  using T = typename SplineT<PREC>::T;
+  constexpr int W = SplineT<PREC>::W;
+  __shared__ T sr[2][kSplineTile + 2 * W];
+  __shared__ T sg[2][kSplineTile + 2 * W];
+  __shared__ T sid[kInvPivots];
+  if (threadIdx.x < kInvPivots) sid[threadIdx.x] = T(P.invd[threadIdx.x]);
+  spline_tile<PREC, kSplineTile>(P, r64, r32, slot, blockIdx.x, blockDim.x, sr, sg, sid);
 }
 
 // ---------------------------------------------------------------------------
@@ -462,90 +514,254 @@ __device__ __forceinline__ void two_sum_into(float &S, float &C, float x) {
   S = s;
 }
 
-// One group's nodes.  Table entry as three float4: (shift, w0, w1, w2),
-// (w3, czh, czl, cfz), (cfy, cyh, cyl, -).  With theta = w1 the spline value
-// is hi_c + del, del = theta (dhi + dlo) + lo_c + w2 M_c + w3 M_{c+1}; where
-// y only feeds the FP32 driver (j < k) its lo part is left out.
-template <int DRV, bool CLAMP, bool LASTJ>
-__device__ __forceinline__ void nodes32(const DrvC<float> &dc, const float4 *__restrict__ A,
-                                        const float2 *__restrict__ B, const NodeF32 *row, int l0,
-                                        int l1, int ii, int last, float tj, float et, float emt,
-                                        float &Sz, float &Cz, float &Fz, float &Fy, float &Sy,
-                                        float &Cy) {
-#pragma unroll 4
-  for (int l = l0; l < l1; ++l) {
-    const float4 *te = reinterpret_cast<const float4 *>(row + l);
-    const float4 e0 = te[0], e1 = te[1], e2 = te[2];
-    float w1 = e0.z, w2 = e0.w, w3 = e1.x;
-    int c0 = ii + __float_as_int(e0.x), c1 = c0 + 1;
-    if (CLAMP) {
-      const bool cl = c0 < 0, ch = c0 >= last;
-      if (cl | ch) {
-        c0 = cl ? 0 : last;
-        c1 = c0;
-        w1 = 0.f;
-        w2 = 0.f;
-        w3 = 0.f;
-      }
+// ---------------------------------------------------------------------------
+// Bulk-copy (TMA) helpers: 1-D cp.async.bulk into shared memory, completion
+// tracked by an mbarrier with an expected byte count.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes,
+                                          uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for a phase of a bulk-copy barrier, at most ~2 s: false if it did not
+// complete (the caller records the failure and carries on; nothing hangs).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (!mbar_try(bar, parity))
+    if (global_ns() - t0 > 2000000000ull) return false;
+  return true;
+}
+__device__ __forceinline__ void group_sync(int g) {
+  asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(kStepTP) : "memory");
+}
+
+// Spline value of one node as hi_c + del (see PairF32 for the layout).
+template <bool CLAMP>
+__device__ __forceinline__ void pair_cells(int ii, int shift, int last, int &c0, int &c1,
+                                           float &w1, float &w2, float &w3) {
+  c0 = ii + shift;
+  c1 = c0 + 1;
+  if (CLAMP) {
+    const bool cl = c0 < 0, ch = c0 >= last;
+    if (cl | ch) {
+      c0 = cl ? 0 : last;
+      c1 = c0;
+      w1 = 0.f;
+      w2 = 0.f;
+      w3 = 0.f;
     }
-    const float4 a = A[c0], b = A[c1];
-    const float2 ma = B[c0], mb = B[c1];
-    const float mz = __fmaf_rn(w2, ma.y, w3 * mb.y);
-    const float zdel = __fadd_rn(
-        __fmaf_rn(w1, __fadd_rn(__fsub_rn(b.z, a.z), __fsub_rn(b.w, a.w)), a.w), mz);
-    const float my = __fmaf_rn(w2, ma.x, w3 * mb.x);
-    float yf, ydel = 0.f;
-    if (LASTJ) {
-      ydel = __fadd_rn(__fmaf_rn(w1, __fadd_rn(__fsub_rn(b.x, a.x), __fsub_rn(b.y, a.y)), a.y), my);
-      yf = a.x + ydel;
-    } else {
-      yf = a.x + __fmaf_rn(w1, __fsub_rn(b.x, a.x), my);
-    }
-    const float zf = a.z + zdel;
-    const float F = driver<DRV>(dc, tj, et, emt, yf, zf);
-    Fz = __fmaf_rn(e1.w, F, Fz);
-    Fy = __fmaf_rn(e2.x, F, Fy);
-    comp_acc(Sz, Cz, e1.y, e1.z, a.z, zdel);
-    if (LASTJ) comp_acc(Sy, Cy, e2.y, e2.z, a.x, ydel);
   }
 }
 
+// One group's node pairs (l, L-1-l).  z^ = hi_c + del with
+// del = theta (dhi + dlo) + lo_c + w2 M_c + w3 M_{c+1}; where y only feeds
+// the FP32 driver (j < k) its lo part is left out.
+// The arithmetic of one node pair, given the two cells' level data.
 template <int DRV, bool LASTJ>
-__device__ __forceinline__ void nodes32_any(bool interior, const DrvC<float> &dc,
+__device__ __forceinline__ void pair_math(const DrvC<float> &dc, float tj, float et, float emt,
+                                          float w1a, float w2a, float w3a, float w1b, float w2b,
+                                          float w3b, const float4 &aa, const float4 &ab,
+                                          const float4 &ba, const float4 &bb, const float2 &maa,
+                                          const float2 &mab, const float2 &mba, const float2 &mbb,
+                                          const float4 &e2, const float4 &e3, float &Sz, float &Cz,
+                                          float &Fz, float &Fy, float &Sy, float &Cy) {
+  const float zda = __fadd_rn(
+      __fmaf_rn(w1a, __fadd_rn(__fsub_rn(ab.z, aa.z), __fsub_rn(ab.w, aa.w)), aa.w),
+      __fmaf_rn(w2a, maa.y, w3a * mab.y));
+  const float zdb = __fadd_rn(
+      __fmaf_rn(w1b, __fadd_rn(__fsub_rn(bb.z, ba.z), __fsub_rn(bb.w, ba.w)), ba.w),
+      __fmaf_rn(w2b, mba.y, w3b * mbb.y));
+  const float mya = __fmaf_rn(w2a, maa.x, w3a * mab.x);
+  const float myb = __fmaf_rn(w2b, mba.x, w3b * mbb.x);
+  float yfa, yfb, yda = 0.f, ydb = 0.f;
+  if (LASTJ) {
+    yda = __fadd_rn(__fmaf_rn(w1a, __fadd_rn(__fsub_rn(ab.x, aa.x), __fsub_rn(ab.y, aa.y)), aa.y), mya);
+    ydb = __fadd_rn(__fmaf_rn(w1b, __fadd_rn(__fsub_rn(bb.x, ba.x), __fsub_rn(bb.y, ba.y)), ba.y), myb);
+    yfa = aa.x + yda;
+    yfb = ba.x + ydb;
+  } else {
+    yfa = aa.x + __fmaf_rn(w1a, __fsub_rn(ab.x, aa.x), mya);
+    yfb = ba.x + __fmaf_rn(w1b, __fsub_rn(bb.x, ba.x), myb);
+  }
+  const float Fa = driver<DRV>(dc, tj, et, emt, yfa, aa.z + zda);
+  const float Fb = driver<DRV>(dc, tj, et, emt, yfb, ba.z + zdb);
+  Fz = __fmaf_rn(e2.z, __fsub_rn(Fa, Fb), Fz);
+  Fy = __fmaf_rn(e2.w, __fadd_rn(Fa, Fb), Fy);
+  // z: the pair's hi parts summed exactly, then one compensated product
+  {
+    const float s = __fadd_rn(aa.z, ba.z);
+    const float bp = __fsub_rn(s, aa.z);
+    const float e1s = __fadd_rn(__fsub_rn(aa.z, __fsub_rn(s, bp)), __fsub_rn(ba.z, bp));
+    comp_acc(Sz, Cz, e2.x, e2.y, s, __fadd_rn(__fadd_rn(zda, zdb), e1s));
+  }
+  if (LASTJ) {
+    const float s = __fadd_rn(aa.x, ba.x);
+    const float bp = __fsub_rn(s, aa.x);
+    const float e1s = __fadd_rn(__fsub_rn(aa.x, __fsub_rn(s, bp)), __fsub_rn(ba.x, bp));
+    comp_acc(Sy, Cy, e3.x, e3.y, s, __fadd_rn(__fadd_rn(yda, ydb), e1s));
+  }
+}
+
+// One group's node pairs (l, L-1-l), level data loaded directly from global
+// memory (L1/L2).  z^ = hi_c + del with del = theta (dhi + dlo) + lo_c +
+// w2 M_c + w3 M_{c+1}; where y only feeds the FP32 driver (j < k) its lo part
+// is left out.
+template <int DRV, bool CLAMP, bool LASTJ, bool COH>
+__device__ __forceinline__ void pairs32(const DrvC<float> &dc, const float4 *__restrict__ A,
+                                        const float2 *__restrict__ B, const PairF32 *row, int q0,
+                                        int q1, int ii, int last, float tj, float et, float emt,
+                                        float &Sz, float &Cz, float &Fz, float &Fy, float &Sy,
+                                        float &Cy) {
+#pragma unroll 2
+  for (int q = q0; q < q1; ++q) {
+    const float4 *te = reinterpret_cast<const float4 *>(row + q);
+    const float4 e0 = te[0], e1 = te[1], e2 = te[2];
+    const float4 e3 = LASTJ ? te[3] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float w1a = e0.z, w2a = e1.x, w3a = e1.y;
+    float w1b = e0.w, w2b = e1.z, w3b = e1.w;
+    int ca0, ca1, cb0, cb1;
+    pair_cells<CLAMP>(ii, __float_as_int(e0.x), last, ca0, ca1, w1a, w2a, w3a);
+    pair_cells<CLAMP>(ii, __float_as_int(e0.y), last, cb0, cb1, w1b, w2b, w3b);
+    const float4 aa = ldl<COH>(A + ca0), ab = ldl<COH>(A + ca1), ba = ldl<COH>(A + cb0),
+                 bb = ldl<COH>(A + cb1);
+    const float2 maa = ldl<COH>(B + ca0), mab = ldl<COH>(B + ca1), mba = ldl<COH>(B + cb0),
+                 mbb = ldl<COH>(B + cb1);
+    pair_math<DRV, LASTJ>(dc, tj, et, emt, w1a, w2a, w3a, w1b, w2b, w3b, aa, ab, ba, bb, maa, mab,
+                          mba, mbb, e2, e3, Sz, Cz, Fz, Fy, Sy, Cy);
+  }
+}
+
+// The same for an interior tile, with the level windows brought into shared
+// memory by bulk copies kTmaStages pairs ahead of use.  For the pair of nodes
+// the window of each node is the kStepTP + 1 cells i0 + shift .. i0 + shift +
+// kStepTP of the level (A: 16-byte records, aligned) and, for B (8-byte
+// records), the same cells from the 16-byte boundary at or below the first.
+// Thread tp == 0 of the group issues the copies; a group barrier after each
+// pair frees its buffer.  Called by all kStepTP threads of group g.
+template <int DRV, bool LASTJ>
+__device__ __forceinline__ void pairs32_tma(const DrvC<float> &dc, const float4 *__restrict__ A,
+                                            const float2 *__restrict__ B, int64_t lev_elem,
+                                            const PairF32 *row, int q0, int q1, int i0, int tp,
+                                            int g, float tj, float et, float emt,
+                                            unsigned char *stage, uint64_t *full, Stats *st,
+                                            float &Sz, float &Cz, float &Fz, float &Fy,
+                                            float &Sy, float &Cy) {
+  const int np = q1 - q0;
+  auto issue = [&](int t) {
+    const PairF32 &e = row[q0 + t];
+    const int buf = t % kTmaStages;
+    unsigned char *d = stage + buf * kStageBytes;
+    const int ca = i0 + e.shift_a, cb = i0 + e.shift_b;
+    const int pa = int((lev_elem + ca) & 1), pb = int((lev_elem + cb) & 1);
+    mbar_expect_tx(full + buf, kStageBytes);
+    bulk_load(d, A + ca, kWinA, full + buf);
+    bulk_load(d + kWinA, A + cb, kWinA, full + buf);
+    bulk_load(d + 2 * kWinA, B + (ca - pa), kWinB, full + buf);
+    bulk_load(d + 2 * kWinA + kWinB, B + (cb - pb), kWinB, full + buf);
+  };
+  if (tp == 0)
+    for (int t = 0; t < np && t < kTmaStages; ++t) issue(t);
+  bool lost = false;
+  for (int t = 0; t < np; ++t) {
+    const int buf = t % kTmaStages;
+    if (!mbar_wait(full + buf, uint32_t((t / kTmaStages) & 1))) lost = true;
+    const float4 *te = reinterpret_cast<const float4 *>(row + q0 + t);
+    const float4 e0 = te[0], e1 = te[1], e2 = te[2];
+    const float4 e3 = LASTJ ? te[3] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int pa = int((lev_elem + i0 + __float_as_int(e0.x)) & 1);
+    const int pb = int((lev_elem + i0 + __float_as_int(e0.y)) & 1);
+    const unsigned char *d = stage + buf * kStageBytes;
+    const float4 *sa = reinterpret_cast<const float4 *>(d);
+    const float4 *sb = reinterpret_cast<const float4 *>(d + kWinA);
+    const float2 *ma = reinterpret_cast<const float2 *>(d + 2 * kWinA) + pa;
+    const float2 *mb = reinterpret_cast<const float2 *>(d + 2 * kWinA + kWinB) + pb;
+    pair_math<DRV, LASTJ>(dc, tj, et, emt, e0.z, e1.x, e1.y, e0.w, e1.z, e1.w, sa[tp], sa[tp + 1],
+                          sb[tp], sb[tp + 1], ma[tp], ma[tp + 1], mb[tp], mb[tp + 1], e2, e3, Sz,
+                          Cz, Fz, Fy, Sy, Cy);
+    group_sync(g);
+    if (tp == 0 && t + kTmaStages < np) {
+      // the buffer was read through the generic proxy: order those reads
+      // before the async-proxy writes of the next copy
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(t + kTmaStages);
+    }
+  }
+  if (lost) {
+    atomicOr(&st->timeout, 1);
+    // let any copy still in flight land before the buffers go away (bounded)
+    for (int t = np > kTmaStages ? np - kTmaStages : 0; t < np; ++t)
+      mbar_wait(full + t % kTmaStages, uint32_t((t / kTmaStages) & 1));
+  }
+}
+
+template <int DRV, bool LASTJ, bool COH>
+__device__ __forceinline__ void pairs32_any(bool interior, const DrvC<float> &dc,
                                             const float4 *__restrict__ A,
-                                            const float2 *__restrict__ B, const NodeF32 *row,
-                                            int l0, int l1, int ii, int last, float tj, float et,
+                                            const float2 *__restrict__ B, const PairF32 *row,
+                                            int q0, int q1, int ii, int last, float tj, float et,
                                             float emt, float &Sz, float &Cz, float &Fz, float &Fy,
                                             float &Sy, float &Cy) {
   if (interior)
-    nodes32<DRV, false, LASTJ>(dc, A, B, row, l0, l1, ii, last, tj, et, emt, Sz, Cz, Fz, Fy, Sy, Cy);
+    pairs32<DRV, false, LASTJ, COH>(dc, A, B, row, q0, q1, ii, last, tj, et, emt, Sz, Cz, Fz, Fy,
+                                    Sy, Cy);
   else
-    nodes32<DRV, true, LASTJ>(dc, A, B, row, l0, l1, ii, last, tj, et, emt, Sz, Cz, Fz, Fy, Sy, Cy);
+    pairs32<DRV, true, LASTJ, COH>(dc, A, B, row, q0, q1, ii, last, tj, et, emt, Sz, Cz, Fz, Fy,
+                                   Sy, Cy);
 }
 
-template <int DRV>
-__global__ void __launch_bounds__(kStepTP * kMaxGroups)
-    k_step32(const Params P, const DrvC<float> dc, float4 *__restrict__ ringA,
-             const float2 *__restrict__ ringB, const NodeF32 *__restrict__ table, int n,
-             Stats *st) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int kL = P.k * P.L;
-  NodeF32 *tab = reinterpret_cast<NodeF32 *>(smem_raw);
-  float *part = reinterpret_cast<float *>(smem_raw + sizeof(NodeF32) * kL);  // [6][G][TP]
-  {
-    const float4 *src = reinterpret_cast<const float4 *>(table);
-    float4 *dst = reinterpret_cast<float4 *>(tab);
-    for (int t = threadIdx.x; t < kL * 3; t += blockDim.x) dst[t] = src[t];
-  }
-  __syncthreads();
-
+// One tile of kStepTP points of level n, called by every thread of the CTA;
+// `tab` (the pair table of the problem) and `part` are in shared memory.
+// Threads of groups g >= G idle.  The caller separates consecutive tiles by
+// a barrier (part is reused).
+template <int DRV, bool TMA, bool COH>
+__device__ __forceinline__ void step_tile32(const Params &P, const DrvC<float> &dc,
+                                            float4 *__restrict__ ringA,
+                                            const float2 *__restrict__ ringB,
+                                            const PairF32 *tab, float *part, int n, int i0,
+                                            Stats *st, unsigned char *stages = nullptr,
+                                            uint64_t *bars = nullptr) {
   const int tp = threadIdx.x % kStepTP, g = threadIdx.x / kStepTP;
-  const int j = g / P.S + 1, lc = g % P.S;
-  const int l0 = lc * P.Lg, l1 = l0 + P.Lg < P.L ? l0 + P.Lg : P.L;
-  const int i0 = blockIdx.x * kStepTP, ii = i0 + tp;
+  const int G = P.G;
   const int last = int(P.Nx - 1);
-  float Sz = 0.f, Cz = 0.f, Fz = 0.f, Fy = 0.f, Sy = 0.f, Cy = 0.f;
-  if (ii <= last) {
+  const int ii = i0 + tp;
+  if (g < G) {
+    const int j = g / P.S + 1, lc = g % P.S;
+    const int q0 = lc * P.Lg, q1 = q0 + P.Lg < P.Lp ? q0 + P.Lg : P.Lp;
+    float Sz = 0.f, Cz = 0.f, Fz = 0.f, Fy = 0.f, Sy = 0.f, Cy = 0.f;
     const int64_t off = int64_t((n + j) % P.nslot) * P.Nx;
     const double tjd = (n + j) * P.dt;
     const float tj = float(tjd);
@@ -554,22 +770,34 @@ __global__ void __launch_bounds__(kStepTP * kMaxGroups)
       et = float(exp(tjd * tjd));
       emt = float(exp(-tjd * tjd));
     }
-    const NodeF32 *row = tab + (j - 1) * P.L;
+    const PairF32 *row = tab + (j - 1) * P.Lp;
     const bool interior = i0 + P.smin[j - 1] >= 0 && i0 + kStepTP + P.smax[j - 1] <= last;
-    if (j == P.k)
-      nodes32_any<DRV, true>(interior, dc, ringA + off, ringB + off, row, l0, l1, ii, last, tj,
-                             et, emt, Sz, Cz, Fz, Fy, Sy, Cy);
-    else
-      nodes32_any<DRV, false>(interior, dc, ringA + off, ringB + off, row, l0, l1, ii, last, tj,
-                              et, emt, Sz, Cz, Fz, Fy, Sy, Cy);
+    if (TMA && interior) {
+      // every thread of the group takes part (barriers inside)
+      unsigned char *stg = stages + size_t(g) * kTmaStages * kStageBytes;
+      uint64_t *bar = bars + g * kTmaStages;
+      if (j == P.k)
+        pairs32_tma<DRV, true>(dc, ringA + off, ringB + off, off, row, q0, q1, i0, tp, g, tj, et,
+                               emt, stg, bar, st, Sz, Cz, Fz, Fy, Sy, Cy);
+      else
+        pairs32_tma<DRV, false>(dc, ringA + off, ringB + off, off, row, q0, q1, i0, tp, g, tj, et,
+                                emt, stg, bar, st, Sz, Cz, Fz, Fy, Sy, Cy);
+      if (ii > last) Sz = Cz = Fz = Fy = Sy = Cy = 0.f;
+    } else if (ii <= last) {
+      if (j == P.k)
+        pairs32_any<DRV, true, COH>(interior, dc, ringA + off, ringB + off, row, q0, q1, ii, last,
+                                    tj, et, emt, Sz, Cz, Fz, Fy, Sy, Cy);
+      else
+        pairs32_any<DRV, false, COH>(interior, dc, ringA + off, ringB + off, row, q0, q1, ii,
+                                     last, tj, et, emt, Sz, Cz, Fz, Fy, Sy, Cy);
+    }
+    part[(0 * G + g) * kStepTP + tp] = Sz;
+    part[(1 * G + g) * kStepTP + tp] = Cz;
+    part[(2 * G + g) * kStepTP + tp] = Fz;
+    part[(3 * G + g) * kStepTP + tp] = Fy;
+    part[(4 * G + g) * kStepTP + tp] = Sy;
+    part[(5 * G + g) * kStepTP + tp] = Cy;
   }
-  const int G = P.G;
-  part[(0 * G + g) * kStepTP + tp] = Sz;
-  part[(1 * G + g) * kStepTP + tp] = Cz;
-  part[(2 * G + g) * kStepTP + tp] = Fz;
-  part[(3 * G + g) * kStepTP + tp] = Fy;
-  part[(4 * G + g) * kStepTP + tp] = Sy;
-  part[(5 * G + g) * kStepTP + tp] = Cy;
   __syncthreads();
   if (g != 0) return;
 
@@ -605,7 +833,7 @@ __global__ void __launch_bounds__(kStepTP * kMaxGroups)
     // increments are within a factor two, so their float difference carries
     // no rounding).  A two-cycle across a rounding boundary of the FP32
     // argument is as far as the FP32 driver can resolve, and ends it too.
-    const float4 prev = ringA[int64_t((n + 1) % P.nslot) * P.Nx + ii];
+    const float4 prev = ldl<COH>(ringA + int64_t((n + 1) % P.nslot) * P.Nx + ii);
     float dl = __fsub_rn(prev.x, Ayf), dpp = __int_as_float(0x7fc00000);
     while (it < P.picard_max) {
       const float dn = hg0 * driver<DRV>(dc, tn, etn, emtn, Ayf + dl, zf);
@@ -623,12 +851,46 @@ __global__ void __launch_bounds__(kStepTP * kMaxGroups)
   record_picard(st, active, it, d, P.picard_tol);
 }
 
+// Shared memory of k_step32: bulk-copy stages (G x kTmaStages x kStageBytes),
+// their barriers, the pair table, the groups' partial sums.
+__host__ __device__ inline size_t step32_bar_bytes(int G) {
+  return (size_t(G) * kTmaStages * 8 + 127) & ~size_t(127);
+}
+__host__ __device__ inline size_t step32_smem(int G, int kP) {
+  return size_t(G) * kTmaStages * kStageBytes + step32_bar_bytes(G) +
+         sizeof(PairF32) * size_t(kP) + sizeof(float) * 6 * size_t(G) * kStepTP;
+}
+
+template <int DRV>
+__global__ void __launch_bounds__(kStepTP * kMaxGroups)
+    k_step32(const Params P, const DrvC<float> dc, float4 *__restrict__ ringA,
+             const float2 *__restrict__ ringB, const PairF32 *__restrict__ table, int n,
+             Stats *st) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int kP = P.k * P.Lp;
+  unsigned char *stages = smem_raw;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + size_t(P.G) * kTmaStages * kStageBytes);
+  PairF32 *tab = reinterpret_cast<PairF32 *>(reinterpret_cast<unsigned char *>(bars) +
+                                             step32_bar_bytes(P.G));
+  float *part = reinterpret_cast<float *>(tab + kP);  // [6][G][TP]
+  {
+    const float4 *src = reinterpret_cast<const float4 *>(table);
+    float4 *dst = reinterpret_cast<float4 *>(tab);
+    for (int t = threadIdx.x; t < kP * 4; t += blockDim.x) dst[t] = src[t];
+  }
+  if (threadIdx.x < P.G * kTmaStages) mbar_init(bars + threadIdx.x, 1);
+  fence_barrier_init();
+  __syncthreads();
+  step_tile32<DRV, true, false>(P, dc, ringA, ringB, tab, part, n, blockIdx.x * kStepTP, st, stages,
+                                bars);
+}
+
 // ---------------------------------------------------------------------------
 // S4: readout of y^0, z^0 at x0 by the spline (Section 3.1 step 3).
 // ---------------------------------------------------------------------------
-template <int PREC>
-__global__ void k_readout(const Params P, Ring64 r64, Ring32 r32, int slot, Stats *st) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+template <int PREC, bool COH = false>
+__device__ void readout_values(const Params &P, Ring64 r64, Ring32 r32, int slot, double &ay,
+                               double &az) {
   const int64_t off = int64_t(slot) * P.Nx;
   const double s = (P.x0 - P.x_min) / P.dx;
   int64_t c = (int64_t)floor(s);
@@ -645,21 +907,28 @@ __global__ void k_readout(const Params P, Ring64 r64, Ring32 r32, int slot, Stat
     th = s - double(c);
   }
   for (int q = 0; q < 2; ++q) {
-    if (PREC == BSDE_FP64) {
-      const double4_32a a = r64.ring[off + c + q];
+    if constexpr (PREC == BSDE_FP64) {
+      const double4_32a a = ldl<COH>(r64.ring + off + c + q);
       v[0][q] = a.x; M[0][q] = a.y; v[1][q] = a.z; M[1][q] = a.w;
     } else {
-      const float4 a = r32.A[off + c + q];
-      const float2 b = r32.B[off + c + q];
+      const float4 a = ldl<COH>(r32.A + off + c + q);
+      const float2 b = ldl<COH>(r32.B + off + c + q);
       v[0][q] = double(a.x) + double(a.y); M[0][q] = b.x;
       v[1][q] = double(a.z) + double(a.w); M[1][q] = b.y;
     }
   }
   const double om = 1.0 - th, c6 = P.dx * P.dx / 6.0;
-  const double ay = om * v[0][0] + th * v[0][1] +
-                    c6 * ((om * om * om - om) * M[0][0] + (th * th * th - th) * M[0][1]);
-  const double az = om * v[1][0] + th * v[1][1] +
-                    c6 * ((om * om * om - om) * M[1][0] + (th * th * th - th) * M[1][1]);
+  ay = om * v[0][0] + th * v[0][1] +
+       c6 * ((om * om * om - om) * M[0][0] + (th * th * th - th) * M[0][1]);
+  az = om * v[1][0] + th * v[1][1] +
+       c6 * ((om * om * om - om) * M[1][0] + (th * th * th - th) * M[1][1]);
+}
+
+template <int PREC>
+__global__ void k_readout(const Params P, Ring64 r64, Ring32 r32, int slot, Stats *st) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double ay, az;
+  readout_values<PREC>(P, r64, r32, slot, ay, az);
   st->y0 = ay;
   st->z0 = az;
 }

@@ -1,0 +1,124 @@
+"""Batched solves (one persistent launch for many uneven problems) against
+single solves and the oracle."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1909_13560_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+THREADS = max(1, os.cpu_count() or 1)
+TOL32 = 2e-7
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1909_13560_gb300 import bsde
+    bsde.load()
+    return bsde
+
+
+def _mixed(count=40, seed=7):
+    """Uneven problems: the config4 recipe at smaller sizes, plus
+    lending/borrowing calls and the paper's two nonlinear examples."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        kind = i % 5
+        k = int(rng.integers(1, 7))
+        N = int(8 << int(rng.integers(0, 3)))
+        k = min(k, N)
+        Nx = int(rng.integers(200, 3000))
+        if kind <= 1:
+            out.append(W.call_problem(strike=float(rng.uniform(70, 130)),
+                                      sigma=float(rng.uniform(0.1, 0.5)),
+                                      T=float(rng.uniform(0.25, 2.0)),
+                                      r=float(rng.uniform(0.0, 0.05)), Nx=Nx, N=N, k=k, L=16))
+        elif kind == 2:
+            out.append(W.call_problem(strike=100.0, sigma=0.2, T=0.5, r=0.04, R=0.06, mu=0.06,
+                                      Nx=Nx, N=N, k=k, L=16, driver="LB"))
+        elif kind == 3:
+            out.append(W.ex1_problem(Nx=Nx, N=N, k=k, L=12, x_lim=8.0))
+        else:
+            out.append(W.ex2_problem(Nx=Nx, N=N, k=k, L=12, x_lim=8.0))
+    return out
+
+
+def test_batch_equals_single_solves(B):
+    probs = _mixed()
+    bs = B.BatchSolver(probs)
+    res = bs.solve()
+    bs.close()
+    for p, r in zip(probs, res):
+        s = B.solve(p, "fp32c")
+        assert r["y0"] == s["y0"] and r["z0"] == s["z0"], (p["driver"], p["Nx"], p["N"], p["k"])
+        assert r["status"] == s["status"]
+
+
+def test_batch_alone_equals_in_the_mix(B):
+    probs = _mixed(count=30, seed=11)
+    mix = B.BatchSolver(probs)
+    res = mix.solve()
+    mix.close()
+    for i in (0, 7, 19, 29):
+        one = B.BatchSolver([probs[i]])
+        r1 = one.solve()[0]
+        one.close()
+        assert r1["y0"] == res[i]["y0"] and r1["z0"] == res[i]["z0"]
+
+
+@pytest.mark.parametrize("cluster,groups", [(1, 4), (4, 4), (8, 2), (2, 6)])
+def test_batch_configs_agree_with_oracle(B, cluster, groups):
+    probs = _mixed(count=12, seed=3)
+    bs = B.BatchSolver(probs)
+    bs.set_config(cluster, groups)
+    assert bs.config() == {"cluster": cluster, "target_groups": groups}
+    res = bs.solve()
+    bs.close()
+    for p, r in zip(probs, res):
+        ref = O.solve(p, threads=THREADS, want_level=True)
+        scale = max(1.0, float(np.max(np.abs(ref["y"]))))
+        zscale = max(1.0, float(np.max(np.abs(ref["z"]))))
+        assert abs(r["y0"] - ref["y0"]) <= TOL32 * scale, (p["driver"], r["y0"], ref["y0"])
+        assert abs(r["z0"] - ref["z0"]) <= TOL32 * zscale, (p["driver"], r["z0"], ref["z0"])
+
+
+def test_batch_autotune_picks_a_valid_config(B):
+    probs = _mixed(count=20, seed=5)
+    bs = B.BatchSolver(probs)
+    before = bs.solve()
+    best = bs.autotune()
+    assert best["cluster"] in (1, 2, 4, 8) and best["target_groups"] in (2, 4, 6)
+    assert bs.config() == best
+    after = bs.solve()
+    bs.close()
+    for a, b in zip(before, after):
+        assert abs(a["y0"] - b["y0"]) <= 1e-6 * max(1.0, abs(a["y0"]))
+
+
+def test_batch_rejects_fp64_problems(B):
+    with pytest.raises(B.BsdeError) as ei:
+        B.bsde_batch_workspace_bytes([W.sin_problem()], "fp64")
+    assert ei.value.code == B.BSDE_EINVAL
+
+
+def test_config4_sample_matches_closed_form(B):
+    """A seeded sample of the 4096-instance Black-Scholes batch: every price
+    within the scheme's accuracy of the closed form."""
+    probs = W.config4(count=64)
+    bs = B.BatchSolver(probs)
+    res = bs.solve()
+    bs.close()
+    errs = []
+    for p, r in zip(probs, res):
+        u, _ = O.exact(p, 0.0, p["x0"])
+        errs.append(abs(r["y0"] - u))
+    errs = np.array(errs)
+    print("config4 sample |y0 - exact|: median %.2e max %.2e" % (np.median(errs), errs.max()))
+    assert np.all(np.isfinite(errs))

@@ -1,0 +1,118 @@
+"""The continuous-batching server: requests admitted by device-memory
+footprint while others run, results identical alone and in the mix."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_1909_13560_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1909_13560_gb300 import bsde
+    bsde.load()
+    return bsde
+
+
+def _requests(count=24, seed=19):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        if i % 3:
+            out.append(W.call_problem(strike=float(rng.uniform(70, 130)),
+                                      sigma=float(rng.uniform(0.1, 0.5)),
+                                      T=float(rng.uniform(0.25, 2.0)), r=float(rng.uniform(0, 0.05)),
+                                      Nx=int(rng.integers(512, 4096)), N=int(rng.integers(8, 48)),
+                                      k=int(rng.integers(1, 5)), L=16))
+        else:
+            r = float(rng.uniform(0, 0.05))
+            out.append(W.call_problem(strike=float(rng.uniform(70, 130)), sigma=0.2, T=0.5, r=r,
+                                      R=r + 0.02, mu=0.06, Nx=int(rng.integers(512, 4096)),
+                                      N=int(rng.integers(8, 48)), k=int(rng.integers(1, 5)), L=16,
+                                      driver="LB"))
+    return out
+
+
+def _wait_all(srv, n, timeout=60.0):
+    got = {}
+    t0 = time.time()
+    while len(got) < n:
+        for slot, res in srv.poll():
+            got[slot] = res
+        assert time.time() - t0 < timeout, "server did not finish"
+    return got
+
+
+def test_results_alone_equal_in_the_mix(B):
+    reqs = _requests()
+    srv = B.Server(slots=64, pool_bytes=1 << 30)
+    srv.start(cluster=1, idle_ms=20000)
+    try:
+        slots = [srv.submit(p) for p in reqs]
+        assert all(s is not None for s in slots)
+        mix = _wait_all(srv, len(reqs))
+        mix = [mix[s] for s in slots]
+        alone = []
+        for p in reqs:
+            s = srv.submit(p)
+            alone.append(_wait_all(srv, 1)[s])
+    finally:
+        srv.stop()
+        srv.close()
+    for a, m in zip(alone, mix):
+        assert a["y0"] == m["y0"] and a["z0"] == m["z0"]
+    # and the same as the batched solve of the same problems
+    bs = B.BatchSolver(reqs)
+    bs.set_config(1, 4)
+    res = bs.solve()
+    bs.close()
+    for r, m in zip(res, mix):
+        assert r["y0"] == m["y0"] and r["z0"] == m["z0"]
+
+
+def test_admission_by_footprint(B):
+    """A pool that holds two requests at a time: everything still completes,
+    never more than two in flight."""
+    from paper_1909_13560_gb300 import serve
+    reqs = [W.call_problem(Nx=2048, N=24, k=3, L=16, strike=90 + i) for i in range(10)]
+    one = B.bsde_request_bytes(reqs[0])
+    srv = B.Server(slots=16, pool_bytes=2 * one + 256)
+    srv.start(cluster=1, idle_ms=20000)
+    try:
+        records, summary = serve.serve(srv, [(0.0, p) for p in reqs])
+    finally:
+        srv.stop()
+        srv.close()
+    assert summary["requests"] == 10 and summary["max_inflight"] <= 2
+    assert all(r is not None and np.isfinite(r["result"]["y0"]) for r in records)
+
+
+def test_serving_loop_statistics(B):
+    from paper_1909_13560_gb300 import serve
+    rng = np.random.default_rng(2)
+    reqs = _requests(count=60, seed=23)
+    t = np.cumsum(rng.exponential(1.0 / 2000.0, len(reqs)))
+    srv = B.Server(slots=128, pool_bytes=1 << 30)
+    srv.start(cluster=1, idle_ms=20000)
+    try:
+        records, summary = serve.serve(srv, list(zip(t.tolist(), reqs)))
+    finally:
+        srv.stop()
+        srv.close()
+    print(summary)
+    assert summary["requests"] == 60
+    assert 0 < summary["p50_ms"] <= summary["p99_ms"]
+    assert all(r["done"] >= r["admitted"] >= r["arrival"] for r in records)
+
+
+def test_start_and_stop_without_requests(B):
+    srv = B.Server(slots=4, pool_bytes=1 << 20)
+    srv.start(cluster=2, idle_ms=20000)
+    srv.stop()
+    srv.close()
