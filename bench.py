@@ -200,11 +200,12 @@ def run_ours(args, rank, world, local_rank):
     from paper_1909_13560_gb300 import workloads as W
 
     dist = _dist_init(world)
+    ks = tuple(args.ks)
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream(dev)
     sp = stream.cuda_stream
-    probs = [W.config2(k=k) for k in KS]
+    probs = [W.config2(k=k) for k in ks]
     solvers = [B.Solver(p, args.precision, device=dev) for p in probs]
     units_per_step = sum(W.gp_steps(p) for p in probs)
     launches_per_step = sum(s.launches for s in solvers)
@@ -248,7 +249,7 @@ def run_ours(args, rank, world, local_rank):
     gold = _golden()
     rows = []
     ok = True
-    for k, s in zip(KS, solvers):
+    for k, s in zip(ks, solvers):
         r = B.bsde_result_fetch(s.plan, sp)
         g = gold.get(k)
         row = {"k": k, "y0": r.y0, "z0": r.z0, "picard_iters_max": r.picard_iters_max}
@@ -265,7 +266,7 @@ def run_ours(args, rank, world, local_rank):
     # resident after the solve)
     reps = 20
     kern_ms, kern_flops = 0.0, 0.0
-    for k, p, s in zip(KS, probs, solvers):
+    for k, p, s in zip(ks, probs, solvers):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         B.bsde_enqueue_level(s.plan, sp, 0, 1)
         e0.record(stream)
@@ -324,7 +325,7 @@ def run_ours(args, rank, world, local_rank):
             "config": {"workload": "config2: Black-Scholes call in log price (S0=K=100, "
                                    "r=.03, mu=.05, sigma=.2, T=1, x in ln100 +- 6 sigma), "
                                    "Nx=65536, N=256, k=1..6 (one solve each per step), L=16",
-                       "Nx": 65536, "N": 256, "k": list(KS), "L": 16,
+                       "Nx": 65536, "N": 256, "k": list(ks), "L": 16,
                        "precision": args.precision,
                        "l2": "flushed between steps (256 MiB write, outside the timed events); "
                              "within a solve the level ring (<= 15 MB) is L2-resident by design",
@@ -333,7 +334,7 @@ def run_ours(args, rank, world, local_rank):
             "roofline": {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                          "peak_source": f"derived: 152 SMs x {'128 FP32 lanes' if args.precision == 'fp32c' else '2 FP64 FMA units'} x 2 flop x {sm_max:.0f} MHz",
-                         "flop_per_gp_step": {str(k): flops_per_gp_step(k, 16) for k in KS},
+                         "flop_per_gp_step": {str(k): flops_per_gp_step(k, 16) for k in ks},
                          "avg_launch_ms": kern_ms / sum(p['N'] - p['k'] + 1 for p in probs)},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
@@ -535,6 +536,9 @@ def main():
                          "config5: the serving run (Poisson arrivals, continuous batching)")
     ap.add_argument("--duration", type=float, default=10.0, help="config5: seconds of arrivals")
     ap.add_argument("--rate", type=float, default=2000.0, help="config5: arrivals per second")
+    ap.add_argument("--ks", type=lambda v: [int(t) for t in v.split(",")], default=list(KS),
+                    help="config2: the step counts k to solve (default 1,2,3,4,5,6; a subset "
+                         "is for profiling one kernel shape, not a bench line)")
     ap.add_argument("--cpu-levels", type=int, default=64)
     ap.add_argument("--ref-levels", type=int, default=12)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -229,15 +229,19 @@ BSDE_API void bsde_batch_free(bsde_batch_t *b);
  * polled.  Problems must be BSDE_FP32C with the closed-form start.  A request
  * gives the same result alone and in any mix (same kernels per tile, same
  * order of operations).  The server's waits for new requests are bounded: a
- * cluster that finds no request for idle_ms milliseconds leaves and the
- * server reports BSDE_ETIMEOUT at bsde_server_stop. */
+ * cluster that finds no request for idle_ms milliseconds stops the whole
+ * server (every cluster leaves after its current request).  From then on
+ * bsde_server_submit returns BSDE_ETIMEOUT, bsde_server_poll hands back the
+ * requests no cluster will serve with status BSDE_ETIMEOUT and NaN values,
+ * and bsde_server_stop returns BSDE_ETIMEOUT; after stop and a poll of every
+ * request, bsde_server_start may launch it again. */
 typedef struct bsde_server_s bsde_server_t;
 
 /* Device bytes a request for *p occupies in the pool (its level ring). */
 BSDE_API int bsde_request_bytes(const bsde_problem *p, size_t *bytes);
 
-/* Workspace for a server with `slots` request slots and a pool of
- * pool_bytes for level rings. */
+/* Workspace for a server with `slots` request slots (1..65536) and a pool
+ * of pool_bytes for level rings. */
 BSDE_API int bsde_server_workspace_bytes(int slots, size_t pool_bytes, size_t *bytes);
 
 /* Bind a server to dev_workspace (caller-owned device memory); allocates its
@@ -246,11 +250,14 @@ BSDE_API int bsde_server_create(void *dev_workspace, size_t bytes, int slots,
                                 size_t pool_bytes, bsde_server_t **out);
 
 /* Launch the persistent kernel on `stream` (clusters of `cluster` CTAs, as
- * many as fit on the GPU at once). */
+ * many as fit on the GPU at once).  The kernel holds the stream until
+ * bsde_server_stop; give it a stream of its own.  BSDE_EINVAL while a
+ * request of an earlier run is still unpolled. */
 BSDE_API int bsde_server_start(bsde_server_t *s, void *stream, int cluster, int idle_ms);
 
 /* Admit a request: BSDE_OK with *slot set, BSDE_BUSY when no slot or pool
- * memory is free now, BSDE_EINVAL for a bad problem.  Non-blocking. */
+ * memory is free now, BSDE_EINVAL for a bad problem, BSDE_ETIMEOUT once the
+ * server has stopped itself.  Non-blocking. */
 BSDE_API int bsde_server_submit(bsde_server_t *s, const bsde_problem *p, int *slot);
 
 /* Collect up to max finished requests: their slots and results; frees their

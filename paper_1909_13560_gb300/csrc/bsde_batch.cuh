@@ -81,7 +81,7 @@ __device__ void batch_instance(BatchSmem &sm, unsigned char *ws, Stats *st,
   const int ntiles = int((P.Nx + kStepTP - 1) / kStepTP);
   for (int n = P.N - P.k; n >= 0; --n) {
     for (int t = crank; t < ntiles; t += csize) {
-      step_tile32<DRV, false, true>(P, sm.D.dc32, ringA, ringB, sm.tab, sm.part, n, t * kStepTP, st);
+      step_tile32<DRV, true>(P, sm.D.dc32, ringA, ringB, sm.tab, sm.part, n, t * kStepTP, st);
       __syncthreads();
     }
     cl.sync();
@@ -103,7 +103,7 @@ __device__ void batch_instance(BatchSmem &sm, unsigned char *ws, Stats *st,
 __global__ void __launch_bounds__(kBatchThreads, 2)
     k_batch32(const InstDesc *__restrict__ descs, const int *__restrict__ order, int count,
               int *queue, unsigned char *ws, Stats *stats) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   BatchSmem &sm = *reinterpret_cast<BatchSmem *>(smem_raw);
   cg::cluster_group cl = cg::this_cluster();
   while (true) {
@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2)
     {
       const float4 *src = reinterpret_cast<const float4 *>(ws + sm.D.ptable);
       float4 *dst = reinterpret_cast<float4 *>(sm.tab);
-      const int n4 = sm.D.P.k * sm.D.P.Lp * 4;
+      const int n4 = sm.D.P.k * sm.D.P.Lp * kPairVec;
       for (int t = threadIdx.x; t < n4; t += blockDim.x) dst[t] = src[t];
       if (threadIdx.x < kInvPivots) sm.sid[threadIdx.x] = float(sm.D.P.invd[threadIdx.x]);
     }

@@ -2,6 +2,7 @@
 // backward loop, solve and result transfer.  Kernels: bsde_kernels.cuh.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
@@ -11,6 +12,7 @@
 #include <new>
 #include <numeric>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "bsde_internal.h"
@@ -83,30 +85,43 @@ static void driver_coefs(const Params &P, DrvC<double> &c64, DrvC<float> &c32) {
   c32 = DrvC<float>{float(c64.ca), float(c64.cb), float(c64.cc), float(c64.cis)};
 }
 
+// Launch with programmatic stream serialization: the kernel may begin (and
+// stage what it owns) while its predecessor on the stream finishes; it waits
+// (griddepcontrol.wait) before reading anything the predecessor wrote.
+template <typename... KArgs, typename... Args>
+static void launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem,
+                       cudaStream_t s, Args &&...args) {
+  cudaLaunchConfig_t lc{};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  lc.gridDim = dim3(grid, 1, 1);
+  lc.blockDim = dim3(block, 1, 1);
+  lc.dynamicSmemBytes = smem;
+  lc.stream = s;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  cudaLaunchKernelEx(&lc, kernel, std::forward<Args>(args)...);
+}
+
 template <int PREC, int DRV>
 static void launch_step(bsde_plan_t *pl, cudaStream_t s, int n) {
   const Params &P = pl->P;
-  const int threads = kStepTP * P.G;
+  const unsigned threads = unsigned(kStepTP * P.G);
   const unsigned blocks = unsigned((P.Nx + kStepTP - 1) / kStepTP);
   const int kL = P.k * P.L;
   Stats *st = reinterpret_cast<Stats *>(pl->ws + pl->lay.stats);
   if (PREC == BSDE_FP64) {
     const size_t sm = sizeof(NodeF64) * kL + sizeof(double) * 2 * P.G * kStepTP;
-    k_step64<DRV><<<blocks, threads, sm, s>>>(
-        P, pl->dc64, reinterpret_cast<double4_32a *>(pl->ws + pl->lay.ring64),
-        reinterpret_cast<const NodeF64 *>(pl->ws + pl->lay.table), n, st);
+    launch_pdl(k_step64<DRV>, blocks, threads, sm, s, P, pl->dc64,
+               reinterpret_cast<double4_32a *>(pl->ws + pl->lay.ring64),
+               reinterpret_cast<const NodeF64 *>(pl->ws + pl->lay.table), n, st);
   } else {
     const size_t sm = step32_smem(P.G, P.k * P.Lp);
-    static bool attr_set = false;  // per driver instantiation
-    if (!attr_set) {
-      cudaFuncSetAttribute(k_step32<DRV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           int(step32_smem(kMaxGroups, kMaxK * kMaxL / 2)));
-      attr_set = true;
-    }
-    k_step32<DRV><<<blocks, threads, sm, s>>>(
-        P, pl->dc32, reinterpret_cast<float4 *>(pl->ws + pl->lay.ringA),
-        reinterpret_cast<const float2 *>(pl->ws + pl->lay.ringB),
-        reinterpret_cast<const PairF32 *>(pl->ws + pl->lay.ptable), n, st);
+    launch_pdl(k_step32<DRV>, blocks, threads, sm, s, P, pl->dc32,
+               reinterpret_cast<float4 *>(pl->ws + pl->lay.ringA),
+               reinterpret_cast<const float2 *>(pl->ws + pl->lay.ringB),
+               reinterpret_cast<const PairF32 *>(pl->ws + pl->lay.ptable), n, st);
   }
 }
 
@@ -128,7 +143,7 @@ static int64_t enqueue_spline(bsde_plan_t *pl, cudaStream_t s, int slot) {
   Ring32 r32{reinterpret_cast<float4 *>(pl->ws + pl->lay.ringA),
              reinterpret_cast<float2 *>(pl->ws + pl->lay.ringB)};
   const unsigned blocks = unsigned((P.Nx - 2 + kSplineTile - 1) / kSplineTile);
-  k_spline<PREC><<<blocks, kSplineTile / kSplineChunk, 0, s>>>(P, r64, r32, slot);
+  launch_pdl(k_spline<PREC>, blocks, unsigned(kSplineTile / kSplineChunk), 0, s, P, r64, r32, slot);
   return 1;
 }
 
@@ -827,7 +842,8 @@ int bsde_request_bytes(const bsde_problem *p, size_t *bytes) {
 }
 
 int bsde_server_workspace_bytes(int slots, size_t pool_bytes, size_t *bytes) {
-  if (slots < 1 || !bytes) return fail(BSDE_EINVAL, "bad server arguments");
+  // at most one unread ring entry per slot: slots <= ring positions
+  if (slots < 1 || slots > kServerRing || !bytes) return fail(BSDE_EINVAL, "bad server arguments");
   auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
   *bytes = up(sizeof(ServerDev)) + up(sizeof(Stats) * size_t(slots)) + up(pool_bytes);
   return BSDE_OK;
@@ -883,7 +899,13 @@ int bsde_server_start(bsde_server_t *s, void *stream, int cluster, int idle_ms) 
     return fail(BSDE_EINVAL, "bad server launch arguments");
   DeviceGuard guard(s->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  for (int i = 0; i < s->nslots; ++i)
+    if (s->busy[i]) return fail(BSDE_EINVAL, "poll every request of the last run before a restart");
+  // a fresh run: the device claims ring positions from 0 again
+  s->tail = 0;
+  s->ctl->req_tail = 0;
   s->ctl->shutdown = 0;
+  s->ctl->stopped = 0;
   BSDE_CUDA_TRY(cudaMemsetAsync(s->ws + s->off_dev, 0, sizeof(ServerDev), st));
   const size_t smem = sizeof(BatchSmem);
   BSDE_CUDA_TRY(cudaFuncSetAttribute(k_server32, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -917,6 +939,8 @@ int bsde_server_start(bsde_server_t *s, void *stream, int cluster, int idle_ms) 
 int bsde_server_submit(bsde_server_t *s, const bsde_problem *p, int *slot) {
   if (!s || !p || !slot) return fail(BSDE_EINVAL, "null argument");
   if (!s->running) return fail(BSDE_EINVAL, "server not running");
+  if (__atomic_load_n(&s->ctl->stopped, __ATOMIC_ACQUIRE))
+    return fail(BSDE_ETIMEOUT, "server stopped: its idle limit passed; poll, stop and start it again");
   if (validate(*p) || p->precision != BSDE_FP32C) return fail(BSDE_EINVAL, "invalid request");
   if (s->free_slots.empty()) return BSDE_BUSY;
   const size_t need = request_bytes(*p);
@@ -957,11 +981,24 @@ int bsde_server_submit(bsde_server_t *s, const bsde_problem *p, int *slot) {
 
 int bsde_server_poll(bsde_server_t *s, int max, int *slots, bsde_result *results) {
   if (!s || max < 0) return fail(BSDE_EINVAL, "bad poll arguments");
+  // once the device has stopped itself and its kernel has ended, requests
+  // still without a result will never get one: report them as timed out
+  bool lost = false;
+  if (s->running && __atomic_load_n(&s->ctl->stopped, __ATOMIC_ACQUIRE)) {
+    DeviceGuard guard(s->device);
+    lost = cudaStreamQuery(s->stream) == cudaSuccess;
+  }
   int got = 0;
   for (int sl = 0; sl < s->nslots && got < max; ++sl) {
     if (!s->busy[sl]) continue;
-    if (__atomic_load_n(&s->slots[sl].done, __ATOMIC_ACQUIRE) != 1u) continue;
-    const Stats st = s->slots[sl].result;
+    const bool done = __atomic_load_n(&s->slots[sl].done, __ATOMIC_ACQUIRE) == 1u;
+    if (!done && !lost) continue;
+    Stats st = s->slots[sl].result;
+    if (!done) {
+      std::memset(&st, 0, sizeof(st));
+      st.y0 = st.z0 = std::nan("");
+      st.timeout = 1;
+    }
     if (results) {
       bsde_result &r = results[got];
       r.y0 = st.y0;

@@ -151,6 +151,12 @@ int fill_params(const bsde_problem &p, Params &P) {
   P.lb_sign = p.lb_sign;
   P.strike = p.strike;
   P.picard_tol = p.picard_tol;
+  {
+    // |d| <= tol for a float d is exactly |d| <= the largest float <= tol
+    float tf = (float)p.picard_tol;
+    if ((double)tf > p.picard_tol) tf = std::nextafter(tf, 0.0f);
+    P.picard_tol_f = tf;
+  }
   gamma_tables(p.k, P.gy, P.gz);
   P.h = p.k * P.dt;
   P.hg0 = P.h * P.gy[0];
@@ -280,18 +286,23 @@ void build_tables(Params &P, NodeF64 *t64, NodeF32 *t32, PairF32 *tp, int target
         PairF32 pr{};
         pr.shift_a = na.shift;
         pr.shift_b = nb.shift;
-        pr.w1a = na.w1;
-        pr.w1b = nb.w1;
-        pr.w2a = na.w2;
-        pr.w3a = na.w3;
-        pr.w2b = nb.w2;
-        pr.w3b = nb.w3;
-        pr.czh = na.czh * half;
-        pr.czl = na.czl * half;
         pr.cfz = na.cfz;  // zero for the middle node (DeltaW = 0)
         pr.cfy = na.cfy * half;
-        pr.cyh = na.cyh * half;
-        pr.cyl = na.cyl * half;
+        for (int v = 0; v < 2; ++v) {
+          pr.w1a[v] = na.w1;
+          pr.w2a[v] = na.w2;
+          pr.w3a[v] = na.w3;
+          pr.w1b[v] = nb.w1;
+          pr.w2b[v] = nb.w2;
+          pr.w3b[v] = nb.w3;
+        }
+        // lanes (y, z)
+        pr.ch[0] = na.cyh * half;
+        pr.ch[1] = na.czh * half;
+        pr.nch[0] = -pr.ch[0];
+        pr.nch[1] = -pr.ch[1];
+        pr.ncl[0] = -(na.cyl * half);
+        pr.ncl[1] = -(na.czl * half);
         tp[(j - 1) * P.Lp + q] = pr;
       }
     }

@@ -13,14 +13,9 @@ constexpr int kMaxK = 6;
 constexpr int kMaxL = 64;
 constexpr int kInvPivots = 64;   // exact 1/d_m of the spline LU for m < 64
 constexpr int kStepTP = 64;      // grid points per CTA in the step kernels
-constexpr int kMaxGroups = 8;    // (j, l-chunk) groups per point
+constexpr int kMaxGroups = 6;    // (j, l-chunk) groups per point
 constexpr int kSplineTile = 512;  // unknowns per CTA in the spline kernel
 constexpr int kSplineChunk = 4;   // unknowns per thread (serial recurrence)
-constexpr int kTmaStages = 3;     // pipeline depth of the bulk-copy step path
-// one stage: the A windows (65 float4) and B windows (66 float2) of a node pair
-constexpr int kWinA = (kStepTP + 1) * 16, kWinB = (kStepTP + 2) * 8;
-constexpr int kStageBytes = 2 * kWinA + 2 * kWinB;
-constexpr unsigned kWaitLimit = 1u << 26;  // polls of a bulk-copy barrier before giving up
 
 // Per (j, l) entry of the node tables.  The off-grid point
 // x_i + a_x j dt + b_x sqrt(2 j dt) a_l sits in cell i + shift at relative
@@ -52,13 +47,20 @@ struct NodeF32 {
 // added exactly (TwoSum) before one compensated product, and the driver
 // terms enter as cfz (F_a - F_b) and cfy (F_a + F_b).  For odd L the middle
 // node (a = 0, DeltaW = 0) is a pair with itself and halved coefficients.
-// Layout as four float4: (shift_a, shift_b, w1a, w1b), (w2a, w3a, w2b, w3b),
-// (czh, czl, cfz, cfy), (cyh, cyl, -, -); w1 = theta, w0 = 1 - theta.
+// The arithmetic runs on (y, z) lane pairs (packed FP32x2), so every weight
+// is stored twice, once per lane, and the compensated-sum coefficients are
+// lane pairs (cy, cz): hi parts, and negated hi and lo parts, which let the
+// error terms be formed by fused multiply-adds alone.  Six float4:
+// (shift_a, shift_b, cfz, cfy), (w1a, w1a, w2a, w2a), (w3a, w3a, w1b, w1b),
+// (w2b, w2b, w3b, w3b), (cyh, czh, -cyh, -czh), (-cyl, -czl, 0, 0);
+// w1 = theta, w0 = 1 - theta.  cy is zero for j < k.
 struct PairF32 {
   int32_t shift_a, shift_b;
-  float w1a, w1b, w2a, w3a, w2b, w3b;
-  float czh, czl, cfz, cfy, cyh, cyl, pad0, pad1;
+  float cfz, cfy;
+  float w1a[2], w2a[2], w3a[2], w1b[2], w2b[2], w3b[2];
+  float ch[2], nch[2], ncl[2], pad[2];
 };
+constexpr int kPairVec = int(sizeof(PairF32) / 16);  // float4 per entry
 
 // Everything a kernel needs to know about one problem.
 struct Params {
@@ -67,6 +69,7 @@ struct Params {
   double T, dt, dx, x_min, x_max, x0, a_x, b_x;
   double r, mu, sigma, R, delta, lb_sign, strike;
   double picard_tol;
+  float picard_tol_f;  // the largest float <= picard_tol (FP32 Picard test)
   double gy[kMaxK + 1], gz[kMaxK + 1];
   double h;       // k dt
   double hg0;     // k dt gy_0 (weight of the implicit term)

@@ -114,13 +114,14 @@ __device__ void closed_form(const Params &P, double t, double x, bool smooth_lev
 
 // ---------------------------------------------------------------------------
 // Level storage.  FP64: double4_32a (y, M_y, z, M_z) per node.  FP32C: float4
-// (y_hi, y_lo, z_hi, z_lo) plus float2 (M_y, M_z) per node, value = hi + lo.
+// (y_hi, z_hi, y_lo, z_lo) plus float2 (M_y, M_z) per node, value = hi + lo;
+// the (y, z) lane pairs feed packed FP32x2 arithmetic directly.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void split_store(float4 *A, int64_t i, double y, double z) {
   const float yh = __double2float_rn(y), zh = __double2float_rn(z);
   const float yl = __double2float_rn(__dsub_rn(y, (double)yh));
   const float zl = __double2float_rn(__dsub_rn(z, (double)zh));
-  A[i] = make_float4(yh, yl, zh, zl);
+  A[i] = make_float4(yh, zh, yl, zl);
 }
 
 // Level loads.  Within one launch of the per-level kernels the levels they
@@ -133,6 +134,14 @@ __device__ __forceinline__ T ldl(const T *p) {
     return __ldcg(p);
   else
     return *p;
+}
+
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization may start while its predecessor on the stream finishes; it
+// waits here, before touching anything the predecessor wrote.  (A no-op for
+// an ordinary launch.)
+__device__ __forceinline__ void wait_predecessor() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 struct Ring64 {
@@ -210,8 +219,8 @@ __global__ void k_export(const Params P, Ring64 r64, Ring32 r32, double *sy, dou
       sz[i] = v.z;
     } else {
       const float4 v = r32.A[off + i];
-      sy[i] = double(v.x) + double(v.y);
-      sz[i] = double(v.z) + double(v.w);
+      sy[i] = double(v.x) + double(v.z);
+      sz[i] = double(v.y) + double(v.w);
     }
   }
 }
@@ -281,10 +290,10 @@ __device__ __forceinline__ void spline_tile(const Params &P, Ring64 r64, Ring32 
       const float4 v0 = ldl<COH>(r32.A + off + m), v1 = ldl<COH>(r32.A + off + m + 1),
                    v2 = ldl<COH>(r32.A + off + m + 2);
       const float inv6 = float(P.inv_dx2_6);
-      const float d1y = __fadd_rn(__fsub_rn(v1.x, v0.x), __fsub_rn(v1.y, v0.y));
-      const float d2y = __fadd_rn(__fsub_rn(v2.x, v1.x), __fsub_rn(v2.y, v1.y));
-      const float d1z = __fadd_rn(__fsub_rn(v1.z, v0.z), __fsub_rn(v1.w, v0.w));
-      const float d2z = __fadd_rn(__fsub_rn(v2.z, v1.z), __fsub_rn(v2.w, v1.w));
+      const float d1y = __fadd_rn(__fsub_rn(v1.x, v0.x), __fsub_rn(v1.z, v0.z));
+      const float d2y = __fadd_rn(__fsub_rn(v2.x, v1.x), __fsub_rn(v2.z, v1.z));
+      const float d1z = __fadd_rn(__fsub_rn(v1.y, v0.y), __fsub_rn(v1.w, v0.w));
+      const float d2z = __fadd_rn(__fsub_rn(v2.y, v1.y), __fsub_rn(v2.w, v1.w));
       ry = inv6 * __fsub_rn(d2y, d1y);
       rz = inv6 * __fsub_rn(d2z, d1z);
     }
@@ -353,11 +362,14 @@ __global__ void __launch_bounds__(kSplineTile / kSplineChunk)
   __shared__ T sg[2][kSplineTile + 2 * W];
   __shared__ T sid[kInvPivots];
   if (threadIdx.x < kInvPivots) sid[threadIdx.x] = T(P.invd[threadIdx.x]);
+  wait_predecessor();
   spline_tile<PREC, kSplineTile>(P, r64, r32, slot, blockIdx.x, blockDim.x, sr, sg, sid);
 }
 
 // ---------------------------------------------------------------------------
-// Picard statistics: per-warp maxima folded into the Stats block.
+// Picard statistics: per-warp maxima folded into the Stats block.  Every
+// warp of every CTA reports, so an atomic is issued only when it would change
+// the block (the fields only grow; the check reads them from L2).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void record_picard(Stats *st, bool active, int it, double d,
                                               double tol) {
@@ -370,9 +382,9 @@ __device__ __forceinline__ void record_picard(Stats *st, bool active, int it, do
   }
   const unsigned nc = __reduce_or_sync(full, (active && d > tol) ? 1u : 0u);
   if ((threadIdx.x & 31) == 0) {
-    atomicMax(&st->iters_max, int(itm));
-    atomicMax(&st->resid_bits, db);
-    if (nc) atomicOr(&st->nonconv, 1);
+    if (int(itm) > __ldcg(&st->iters_max)) atomicMax(&st->iters_max, int(itm));
+    if (db > __ldcg(&st->resid_bits)) atomicMax(&st->resid_bits, db);
+    if (nc && !__ldcg(&st->nonconv)) atomicOr(&st->nonconv, 1);
   }
 }
 
@@ -432,12 +444,13 @@ template <int DRV>
 __global__ void __launch_bounds__(kStepTP * kMaxGroups)
     k_step64(const Params P, const DrvC<double> dc, double4_32a *__restrict__ ring,
              const NodeF64 *__restrict__ table, int n, Stats *st) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   const int kL = P.k * P.L;
   NodeF64 *tab = reinterpret_cast<NodeF64 *>(smem_raw);
   double *part = reinterpret_cast<double *>(smem_raw + sizeof(NodeF64) * kL);  // [2][G][TP]
   for (int t = threadIdx.x; t < kL; t += blockDim.x) tab[t] = table[t];
   __syncthreads();
+  wait_predecessor();
 
   const int tp = threadIdx.x % kStepTP, g = threadIdx.x / kStepTP;
   const int j = g / P.S + 1, lc = g % P.S;
@@ -487,24 +500,64 @@ __global__ void __launch_bounds__(kStepTP * kMaxGroups)
 
 // ---------------------------------------------------------------------------
 // FP32C: the spline value at a node is kept as the unevaluated sum hi_c + del,
-// del = theta (hi_{c+1} - hi_c) + (lo and spline-curvature parts), computed in
+// del = theta (v_{c+1} - v_c) + lo_c + (spline-curvature part), computed in
 // FP32 (|del| ~ dx |y'|, so its rounding is far below that of y).  The z and
 // y sums take the exact product of the coefficient's hi part with hi_c (FMA)
 // and add it by TwoSum into an (S, C) pair; the driver terms, which carry a
 // dt-sized or sqrt(dt)-sized weight, are summed in plain FP32.  The final
-// combination of z^n and A, the Picard iteration and its test run in FP64.
+// combination of z^n and A runs in FP64.
+// y and z go through the same arithmetic with the same weights, so it runs on
+// (y, z) lane pairs with packed FP32x2 instructions (one instruction, two
+// correctly rounded results).
 // ---------------------------------------------------------------------------
+// Packed FP32x2 operations.  Written as inline PTX on 64-bit register pairs
+// so that the two lanes stay in one aligned register pair from load to use.
+#define BSDE_F2_OP2(name, op)                                                           \
+  __device__ __forceinline__ float2 name(float2 a, float2 b) {                         \
+    float2 d;                                                                           \
+    asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"  \
+        " " op ".rn.f32x2 rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}"                       \
+        : "=f"(d.x), "=f"(d.y)                                                          \
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));                                      \
+    return d;                                                                           \
+  }
+BSDE_F2_OP2(f2add, "add")
+BSDE_F2_OP2(f2sub, "sub")
+BSDE_F2_OP2(f2mul, "mul")
+#undef BSDE_F2_OP2
+__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n .reg .b64 ra, rb, rc, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+      " mov.b64 rc, {%6, %7};\n fma.rn.f32x2 rd, ra, rb, rc;\n mov.b64 {%0, %1}, rd;\n}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+__device__ __forceinline__ float2 lo2(const float4 &v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float2 hi2(const float4 &v) { return make_float2(v.x, v.y); }
+
+// s + e = a + b exactly, lane by lane (TwoSum)
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2 &s, float2 &e) {
+  s = f2add(a, b);
+  const float2 bp = f2sub(s, a);
+  e = f2add(f2sub(a, f2sub(s, bp)), f2sub(b, bp));
+}
+
 // S += ch*hi exactly (error-free product by FMA, TwoSum), C += the rounding
-// errors plus the small terms ch*del + cl*hi.
-__device__ __forceinline__ void comp_acc(float &S, float &C, float ch, float cl, float hi,
-                                         float del) {
-  const float p = __fmul_rn(ch, hi);
-  const float e = __fmaf_rn(ch, hi, -p);
-  const float s = __fadd_rn(S, p);
-  const float bp = __fsub_rn(s, S);
-  const float err = __fadd_rn(__fsub_rn(S, __fsub_rn(s, bp)), __fsub_rn(p, bp));
-  S = s;
-  C = __fadd_rn(C, __fadd_rn(err, __fmaf_rn(ch, del, __fmaf_rn(cl, hi, e))));
+// errors plus the small terms ch*del + cl*hi; nch = -ch, ncl = -cl.  The
+// product error is formed negated (-e = nch*hi + p), which keeps every step a
+// plain FMA, add or subtract.
+__device__ __forceinline__ void comp_acc2(float2 &S, float2 &C, float2 ch, float2 nch,
+                                          float2 ncl, float2 hi, float2 del) {
+  const float2 p = f2mul(ch, hi);
+  const float2 ne = f2fma(nch, hi, p);
+  const float2 sn = f2add(S, p);
+  const float2 bp = f2sub(sn, S);
+  const float2 err = f2add(f2sub(S, f2sub(sn, bp)), f2sub(p, bp));
+  S = sn;
+  // -(ch*del + cl*hi + e) = nch*del + (ncl*hi + (-e))
+  const float2 nt = f2fma(nch, del, f2fma(ncl, hi, ne));
+  C = f2sub(f2add(C, err), nt);
 }
 
 __device__ __forceinline__ void two_sum_into(float &S, float &C, float x) {
@@ -515,64 +568,17 @@ __device__ __forceinline__ void two_sum_into(float &S, float &C, float x) {
 }
 
 // ---------------------------------------------------------------------------
-// Bulk-copy (TMA) helpers: 1-D cp.async.bulk into shared memory, completion
-// tracked by an mbarrier with an expected byte count.
+// Device clock for bounded waits (ns).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
-               : "memory");
-}
-__device__ __forceinline__ void fence_barrier_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes,
-                                          uint64_t *bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_addr(dst)),
-      "l"(src), "r"(bytes), "r"(smem_addr(bar))
-      : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
 __device__ __forceinline__ uint64_t global_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// Wait for a phase of a bulk-copy barrier, at most ~2 s: false if it did not
-// complete (the caller records the failure and carries on; nothing hangs).
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-  if (mbar_try(bar, parity)) return true;
-  const uint64_t t0 = global_ns();
-  while (!mbar_try(bar, parity))
-    if (global_ns() - t0 > 2000000000ull) return false;
-  return true;
-}
-__device__ __forceinline__ void group_sync(int g) {
-  asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(kStepTP) : "memory");
-}
-
-// Spline value of one node as hi_c + del (see PairF32 for the layout).
+// Cells of one node for point ii.  A node off the grid clamps to the end
+// value: both cells become the end cell and the caller zeroes the weights.
 template <bool CLAMP>
-__device__ __forceinline__ void pair_cells(int ii, int shift, int last, int &c0, int &c1,
-                                           float &w1, float &w2, float &w3) {
+__device__ __forceinline__ bool pair_cells(int ii, int shift, int last, int &c0, int &c1) {
   c0 = ii + shift;
   c1 = c0 + 1;
   if (CLAMP) {
@@ -580,309 +586,252 @@ __device__ __forceinline__ void pair_cells(int ii, int shift, int last, int &c0,
     if (cl | ch) {
       c0 = cl ? 0 : last;
       c1 = c0;
-      w1 = 0.f;
-      w2 = 0.f;
-      w3 = 0.f;
+      return true;
     }
   }
+  return false;
 }
 
-// One group's node pairs (l, L-1-l).  z^ = hi_c + del with
-// del = theta (dhi + dlo) + lo_c + w2 M_c + w3 M_{c+1}; where y only feeds
-// the FP32 driver (j < k) its lo part is left out.
-// The arithmetic of one node pair, given the two cells' level data.
-template <int DRV, bool LASTJ>
+// (y, z) spline value of one node as hi + del from the level data of its
+// cells c, c+1: A = (y_hi, z_hi, y_lo, z_lo), B = (M_y, M_z).
+__device__ __forceinline__ void node_value(const float4 &a0, const float4 &a1, const float2 &m0,
+                                           const float2 &m1, float2 w1, float2 w2, float2 w3,
+                                           float2 &hi, float2 &del) {
+  hi = hi2(a0);
+  const float2 l0 = lo2(a0);
+  const float2 d = f2add(f2sub(hi2(a1), hi), f2sub(lo2(a1), l0));
+  del = f2add(f2fma(w1, d, l0), f2fma(w2, m0, f2mul(w3, m1)));
+}
+
+// The arithmetic of one node pair (see PairF32 for the entry e0..e5), given
+// the level data of the two nodes' cells.  S, C: compensated (y, z) sums;
+// Fz, Fy: driver terms.
+template <int DRV>
 __device__ __forceinline__ void pair_math(const DrvC<float> &dc, float tj, float et, float emt,
-                                          float w1a, float w2a, float w3a, float w1b, float w2b,
-                                          float w3b, const float4 &aa, const float4 &ab,
-                                          const float4 &ba, const float4 &bb, const float2 &maa,
-                                          const float2 &mab, const float2 &mba, const float2 &mbb,
-                                          const float4 &e2, const float4 &e3, float &Sz, float &Cz,
-                                          float &Fz, float &Fy, float &Sy, float &Cy) {
-  const float zda = __fadd_rn(
-      __fmaf_rn(w1a, __fadd_rn(__fsub_rn(ab.z, aa.z), __fsub_rn(ab.w, aa.w)), aa.w),
-      __fmaf_rn(w2a, maa.y, w3a * mab.y));
-  const float zdb = __fadd_rn(
-      __fmaf_rn(w1b, __fadd_rn(__fsub_rn(bb.z, ba.z), __fsub_rn(bb.w, ba.w)), ba.w),
-      __fmaf_rn(w2b, mba.y, w3b * mbb.y));
-  const float mya = __fmaf_rn(w2a, maa.x, w3a * mab.x);
-  const float myb = __fmaf_rn(w2b, mba.x, w3b * mbb.x);
-  float yfa, yfb, yda = 0.f, ydb = 0.f;
-  if (LASTJ) {
-    yda = __fadd_rn(__fmaf_rn(w1a, __fadd_rn(__fsub_rn(ab.x, aa.x), __fsub_rn(ab.y, aa.y)), aa.y), mya);
-    ydb = __fadd_rn(__fmaf_rn(w1b, __fadd_rn(__fsub_rn(bb.x, ba.x), __fsub_rn(bb.y, ba.y)), ba.y), myb);
-    yfa = aa.x + yda;
-    yfb = ba.x + ydb;
-  } else {
-    yfa = aa.x + __fmaf_rn(w1a, __fsub_rn(ab.x, aa.x), mya);
-    yfb = ba.x + __fmaf_rn(w1b, __fsub_rn(bb.x, ba.x), myb);
-  }
-  const float Fa = driver<DRV>(dc, tj, et, emt, yfa, aa.z + zda);
-  const float Fb = driver<DRV>(dc, tj, et, emt, yfb, ba.z + zdb);
-  Fz = __fmaf_rn(e2.z, __fsub_rn(Fa, Fb), Fz);
-  Fy = __fmaf_rn(e2.w, __fadd_rn(Fa, Fb), Fy);
-  // z: the pair's hi parts summed exactly, then one compensated product
-  {
-    const float s = __fadd_rn(aa.z, ba.z);
-    const float bp = __fsub_rn(s, aa.z);
-    const float e1s = __fadd_rn(__fsub_rn(aa.z, __fsub_rn(s, bp)), __fsub_rn(ba.z, bp));
-    comp_acc(Sz, Cz, e2.x, e2.y, s, __fadd_rn(__fadd_rn(zda, zdb), e1s));
-  }
-  if (LASTJ) {
-    const float s = __fadd_rn(aa.x, ba.x);
-    const float bp = __fsub_rn(s, aa.x);
-    const float e1s = __fadd_rn(__fsub_rn(aa.x, __fsub_rn(s, bp)), __fsub_rn(ba.x, bp));
-    comp_acc(Sy, Cy, e3.x, e3.y, s, __fadd_rn(__fadd_rn(yda, ydb), e1s));
-  }
+                                          const float4 &e0, const float4 &e1, const float4 &e2,
+                                          const float4 &e3, const float4 &e4, const float4 &e5,
+                                          const float4 &aa, const float4 &ab, const float4 &ba,
+                                          const float4 &bb, const float2 &maa, const float2 &mab,
+                                          const float2 &mba, const float2 &mbb, float2 &S,
+                                          float2 &C, float &Fz, float &Fy) {
+  float2 ha, da, hb, db;
+  node_value(aa, ab, maa, mab, hi2(e1), lo2(e1), hi2(e2), ha, da);
+  node_value(ba, bb, mba, mbb, lo2(e2), hi2(e3), lo2(e3), hb, db);
+  const float2 va = f2add(ha, da), vb = f2add(hb, db);
+  const float Fa = driver<DRV>(dc, tj, et, emt, va.x, va.y);
+  const float Fb = driver<DRV>(dc, tj, et, emt, vb.x, vb.y);
+  Fz = __fmaf_rn(e0.z, __fsub_rn(Fa, Fb), Fz);
+  Fy = __fmaf_rn(e0.w, __fadd_rn(Fa, Fb), Fy);
+  // the pair's hi parts summed exactly, then one compensated product
+  float2 hs, he;
+  two_sum2(ha, hb, hs, he);
+  comp_acc2(S, C, hi2(e4), lo2(e4), hi2(e5), hs, f2add(f2add(da, db), he));
 }
 
-// One group's node pairs (l, L-1-l), level data loaded directly from global
-// memory (L1/L2).  z^ = hi_c + del with del = theta (dhi + dlo) + lo_c +
-// w2 M_c + w3 M_{c+1}; where y only feeds the FP32 driver (j < k) its lo part
-// is left out.
-template <int DRV, bool CLAMP, bool LASTJ, bool COH>
+// Accumulators of one point: compensated (y, z) sums and the driver terms.
+struct Acc32 {
+  float2 S, C;
+  float Fz, Fy;
+};
+
+// One group's node pairs for point ii, level data loaded directly from
+// global memory (L1/L2).  With CLAMP false every cell must lie on the grid.
+template <int DRV, bool CLAMP, bool COH>
 __device__ __forceinline__ void pairs32(const DrvC<float> &dc, const float4 *__restrict__ A,
                                         const float2 *__restrict__ B, const PairF32 *row, int q0,
                                         int q1, int ii, int last, float tj, float et, float emt,
-                                        float &Sz, float &Cz, float &Fz, float &Fy, float &Sy,
-                                        float &Cy) {
-#pragma unroll 2
+                                        Acc32 &acc) {
+#pragma unroll 1
   for (int q = q0; q < q1; ++q) {
     const float4 *te = reinterpret_cast<const float4 *>(row + q);
-    const float4 e0 = te[0], e1 = te[1], e2 = te[2];
-    const float4 e3 = LASTJ ? te[3] : make_float4(0.f, 0.f, 0.f, 0.f);
-    float w1a = e0.z, w2a = e1.x, w3a = e1.y;
-    float w1b = e0.w, w2b = e1.z, w3b = e1.w;
+    const float4 e0 = te[0], e4 = te[4], e5 = te[5];
+    float4 e1 = te[1], e2 = te[2], e3 = te[3];
     int ca0, ca1, cb0, cb1;
-    pair_cells<CLAMP>(ii, __float_as_int(e0.x), last, ca0, ca1, w1a, w2a, w3a);
-    pair_cells<CLAMP>(ii, __float_as_int(e0.y), last, cb0, cb1, w1b, w2b, w3b);
+    if (pair_cells<CLAMP>(ii, __float_as_int(e0.x), last, ca0, ca1)) {
+      e1 = make_float4(0.f, 0.f, 0.f, 0.f);
+      e2.x = e2.y = 0.f;
+    }
+    if (pair_cells<CLAMP>(ii, __float_as_int(e0.y), last, cb0, cb1)) {
+      e2.z = e2.w = 0.f;
+      e3 = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     const float4 aa = ldl<COH>(A + ca0), ab = ldl<COH>(A + ca1), ba = ldl<COH>(A + cb0),
                  bb = ldl<COH>(A + cb1);
     const float2 maa = ldl<COH>(B + ca0), mab = ldl<COH>(B + ca1), mba = ldl<COH>(B + cb0),
                  mbb = ldl<COH>(B + cb1);
-    pair_math<DRV, LASTJ>(dc, tj, et, emt, w1a, w2a, w3a, w1b, w2b, w3b, aa, ab, ba, bb, maa, mab,
-                          mba, mbb, e2, e3, Sz, Cz, Fz, Fy, Sy, Cy);
+    pair_math<DRV>(dc, tj, et, emt, e0, e1, e2, e3, e4, e5, aa, ab, ba, bb, maa, mab, mba, mbb,
+                   acc.S, acc.C, acc.Fz, acc.Fy);
   }
 }
 
-// The same for an interior tile, with the level windows brought into shared
-// memory by bulk copies kTmaStages pairs ahead of use.  For the pair of nodes
-// the window of each node is the kStepTP + 1 cells i0 + shift .. i0 + shift +
-// kStepTP of the level (A: 16-byte records, aligned) and, for B (8-byte
-// records), the same cells from the 16-byte boundary at or below the first.
-// Thread tp == 0 of the group issues the copies; a group barrier after each
-// pair frees its buffer.  Called by all kStepTP threads of group g.
-template <int DRV, bool LASTJ>
-__device__ __forceinline__ void pairs32_tma(const DrvC<float> &dc, const float4 *__restrict__ A,
-                                            const float2 *__restrict__ B, int64_t lev_elem,
-                                            const PairF32 *row, int q0, int q1, int i0, int tp,
-                                            int g, float tj, float et, float emt,
-                                            unsigned char *stage, uint64_t *full, Stats *st,
-                                            float &Sz, float &Cz, float &Fz, float &Fy,
-                                            float &Sy, float &Cy) {
-  const int np = q1 - q0;
-  auto issue = [&](int t) {
-    const PairF32 &e = row[q0 + t];
-    const int buf = t % kTmaStages;
-    unsigned char *d = stage + buf * kStageBytes;
-    const int ca = i0 + e.shift_a, cb = i0 + e.shift_b;
-    const int pa = int((lev_elem + ca) & 1), pb = int((lev_elem + cb) & 1);
-    mbar_expect_tx(full + buf, kStageBytes);
-    bulk_load(d, A + ca, kWinA, full + buf);
-    bulk_load(d + kWinA, A + cb, kWinA, full + buf);
-    bulk_load(d + 2 * kWinA, B + (ca - pa), kWinB, full + buf);
-    bulk_load(d + 2 * kWinA + kWinB, B + (cb - pb), kWinB, full + buf);
-  };
-  if (tp == 0)
-    for (int t = 0; t < np && t < kTmaStages; ++t) issue(t);
-  bool lost = false;
-  for (int t = 0; t < np; ++t) {
-    const int buf = t % kTmaStages;
-    if (!mbar_wait(full + buf, uint32_t((t / kTmaStages) & 1))) lost = true;
-    const float4 *te = reinterpret_cast<const float4 *>(row + q0 + t);
-    const float4 e0 = te[0], e1 = te[1], e2 = te[2];
-    const float4 e3 = LASTJ ? te[3] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const int pa = int((lev_elem + i0 + __float_as_int(e0.x)) & 1);
-    const int pb = int((lev_elem + i0 + __float_as_int(e0.y)) & 1);
-    const unsigned char *d = stage + buf * kStageBytes;
-    const float4 *sa = reinterpret_cast<const float4 *>(d);
-    const float4 *sb = reinterpret_cast<const float4 *>(d + kWinA);
-    const float2 *ma = reinterpret_cast<const float2 *>(d + 2 * kWinA) + pa;
-    const float2 *mb = reinterpret_cast<const float2 *>(d + 2 * kWinA + kWinB) + pb;
-    pair_math<DRV, LASTJ>(dc, tj, et, emt, e0.z, e1.x, e1.y, e0.w, e1.z, e1.w, sa[tp], sa[tp + 1],
-                          sb[tp], sb[tp + 1], ma[tp], ma[tp + 1], mb[tp], mb[tp + 1], e2, e3, Sz,
-                          Cz, Fz, Fy, Sy, Cy);
-    group_sync(g);
-    if (tp == 0 && t + kTmaStages < np) {
-      // the buffer was read through the generic proxy: order those reads
-      // before the async-proxy writes of the next copy
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue(t + kTmaStages);
+// Group g of a tile: pairs q0..q1 of level n + j, g = (j - 1) S + chunk.
+struct Group32 {
+  int j, q0, q1;
+  bool interior;  // every node cell of every point of the tile on the grid
+};
+__device__ __forceinline__ Group32 group32(const Params &P, int g, int i0) {
+  Group32 w;
+  w.j = g / P.S + 1;
+  const int lc = g % P.S;
+  w.q0 = lc * P.Lg;
+  w.q1 = w.q0 + P.Lg < P.Lp ? w.q0 + P.Lg : P.Lp;
+  w.interior = i0 + P.smin[w.j - 1] >= 0 && i0 + kStepTP + P.smax[w.j - 1] <= int(P.Nx - 1);
+  return w;
+}
+
+// Driver time constants of level m (t, exp(t^2), exp(-t^2) for Example 2).
+template <int DRV>
+__device__ __forceinline__ void level_time(const Params &P, int m, float &t, float &et,
+                                           float &emt) {
+  const double td = m * P.dt;
+  t = float(td);
+  et = emt = 0.f;
+  if constexpr (DRV == BSDE_DRIVER_EX2) {
+    et = float(exp(td * td));
+    emt = float(exp(-td * td));
+  }
+}
+
+__device__ __forceinline__ void store_partials(float *part, int G, int g, int tp,
+                                               const Acc32 &a) {
+  // lanes: y (x), z (y); part is [6][G][kStepTP]
+  const int o = g * kStepTP + tp, gs = G * kStepTP;
+  part[0 * gs + o] = a.S.y;
+  part[1 * gs + o] = a.C.y;
+  part[2 * gs + o] = a.Fz;
+  part[3 * gs + o] = a.Fy;
+  part[4 * gs + o] = a.S.x;
+  part[5 * gs + o] = a.C.x;
+}
+
+// The last part of the step for the kStepTP points of a tile, by the threads
+// tid < kStepTP of the CTA (the others pass through; all threads call it):
+// the groups' partial sums are added, z^n and the explicit part A of y^n are
+// formed as normalized float pairs (hi + lo, ~48 significant bits), y^n is
+// found by Picard iteration on the increment delta = y^n - A =
+// k dt gy_0 f(t_n, A + delta, z^n), and (y^n, z^n) is stored.
+// The driver sees y in FP32, so the iteration runs in FP32; the test
+// |delta^(p+1) - delta^(p)| <= tol is exact (near convergence the two
+// increments are within a factor two, so their float difference carries no
+// rounding; a float is <= tol exactly when it is <= picard_tol_f).  A
+// two-cycle across a rounding boundary of the FP32 argument is as far as the
+// FP32 driver can resolve, and ends it too.
+template <int DRV, bool COH>
+__device__ __forceinline__ void finish_points32(const Params &P, const DrvC<float> &dc,
+                                                float4 *__restrict__ ringA, const float *part,
+                                                int G, int n, int i0, Stats *st) {
+  const int tid = threadIdx.x;
+  const int ii = i0 + tid;
+  const bool active = tid < kStepTP && ii <= int(P.Nx - 1);
+  int it = 0;
+  float d = 0.f;
+  if (active) {
+    const int gs = G * kStepTP;
+    float zS = 0.f, zC = 0.f, yS = 0.f, yC = 0.f, fz = 0.f, fy = 0.f;
+    for (int q = 0; q < G; ++q) {
+      const int o = q * kStepTP + tid;
+      two_sum_into(zS, zC, part[0 * gs + o]);
+      zC = __fadd_rn(zC, part[1 * gs + o]);
+      fz = __fadd_rn(fz, part[2 * gs + o]);
+      fy = __fadd_rn(fy, part[3 * gs + o]);
+      two_sum_into(yS, yC, part[4 * gs + o]);
+      yC = __fadd_rn(yC, part[5 * gs + o]);
     }
+    // z^n = zS + (zC + fz) and A = yS + (yC + fy) as exact float pairs
+    float zh = zS, zl = 0.f, Ah = yS, Al = 0.f;
+    two_sum_into(zh, zl, __fadd_rn(zC, fz));
+    two_sum_into(Ah, Al, __fadd_rn(yC, fy));
+    float tn, etn, emtn;
+    level_time<DRV>(P, n, tn, etn, emtn);
+    const float hg0 = float(P.hg0);
+    const float4 prev = ldl<COH>(ringA + int64_t((n + 1) % P.nslot) * P.Nx + ii);
+    float dl = __fsub_rn(prev.x, Ah), dpp = __int_as_float(0x7fc00000);
+    while (it < P.picard_max) {
+      const float dn = hg0 * driver<DRV>(dc, tn, etn, emtn, Ah + dl, zh);
+      ++it;
+      d = fabsf(__fsub_rn(dn, dl));
+      const bool cyc = dn == dpp;
+      dpp = dl;
+      dl = dn;
+      if (cyc) d = 0.f;
+      if (d <= P.picard_tol_f) break;
+    }
+    // y^n = A + delta, renormalized
+    float yh = Ah, yl = Al;
+    two_sum_into(yh, yl, dl);
+    const float s = __fadd_rn(yh, yl);
+    yl = __fsub_rn(yl, __fsub_rn(s, yh));
+    yh = s;
+    const float s2 = __fadd_rn(zh, zl);
+    zl = __fsub_rn(zl, __fsub_rn(s2, zh));
+    zh = s2;
+    ringA[int64_t(n % P.nslot) * P.Nx + ii] = make_float4(yh, zh, yl, zl);
   }
-  if (lost) {
-    atomicOr(&st->timeout, 1);
-    // let any copy still in flight land before the buffers go away (bounded)
-    for (int t = np > kTmaStages ? np - kTmaStages : 0; t < np; ++t)
-      mbar_wait(full + t % kTmaStages, uint32_t((t / kTmaStages) & 1));
-  }
+  record_picard(st, active, it, double(d), P.picard_tol);
 }
 
-template <int DRV, bool LASTJ, bool COH>
-__device__ __forceinline__ void pairs32_any(bool interior, const DrvC<float> &dc,
-                                            const float4 *__restrict__ A,
-                                            const float2 *__restrict__ B, const PairF32 *row,
-                                            int q0, int q1, int ii, int last, float tj, float et,
-                                            float emt, float &Sz, float &Cz, float &Fz, float &Fy,
-                                            float &Sy, float &Cy) {
-  if (interior)
-    pairs32<DRV, false, LASTJ, COH>(dc, A, B, row, q0, q1, ii, last, tj, et, emt, Sz, Cz, Fz, Fy,
-                                    Sy, Cy);
-  else
-    pairs32<DRV, true, LASTJ, COH>(dc, A, B, row, q0, q1, ii, last, tj, et, emt, Sz, Cz, Fz, Fy,
-                                   Sy, Cy);
-}
-
-// One tile of kStepTP points of level n, called by every thread of the CTA;
-// `tab` (the pair table of the problem) and `part` are in shared memory.
-// Threads of groups g >= G idle.  The caller separates consecutive tiles by
-// a barrier (part is reused).
-template <int DRV, bool TMA, bool COH>
+// One tile of kStepTP points of level n with direct loads, called by every
+// thread of the CTA; `tab` (the pair table of the problem) and `part` are in
+// shared memory.  Thread tp of group g accumulates the pairs of group g for
+// point i0 + tp; threads of groups g >= G idle.  The caller separates
+// consecutive tiles by a barrier (part is reused).
+template <int DRV, bool COH>
 __device__ __forceinline__ void step_tile32(const Params &P, const DrvC<float> &dc,
                                             float4 *__restrict__ ringA,
                                             const float2 *__restrict__ ringB,
                                             const PairF32 *tab, float *part, int n, int i0,
-                                            Stats *st, unsigned char *stages = nullptr,
-                                            uint64_t *bars = nullptr) {
+                                            Stats *st) {
   const int tp = threadIdx.x % kStepTP, g = threadIdx.x / kStepTP;
   const int G = P.G;
   const int last = int(P.Nx - 1);
-  const int ii = i0 + tp;
   if (g < G) {
-    const int j = g / P.S + 1, lc = g % P.S;
-    const int q0 = lc * P.Lg, q1 = q0 + P.Lg < P.Lp ? q0 + P.Lg : P.Lp;
-    float Sz = 0.f, Cz = 0.f, Fz = 0.f, Fy = 0.f, Sy = 0.f, Cy = 0.f;
-    const int64_t off = int64_t((n + j) % P.nslot) * P.Nx;
-    const double tjd = (n + j) * P.dt;
-    const float tj = float(tjd);
-    float et = 0.f, emt = 0.f;
-    if constexpr (DRV == BSDE_DRIVER_EX2) {
-      et = float(exp(tjd * tjd));
-      emt = float(exp(-tjd * tjd));
-    }
-    const PairF32 *row = tab + (j - 1) * P.Lp;
-    const bool interior = i0 + P.smin[j - 1] >= 0 && i0 + kStepTP + P.smax[j - 1] <= last;
-    if (TMA && interior) {
-      // every thread of the group takes part (barriers inside)
-      unsigned char *stg = stages + size_t(g) * kTmaStages * kStageBytes;
-      uint64_t *bar = bars + g * kTmaStages;
-      if (j == P.k)
-        pairs32_tma<DRV, true>(dc, ringA + off, ringB + off, off, row, q0, q1, i0, tp, g, tj, et,
-                               emt, stg, bar, st, Sz, Cz, Fz, Fy, Sy, Cy);
-      else
-        pairs32_tma<DRV, false>(dc, ringA + off, ringB + off, off, row, q0, q1, i0, tp, g, tj, et,
-                                emt, stg, bar, st, Sz, Cz, Fz, Fy, Sy, Cy);
-      if (ii > last) Sz = Cz = Fz = Fy = Sy = Cy = 0.f;
-    } else if (ii <= last) {
-      if (j == P.k)
-        pairs32_any<DRV, true, COH>(interior, dc, ringA + off, ringB + off, row, q0, q1, ii, last,
-                                    tj, et, emt, Sz, Cz, Fz, Fy, Sy, Cy);
-      else
-        pairs32_any<DRV, false, COH>(interior, dc, ringA + off, ringB + off, row, q0, q1, ii,
-                                     last, tj, et, emt, Sz, Cz, Fz, Fy, Sy, Cy);
-    }
-    part[(0 * G + g) * kStepTP + tp] = Sz;
-    part[(1 * G + g) * kStepTP + tp] = Cz;
-    part[(2 * G + g) * kStepTP + tp] = Fz;
-    part[(3 * G + g) * kStepTP + tp] = Fy;
-    part[(4 * G + g) * kStepTP + tp] = Sy;
-    part[(5 * G + g) * kStepTP + tp] = Cy;
+    const Group32 w = group32(P, g, i0);
+    Acc32 acc{make_float2(0.f, 0.f), make_float2(0.f, 0.f), 0.f, 0.f};
+    const int64_t off = int64_t((n + w.j) % P.nslot) * P.Nx;
+    float tj, et, emt;
+    level_time<DRV>(P, n + w.j, tj, et, emt);
+    const PairF32 *row = tab + (w.j - 1) * P.Lp;
+    if (w.interior)
+      pairs32<DRV, false, COH>(dc, ringA + off, ringB + off, row, w.q0, w.q1, i0 + tp, last, tj,
+                               et, emt, acc);
+    else  // cells clamp onto the grid, so points past the end are harmless
+      pairs32<DRV, true, COH>(dc, ringA + off, ringB + off, row, w.q0, w.q1, i0 + tp, last, tj,
+                              et, emt, acc);
+    store_partials(part, G, g, tp, acc);
   }
   __syncthreads();
-  if (g != 0) return;
-
-  const bool active = ii <= last;
-  int it = 0;
-  double d = 0.0;
-  if (active) {
-    float zS = 0.f, zC = 0.f, yS = 0.f, yC = 0.f, fz = 0.f, fy = 0.f;
-    for (int q = 0; q < G; ++q) {
-      two_sum_into(zS, zC, part[(0 * G + q) * kStepTP + tp]);
-      zC = __fadd_rn(zC, part[(1 * G + q) * kStepTP + tp]);
-      fz = __fadd_rn(fz, part[(2 * G + q) * kStepTP + tp]);
-      fy = __fadd_rn(fy, part[(3 * G + q) * kStepTP + tp]);
-      two_sum_into(yS, yC, part[(4 * G + q) * kStepTP + tp]);
-      yC = __fadd_rn(yC, part[(5 * G + q) * kStepTP + tp]);
-    }
-    // combination of z^n and of the explicit part A of y^n in FP64
-    const double z = double(zS) + (double(zC) + double(fz));
-    const double Ay = double(yS) + (double(yC) + double(fy));
-    const double tnd = n * P.dt;
-    const float tn = float(tnd);
-    float etn = 0.f, emtn = 0.f;
-    if constexpr (DRV == BSDE_DRIVER_EX2) {
-      etn = float(exp(tnd * tnd));
-      emtn = float(exp(-tnd * tnd));
-    }
-    const float zf = __double2float_rn(z);
-    const float Ayf = __double2float_rn(Ay);
-    const float hg0 = float(P.hg0);
-    // Picard on the increment delta = y^n - A = k dt gy_0 f(t_n, A + delta, z^n).
-    // The driver sees y in FP32, so the iteration runs in FP32; the test
-    // |delta^(p+1) - delta^(p)| <= tol is exact (near convergence the two
-    // increments are within a factor two, so their float difference carries
-    // no rounding).  A two-cycle across a rounding boundary of the FP32
-    // argument is as far as the FP32 driver can resolve, and ends it too.
-    const float4 prev = ldl<COH>(ringA + int64_t((n + 1) % P.nslot) * P.Nx + ii);
-    float dl = __fsub_rn(prev.x, Ayf), dpp = __int_as_float(0x7fc00000);
-    while (it < P.picard_max) {
-      const float dn = hg0 * driver<DRV>(dc, tn, etn, emtn, Ayf + dl, zf);
-      ++it;
-      d = double(fabsf(__fsub_rn(dn, dl)));
-      const bool cyc = dn == dpp;
-      dpp = dl;
-      dl = dn;
-      if (cyc) d = 0.0;
-      if (d <= P.picard_tol) break;
-    }
-    const double y = Ay + double(dl);
-    split_store(ringA + int64_t(n % P.nslot) * P.Nx, ii, y, z);
-  }
-  record_picard(st, active, it, d, P.picard_tol);
+  finish_points32<DRV, COH>(P, dc, ringA, part, G, n, i0, st);
 }
 
-// Shared memory of k_step32: bulk-copy stages (G x kTmaStages x kStageBytes),
-// their barriers, the pair table, the groups' partial sums.
-__host__ __device__ inline size_t step32_bar_bytes(int G) {
-  return (size_t(G) * kTmaStages * 8 + 127) & ~size_t(127);
-}
+
+// ---------------------------------------------------------------------------
+// The FP32C step kernel of one level: one CTA per tile of kStepTP points and
+// G groups of kStepTP threads, level data through L1 (the k level windows of
+// the CTA's nodes are reused by neighbouring threads' cells c + 1 and by the
+// neighbouring CTAs on the SM).
+// ---------------------------------------------------------------------------
 __host__ __device__ inline size_t step32_smem(int G, int kP) {
-  return size_t(G) * kTmaStages * kStageBytes + step32_bar_bytes(G) +
-         sizeof(PairF32) * size_t(kP) + sizeof(float) * 6 * size_t(G) * kStepTP;
+  return sizeof(PairF32) * size_t(kP) + sizeof(float) * 6 * size_t(G) * kStepTP;
 }
 
 template <int DRV>
-__global__ void __launch_bounds__(kStepTP * kMaxGroups)
+__global__ void __launch_bounds__(kStepTP * kMaxGroups, 3)
     k_step32(const Params P, const DrvC<float> dc, float4 *__restrict__ ringA,
              const float2 *__restrict__ ringB, const PairF32 *__restrict__ table, int n,
              Stats *st) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int kP = P.k * P.Lp;
-  unsigned char *stages = smem_raw;
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + size_t(P.G) * kTmaStages * kStageBytes);
-  PairF32 *tab = reinterpret_cast<PairF32 *>(reinterpret_cast<unsigned char *>(bars) +
-                                             step32_bar_bytes(P.G));
-  float *part = reinterpret_cast<float *>(tab + kP);  // [6][G][TP]
+  PairF32 *tab = reinterpret_cast<PairF32 *>(smem_raw);
+  float *part = reinterpret_cast<float *>(tab + kP);  // [6][G][kStepTP]
   {
+    // the pair table is written once, at plan time
     const float4 *src = reinterpret_cast<const float4 *>(table);
     float4 *dst = reinterpret_cast<float4 *>(tab);
-    for (int t = threadIdx.x; t < kP * 4; t += blockDim.x) dst[t] = src[t];
+    for (int t = threadIdx.x; t < kP * kPairVec; t += blockDim.x) dst[t] = src[t];
   }
-  if (threadIdx.x < P.G * kTmaStages) mbar_init(bars + threadIdx.x, 1);
-  fence_barrier_init();
   __syncthreads();
-  step_tile32<DRV, true, false>(P, dc, ringA, ringB, tab, part, n, blockIdx.x * kStepTP, st, stages,
-                                bars);
+  wait_predecessor();
+  step_tile32<DRV, false>(P, dc, ringA, ringB, tab, part, n, blockIdx.x * kStepTP, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -913,8 +862,8 @@ __device__ void readout_values(const Params &P, Ring64 r64, Ring32 r32, int slot
     } else {
       const float4 a = ldl<COH>(r32.A + off + c + q);
       const float2 b = ldl<COH>(r32.B + off + c + q);
-      v[0][q] = double(a.x) + double(a.y); M[0][q] = b.x;
-      v[1][q] = double(a.z) + double(a.w); M[1][q] = b.y;
+      v[0][q] = double(a.x) + double(a.z); M[0][q] = b.x;
+      v[1][q] = double(a.y) + double(a.w); M[1][q] = b.y;
     }
   }
   const double om = 1.0 - th, c6 = P.dx * P.dx / 6.0;

@@ -17,11 +17,15 @@ namespace bsde {
 
 constexpr int kServerRing = 1 << 16;  // request ring positions (indices wrap)
 
-// Host-mapped control block (written by the host, read by the device).
+// Host-mapped control block.  The first line is written by the host, the
+// second by the device.
 struct alignas(64) ServerCtl {
   uint32_t req_tail;   // requests published so far
   uint32_t shutdown;   // nonzero: clusters exit once they find no request
   uint32_t pad[14];
+  uint32_t stopped;    // set by the device: a cluster's idle limit passed and
+                       // every cluster leaves after its current request
+  uint32_t pad2[15];
   int32_t req_slot[kServerRing];
 };
 
@@ -53,14 +57,16 @@ __device__ __forceinline__ void st_release_sys(uint32_t *p, uint32_t v) {
 __global__ void __launch_bounds__(kBatchThreads, 2)
     k_server32(ServerCtl *ctl, ServerSlot *slots, ServerDev *dev, Stats *dstats,
                unsigned char *pool, unsigned long long idle_ns) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   BatchSmem &sm = *reinterpret_cast<BatchSmem *>(smem_raw);
   cg::cluster_group cl = cg::this_cluster();
   while (true) {
     if (cl.block_rank() == 0 && threadIdx.x == 0) {
       const uint32_t pos = atomicAdd(&dev->req_head, 1u);
       // wait until the host publishes ring position pos, or shuts down, or
-      // the idle limit passes (then flag the error and leave)
+      // the idle limit passes.  A cluster that gives up leaves pos claimed
+      // and unserved, so it stops the whole server: the others leave too and
+      // the host reports the requests that no cluster will serve.
       int slot = -1;
       const uint64_t t0 = global_ns();
       while (true) {
@@ -68,9 +74,11 @@ __global__ void __launch_bounds__(kBatchThreads, 2)
           slot = __ldcv(&ctl->req_slot[pos % kServerRing]);
           break;
         }
-        if (ld_acquire_sys(&ctl->shutdown)) break;
+        if (ld_acquire_sys(&ctl->shutdown) || ld_acquire_sys(&ctl->stopped)) break;
         if (global_ns() - t0 > idle_ns) {
           atomicExch(&dev->error, 1);
+          __threadfence_system();
+          st_release_sys(&ctl->stopped, 1u);
           break;
         }
         __nanosleep(2000);
@@ -94,7 +102,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2)
     {
       const float4 *src = reinterpret_cast<const float4 *>(S->tab);
       float4 *dst = reinterpret_cast<float4 *>(sm.tab);
-      const int n4 = sm.D.P.k * sm.D.P.Lp * 4;
+      const int n4 = sm.D.P.k * sm.D.P.Lp * kPairVec;
       for (int t = threadIdx.x; t < n4; t += blockDim.x) dst[t] = __ldcv(src + t);
       if (threadIdx.x < kInvPivots) sm.sid[threadIdx.x] = float(sm.D.P.invd[threadIdx.x]);
     }
@@ -106,6 +114,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2)
       st->iters_max = 0;
       st->nonconv = 0;
       st->timeout = 0;
+      __threadfence();
     }
     __syncthreads();
     cl.sync();

@@ -116,3 +116,26 @@ def test_start_and_stop_without_requests(B):
     srv.start(cluster=2, idle_ms=20000)
     srv.stop()
     srv.close()
+
+
+def test_idle_limit_stops_the_server_and_it_restarts(B):
+    """A server left without requests past its idle limit stops itself: submit
+    and stop report the timeout, and a restart serves requests again."""
+    p = W.call_problem(Nx=1024, N=16, k=2, L=16)
+    srv = B.Server(slots=8, pool_bytes=1 << 24)
+    try:
+        srv.start(cluster=1, idle_ms=100)
+        time.sleep(1.0)
+        with pytest.raises(B.BsdeError):
+            srv.submit(p)
+        assert srv.poll() == []
+        with pytest.raises(B.BsdeError):
+            srv.stop()
+        srv.start(cluster=1, idle_ms=20000)
+        s = srv.submit(p)
+        got = _wait_all(srv, 1)
+        srv.stop()
+    finally:
+        srv.close()
+    ref = B.solve(p, "fp32c")
+    assert got[s]["y0"] == ref["y0"] and got[s]["z0"] == ref["z0"]
