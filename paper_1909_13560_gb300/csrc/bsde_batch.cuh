@@ -70,7 +70,7 @@ __device__ void batch_instance(BatchSmem &sm, unsigned char *ws, Stats *st,
   const int nst = int((P.Nx - 2 + kBatchSplineTile - 1) / kBatchSplineTile);
   for (int m = 0; m < P.k; ++m) {
     for (int t = crank; t < nst; t += csize) {
-      spline_tile<BSDE_FP32C, kBatchSplineTile, true>(P, r64, r32, (P.N - m) % P.nslot, t, nt, sm.sr,
+      spline_tile<BSDE_FP32C, kBatchSplineTile, true, kBatchThreads>(P, r64, r32, (P.N - m) % P.nslot, t, nt, sm.sr,
                                                 sm.sg, sm.sid);
       __syncthreads();
     }
@@ -86,7 +86,7 @@ __device__ void batch_instance(BatchSmem &sm, unsigned char *ws, Stats *st,
     }
     cl.sync();
     for (int t = crank; t < nst; t += csize) {
-      spline_tile<BSDE_FP32C, kBatchSplineTile, true>(P, r64, r32, n % P.nslot, t, nt, sm.sr, sm.sg,
+      spline_tile<BSDE_FP32C, kBatchSplineTile, true, kBatchThreads>(P, r64, r32, n % P.nslot, t, nt, sm.sr, sm.sg,
                                                 sm.sid);
       __syncthreads();
     }

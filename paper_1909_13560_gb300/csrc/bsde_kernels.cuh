@@ -254,10 +254,11 @@ struct SplineT<BSDE_FP32C> {
 };
 
 // One tile of TS unknowns of the level in `slot`, by the threads tid < nt of
-// the CTA (all threads of the CTA must call it: it holds barriers).
+// the CTA (all threads of the CTA must call it: it holds barriers); NT is the
+// compile-time thread count the right-hand sides are spread over (nt >= NT).
 // sr, sg: [2][TS + 2W] and sid: [kInvPivots] in shared memory; sid must hold
 // the pivots 1/d_m in T before the call.
-template <int PREC, int TS, bool COH = false>
+template <int PREC, int TS, bool COH, int NT>
 __device__ __forceinline__ void spline_tile(const Params &P, Ring64 r64, Ring32 r32, int slot,
                                             int tile, int nt,
                                             typename SplineT<PREC>::T (*sr)[TS + 2 * SplineT<PREC>::W],
@@ -276,29 +277,52 @@ __device__ __forceinline__ void spline_tile(const Params &P, Ring64 r64, Ring32 
   const int tid = threadIdx.x;
   if (a >= u) return;  // uniform over the CTA
 
-  // right-hand sides
-  for (int m = ra + tid; m < rb && tid < nt; m += nt) {
-    T ry, rz;
-    if constexpr (PREC == BSDE_FP64) {
-      const double4_32a v0 = ldl<COH>(r64.ring + off + m), v1 = ldl<COH>(r64.ring + off + m + 1),
-                        v2 = ldl<COH>(r64.ring + off + m + 2);
-      ry = P.inv_dx2_6 * (v0.x - 2.0 * v1.x + v2.x);
-      rz = P.inv_dx2_6 * (v0.z - 2.0 * v1.z + v2.z);
-    } else {
-      // (hi, lo) pairs: neighbouring hi values differ exactly (Sterbenz) away
-      // from sign changes, so the second difference keeps the pair precision
-      const float4 v0 = ldl<COH>(r32.A + off + m), v1 = ldl<COH>(r32.A + off + m + 1),
-                   v2 = ldl<COH>(r32.A + off + m + 2);
-      const float inv6 = float(P.inv_dx2_6);
-      const float d1y = __fadd_rn(__fsub_rn(v1.x, v0.x), __fsub_rn(v1.z, v0.z));
-      const float d2y = __fadd_rn(__fsub_rn(v2.x, v1.x), __fsub_rn(v2.z, v1.z));
-      const float d1z = __fadd_rn(__fsub_rn(v1.y, v0.y), __fsub_rn(v1.w, v0.w));
-      const float d2z = __fadd_rn(__fsub_rn(v2.y, v1.y), __fsub_rn(v2.w, v1.w));
-      ry = inv6 * __fsub_rn(d2y, d1y);
-      rz = inv6 * __fsub_rn(d2z, d1z);
+  // right-hand sides, RC consecutive unknowns per thread: the RC + 2 level
+  // values of a chunk are loaded together (NT threads cover the tile and its
+  // halos)
+  constexpr int RC = (TS + 2 * W + NT - 1) / NT;
+  {
+    const int m0 = ra + tid * RC;
+    if (tid < NT && m0 < rb) {
+      if constexpr (PREC == BSDE_FP64) {
+        double vy[RC + 2], vz[RC + 2];
+#pragma unroll
+        for (int q = 0; q < RC + 2; ++q) {
+          const double4_32a v = m0 + q < rb + 2 ? ldl<COH>(r64.ring + off + m0 + q)
+                                                : make_double4_32a(0.0, 0.0, 0.0, 0.0);
+          vy[q] = v.x;
+          vz[q] = v.z;
+        }
+#pragma unroll
+        for (int q = 0; q < RC; ++q) {
+          if (m0 + q < rb) {
+            sr[0][m0 + q - base] = P.inv_dx2_6 * (vy[q] - 2.0 * vy[q + 1] + vy[q + 2]);
+            sr[1][m0 + q - base] = P.inv_dx2_6 * (vz[q] - 2.0 * vz[q + 1] + vz[q + 2]);
+          }
+        }
+      } else {
+        // (hi, lo) pairs: neighbouring hi values differ exactly (Sterbenz)
+        // away from sign changes, so the differences keep the pair precision
+        float4 v[RC + 2];
+#pragma unroll
+        for (int q = 0; q < RC + 2; ++q)
+          v[q] = m0 + q < rb + 2 ? ldl<COH>(r32.A + off + m0 + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float inv6 = float(P.inv_dx2_6);
+#pragma unroll
+        for (int q = 0; q < RC; ++q) {
+          if (m0 + q < rb) {
+            const float d1y = __fadd_rn(__fsub_rn(v[q + 1].x, v[q].x), __fsub_rn(v[q + 1].z, v[q].z));
+            const float d2y =
+                __fadd_rn(__fsub_rn(v[q + 2].x, v[q + 1].x), __fsub_rn(v[q + 2].z, v[q + 1].z));
+            const float d1z = __fadd_rn(__fsub_rn(v[q + 1].y, v[q].y), __fsub_rn(v[q + 1].w, v[q].w));
+            const float d2z =
+                __fadd_rn(__fsub_rn(v[q + 2].y, v[q + 1].y), __fsub_rn(v[q + 2].w, v[q + 1].w));
+            sr[0][m0 + q - base] = inv6 * __fsub_rn(d2y, d1y);
+            sr[1][m0 + q - base] = inv6 * __fsub_rn(d2z, d1z);
+          }
+        }
+      }
     }
-    sr[0][m - base] = ry;
-    sr[1][m - base] = rz;
   }
   __syncthreads();
 
@@ -363,7 +387,8 @@ __global__ void __launch_bounds__(kSplineTile / kSplineChunk)
   __shared__ T sid[kInvPivots];
   if (threadIdx.x < kInvPivots) sid[threadIdx.x] = T(P.invd[threadIdx.x]);
   wait_predecessor();
-  spline_tile<PREC, kSplineTile>(P, r64, r32, slot, blockIdx.x, blockDim.x, sr, sg, sid);
+  spline_tile<PREC, kSplineTile, false, kSplineTile / kSplineChunk>(P, r64, r32, slot, blockIdx.x,
+                                                                    blockDim.x, sr, sg, sid);
 }
 
 // ---------------------------------------------------------------------------
