@@ -32,8 +32,9 @@ struct alignas(16) BatchSmem {
   InstDesc D;
   PairF32 tab[kMaxK * (kMaxL / 2)];
   float part[6 * 6 * kStepTP];
-  float sr[2][kBatchSplineTile + 2 * SplineT<BSDE_FP32C>::W];
-  float sg[2][kBatchSplineTile + 2 * SplineT<BSDE_FP32C>::W];
+  float sr[2][spline_span<BSDE_FP32C>(kBatchSplineTile)];
+  float sg[2][spline_span<BSDE_FP32C>(kBatchSplineTile)];
+  float sd[2][spline_span<BSDE_FP32C>(kBatchSplineTile)];
   float sid[kInvPivots];
   int inst;
 };
@@ -58,9 +59,9 @@ __device__ void batch_instance(BatchSmem &sm, unsigned char *ws, Stats *st,
   const int crank = int(cl.block_rank()), csize = int(cl.num_blocks());
   const int tid = threadIdx.x, nt = blockDim.x;
   float4 *ringA = reinterpret_cast<float4 *>(ws + sm.D.ringA);
-  float2 *ringB = reinterpret_cast<float2 *>(ws + sm.D.ringB);
+
   Ring64 r64{nullptr};
-  Ring32 r32{ringA, ringB};
+  const Ring32 r32 = ring32(ringA, ws + sm.D.ringB, P);
 
   // the k initial levels and their splines
   for (int m = 0; m < P.k; ++m)
@@ -70,8 +71,8 @@ __device__ void batch_instance(BatchSmem &sm, unsigned char *ws, Stats *st,
   const int nst = int((P.Nx - 2 + kBatchSplineTile - 1) / kBatchSplineTile);
   for (int m = 0; m < P.k; ++m) {
     for (int t = crank; t < nst; t += csize) {
-      spline_tile<BSDE_FP32C, kBatchSplineTile, true, kBatchThreads>(P, r64, r32, (P.N - m) % P.nslot, t, nt, sm.sr,
-                                                sm.sg, sm.sid);
+      spline_tile<BSDE_FP32C, kBatchSplineTile, true, kBatchThreads>(
+          P, r64, r32, (P.N - m) % P.nslot, t, nt, sm.sr, sm.sg, sm.sd, sm.sid);
       __syncthreads();
     }
   }
@@ -81,13 +82,13 @@ __device__ void batch_instance(BatchSmem &sm, unsigned char *ws, Stats *st,
   const int ntiles = int((P.Nx + kStepTP - 1) / kStepTP);
   for (int n = P.N - P.k; n >= 0; --n) {
     for (int t = crank; t < ntiles; t += csize) {
-      step_tile32<DRV, true>(P, sm.D.dc32, ringA, ringB, sm.tab, sm.part, n, t * kStepTP, st);
+      step_tile32<DRV, true>(P, sm.D.dc32, r32, sm.tab, sm.part, n, t * kStepTP, st);
       __syncthreads();
     }
     cl.sync();
     for (int t = crank; t < nst; t += csize) {
-      spline_tile<BSDE_FP32C, kBatchSplineTile, true, kBatchThreads>(P, r64, r32, n % P.nslot, t, nt, sm.sr, sm.sg,
-                                                sm.sid);
+      spline_tile<BSDE_FP32C, kBatchSplineTile, true, kBatchThreads>(
+          P, r64, r32, n % P.nslot, t, nt, sm.sr, sm.sg, sm.sd, sm.sid);
       __syncthreads();
     }
     cl.sync();

@@ -119,8 +119,7 @@ static void launch_step(bsde_plan_t *pl, cudaStream_t s, int n) {
   } else {
     const size_t sm = step32_smem(P.G, P.k * P.Lp);
     launch_pdl(k_step32<DRV>, blocks, threads, sm, s, P, pl->dc32,
-               reinterpret_cast<float4 *>(pl->ws + pl->lay.ringA),
-               reinterpret_cast<const float2 *>(pl->ws + pl->lay.ringB),
+               ring32(pl->ws + pl->lay.ringA, pl->ws + pl->lay.ringB, P),
                reinterpret_cast<const PairF32 *>(pl->ws + pl->lay.ptable), n, st);
   }
 }
@@ -140,8 +139,7 @@ template <int PREC>
 static int64_t enqueue_spline(bsde_plan_t *pl, cudaStream_t s, int slot) {
   const Params &P = pl->P;
   Ring64 r64{reinterpret_cast<double4_32a *>(pl->ws + pl->lay.ring64)};
-  Ring32 r32{reinterpret_cast<float4 *>(pl->ws + pl->lay.ringA),
-             reinterpret_cast<float2 *>(pl->ws + pl->lay.ringB)};
+  const Ring32 r32 = ring32(pl->ws + pl->lay.ringA, pl->ws + pl->lay.ringB, P);
   const unsigned blocks = unsigned((P.Nx - 2 + kSplineTile - 1) / kSplineTile);
   launch_pdl(k_spline<PREC>, blocks, unsigned(kSplineTile / kSplineChunk), 0, s, P, r64, r32, slot);
   return 1;
@@ -152,8 +150,7 @@ template <int PREC>
 static int64_t enqueue_solve(bsde_plan_t *pl, cudaStream_t s, bool imported) {
   const Params &P = pl->P;
   Ring64 r64{reinterpret_cast<double4_32a *>(pl->ws + pl->lay.ring64)};
-  Ring32 r32{reinterpret_cast<float4 *>(pl->ws + pl->lay.ringA),
-             reinterpret_cast<float2 *>(pl->ws + pl->lay.ringB)};
+  const Ring32 r32 = ring32(pl->ws + pl->lay.ringA, pl->ws + pl->lay.ringB, P);
   Stats *st = reinterpret_cast<Stats *>(pl->ws + pl->lay.stats);
   double *sy = reinterpret_cast<double *>(pl->ws + pl->lay.stage);
   double *sz = sy + int64_t(P.k) * P.Nx;
@@ -522,7 +519,7 @@ static int batch_layout(int n, const bsde_problem *ps, BatchLayout &L) {
     const size_t nx = size_t(p.Nx), ns = size_t(p.k + 1);
     L.ptable[i] = off; off = up(off + size_t(p.k) * ((p.L + 1) / 2) * sizeof(PairF32));
     L.ringA[i] = off; off = up(off + ns * nx * 16);
-    L.ringB[i] = off; off = up(off + ns * nx * 8 + 64);
+    L.ringB[i] = off; off = up(off + ns * nx * (16 + 8));
   }
   L.total = off;
   return BSDE_OK;
@@ -798,7 +795,7 @@ namespace bsde {
 static size_t request_bytes(const bsde_problem &p) {
   auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
   const size_t nx = size_t(p.Nx), ns = size_t(p.k + 1);
-  return up(ns * nx * 16) + up(ns * nx * 8 + 64);
+  return up(ns * nx * 16) + up(ns * nx * (16 + 8));
 }
 
 static bool pool_alloc(bsde_server_t *s, size_t bytes, size_t &off) {

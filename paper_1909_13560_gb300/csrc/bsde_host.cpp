@@ -181,7 +181,7 @@ Layout layout_for(const bsde_problem &p) {
     L.ring64 = off; off = up(off + ns * nx * 32);
   } else {
     L.ringA = off; off = up(off + ns * nx * 16);
-    L.ringB = off; off = up(off + ns * nx * 8 + 64);  // bulk copies may read 8 B past a level
+    L.ringB = off; off = up(off + ns * nx * (16 + 8));  // interval records (d, P), Q
   }
   L.table = off; off = up(off + size_t(p.k) * p.L * (p.precision == BSDE_FP64 ? sizeof(NodeF64) : sizeof(NodeF32)));
   L.ptable = off; off = up(off + size_t(p.k) * ((p.L + 1) / 2) * sizeof(PairF32));
@@ -288,13 +288,13 @@ void build_tables(Params &P, NodeF64 *t64, NodeF32 *t32, PairF32 *tp, int target
         pr.shift_b = nb.shift;
         pr.cfz = na.cfz;  // zero for the middle node (DeltaW = 0)
         pr.cfy = na.cfy * half;
+        const double tha = double(na.w1), thb = double(nb.w1);
+        const float kaa = float(-c6 * tha * (1.0 - tha)), kab = float(-c6 * thb * (1.0 - thb));
         for (int v = 0; v < 2; ++v) {
-          pr.w1a[v] = na.w1;
-          pr.w2a[v] = na.w2;
-          pr.w3a[v] = na.w3;
-          pr.w1b[v] = nb.w1;
-          pr.w2b[v] = nb.w2;
-          pr.w3b[v] = nb.w3;
+          pr.tha[v] = na.w1;
+          pr.kaa[v] = kaa;
+          pr.thb[v] = nb.w1;
+          pr.kab[v] = kab;
         }
         // lanes (y, z)
         pr.ch[0] = na.cyh * half;

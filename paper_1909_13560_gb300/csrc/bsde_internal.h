@@ -50,14 +50,16 @@ struct NodeF32 {
 // The arithmetic runs on (y, z) lane pairs (packed FP32x2), so every weight
 // is stored twice, once per lane, and the compensated-sum coefficients are
 // lane pairs (cy, cz): hi parts, and negated hi and lo parts, which let the
-// error terms be formed by fused multiply-adds alone.  Six float4:
-// (shift_a, shift_b, cfz, cfy), (w1a, w1a, w2a, w2a), (w3a, w3a, w1b, w1b),
-// (w2b, w2b, w3b, w3b), (cyh, czh, -cyh, -czh), (-cyl, -czl, 0, 0);
-// w1 = theta, w0 = 1 - theta.  cy is zero for j < k.
+// error terms be formed by fused multiply-adds alone.  Five float4:
+// (shift_a, shift_b, cfz, cfy), (th_a, th_a, ka_a, ka_a),
+// (th_b, th_b, ka_b, ka_b), (cyh, czh, -cyh, -czh), (-cyl, -czl, 0, 0);
+// th = theta, ka = -theta (1 - theta) dx^2 / 6 (the spline value is
+// v_c + theta d + ka (P + theta Q) on the interval records).  cy is zero for
+// j < k.
 struct PairF32 {
   int32_t shift_a, shift_b;
   float cfz, cfy;
-  float w1a[2], w2a[2], w3a[2], w1b[2], w2b[2], w3b[2];
+  float tha[2], kaa[2], thb[2], kab[2];
   float ch[2], nch[2], ncl[2], pad[2];
 };
 constexpr int kPairVec = int(sizeof(PairF32) / 16);  // float4 per entry
@@ -86,7 +88,7 @@ struct Params {
 struct Layout {
   size_t ring64;   // FP64: double4 (y, M_y, z, M_z) x nslot x Nx
   size_t ringA;    // FP32C: float4 (y_hi, y_lo, z_hi, z_lo) x nslot x Nx
-  size_t ringB;    // FP32C: float2 (M_y, M_z) x nslot x Nx
+  size_t ringB;    // FP32C: interval records, float4 (d, P) then float2 Q, x nslot x Nx
   size_t table;    // node table (k L entries)
   size_t ptable;   // FP32C pair table (k ceil(L/2) entries)
   size_t stage;    // 2 x k x Nx doubles: imported initial levels / exported level 0

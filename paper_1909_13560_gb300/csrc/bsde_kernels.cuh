@@ -147,10 +147,21 @@ __device__ __forceinline__ void wait_predecessor() {
 struct Ring64 {
   double4_32a *ring;
 };
+// FP32C level slots: A = (y_hi, z_hi, y_lo, z_lo) per node; per interval
+// [x_c, x_{c+1}] the spline as B = (d_y, d_z, P_y, P_z), C = (Q_y, Q_z) with
+// d = v_{c+1} - v_c, P = 2 M_c + M_{c+1}, Q = M_{c+1} - M_c (zero for the
+// last node), so that the spline value at x_c + theta dx is
+// v_c + theta d + kappa (P + theta Q), kappa = -theta (1 - theta) dx^2 / 6.
+// B and C share one allocation: C follows the nslot Nx records of B.
 struct Ring32 {
   float4 *A;
-  float2 *B;
+  float4 *B;
+  float2 *C;
 };
+__host__ __device__ inline Ring32 ring32(void *A, void *B, const Params &P) {
+  float4 *b = static_cast<float4 *>(B);
+  return Ring32{static_cast<float4 *>(A), b, reinterpret_cast<float2 *>(b + int64_t(P.nslot) * P.Nx)};
+}
 
 __global__ void k_reset_stats(Stats *s) {
   if (threadIdx.x == 0) {
@@ -233,12 +244,14 @@ __global__ void k_export(const Params P, Ring64 r64, Ring32 r32, double *sy, dou
 // M_0 = M_{Nx-1} = 0.  LU of tridiag(1, 4, 1): forward g_m = r_m - g_{m-1}/d_{m-1},
 // backward u_m = (g_m - u_{m+1})/d_m.  Both recurrences contract by 2 - sqrt 3
 // per step, so a chunk of unknowns started W steps early from zero is exact
-// to (2 - sqrt 3)^{W+1}: W = 32 (1.4e-19) in FP64, W = 16 (1.9e-10, far below
-// what M contributes at weight dx^2/6) in FP32C.
-// One CTA owns a tile of kSplineTile unknowns: it stages the level values of
-// the tile and its halo in shared memory, forms r, runs the forward sweep of
+// to (2 - sqrt 3)^{W+1}: W = 32 (1.4e-19) in FP64; W = 12 (3.7e-8) in FP32C,
+// where M enters a value at weight |kappa| <= dx^2/24, so the truncation is a
+// few 1e-12 of the value at most (below the FP32C resolution of the sums).
+// One CTA owns a tile of kSplineTile unknowns: it loads the level values of
+// the tile and its halo, forms r in shared memory, runs the forward sweep of
 // each thread's chunk (warm-up from the left), then the backward sweep
-// (warm-up from the right over the neighbouring chunks' g), all on chip.
+// (warm-up from the right over the neighbouring chunks' g), all on chip.  In
+// FP32C it then writes the interval records (d, P, Q) of its cells.
 // ---------------------------------------------------------------------------
 template <int PREC>
 struct SplineT;
@@ -250,19 +263,30 @@ struct SplineT<BSDE_FP64> {
 template <>
 struct SplineT<BSDE_FP32C> {
   using T = float;
-  static constexpr int W = 16;
+  static constexpr int W = 12;
 };
+
+// Shared-memory span of a spline tile of TS unknowns: the tile, W on the
+// left and W + 2 on the right.
+template <int PREC>
+__host__ __device__ constexpr int spline_span(int TS) {
+  return TS + 2 * SplineT<PREC>::W + 2;
+}
 
 // One tile of TS unknowns of the level in `slot`, by the threads tid < nt of
 // the CTA (all threads of the CTA must call it: it holds barriers); NT is the
 // compile-time thread count the right-hand sides are spread over (nt >= NT).
-// sr, sg: [2][TS + 2W] and sid: [kInvPivots] in shared memory; sid must hold
-// the pivots 1/d_m in T before the call.
+// sr, sg, sd: [2][spline_span(TS)] and sid: [kInvPivots] in shared memory;
+// sid must hold the pivots 1/d_m in T before the call.
+// Unknown m is M_{m+1}; the tile is unknowns [a, b), the forward sweep runs
+// over [a, rb) and the backward one over [a, min(b + 1, u)) (one more on the
+// right: FP32C cell b needs M_{b+1}).
 template <int PREC, int TS, bool COH, int NT>
 __device__ __forceinline__ void spline_tile(const Params &P, Ring64 r64, Ring32 r32, int slot,
                                             int tile, int nt,
-                                            typename SplineT<PREC>::T (*sr)[TS + 2 * SplineT<PREC>::W],
-                                            typename SplineT<PREC>::T (*sg)[TS + 2 * SplineT<PREC>::W],
+                                            typename SplineT<PREC>::T (*sr)[spline_span<PREC>(TS)],
+                                            typename SplineT<PREC>::T (*sg)[spline_span<PREC>(TS)],
+                                            typename SplineT<PREC>::T (*sd)[spline_span<PREC>(TS)],
                                             const typename SplineT<PREC>::T *sid) {
   using T = typename SplineT<PREC>::T;
   constexpr int W = SplineT<PREC>::W;
@@ -271,19 +295,20 @@ __device__ __forceinline__ void spline_tile(const Params &P, Ring64 r64, Ring32 
   const int a = tile * TS;
   const int b = a + TS < u ? a + TS : u;
   const int ra = a - W > 0 ? a - W : 0;
-  const int rb = b + W < u ? b + W : u;
+  const int rb = b + W + 1 < u ? b + W + 1 : u;
+  const int bx = b + 1 < u ? b + 1 : u;
   const int base = a - W;
   const int64_t off = int64_t(slot) * P.Nx;
   const int tid = threadIdx.x;
   if (a >= u) return;  // uniform over the CTA
 
-  // right-hand sides, RC consecutive unknowns per thread: the RC + 2 level
-  // values of a chunk are loaded together (NT threads cover the tile and its
-  // halos)
-  constexpr int RC = (TS + 2 * W + NT - 1) / NT;
+  // right-hand sides r_m (m in [ra, rb)) and, in FP32C, first differences
+  // d_m = v_{m+1} - v_m (m in [ra, rb]), RC consecutive m per thread: the
+  // RC + 2 level values of a chunk are loaded together
+  constexpr int RC = (TS + 2 * W + 2 + NT - 1) / NT;
   {
     const int m0 = ra + tid * RC;
-    if (tid < NT && m0 < rb) {
+    if (tid < NT && m0 <= rb) {
       if constexpr (PREC == BSDE_FP64) {
         double vy[RC + 2], vz[RC + 2];
 #pragma unroll
@@ -308,17 +333,21 @@ __device__ __forceinline__ void spline_tile(const Params &P, Ring64 r64, Ring32 
         for (int q = 0; q < RC + 2; ++q)
           v[q] = m0 + q < rb + 2 ? ldl<COH>(r32.A + off + m0 + q) : make_float4(0.f, 0.f, 0.f, 0.f);
         const float inv6 = float(P.inv_dx2_6);
+        float dy[RC + 1], dz[RC + 1];
+#pragma unroll
+        for (int q = 0; q < RC + 1; ++q) {
+          dy[q] = __fadd_rn(__fsub_rn(v[q + 1].x, v[q].x), __fsub_rn(v[q + 1].z, v[q].z));
+          dz[q] = __fadd_rn(__fsub_rn(v[q + 1].y, v[q].y), __fsub_rn(v[q + 1].w, v[q].w));
+        }
 #pragma unroll
         for (int q = 0; q < RC; ++q) {
           if (m0 + q < rb) {
-            const float d1y = __fadd_rn(__fsub_rn(v[q + 1].x, v[q].x), __fsub_rn(v[q + 1].z, v[q].z));
-            const float d2y =
-                __fadd_rn(__fsub_rn(v[q + 2].x, v[q + 1].x), __fsub_rn(v[q + 2].z, v[q + 1].z));
-            const float d1z = __fadd_rn(__fsub_rn(v[q + 1].y, v[q].y), __fsub_rn(v[q + 1].w, v[q].w));
-            const float d2z =
-                __fadd_rn(__fsub_rn(v[q + 2].y, v[q + 1].y), __fsub_rn(v[q + 2].w, v[q + 1].w));
-            sr[0][m0 + q - base] = inv6 * __fsub_rn(d2y, d1y);
-            sr[1][m0 + q - base] = inv6 * __fsub_rn(d2z, d1z);
+            sr[0][m0 + q - base] = inv6 * __fsub_rn(dy[q + 1], dy[q]);
+            sr[1][m0 + q - base] = inv6 * __fsub_rn(dz[q + 1], dz[q]);
+          }
+          if (m0 + q <= rb) {
+            sd[0][m0 + q - base] = dy[q];
+            sd[1][m0 + q - base] = dz[q];
           }
         }
       }
@@ -343,9 +372,11 @@ __device__ __forceinline__ void spline_tile(const Params &P, Ring64 r64, Ring32 
   }
   __syncthreads();
 
-  // backward sweep over the chunks of the tile, warm-up from the right
-  for (int s0 = a + tid * C; s0 < b && tid < nt; s0 += nt * C) {
-    const int e = s0 + C < b ? s0 + C : b;
+  // backward sweep over the chunks of [a, bx), warm-up from the right; the
+  // results go to the ring (FP64) or, for the records, to sr (FP32C: r is
+  // no longer needed)
+  for (int s0 = a + tid * C; s0 < bx && tid < nt; s0 += nt * C) {
+    const int e = s0 + C < bx ? s0 + C : bx;
     const int top = e + W < u ? e + W : u;
     T my = T(0), mz = T(0);
     for (int m = top - 1; m >= s0; --m) {
@@ -354,24 +385,43 @@ __device__ __forceinline__ void spline_tile(const Params &P, Ring64 r64, Ring32 
       mz = (sg[1][m - base] - mz) * id;
       if (m < e) {
         if constexpr (PREC == BSDE_FP64) {
-          r64.ring[off + m + 1].y = my;
-          r64.ring[off + m + 1].w = mz;
+          if (m < b) {
+            r64.ring[off + m + 1].y = my;
+            r64.ring[off + m + 1].w = mz;
+          }
         } else {
-          r32.B[off + m + 1] = make_float2(my, mz);
+          sr[0][m - base] = my;
+          sr[1][m - base] = mz;
         }
       }
     }
   }
-  if (tile == 0 && tid == 0) {
-    // natural end conditions M_0 = M_{Nx-1} = 0
-    if constexpr (PREC == BSDE_FP64) {
+  if constexpr (PREC == BSDE_FP64) {
+    if (tile == 0 && tid == 0) {
+      // natural end conditions M_0 = M_{Nx-1} = 0
       r64.ring[off].y = 0.0;
       r64.ring[off].w = 0.0;
       r64.ring[off + P.Nx - 1].y = 0.0;
       r64.ring[off + P.Nx - 1].w = 0.0;
-    } else {
-      r32.B[off] = make_float2(0.f, 0.f);
-      r32.B[off + P.Nx - 1] = make_float2(0.f, 0.f);
+    }
+  } else {
+    __syncthreads();
+    // interval records of cells a + 1 .. b (and 0 for the first tile, and the
+    // last node for the last tile); M_0 = M_{Nx-1} = 0 (natural spline)
+    const int c0 = a == 0 ? 0 : a + 1;
+    const int c1 = b == u ? u + 1 : b;  // inclusive
+    for (int c = c0 + tid; c <= c1 && tid < nt; c += nt) {
+      float4 rec = make_float4(0.f, 0.f, 0.f, 0.f);
+      float2 q = make_float2(0.f, 0.f);
+      if (c <= u) {
+        const float my0 = c == 0 ? 0.f : sr[0][c - 1 - base], mz0 = c == 0 ? 0.f : sr[1][c - 1 - base];
+        const float my1 = c == u ? 0.f : sr[0][c - base], mz1 = c == u ? 0.f : sr[1][c - base];
+        rec = make_float4(sd[0][c - base], sd[1][c - base], __fmaf_rn(2.f, my0, my1),
+                          __fmaf_rn(2.f, mz0, mz1));
+        q = make_float2(__fsub_rn(my1, my0), __fsub_rn(mz1, mz0));
+      }
+      r32.B[off + c] = rec;
+      r32.C[off + c] = q;
     }
   }
 }
@@ -381,14 +431,13 @@ template <int PREC>
 __global__ void __launch_bounds__(kSplineTile / kSplineChunk)
     k_spline(const Params P, Ring64 r64, Ring32 r32, int slot) {
   using T = typename SplineT<PREC>::T;
-  constexpr int W = SplineT<PREC>::W;
-  __shared__ T sr[2][kSplineTile + 2 * W];
-  __shared__ T sg[2][kSplineTile + 2 * W];
+  constexpr int S = spline_span<PREC>(kSplineTile);
+  __shared__ T sr[2][S], sg[2][S], sd[2][S];
   __shared__ T sid[kInvPivots];
   if (threadIdx.x < kInvPivots) sid[threadIdx.x] = T(P.invd[threadIdx.x]);
   wait_predecessor();
   spline_tile<PREC, kSplineTile, false, kSplineTile / kSplineChunk>(P, r64, r32, slot, blockIdx.x,
-                                                                    blockDim.x, sr, sg, sid);
+                                                                    blockDim.x, sr, sg, sd, sid);
 }
 
 // ---------------------------------------------------------------------------
@@ -600,17 +649,15 @@ __device__ __forceinline__ uint64_t global_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// Cells of one node for point ii.  A node off the grid clamps to the end
-// value: both cells become the end cell and the caller zeroes the weights.
+// Cell of one node for point ii.  A node off the grid clamps to the end
+// value: the cell becomes the end node and the caller zeroes the weights.
 template <bool CLAMP>
-__device__ __forceinline__ bool pair_cells(int ii, int shift, int last, int &c0, int &c1) {
-  c0 = ii + shift;
-  c1 = c0 + 1;
+__device__ __forceinline__ bool pair_cell(int ii, int shift, int last, int &c) {
+  c = ii + shift;
   if (CLAMP) {
-    const bool cl = c0 < 0, ch = c0 >= last;
-    if (cl | ch) {
-      c0 = cl ? 0 : last;
-      c1 = c0;
+    const bool lo = c < 0, hi = c >= last;
+    if (lo | hi) {
+      c = lo ? 0 : last;
       return true;
     }
   }
@@ -618,30 +665,27 @@ __device__ __forceinline__ bool pair_cells(int ii, int shift, int last, int &c0,
 }
 
 // (y, z) spline value of one node as hi + del from the level data of its
-// cells c, c+1: A = (y_hi, z_hi, y_lo, z_lo), B = (M_y, M_z).
-__device__ __forceinline__ void node_value(const float4 &a0, const float4 &a1, const float2 &m0,
-                                           const float2 &m1, float2 w1, float2 w2, float2 w3,
-                                           float2 &hi, float2 &del) {
-  hi = hi2(a0);
-  const float2 l0 = lo2(a0);
-  const float2 d = f2add(f2sub(hi2(a1), hi), f2sub(lo2(a1), l0));
-  del = f2add(f2fma(w1, d, l0), f2fma(w2, m0, f2mul(w3, m1)));
+// cell c: A = (y_hi, z_hi, y_lo, z_lo) and the interval record B = (d, P),
+// C = Q (see Ring32); th = (theta, theta), ka = (kappa, kappa).
+__device__ __forceinline__ void node_value(const float4 &a, const float4 &bq, const float2 &cq,
+                                           float2 th, float2 ka, float2 &hi, float2 &del) {
+  hi = hi2(a);
+  del = f2fma(ka, f2fma(th, cq, lo2(bq)), f2fma(th, hi2(bq), lo2(a)));
 }
 
-// The arithmetic of one node pair (see PairF32 for the entry e0..e5), given
+// The arithmetic of one node pair (see PairF32 for the entry e0..e4), given
 // the level data of the two nodes' cells.  S, C: compensated (y, z) sums;
 // Fz, Fy: driver terms.
 template <int DRV>
 __device__ __forceinline__ void pair_math(const DrvC<float> &dc, float tj, float et, float emt,
                                           const float4 &e0, const float4 &e1, const float4 &e2,
-                                          const float4 &e3, const float4 &e4, const float4 &e5,
-                                          const float4 &aa, const float4 &ab, const float4 &ba,
-                                          const float4 &bb, const float2 &maa, const float2 &mab,
-                                          const float2 &mba, const float2 &mbb, float2 &S,
-                                          float2 &C, float &Fz, float &Fy) {
+                                          const float4 &e3, const float4 &e4, const float4 &aa,
+                                          const float4 &ab, const float2 &ac, const float4 &ba,
+                                          const float4 &bb, const float2 &bc, float2 &S, float2 &C,
+                                          float &Fz, float &Fy) {
   float2 ha, da, hb, db;
-  node_value(aa, ab, maa, mab, hi2(e1), lo2(e1), hi2(e2), ha, da);
-  node_value(ba, bb, mba, mbb, lo2(e2), hi2(e3), lo2(e3), hb, db);
+  node_value(aa, ab, ac, hi2(e1), lo2(e1), ha, da);
+  node_value(ba, bb, bc, hi2(e2), lo2(e2), hb, db);
   const float2 va = f2add(ha, da), vb = f2add(hb, db);
   const float Fa = driver<DRV>(dc, tj, et, emt, va.x, va.y);
   const float Fb = driver<DRV>(dc, tj, et, emt, vb.x, vb.y);
@@ -650,7 +694,7 @@ __device__ __forceinline__ void pair_math(const DrvC<float> &dc, float tj, float
   // the pair's hi parts summed exactly, then one compensated product
   float2 hs, he;
   two_sum2(ha, hb, hs, he);
-  comp_acc2(S, C, hi2(e4), lo2(e4), hi2(e5), hs, f2add(f2add(da, db), he));
+  comp_acc2(S, C, hi2(e3), lo2(e3), hi2(e4), hs, f2add(f2add(da, db), he));
 }
 
 // Accumulators of one point: compensated (y, z) sums and the driver terms.
@@ -662,30 +706,25 @@ struct Acc32 {
 // One group's node pairs for point ii, level data loaded directly from
 // global memory (L1/L2).  With CLAMP false every cell must lie on the grid.
 template <int DRV, bool CLAMP, bool COH>
-__device__ __forceinline__ void pairs32(const DrvC<float> &dc, const float4 *__restrict__ A,
-                                        const float2 *__restrict__ B, const PairF32 *row, int q0,
-                                        int q1, int ii, int last, float tj, float et, float emt,
-                                        Acc32 &acc) {
+__device__ __forceinline__ void pairs32(const DrvC<float> &dc, Ring32 r, int64_t off,
+                                        const PairF32 *row, int q0, int q1, int ii, int last,
+                                        float tj, float et, float emt, Acc32 &acc) {
+  const float4 *A = r.A + off;
+  const float4 *B = r.B + off;
+  const float2 *Cq = r.C + off;
 #pragma unroll 1
   for (int q = q0; q < q1; ++q) {
     const float4 *te = reinterpret_cast<const float4 *>(row + q);
-    const float4 e0 = te[0], e4 = te[4], e5 = te[5];
-    float4 e1 = te[1], e2 = te[2], e3 = te[3];
-    int ca0, ca1, cb0, cb1;
-    if (pair_cells<CLAMP>(ii, __float_as_int(e0.x), last, ca0, ca1)) {
-      e1 = make_float4(0.f, 0.f, 0.f, 0.f);
-      e2.x = e2.y = 0.f;
-    }
-    if (pair_cells<CLAMP>(ii, __float_as_int(e0.y), last, cb0, cb1)) {
-      e2.z = e2.w = 0.f;
-      e3 = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    const float4 aa = ldl<COH>(A + ca0), ab = ldl<COH>(A + ca1), ba = ldl<COH>(A + cb0),
-                 bb = ldl<COH>(A + cb1);
-    const float2 maa = ldl<COH>(B + ca0), mab = ldl<COH>(B + ca1), mba = ldl<COH>(B + cb0),
-                 mbb = ldl<COH>(B + cb1);
-    pair_math<DRV>(dc, tj, et, emt, e0, e1, e2, e3, e4, e5, aa, ab, ba, bb, maa, mab, mba, mbb,
-                   acc.S, acc.C, acc.Fz, acc.Fy);
+    const float4 e0 = te[0], e3 = te[3], e4 = te[4];
+    float4 e1 = te[1], e2 = te[2];
+    int ca, cb;
+    if (pair_cell<CLAMP>(ii, __float_as_int(e0.x), last, ca)) e1 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (pair_cell<CLAMP>(ii, __float_as_int(e0.y), last, cb)) e2 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 aa = ldl<COH>(A + ca), ab = ldl<COH>(B + ca), ba = ldl<COH>(A + cb),
+                 bb = ldl<COH>(B + cb);
+    const float2 ac = ldl<COH>(Cq + ca), bc = ldl<COH>(Cq + cb);
+    pair_math<DRV>(dc, tj, et, emt, e0, e1, e2, e3, e4, aa, ab, ac, ba, bb, bc, acc.S, acc.C,
+                   acc.Fz, acc.Fy);
   }
 }
 
@@ -744,7 +783,7 @@ __device__ __forceinline__ void store_partials(float *part, int G, int g, int tp
 template <int DRV, bool COH>
 __device__ __forceinline__ void finish_points32(const Params &P, const DrvC<float> &dc,
                                                 float4 *__restrict__ ringA, const float *part,
-                                                int G, int n, int i0, Stats *st) {
+                                                int G, int n, int i0, Stats *st, float prev_y) {
   const int tid = threadIdx.x;
   const int ii = i0 + tid;
   const bool active = tid < kStepTP && ii <= int(P.Nx - 1);
@@ -769,8 +808,7 @@ __device__ __forceinline__ void finish_points32(const Params &P, const DrvC<floa
     float tn, etn, emtn;
     level_time<DRV>(P, n, tn, etn, emtn);
     const float hg0 = float(P.hg0);
-    const float4 prev = ldl<COH>(ringA + int64_t((n + 1) % P.nslot) * P.Nx + ii);
-    float dl = __fsub_rn(prev.x, Ah), dpp = __int_as_float(0x7fc00000);
+    float dl = __fsub_rn(prev_y, Ah), dpp = __int_as_float(0x7fc00000);
     while (it < P.picard_max) {
       const float dn = hg0 * driver<DRV>(dc, tn, etn, emtn, Ah + dl, zh);
       ++it;
@@ -801,14 +839,16 @@ __device__ __forceinline__ void finish_points32(const Params &P, const DrvC<floa
 // point i0 + tp; threads of groups g >= G idle.  The caller separates
 // consecutive tiles by a barrier (part is reused).
 template <int DRV, bool COH>
-__device__ __forceinline__ void step_tile32(const Params &P, const DrvC<float> &dc,
-                                            float4 *__restrict__ ringA,
-                                            const float2 *__restrict__ ringB,
+__device__ __forceinline__ void step_tile32(const Params &P, const DrvC<float> &dc, Ring32 r32,
                                             const PairF32 *tab, float *part, int n, int i0,
                                             Stats *st) {
   const int tp = threadIdx.x % kStepTP, g = threadIdx.x / kStepTP;
   const int G = P.G;
   const int last = int(P.Nx - 1);
+  // the Picard start y^{n+1} of the points this thread finishes, loaded early
+  float prev_y = 0.f;
+  if (threadIdx.x < kStepTP && i0 + int(threadIdx.x) <= last)
+    prev_y = ldl<COH>(r32.A + int64_t((n + 1) % P.nslot) * P.Nx + i0 + threadIdx.x).x;
   if (g < G) {
     const Group32 w = group32(P, g, i0);
     Acc32 acc{make_float2(0.f, 0.f), make_float2(0.f, 0.f), 0.f, 0.f};
@@ -817,15 +857,13 @@ __device__ __forceinline__ void step_tile32(const Params &P, const DrvC<float> &
     level_time<DRV>(P, n + w.j, tj, et, emt);
     const PairF32 *row = tab + (w.j - 1) * P.Lp;
     if (w.interior)
-      pairs32<DRV, false, COH>(dc, ringA + off, ringB + off, row, w.q0, w.q1, i0 + tp, last, tj,
-                               et, emt, acc);
+      pairs32<DRV, false, COH>(dc, r32, off, row, w.q0, w.q1, i0 + tp, last, tj, et, emt, acc);
     else  // cells clamp onto the grid, so points past the end are harmless
-      pairs32<DRV, true, COH>(dc, ringA + off, ringB + off, row, w.q0, w.q1, i0 + tp, last, tj,
-                              et, emt, acc);
+      pairs32<DRV, true, COH>(dc, r32, off, row, w.q0, w.q1, i0 + tp, last, tj, et, emt, acc);
     store_partials(part, G, g, tp, acc);
   }
   __syncthreads();
-  finish_points32<DRV, COH>(P, dc, ringA, part, G, n, i0, st);
+  finish_points32<DRV, COH>(P, dc, r32.A, part, G, n, i0, st, prev_y);
 }
 
 
@@ -841,9 +879,8 @@ __host__ __device__ inline size_t step32_smem(int G, int kP) {
 
 template <int DRV>
 __global__ void __launch_bounds__(kStepTP * kMaxGroups, 3)
-    k_step32(const Params P, const DrvC<float> dc, float4 *__restrict__ ringA,
-             const float2 *__restrict__ ringB, const PairF32 *__restrict__ table, int n,
-             Stats *st) {
+    k_step32(const Params P, const DrvC<float> dc, Ring32 r32, const PairF32 *__restrict__ table,
+             int n, Stats *st) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int kP = P.k * P.Lp;
   PairF32 *tab = reinterpret_cast<PairF32 *>(smem_raw);
@@ -856,7 +893,7 @@ __global__ void __launch_bounds__(kStepTP * kMaxGroups, 3)
   }
   __syncthreads();
   wait_predecessor();
-  step_tile32<DRV, false>(P, dc, ringA, ringB, tab, part, n, blockIdx.x * kStepTP, st);
+  step_tile32<DRV, false>(P, dc, r32, tab, part, n, blockIdx.x * kStepTP, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -886,16 +923,24 @@ __device__ void readout_values(const Params &P, Ring64 r64, Ring32 r32, int slot
       v[0][q] = a.x; M[0][q] = a.y; v[1][q] = a.z; M[1][q] = a.w;
     } else {
       const float4 a = ldl<COH>(r32.A + off + c + q);
-      const float2 b = ldl<COH>(r32.B + off + c + q);
-      v[0][q] = double(a.x) + double(a.z); M[0][q] = b.x;
-      v[1][q] = double(a.y) + double(a.w); M[1][q] = b.y;
+      v[0][q] = double(a.x) + double(a.z);
+      v[1][q] = double(a.y) + double(a.w);
     }
   }
   const double om = 1.0 - th, c6 = P.dx * P.dx / 6.0;
-  ay = om * v[0][0] + th * v[0][1] +
-       c6 * ((om * om * om - om) * M[0][0] + (th * th * th - th) * M[0][1]);
-  az = om * v[1][0] + th * v[1][1] +
-       c6 * ((om * om * om - om) * M[1][0] + (th * th * th - th) * M[1][1]);
+  if constexpr (PREC == BSDE_FP64) {
+    ay = om * v[0][0] + th * v[0][1] +
+         c6 * ((om * om * om - om) * M[0][0] + (th * th * th - th) * M[0][1]);
+    az = om * v[1][0] + th * v[1][1] +
+         c6 * ((om * om * om - om) * M[1][0] + (th * th * th - th) * M[1][1]);
+  } else {
+    // curvature part kappa (P + theta Q) of the interval record
+    const float4 rb = ldl<COH>(r32.B + off + c);
+    const float2 rq = ldl<COH>(r32.C + off + c);
+    const double ka = -c6 * th * om;
+    ay = om * v[0][0] + th * v[0][1] + ka * (double(rb.z) + th * double(rq.x));
+    az = om * v[1][0] + th * v[1][1] + ka * (double(rb.w) + th * double(rq.y));
+  }
 }
 
 template <int PREC>
