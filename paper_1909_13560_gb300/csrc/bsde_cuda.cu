@@ -71,6 +71,14 @@ struct bsde_plan_s {
 
 namespace bsde {
 
+// Threads of the step kernels the GPU holds at once (36 warps per SM at the
+// kernels' register use), or 0 if the device cannot be queried.
+static long resident_step_threads(int device) {
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
+  return long(sms) * 36 * 32;
+}
+
 static void driver_coefs(const Params &P, DrvC<double> &c64, DrvC<float> &c32) {
   c64 = DrvC<double>{0.0, 0.0, 0.0, 0.0};
   if (P.driver == BSDE_DRIVER_BS) {
@@ -140,8 +148,9 @@ static int64_t enqueue_spline(bsde_plan_t *pl, cudaStream_t s, int slot) {
   const Params &P = pl->P;
   Ring64 r64{reinterpret_cast<double4_32a *>(pl->ws + pl->lay.ring64)};
   const Ring32 r32 = ring32(pl->ws + pl->lay.ringA, pl->ws + pl->lay.ringB, P);
-  const unsigned blocks = unsigned((P.Nx - 2 + kSplineTile - 1) / kSplineTile);
-  launch_pdl(k_spline<PREC>, blocks, unsigned(kSplineTile / kSplineChunk), 0, s, P, r64, r32, slot);
+  constexpr int TS = SplineLaunch<PREC>::TS;
+  const unsigned blocks = unsigned((P.Nx - 2 + TS - 1) / TS);
+  launch_pdl(k_spline<PREC>, blocks, unsigned(SplineLaunch<PREC>::NT), 0, s, P, r64, r32, slot);
   return 1;
 }
 
@@ -241,7 +250,7 @@ int bsde_plan(const bsde_problem *p, void *dev_workspace, size_t bytes, bsde_pla
     delete pl;
     return fail(BSDE_ENOMEM, "table allocation");
   }
-  build_tables(pl->P, t64, t32, tp);
+  build_tables(pl->P, t64, t32, tp, 4, kMaxGroups, resident_step_threads(pl->device));
   cudaError_t e;
   if (P.precision == BSDE_FP64) {
     e = cudaMemcpy(pl->ws + lay.table, t64, sizeof(NodeF64) * kL, cudaMemcpyHostToDevice);
@@ -441,7 +450,7 @@ extern "C" int bsde_solve_noalloc(const bsde_problem *p, void *stream, const dou
   NodeF64 t64[kMaxK * kMaxL];
   NodeF32 t32[kMaxK * kMaxL];
   PairF32 tpr[kMaxK * kMaxL];
-  build_tables(pl.P, t64, t32, tpr);
+  build_tables(pl.P, t64, t32, tpr, 4, kMaxGroups, resident_step_threads(pl.device));
   if (P.precision == BSDE_FP64) {
     BSDE_CUDA_TRY(cudaMemcpyAsync(pl.ws + pl.lay.table, t64, sizeof(NodeF64) * kL,
                                   cudaMemcpyHostToDevice, s));

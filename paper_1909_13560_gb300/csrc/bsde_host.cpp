@@ -192,14 +192,17 @@ Layout layout_for(const bsde_problem &p) {
 }
 
 // Work split of the step kernels: enough (j, l-chunk) groups per point that a
-// level of a modest grid still fills the GPU (at least four groups).
-static void work_split(Params &P, int target_groups, int max_groups) {
+// level of a modest grid still fills the GPU (at least target_groups), but no
+// more threads per level than the GPU holds at once when that is known
+// (resident_threads > 0): a level that fits one wave is not split further.
+static void work_split(Params &P, int target_groups, int max_groups, long resident_threads) {
   // FP64 splits the L nodes, FP32C the ceil(L/2) symmetric pairs
   P.Lp = (P.L + 1) / 2;
   const int units = P.precision == BSDE_FP64 ? P.L : P.Lp;
   int S = (target_groups + P.k - 1) / P.k;
   if (S * P.k > max_groups) S = max_groups / P.k;
   if (S > units) S = units;
+  while (S > 1 && resident_threads > 0 && long(P.Nx) * P.k * S > resident_threads) --S;
   if (S < 1) S = 1;
   P.S = S;
   P.Lg = (units + S - 1) / S;
@@ -226,8 +229,8 @@ static void cached_rule(int L, double *a, double *w) {
 }
 
 void build_tables(Params &P, NodeF64 *t64, NodeF32 *t32, PairF32 *tp, int target_groups,
-                  int max_groups) {
-  work_split(P, target_groups, max_groups);
+                  int max_groups, long resident_threads) {
+  work_split(P, target_groups, max_groups, resident_threads);
   double a[kMaxL], w[kMaxL];
   cached_rule(P.L, a, w);
   const double rpi = 1.0 / std::sqrt(M_PI);

@@ -14,8 +14,10 @@ constexpr int kMaxL = 64;
 constexpr int kInvPivots = 64;   // exact 1/d_m of the spline LU for m < 64
 constexpr int kStepTP = 64;      // grid points per CTA in the step kernels
 constexpr int kMaxGroups = 6;    // (j, l-chunk) groups per point
-constexpr int kSplineTile = 512;  // unknowns per CTA in the spline kernel
-constexpr int kSplineChunk = 4;   // unknowns per thread (serial recurrence)
+constexpr int kSplineTile = 512;  // unknowns per CTA in the FP64 spline kernel
+constexpr int kSplineTile32 = 256;  // unknowns (and threads) per CTA in the FP32C one
+constexpr int kSplineChunk = 4;   // unknowns per thread (serial recurrence, FP64)
+constexpr int kSplineHead = 16;   // FP32C: pivots of the spline LU are constant beyond this
 
 // Per (j, l) entry of the node tables.  The off-grid point
 // x_i + a_x j dt + b_x sqrt(2 j dt) a_l sits in cell i + shift at relative
@@ -112,6 +114,7 @@ Layout layout_for(const bsde_problem &p);
 int gauss_hermite(int L, double *nodes, double *weights);
 int gamma_tables(int k, double *gy, double *gz);
 void build_tables(Params &P, NodeF64 *t64, NodeF32 *t32, PairF32 *tp = nullptr,
-                  int target_groups = 4, int max_groups = kMaxGroups);
+                  int target_groups = 4, int max_groups = kMaxGroups,
+                  long resident_threads = 0);
 
 }  // namespace bsde

@@ -301,6 +301,7 @@ __device__ __forceinline__ void spline_tile(const Params &P, Ring64 r64, Ring32 
   const int64_t off = int64_t(slot) * P.Nx;
   const int tid = threadIdx.x;
   if (a >= u) return;  // uniform over the CTA
+  auto bar_sync = [] { __syncthreads(); };
 
   // right-hand sides r_m (m in [ra, rb)) and, in FP32C, first differences
   // d_m = v_{m+1} - v_m (m in [ra, rb]), RC consecutive m per thread: the
@@ -355,44 +356,95 @@ __device__ __forceinline__ void spline_tile(const Params &P, Ring64 r64, Ring32 
   }
   __syncthreads();
 
-  // forward sweep over the chunks of [a, rb): the tile and its right halo
-  for (int s0 = a + tid * C; s0 < rb && tid < nt; s0 += nt * C) {
-    const int e = s0 + C < rb ? s0 + C : rb;
-    const int st = s0 - W > 0 ? s0 - W : 0;
-    T gy = T(0), gz = T(0);
-    for (int m = st; m < e; ++m) {
-      const T id = m > 0 ? sid[m - 1 < kInvPivots ? m - 1 : kInvPivots - 1] : T(0);
-      gy = sr[0][m - base] - gy * id;
-      gz = sr[1][m - base] - gz * id;
-      if (m >= s0) {
+  if constexpr (PREC == BSDE_FP64) {
+    // forward sweep over the chunks of [a, rb): the tile and its right halo
+    for (int s0 = a + tid * C; s0 < rb && tid < nt; s0 += nt * C) {
+      const int e = s0 + C < rb ? s0 + C : rb;
+      const int st = s0 - W > 0 ? s0 - W : 0;
+      T gy = T(0), gz = T(0);
+      for (int m = st; m < e; ++m) {
+        const T id = m > 0 ? sid[m - 1 < kInvPivots ? m - 1 : kInvPivots - 1] : T(0);
+        gy = sr[0][m - base] - gy * id;
+        gz = sr[1][m - base] - gz * id;
+        if (m >= s0) {
+          sg[0][m - base] = gy;
+          sg[1][m - base] = gz;
+        }
+      }
+    }
+    bar_sync();
+
+    // backward sweep over the chunks of the tile, warm-up from the right
+    for (int s0 = a + tid * C; s0 < b && tid < nt; s0 += nt * C) {
+      const int e = s0 + C < b ? s0 + C : b;
+      const int top = e + W < u ? e + W : u;
+      T my = T(0), mz = T(0);
+      for (int m = top - 1; m >= s0; --m) {
+        const T id = sid[m < kInvPivots ? m : kInvPivots - 1];
+        my = (sg[0][m - base] - my) * id;
+        mz = (sg[1][m - base] - mz) * id;
+        if (m < e) {
+          r64.ring[off + m + 1].y = my;
+          r64.ring[off + m + 1].w = mz;
+        }
+      }
+    }
+  } else {
+    // FP32C: beyond the first kSplineHead unknowns the pivots are 2 + sqrt 3
+    // to FP32 precision, and both recurrences become sums over W + 1 terms
+    // with weights rho^q (rho = 1 / (2 + sqrt 3)), the same truncation as
+    // the warm-up of a serial chunk but with no serial chain:
+    //   g_m = sum_q (-rho)^q r_{m-q},     u_m = sum_q rho (-rho)^q g_{m+q}
+    // (the backward sum stops at the last unknown, where u = rho g exactly).
+    // The first tile runs its head (forward, m < H + W) and tail (backward,
+    // m < H) serially with the exact pivots.
+    constexpr int H = kSplineHead;
+    constexpr int F0 = H + W;
+    const T rho = sid[H];
+    if (a < F0 && tid == 0) {
+      T gy = T(0), gz = T(0);
+      const int e = F0 < rb ? F0 : rb;
+      for (int m = 0; m < e; ++m) {
+        const T id = m > 0 ? sid[m - 1] : T(0);
+        gy = sr[0][m - base] - gy * id;
+        gz = sr[1][m - base] - gz * id;
         sg[0][m - base] = gy;
         sg[1][m - base] = gz;
       }
     }
-  }
-  __syncthreads();
-
-  // backward sweep over the chunks of [a, bx), warm-up from the right; the
-  // results go to the ring (FP64) or, for the records, to sr (FP32C: r is
-  // no longer needed)
-  for (int s0 = a + tid * C; s0 < bx && tid < nt; s0 += nt * C) {
-    const int e = s0 + C < bx ? s0 + C : bx;
-    const int top = e + W < u ? e + W : u;
-    T my = T(0), mz = T(0);
-    for (int m = top - 1; m >= s0; --m) {
-      const T id = sid[m < kInvPivots ? m : kInvPivots - 1];
-      my = (sg[0][m - base] - my) * id;
-      mz = (sg[1][m - base] - mz) * id;
-      if (m < e) {
-        if constexpr (PREC == BSDE_FP64) {
-          if (m < b) {
-            r64.ring[off + m + 1].y = my;
-            r64.ring[off + m + 1].w = mz;
-          }
-        } else {
-          sr[0][m - base] = my;
-          sr[1][m - base] = mz;
-        }
+    for (int m = (a > F0 ? a : F0) + tid; m < rb && tid < nt; m += nt) {
+      T gy = sr[0][m - base], gz = sr[1][m - base], c = T(1);
+#pragma unroll
+      for (int q = 1; q <= W; ++q) {
+        c = -c * rho;
+        gy = __fmaf_rn(c, sr[0][m - q - base], gy);
+        gz = __fmaf_rn(c, sr[1][m - q - base], gz);
+      }
+      sg[0][m - base] = gy;
+      sg[1][m - base] = gz;
+    }
+    bar_sync();
+    // backward: M of unknowns [a, bx) into sr (r is no longer needed)
+    for (int m = (a > H ? a : H) + tid; m < bx && tid < nt; m += nt) {
+      const int qmax = u - 1 - m < W ? u - 1 - m : W;
+      T my = T(0), mz = T(0), c = rho;
+      for (int q = 0; q <= qmax; ++q) {
+        my = __fmaf_rn(c, sg[0][m + q - base], my);
+        mz = __fmaf_rn(c, sg[1][m + q - base], mz);
+        c = -c * rho;
+      }
+      sr[0][m - base] = my;
+      sr[1][m - base] = mz;
+    }
+    bar_sync();
+    if (a < H && tid == 0) {
+      const int e = H < bx ? H : bx;  // unknowns [a, e) serially, from u_e down
+      T my = e < u ? sr[0][e - base] : T(0), mz = e < u ? sr[1][e - base] : T(0);
+      for (int m = e - 1; m >= a; --m) {
+        my = (sg[0][m - base] - my) * sid[m];
+        mz = (sg[1][m - base] - mz) * sid[m];
+        sr[0][m - base] = my;
+        sr[1][m - base] = mz;
       }
     }
   }
@@ -427,17 +479,25 @@ __device__ __forceinline__ void spline_tile(const Params &P, Ring64 r64, Ring32 
 }
 
 
+// Spline kernel tiles: FP64 runs serial chunks of kSplineChunk unknowns per
+// thread; FP32C one unknown per thread (its sweeps are sums, not chains).
 template <int PREC>
-__global__ void __launch_bounds__(kSplineTile / kSplineChunk)
+struct SplineLaunch {
+  static constexpr int TS = PREC == BSDE_FP64 ? kSplineTile : kSplineTile32;
+  static constexpr int NT = PREC == BSDE_FP64 ? kSplineTile / kSplineChunk : kSplineTile32;
+};
+
+template <int PREC>
+__global__ void __launch_bounds__(SplineLaunch<PREC>::NT)
     k_spline(const Params P, Ring64 r64, Ring32 r32, int slot) {
   using T = typename SplineT<PREC>::T;
-  constexpr int S = spline_span<PREC>(kSplineTile);
+  constexpr int TS = SplineLaunch<PREC>::TS, NT = SplineLaunch<PREC>::NT;
+  constexpr int S = spline_span<PREC>(TS);
   __shared__ T sr[2][S], sg[2][S], sd[2][S];
   __shared__ T sid[kInvPivots];
   if (threadIdx.x < kInvPivots) sid[threadIdx.x] = T(P.invd[threadIdx.x]);
   wait_predecessor();
-  spline_tile<PREC, kSplineTile, false, kSplineTile / kSplineChunk>(P, r64, r32, slot, blockIdx.x,
-                                                                    blockDim.x, sr, sg, sd, sid);
+  spline_tile<PREC, TS, false, NT>(P, r64, r32, slot, blockIdx.x, blockDim.x, sr, sg, sd, sid);
 }
 
 // ---------------------------------------------------------------------------
