@@ -205,3 +205,26 @@ def test_config2_full_size(B, k):
             assert abs(got["z0"] - ref["z0"]) <= 1e-8 * abs(ref["z0"])
         else:
             assert math.isfinite(got["y0"]) and math.isfinite(got["z0"])
+
+
+@pytest.mark.parametrize("k", [2, 4])
+def test_config3_reduced_size(B, k):
+    """Lending/borrowing call (r = .04, R = .06) at the reduced parity size
+    Nx = 2^16, N = 256: k = 2 converges and matches the oracle strictly (and
+    the closed form, Black-Scholes at r - (R - r), to the scheme's accuracy);
+    k = 4 diverges on this grid in the oracle too, and the FP64 run follows
+    it to a relative 1e-8."""
+    p = W.config3(Nx=1 << 16, N=256, k=k)
+    ref = O.solve(p, threads=THREADS, want_level=True)
+    exact = O.exact(p, 0.0, p["x0"])[0]
+    for prec in ("fp64", "fp32c"):
+        got = B.solve(p, prec, want_level=True)
+        print(f"config3 k={k} {prec}: y0 {got['y0']:.10f} oracle {ref['y0']:.10f} exact {exact:.6f}")
+        if k == 2:
+            _cmp(got, ref, TOL64 if prec == "fp64" else TOL32, f"config3 k={k} {prec}")
+            assert abs(got["y0"] - exact) < 2e-3
+        elif prec == "fp64":
+            assert abs(got["y0"] - ref["y0"]) <= 1e-8 * abs(ref["y0"])
+            assert abs(got["z0"] - ref["z0"]) <= 1e-8 * abs(ref["z0"])
+        else:
+            assert math.isfinite(got["y0"]) and math.isfinite(got["z0"])
