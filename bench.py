@@ -230,7 +230,9 @@ def run_ours(args, rank, world, local_rank):
     sp = stream.cuda_stream
     c3 = args.workload == "config3"
     if c3:
-        ks = (4,) if tuple(args.ks) == KS else ks
+        # the configuration's k = 4, beside k = 2 (which converges on this
+        # grid; k = 4 diverges as the oracle does at the reduced size)
+        ks = (2, 4) if tuple(args.ks) == KS else ks
         probs = [W.config3(k=k) for k in ks]
     else:
         probs = [W.config2(k=k) for k in ks]
@@ -286,7 +288,7 @@ def run_ours(args, rank, world, local_rank):
             exact = _call_price(p)
             row = {"k": k, "y0": r.y0, "z0": r.z0, "picard_iters_max": r.picard_iters_max,
                    "exact_y0": exact, "err_y0_vs_exact": abs(r.y0 - exact),
-                   "diverged": abs(r.y0 - exact) > 1.0}
+                   "diverged": not (abs(r.y0 - exact) <= 1.0)}
             rows.append(row)
             continue
         row = {"k": k, "y0": r.y0, "z0": r.z0, "picard_iters_max": r.picard_iters_max}
@@ -297,7 +299,7 @@ def run_ours(args, rank, world, local_rank):
             # where the scheme itself diverges on this grid (the FP64 oracle is
             # far from the price), the run follows the oracle's growth and no
             # absolute tolerance applies: reported, not gated
-            row["diverged"] = abs(g["y0"] - g["exact_y0"]) > 1.0
+            row["diverged"] = not (abs(g["y0"] - g["exact_y0"]) <= 1.0)
             if not row["diverged"]:
                 tol = (1e-12 if args.precision == "fp64" else 1e-6) * max(1.0, abs(g["y0"]))
                 row["within_tol"] = row["err_y0_vs_oracle"] <= tol
@@ -378,7 +380,7 @@ def run_ours(args, rank, world, local_rank):
             "data": "synthetic",
             "config": {"workload": ("config3: call with lending/borrowing rates (r=.04, R=.06, "
                                     "mu=.06, sigma=.2, T=.5, K=100, x in ln100 +- 6 sigma sqrt T), "
-                                    f"Nx=2^20, N=1024, k={','.join(map(str, ks))}, L=16, one solve per step")
+                                    f"Nx=2^20, N=1024, k={','.join(map(str, ks))} (one solve each per step), L=16")
                                    if c3 else
                                    "config2: Black-Scholes call in log price (S0=K=100, "
                                    "r=.03, mu=.05, sigma=.2, T=1, x in ln100 +- 6 sigma), "
