@@ -337,6 +337,18 @@ def run_ours(args, rank, world, local_rank):
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak = _alu_peak_tflops(args.precision, sm_max)
     achieved = kern_flops / (kern_ms / 1000.0) / 1e12
+    # the FP32C step kernel streams one A record (16 B) and one interval
+    # record (24 B) per point and node from L2: its L2 -> SM rate against
+    # the L2 read bandwidth measured now by a plain streaming kernel
+    l2 = None
+    if args.precision == "fp32c":
+        l2_bytes = sum(40.0 * p["Nx"] * k * p["L"] * (p["N"] - k + 1) for k, p in zip(ks, probs))
+        l2_peak = B.l2_read_bandwidth(device=dev)
+        l2_gbs = l2_bytes / (kern_ms / 1000.0) / 1e9
+        l2 = {"achieved": l2_gbs, "peak": l2_peak, "unit": "GB/s", "frac": l2_gbs / l2_peak,
+              "bytes_per_point_node": 40,
+              "peak_source": "measured in this run: bsde_l2_read_probe, 48 MiB L2-resident "
+                             "buffer read 40 times by 8 CTAs per SM with 16-byte loads"}
 
     # end to end through the C ABI with host buffers: initial levels copied in
     # from pinned memory, level 0 and the result read back, every step
@@ -406,7 +418,8 @@ def run_ours(args, rank, world, local_rank):
                          "peak_source": f"derived: 152 SMs x {'128 FP32 lanes' if args.precision == 'fp32c' else '2 FP64 FMA units'} x 2 flop x {sm_max:.0f} MHz",
                          "flop_per_gp_step": {str(k): flops_per_gp_step(k, 16) for k in ks},
                          "avg_launch_ms": kern_ms / sum(p['N'] - p['k'] + 1 for p in probs),
-                         "step_launch_us": step_us},
+                         "step_launch_us": step_us,
+                         "l2": l2},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches_per_step * args.steps,

@@ -179,6 +179,17 @@ BSDE_API const char *bsde_last_error(void);
 BSDE_API int bsde_gauss_hermite(int L, double *nodes, double *weights);
 BSDE_API int bsde_gamma(int k, double *gy, double *gz);
 
+/* Measurement helper (no counterpart in the paper): enqueue on `stream` one
+ * launch that reads the `bytes` of device buffer `buf` `reps` times with
+ * 16-byte loads from every SM (each CTA a contiguous slice, again and again)
+ * and adds a float per CTA into `sink` (grid floats, device memory).
+ * With a buffer that fits in L2 this times the L2 -> SM read bandwidth the
+ * step kernels' level loads draw on.  `buf` 16-byte aligned, bytes a
+ * multiple of 16 and at least 16 * grid * 256, grid <= 65535.  Returns
+ * BSDE_EINVAL for bad arguments, BSDE_ECUDA if the launch fails. */
+BSDE_API int bsde_l2_read_probe(const void *buf, size_t bytes, int reps, int grid, void *sink,
+                                void *stream);
+
 /* ---- batched solves ------------------------------------------------------
  * Many independent problems (uneven Nx, N, k, driver, parameters; all
  * precision BSDE_FP32C, closed-form start) solved by one persistent launch:

@@ -69,7 +69,7 @@ _SYMBOLS = ("bsde_workspace_bytes", "bsde_plan", "bsde_solve", "bsde_result_fetc
             "bsde_batch_get_config", "bsde_batch_autotune", "bsde_solve_batch", "bsde_batch_free",
             "bsde_request_bytes", "bsde_server_workspace_bytes", "bsde_server_create",
             "bsde_server_start", "bsde_server_submit", "bsde_server_poll", "bsde_server_stop",
-            "bsde_server_free")
+            "bsde_server_free", "bsde_l2_read_probe")
 
 
 def load(path: str = LIB_PATH):
@@ -119,6 +119,7 @@ def load(path: str = LIB_PATH):
     lib.bsde_server_stop.argtypes = [vp]
     lib.bsde_server_free.argtypes = [vp]
     lib.bsde_server_free.restype = None
+    lib.bsde_l2_read_probe.argtypes = [vp, ctypes.c_size_t, ctypes.c_int, ctypes.c_int, vp, vp]
     _lib = lib
     return lib
 
@@ -480,3 +481,27 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def l2_read_bandwidth(mib: int = 48, reps: int = 40, device=None) -> float:
+    """L2 -> SM read bandwidth in GB/s: a buffer that fits in L2, read `reps`
+    times by one launch of 16-byte loads (after one warm-up launch), timed
+    with CUDA events on the launching stream."""
+    import torch
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    props = torch.cuda.get_device_properties(dev)
+    grid = 8 * props.multi_processor_count
+    buf = torch.ones((mib << 20) // 4, dtype=torch.float32, device=dev)
+    sink = torch.zeros(grid, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    lib = load()
+    args = (ctypes.c_void_p(buf.data_ptr()), buf.numel() * 4, 1, grid,
+            ctypes.c_void_p(sink.data_ptr()), ctypes.c_void_p(stream.cuda_stream))
+    _check(lib.bsde_l2_read_probe(*args), "bsde_l2_read_probe")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    _check(lib.bsde_l2_read_probe(args[0], args[1], reps, grid, args[4], args[5]),
+           "bsde_l2_read_probe")
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    return buf.numel() * 4 * reps / (e0.elapsed_time(e1) / 1e3) / 1e9

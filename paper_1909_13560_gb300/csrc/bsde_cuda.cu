@@ -390,6 +390,17 @@ int bsde_gamma(int k, double *gy, double *gz) {
   return gamma_tables(k, gy, gz);
 }
 
+int bsde_l2_read_probe(const void *buf, size_t bytes, int reps, int grid, void *sink,
+                       void *stream) {
+  if (!buf || !sink || reps < 1 || grid < 1 || grid > 65535 || bytes % 16 ||
+      reinterpret_cast<uintptr_t>(buf) % 16 || bytes < size_t(16) * 256 * size_t(grid))
+    return fail(BSDE_EINVAL, "bad probe arguments");
+  k_l2_read<<<unsigned(grid), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      static_cast<const float4 *>(buf), bytes / 16, reps, static_cast<float *>(sink));
+  BSDE_CUDA_TRY(cudaGetLastError());
+  return BSDE_OK;
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------

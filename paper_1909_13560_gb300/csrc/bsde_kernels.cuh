@@ -957,6 +957,29 @@ __global__ void __launch_bounds__(kStepTP * kMaxGroups, 3)
 }
 
 // ---------------------------------------------------------------------------
+// Measurement helper: every CTA streams its contiguous slice of `n` float4
+// `reps` times with coalesced 16-byte loads through L2 (up to four in
+// flight per thread) and adds a sum into sink[CTA] so no load is dropped.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_l2_read(const float4 *__restrict__ buf, size_t n,
+                                                 int reps, float *sink) {
+  const size_t per = n / gridDim.x;
+  const float4 *p = buf + per * blockIdx.x;
+  float acc = 0.f;
+  for (int r = 0; r < reps; ++r) {
+    size_t i = threadIdx.x;
+    for (; i + 3 * 256 < per; i += 4 * 256) {
+      const float4 a = __ldcg(p + i), b = __ldcg(p + i + 256), c = __ldcg(p + i + 512),
+                   d = __ldcg(p + i + 768);
+      acc += (a.x + b.y) + (c.z + d.w);
+    }
+    for (; i < per; i += 256) acc += __ldcg(p + i).x;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(sink + blockIdx.x, acc);
+}
+
+// ---------------------------------------------------------------------------
 // S4: readout of y^0, z^0 at x0 by the spline (Section 3.1 step 3).
 // ---------------------------------------------------------------------------
 template <int PREC, bool COH = false>
