@@ -6,18 +6,19 @@
  * What is solved (Section 2.2, Eq. 20-21; Section 3.1):
  *   the decoupled FBSDE  dX = a_x dt + b_x dW,  -dy = f(t, y, z) dt - z dW,
  *   y_T = g(X_T), on a uniform grid x_i = x_min + i*dx (i = 0..Nx-1),
- *   dx = (x_max - x_min)/(Nx-1), with N time steps dt = T/N.  Going backward
- *   from the k initial levels N, N-1, ..., N-k+1, every level n = N-k..0 is
- *   computed at every grid point from the k later levels:
+ *   dx = (x_max - x_min)/(Nx-1), with N time steps dt = T/N.  With K_y = k
+ *   steps for y, K_z = k_z steps for z and K = max(K_y, K_z) (Eq. 16), going
+ *   backward from the K initial levels N, N-1, ..., N-K+1, every level
+ *   n = N-K..0 is computed at every grid point from the K later levels:
  *     - Gauss-Hermite estimates (Eq. 21, L nodes) of E[z^], E[f], E[f dW],
  *       E[y^], E[y^ dW] over the off-grid points
- *       x_i + a_x j dt + b_x sqrt(2 j dt) a_l, j = 1..k, l = 1..L, where y^
+ *       x_i + a_x j dt + b_x sqrt(2 j dt) a_l, j = 1..K, l = 1..L, where y^
  *       and z^ are natural cubic splines of the level values (Section 3.3),
  *       constant outside [x_min, x_max] (Section 3.2);
- *     - z^n explicitly from the second line of Eq. 20;
- *     - y^n from the first line of Eq. 20 by Picard iteration on the implicit
- *       term f(t_n, y^n, z^n) (Section 3.1 step 3).
- *   gamma coefficients: Tables 1 and 2 (K_y = K_z = k <= 6).
+ *     - z^n explicitly from the second line of Eq. 20 (K_z steps);
+ *     - y^n from the first line of Eq. 20 (K_y steps) by Picard iteration on
+ *       the implicit term f(t_n, y^n, z^n) (Section 3.1 step 3).
+ *   gamma coefficients: Tables 1 and 2 (K_y, K_z <= 6).
  *
  * Memory model: the caller owns every device buffer (one workspace per
  * plan, sized by bsde_workspace_bytes) and every stream.  A plan owns host
@@ -79,13 +80,33 @@ enum {
                      derivatives from exact float differences of the pairs       */
 };
 
+/* first term of the z line of Eq. 20 */
+enum {
+  BSDE_ZFORM_EZ = 0,   /* E[z^{n+1}], as Eq. 20 prints it                          */
+  BSDE_ZFORM_EYDW = 1  /* E[y^{n+1} DeltaW_1] / dt, the term it replaces (Eq. 12
+                          with l = 1).  Stable for K_z = 1 only, where it is the
+                          second-order theta = 1/2 scheme: for K_z >= 2 the z
+                          recurrence has a root of modulus > 1 and the solution
+                          grows without bound as dt -> 0                          */
+};
+
+/* initial levels N-1, ..., N-K+1 (level N is always the terminal condition) */
+enum {
+  BSDE_INIT_EXACT = 0,   /* the closed form of the terminal id at t_{N-m}         */
+  BSDE_INIT_ONESTEP = 1  /* the 1-step scheme (K_y = K_z = 1) run backward from
+                            t_N with step dt / init_substeps on the same grid,
+                            nodes and z form (Section 3.1 step 2)                */
+};
+
 /* return codes */
 enum {
   BSDE_OK = 0,
   BSDE_WARN_NOCONV = 1, /* Picard stopped at picard_max somewhere; results written */
   BSDE_BUSY = 2,        /* server: no free slot or pool memory now; try again later */
-  BSDE_EINVAL = -1,     /* bad problem: k outside 1..min(6, N), Nx < 4, L outside
-                           1..64, x0 outside [x_min, x_max], unknown id, T <= 0    */
+  BSDE_EINVAL = -1,     /* bad problem: k or k_z outside 1..6, max(k, k_z) > N,
+                           Nx < 4, L outside 1..64, x0 outside [x_min, x_max],
+                           unknown id or mode, T <= 0, init_substeps < 1 or
+                           N init_substeps > 2^30 with ONESTEP                    */
   BSDE_ENOSPC = -2,     /* workspace smaller than bsde_workspace_bytes()          */
   BSDE_ECUDA = -3,      /* a CUDA call failed (detail in bsde_last_error())       */
   BSDE_ENOMEM = -4,     /* host allocation failed                                 */
@@ -94,20 +115,27 @@ enum {
 
 /* Problem description (all fields read by bsde_plan; nothing is kept by
  * reference).  Initial levels: unless the caller passes them to bsde_solve,
- * the closed form of the terminal id is evaluated at t_N, ..., t_{N-k+1}
- * (Section 3.1 step 2, read as the exact start); when smoothing = 1 and the terminal is CALL_LOG, level N holds the
- * cell averages of the payoff and of b_x times its derivative over
- * [x_i - dx/2, x_i + dx/2] (Section 5, Example 3).  Callers may instead pass
- * their own k initial levels to bsde_solve. */
+ * level N is the terminal condition and levels N-1..N-K+1 come from
+ * init_mode: the closed form of the terminal id at t_{N-m} (EXACT) or the
+ * one-step start-up (ONESTEP, Section 3.1 step 2); when smoothing = 1 and
+ * the terminal is CALL_LOG, level N holds the cell averages of the payoff and
+ * of b_x times its derivative over [x_i - dx/2, x_i + dx/2] (Section 5,
+ * Example 3).  Callers may instead pass their own K initial levels to
+ * bsde_solve.  A zero-filled tail (k_z, z_form, init_mode, init_substeps all
+ * 0) is the scheme of Eq. 20 with K_y = K_z = k and the closed-form start. */
 typedef struct bsde_problem {
   int32_t driver, terminal, precision, smoothing;
   int32_t picard_max; /* Picard iteration cap (paper: 30)                     */
-  int32_t N, k, L;    /* time steps, steps of the scheme (K_y = K_z), GH nodes */
+  int32_t N, k, L;    /* time steps, steps of the y line (K_y), GH nodes      */
   int64_t Nx;         /* grid points                                          */
   double T, x_min, x_max, x0; /* horizon, grid ends, readout point            */
   double a_x, b_x;    /* forward process dX = a_x dt + b_x dW                 */
   double r, mu, sigma, R, delta, lb_sign, strike; /* driver/payoff parameters */
   double picard_tol;  /* stop when |y^(p+1) - y^(p)| <= picard_tol            */
+  int32_t k_z;        /* K_z, 1..6; 0: K_z = k                                 */
+  int32_t z_form;     /* BSDE_ZFORM_*                                          */
+  int32_t init_mode;  /* BSDE_INIT_*                                           */
+  int32_t init_substeps; /* ONESTEP: 1-step scheme steps per dt, >= 1          */
 } bsde_problem;
 
 typedef struct bsde_result {
@@ -115,7 +143,7 @@ typedef struct bsde_result {
   double picard_resid_max; /* max over points and levels of the last |dy|          */
   int32_t status;          /* BSDE_OK or BSDE_WARN_NOCONV                          */
   int32_t picard_iters_max;
-  int64_t levels_done;     /* N - k + 1                                            */
+  int64_t levels_done;     /* N - K + 1, K = max(k, k_z) (start-up not counted)    */
 } bsde_result;
 
 typedef struct bsde_plan_s bsde_plan_t;
@@ -136,7 +164,7 @@ BSDE_API int bsde_plan(const bsde_problem *p, void *dev_workspace, size_t bytes,
               bsde_plan_t **out);
 
 /* Run the whole backward loop on `stream`.
- *   init_y, init_z: NULL (closed-form start) or k*Nx doubles each, row m
+ *   init_y, init_z: NULL (the start init_mode names) or K*Nx doubles each, row m
  *                   holding level N-m; host memory if init_on_host != 0,
  *                   device memory otherwise.
  *   out_y, out_z:   NULL or Nx doubles each, receiving level 0; host memory
@@ -156,9 +184,9 @@ BSDE_API int bsde_solve(bsde_plan_t *plan, void *stream, const double *init_y,
 BSDE_API int bsde_result_fetch(bsde_plan_t *plan, void *stream, bsde_result *result);
 
 /* Enqueue on `stream`, outside the captured graph, the kernels of backward
- * level n (0 <= n <= N-k): parts & 1 = the step kernel (Gauss-Hermite
+ * level n (0 <= n <= N-K): parts & 1 = the step kernel (Gauss-Hermite
  * expectations, z^n, Picard y^n), parts & 2 = the two spline sweeps of level
- * n.  The ring must hold levels n+1..n+k for meaningful values (after a
+ * n.  The ring must hold levels n+1..n+K for meaningful values (after a
  * completed bsde_solve it does for n = 0, and re-running level 0 then
  * rewrites the same values); every index stays inside the workspace either
  * way.  Used to time the kernels one by one. */
@@ -167,7 +195,9 @@ BSDE_API int bsde_enqueue_level(bsde_plan_t *plan, void *stream, int n, int part
 /* Release the plan's host resources and graphs (not the workspace). */
 BSDE_API void bsde_free(bsde_plan_t *plan);
 
-/* Number of kernel launches one bsde_solve issues (for launch accounting). */
+/* Number of kernel launches one bsde_solve without caller levels issues (for
+ * launch accounting); with caller levels the start-up's launches, if any,
+ * are left out. */
 BSDE_API int64_t bsde_plan_launches(const bsde_plan_t *plan);
 
 BSDE_API const char *bsde_strerror(int code);
@@ -206,8 +236,9 @@ typedef struct bsde_batch_config {
 } bsde_batch_config;
 
 /* Workspace for the n problems ps[0..n-1] (rings, tables, descriptors,
- * queue, per-problem statistics).  BSDE_EINVAL if any problem is invalid or
- * not BSDE_FP32C. */
+ * queue, per-problem statistics).  BSDE_EINVAL if any problem is invalid,
+ * not BSDE_FP32C or asks for the one-step start-up (batches start from the
+ * closed form; K_z and the z form are free). */
 BSDE_API int bsde_batch_workspace_bytes(int n, const bsde_problem *ps, size_t *bytes);
 
 /* Plan the batch on dev_workspace (caller-owned, >= bsde_batch_workspace_bytes,
@@ -267,7 +298,8 @@ BSDE_API int bsde_server_create(void *dev_workspace, size_t bytes, int slots,
 BSDE_API int bsde_server_start(bsde_server_t *s, void *stream, int cluster, int idle_ms);
 
 /* Admit a request: BSDE_OK with *slot set, BSDE_BUSY when no slot or pool
- * memory is free now, BSDE_EINVAL for a bad problem, BSDE_ETIMEOUT once the
+ * memory is free now, BSDE_EINVAL for a bad problem (as for batches: FP32C,
+ * closed-form start), BSDE_ETIMEOUT once the
  * server has stopped itself.  Non-blocking. */
 BSDE_API int bsde_server_submit(bsde_server_t *s, const bsde_problem *p, int *slot);
 

@@ -24,13 +24,22 @@
  *
  * Readings of points where the paper is silent (each also listed in the
  * design notes of the repository):
- *   - b == gamma in Eq. 20; K_y = K_z = k.
+ *   - b == gamma in Eq. 20.  K_y = k and K_z = kz (kz = 0: K_z = k); the
+ *     loop keeps K = max(K_y, K_z) levels (Eq. 16), y takes the K_y-step
+ *     coefficients of Table 1 and E[y^{n+K_y}], z the K_z-step ones of
+ *     Table 2.
+ *   - z form: Eq. 20 as printed takes E[z^{n+1}]; with zform = 1 that term
+ *     is E[y^{n+1} DeltaW_1] / dt instead, the quantity it stands for in the
+ *     reference equation of z (Eq. 12 with l = 1).
  *   - natural spatial spline (M_0 = M_{Nx-1} = 0), solved exactly (Thomas).
  *   - Picard starts from y^{n+1}_i and stops when |y^(p+1)-y^(p)| <= tol or
  *     after picard_max iterations.
- *   - initial levels N..N-k+1 from the closed-form solution; the level-N
- *     call payoff is replaced by its cell average (smoothing, Section 5,
- *     Example 3), or the caller passes the k initial levels explicitly.
+ *   - initial levels N..N-K+1 from the closed-form solution (init_mode 0)
+ *     or, init_mode 1, level N from the closed form and levels N-1..N-K+1
+ *     by the 1-step scheme (K_y = K_z = 1) run backward from t_N with the
+ *     step dt / init_substeps (Section 3.1 step 2); the level-N call payoff
+ *     is replaced by its cell average (smoothing, Section 5, Example 3).
+ *     The caller may also pass the K initial levels explicitly.
  *   - forward process X with constant drift a_x and volatility b_x: the
  *     off-grid point for j steps and GH node a_l is x_i + a_x*j*dt +
  *     b_x*sqrt(2*j*dt)*a_l, while the Brownian increment weighting the
@@ -58,7 +67,17 @@ typedef struct {
   double picard_tol;
   long long Nx;
   int N, k, L;
+  int kz;             /* K_z; 0 means K_z = k (= K_y)                        */
+  int zform;          /* 0: E[z^{n+1}] in the z line (Eq. 20); 1: E[y DW]/dt */
+  int init_mode;      /* 0: closed-form levels; 1: one-step start-up        */
+  int init_substeps;  /* start-up steps per dt (init_mode 1)                */
 } orc_problem;
+
+enum { ORC_INIT_EXACT = 0, ORC_INIT_ONESTEP = 1 };
+
+static int orc_kz(const orc_problem *p) { return p->kz > 0 ? p->kz : p->k; }
+/* K = max(K_y, K_z): the levels one step reads (Eq. 16) */
+static int orc_K(const orc_problem *p) { return p->k > orc_kz(p) ? p->k : orc_kz(p); }
 
 typedef struct {
   double y0, z0;
@@ -327,12 +346,12 @@ static void orc_call_cell_average(double x, double dx, double K, double bx,
   }
 }
 
-/* k initial levels: row m (0 <= m < k) holds level N-m (Section 3.1 step 2,
+/* K initial levels: row m (0 <= m < K) holds level N-m (Section 3.1 step 2,
  * read as the closed form at t_{N-m}). */
 int orc_init_levels(const orc_problem *p, double *init_y, double *init_z) {
   double dt = p->T / p->N;
   double dx = (p->x_max - p->x_min) / (double)(p->Nx - 1);
-  for (int m = 0; m < p->k; ++m) {
+  for (int m = 0; m < orc_K(p); ++m) {
     double t = (p->N - m) * dt;
     for (long long i = 0; i < p->Nx; ++i) {
       double x = p->x_min + (double)i * dx, u, z;
@@ -348,7 +367,11 @@ int orc_init_levels(const orc_problem *p, double *init_y, double *init_z) {
 }
 
 static int orc_check(const orc_problem *p) {
-  if (p->k < 1 || p->k > 6 || p->k > p->N) return -1;
+  if (p->k < 1 || p->k > 6 || p->kz < 0 || p->kz > 6 || orc_K(p) > p->N) return -1;
+  if (p->zform < 0 || p->zform > 1 || p->init_mode < 0 || p->init_mode > 1) return -1;
+  if (p->init_mode == ORC_INIT_ONESTEP &&
+      (p->init_substeps < 1 || (long long)p->N * p->init_substeps > (1LL << 30)))
+    return -1;
   if (p->Nx < 4 || p->L < 1 || p->L > 128) return -1;
   if (!(p->x_max > p->x_min) || !(p->T > 0.0)) return -1;
   if (p->driver < 0 || p->driver > 4) return -1;
@@ -356,7 +379,7 @@ static int orc_check(const orc_problem *p) {
 }
 
 /* Gauss-Hermite estimates (Eq. 21) of the conditional expectations at grid
- * point i for j = 1..k, given levels n+1..n+k (row j-1 of ly/lz, second
+ * point i for j = 1..K, given levels n+1..n+K (row j-1 of ly/lz, second
  * derivatives in lmy/lmz).  out[5*(j-1) + q], q = 0..4:
  *   E_j[z^], E_j[f(t_{n+j}, y^, z^)], E_j[f * DeltaW_j], E_j[y^], E_j[y^ DeltaW_j]. */
 static void orc_point_expectations(const orc_problem *p, int n, long long i,
@@ -368,7 +391,7 @@ static void orc_point_expectations(const orc_problem *p, int n, long long i,
   double dx = (p->x_max - p->x_min) / (double)(p->Nx - 1);
   double xi = p->x_min + (double)i * dx;
   double rpi = 1.0 / sqrt(ORC_PI);
-  for (int j = 1; j <= p->k; ++j) {
+  for (int j = 1; j <= orc_K(p); ++j) {
     double tj = (n + j) * dt;
     double sq = sqrt(2.0 * j * dt);
     double ez = 0.0, ef = 0.0, efw = 0.0, ey = 0.0, eyw = 0.0;
@@ -393,13 +416,13 @@ static void orc_point_expectations(const orc_problem *p, int n, long long i,
   }
 }
 
-/* Public wrapper: expectations at the points idx[0..cnt) for level n, the k
+/* Public wrapper: expectations at the points idx[0..cnt) for level n, the K
  * later levels given as rows of levels_y/levels_z (row j-1 = level n+j). */
 int orc_expectations(const orc_problem *p, int n, const double *levels_y,
                      const double *levels_z, const long long *idx, long long cnt,
                      double *out) {
   if (orc_check(p)) return -1;
-  int k = p->k;
+  int k = orc_K(p);
   long long nx = p->Nx;
   double dx = (p->x_max - p->x_min) / (double)(nx - 1);
   double *my = (double *)malloc((size_t)k * nx * sizeof(double));
@@ -424,25 +447,30 @@ int orc_expectations(const orc_problem *p, int n, const double *levels_y,
 }
 
 /* The backward loop (Eq. 20, Section 3.1 step 3).
- * init_y/init_z: k x Nx, row m = level N-m; NULL -> closed form (orc_init_levels).
- * levels: how many backward levels to compute (n = N-k, N-k-1, ...);
- *         0 or more than N-k+1 -> all of them, down to n = 0.
+ * init_y/init_z: K x Nx, row m = level N-m; NULL -> the problem's start
+ *         (closed form, or the one-step start-up, orc_onestep_levels).
+ * levels: how many backward levels to compute (n = N-K, N-K-1, ...);
+ *         0 or more than N-K+1 -> all of them, down to n = 0.
  * out_y/out_z (optional, Nx each): the last computed level.
  * res: readout at x0 of the last computed level (Section 3.1 step 3 target
- *      (y_0^0, z_0^0)), Picard statistics.
+ *      (y_0^0, z_0^0)), Picard statistics (start-up included).
  * threads: OpenMP threads over grid points (1 = serial). */
+int orc_onestep_levels(const orc_problem *p, double *init_y, double *init_z,
+                       orc_result *stats, int threads);
+
 int orc_solve(const orc_problem *p, const double *init_y, const double *init_z,
               long long levels, double *out_y, double *out_z, orc_result *res,
               int threads) {
   memset(res, 0, sizeof(*res));
   if (orc_check(p)) { res->status = -1; return -1; }
-  const int k = p->k, N = p->N;
+  const int ky = p->k, kz = orc_kz(p), K = orc_K(p), N = p->N;
   const long long nx = p->Nx;
   const double dt = p->T / N;
   const double dx = (p->x_max - p->x_min) / (double)(nx - 1);
-  const int nslot = k + 1;
-  double gy[7], gz[7];
-  orc_gamma(k, gy, gz);
+  const int nslot = K + 1;
+  double gy[7], gz[7], unused[7];
+  orc_gamma(ky, gy, unused);  /* Table 1 row K_y */
+  orc_gamma(kz, unused, gz);  /* Table 2 row K_z */
   double *gh_a = (double *)malloc((size_t)p->L * sizeof(double));
   double *gh_w = (double *)malloc((size_t)p->L * sizeof(double));
   double *Y = (double *)malloc((size_t)nslot * nx * sizeof(double));
@@ -457,46 +485,58 @@ int orc_solve(const orc_problem *p, const double *init_y, const double *init_z,
     return -2;
   }
   orc_gauss_hermite(p->L, gh_a, gh_w);
+  int itmax = 0;
+  double rmax = 0.0;
+  int nonconv = 0;
 
-  /* level N-m lives in slot (N-m) mod (k+1) */
+  /* level N-m lives in slot (N-m) mod (K+1) */
   if (init_y && init_z) {
-    for (int m = 0; m < k; ++m) {
+    for (int m = 0; m < K; ++m) {
       memcpy(Y + (size_t)((N - m) % nslot) * nx, init_y + (size_t)m * nx, (size_t)nx * sizeof(double));
       memcpy(Z + (size_t)((N - m) % nslot) * nx, init_z + (size_t)m * nx, (size_t)nx * sizeof(double));
     }
   } else {
-    double *iy = (double *)malloc((size_t)k * nx * sizeof(double));
-    double *iz = (double *)malloc((size_t)k * nx * sizeof(double));
-    if (!iy || !iz || orc_init_levels(p, iy, iz)) {
+    double *iy = (double *)malloc((size_t)K * nx * sizeof(double));
+    double *iz = (double *)malloc((size_t)K * nx * sizeof(double));
+    orc_result st;
+    memset(&st, 0, sizeof(st));
+    int bad = !iy || !iz;
+    if (!bad) {
+      if (p->init_mode == ORC_INIT_ONESTEP)
+        bad = orc_onestep_levels(p, iy, iz, &st, threads) != 0;
+      else
+        bad = orc_init_levels(p, iy, iz) != 0;
+    }
+    if (bad) {
       free(iy); free(iz);
       free(gh_a); free(gh_w); free(Y); free(Z); free(MY); free(MZ); free(iters); free(resid);
       res->status = -1;
       return -1;
     }
-    for (int m = 0; m < k; ++m) {
+    itmax = st.picard_iters_max;
+    rmax = st.picard_resid_max;
+    nonconv = st.status == 1;
+    for (int m = 0; m < K; ++m) {
       memcpy(Y + (size_t)((N - m) % nslot) * nx, iy + (size_t)m * nx, (size_t)nx * sizeof(double));
       memcpy(Z + (size_t)((N - m) % nslot) * nx, iz + (size_t)m * nx, (size_t)nx * sizeof(double));
     }
     free(iy);
     free(iz);
   }
-  for (int m = 0; m < k; ++m) {
+  for (int m = 0; m < K; ++m) {
     size_t o = (size_t)((N - m) % nslot) * nx;
     orc_spline(nx, dx, Y + o, MY + o);
     orc_spline(nx, dx, Z + o, MZ + o);
   }
 
-  long long total = (long long)(N - k + 1);
+  long long total = (long long)(N - K + 1);
   if (levels <= 0 || levels > total) levels = total;
-  int last = N - k + 1;
-  int itmax = 0;
-  double rmax = 0.0;
-  int nonconv = 0;
+  int last = N - K + 1;
 
   for (long long lv = 0; lv < levels; ++lv) {
-    const int n = N - k - (int)lv;
+    const int n = N - K - (int)lv;
     const double *ly[6], *lz[6], *lmy[6], *lmz[6];
-    for (int j = 1; j <= k; ++j) {
+    for (int j = 1; j <= K; ++j) {
       size_t o = (size_t)((n + j) % nslot) * nx;
       ly[j - 1] = Y + o; lz[j - 1] = Z + o; lmy[j - 1] = MY + o; lmz[j - 1] = MZ + o;
     }
@@ -504,7 +544,7 @@ int orc_solve(const orc_problem *p, const double *init_y, const double *init_z,
     double *zn = Z + (size_t)(n % nslot) * nx;
     const double *yprev = ly[0];
     const double tn = n * dt;
-    const double h = k * dt;
+    const double h = ky * dt;
 
 #ifdef _OPENMP
 #pragma omp parallel for schedule(static) num_threads(threads > 0 ? threads : 1)
@@ -512,17 +552,20 @@ int orc_solve(const orc_problem *p, const double *init_y, const double *init_z,
     for (long long i = 0; i < nx; ++i) {
       double e[30];
       orc_point_expectations(p, n, i, ly, lmy, lz, lmz, gh_a, gh_w, e);
-      /* z: second line of Eq. 20 solved for z^n */
+      /* z: second line of Eq. 20 (K_z steps) solved for z^n; its first term
+       * E[z^{n+1}], or E[y^{n+1} DeltaW_1] / dt in the zform reading */
       double sfw = 0.0, sz = 0.0;
-      for (int j = 1; j <= k; ++j) {
+      for (int j = 1; j <= kz; ++j) {
         sfw += gz[j] * e[5 * (j - 1) + 2];
         sz += gz[j] * e[5 * (j - 1) + 0];
       }
-      double z = (e[0] + sfw - sz) / gz[0];
-      /* y: first line of Eq. 20, implicit in f(t_n, y^n, z^n), by Picard */
+      double first = p->zform ? e[4] / dt : e[0];
+      double z = (first + sfw - sz) / gz[0];
+      /* y: first line of Eq. 20 (K_y steps), implicit in f(t_n, y^n, z^n),
+       * by Picard */
       double sf = 0.0;
-      for (int j = 1; j <= k; ++j) sf += gy[j] * e[5 * (j - 1) + 1];
-      double A = e[5 * (k - 1) + 3] + h * sf;
+      for (int j = 1; j <= ky; ++j) sf += gy[j] * e[5 * (j - 1) + 1];
+      double A = e[5 * (ky - 1) + 3] + h * sf;
       double y = yprev[i];
       double d = 0.0;
       int it = 0;
@@ -558,6 +601,40 @@ int orc_solve(const orc_problem *p, const double *init_y, const double *init_z,
   if (out_y) memcpy(out_y, Y + o, (size_t)nx * sizeof(double));
   if (out_z) memcpy(out_z, Z + o, (size_t)nx * sizeof(double));
   free(gh_a); free(gh_w); free(Y); free(Z); free(MY); free(MZ); free(iters); free(resid);
+  return 0;
+}
+
+/* The start-up of Section 3.1 step 2: level N from the closed form (smoothed
+ * as the problem says), then the 1-step scheme (K_y = K_z = 1, Table 1 and 2
+ * row 1) backward from t_N with the step h = dt / S, S = init_substeps, on the
+ * same grid, Gauss-Hermite rule and z form; level N-m is its level after m S
+ * steps, at t_N - m S h = t_{N-m}.  Rows m = 0..K-1 of init_y/init_z.  The
+ * 1-step runs work on the time grid t = n' h, n' = 0..N S, so every driver
+ * sees the same absolute times as the main loop.  stats (nullable) receives
+ * the start-up's Picard statistics. */
+int orc_onestep_levels(const orc_problem *p, double *init_y, double *init_z,
+                       orc_result *stats, int threads) {
+  if (orc_check(p) || p->init_substeps < 1) return -1;
+  const int K = orc_K(p), S = p->init_substeps;
+  const long long nx = p->Nx;
+  orc_problem q = *p;
+  q.k = 1;
+  q.kz = 0;
+  q.N = p->N * S;
+  q.init_mode = ORC_INIT_EXACT;
+  orc_result acc;
+  memset(&acc, 0, sizeof(acc));
+  if (orc_init_levels(&q, init_y, init_z) != 0) return -1;  /* row 0: level N */
+  for (int m = 1; m < K; ++m) {
+    orc_result r;
+    if (orc_solve(&q, NULL, NULL, (long long)m * S, init_y + (size_t)m * nx,
+                  init_z + (size_t)m * nx, &r, threads) != 0)
+      return -1;
+    if (r.picard_iters_max > acc.picard_iters_max) acc.picard_iters_max = r.picard_iters_max;
+    if (r.picard_resid_max > acc.picard_resid_max) acc.picard_resid_max = r.picard_resid_max;
+    if (r.status == 1) acc.status = 1;
+  }
+  if (stats) *stats = acc;
   return 0;
 }
 

@@ -26,6 +26,7 @@ _lib = None
 
 DRIVERS = {"LIN_SIN": 0, "BS": 1, "LB": 2, "EX1": 3, "EX2": 4}
 TERMINALS = {"SIN": 0, "CALL_LOG": 1, "LOGISTIC": 2, "LNSIN": 3}
+INIT_MODES = {"EXACT": 0, "ONESTEP": 1}
 
 
 class _Problem(ctypes.Structure):
@@ -40,7 +41,8 @@ class _Problem(ctypes.Structure):
         ("delta", ctypes.c_double), ("lb_sign", ctypes.c_double),
         ("strike", ctypes.c_double), ("picard_tol", ctypes.c_double),
         ("Nx", ctypes.c_longlong), ("N", ctypes.c_int), ("k", ctypes.c_int),
-        ("L", ctypes.c_int),
+        ("L", ctypes.c_int), ("kz", ctypes.c_int), ("zform", ctypes.c_int),
+        ("init_mode", ctypes.c_int), ("init_substeps", ctypes.c_int),
     ]
 
 
@@ -87,6 +89,8 @@ def _load():
                                          P(ctypes.c_longlong), ctypes.c_longlong, P(d)]
         lib.orc_solve.argtypes = [P(_Problem), P(d), P(d), ctypes.c_longlong,
                                   P(d), P(d), P(_Result), ctypes.c_int]
+        lib.orc_onestep_levels.argtypes = [P(_Problem), P(d), P(d), P(_Result),
+                                           ctypes.c_int]
         lib.orc_max_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -114,7 +118,18 @@ def _problem(p: dict) -> _Problem:
     s.N = int(p["N"])
     s.k = int(p["k"])
     s.L = int(p["L"])
+    s.kz = int(p.get("kz", 0))
+    s.zform = int(p.get("zform", 0))
+    mode = p.get("init_mode", 0)
+    s.init_mode = INIT_MODES[mode] if isinstance(mode, str) else int(mode)
+    s.init_substeps = int(p.get("init_substeps", 0))
     return s
+
+
+def levels_K(p: dict) -> int:
+    """K = max(K_y, K_z): the levels one backward step reads (Eq. 16)."""
+    kz = int(p.get("kz", 0)) or int(p["k"])
+    return max(int(p["k"]), kz)
 
 
 def gauss_hermite(L: int):
@@ -168,26 +183,44 @@ def exact(p: dict, t: float, x: float):
 
 
 def init_levels(p: dict):
+    """Closed-form levels N..N-K+1 (rows 0..K-1), level N smoothed when the
+    problem asks for it."""
     lib = _load()
     s = _problem(p)
-    iy = np.zeros((s.k, s.Nx))
-    iz = np.zeros((s.k, s.Nx))
+    K = levels_K(p)
+    iy = np.zeros((K, s.Nx))
+    iz = np.zeros((K, s.Nx))
     if lib.orc_init_levels(ctypes.byref(s), _dptr(iy), _dptr(iz)) != 0:
         raise ValueError("no closed form for this problem")
     return iy, iz
 
 
+def onestep_levels(p: dict, threads: int = 1):
+    """Levels N..N-K+1 by the one-step start-up (Section 3.1 step 2) with
+    p["init_substeps"] steps of the 1-step scheme per dt."""
+    lib = _load()
+    s = _problem(p)
+    K = levels_K(p)
+    iy = np.zeros((K, s.Nx))
+    iz = np.zeros((K, s.Nx))
+    res = _Result()
+    if lib.orc_onestep_levels(ctypes.byref(s), _dptr(iy), _dptr(iz), ctypes.byref(res),
+                              int(threads)) != 0:
+        raise ValueError("bad problem or init_substeps < 1")
+    return iy, iz
+
+
 def expectations(p: dict, n: int, levels_y: np.ndarray, levels_z: np.ndarray,
                  idx) -> np.ndarray:
-    """E_j[z^], E_j[f], E_j[f dW], E_j[y^], E_j[y^ dW] (j = 1..k) at grid
+    """E_j[z^], E_j[f], E_j[f dW], E_j[y^], E_j[y^ dW] (j = 1..K) at grid
     points idx for level n; row j-1 of levels_* is level n+j.
-    Returns an array of shape (len(idx), k, 5)."""
+    Returns an array of shape (len(idx), K, 5)."""
     lib = _load()
     s = _problem(p)
     ly = np.ascontiguousarray(levels_y, dtype=np.float64)
     lz = np.ascontiguousarray(levels_z, dtype=np.float64)
     ix = np.ascontiguousarray(np.asarray(idx, dtype=np.int64))
-    out = np.zeros((len(ix), s.k, 5))
+    out = np.zeros((len(ix), levels_K(p), 5))
     rc = lib.orc_expectations(ctypes.byref(s), int(n), _dptr(ly), _dptr(lz),
                               ix.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)),
                               len(ix), _dptr(out))
@@ -207,8 +240,9 @@ def solve(p: dict, init_y=None, init_z=None, levels: int = 0, threads: int = 1,
     if init_y is not None:
         iy = np.ascontiguousarray(init_y, dtype=np.float64)
         iz = np.ascontiguousarray(init_z, dtype=np.float64)
-        if iy.shape != (s.k, s.Nx) or iz.shape != (s.k, s.Nx):
-            raise ValueError("initial levels must have shape (k, Nx)")
+        K = levels_K(p)
+        if iy.shape != (K, s.Nx) or iz.shape != (K, s.Nx):
+            raise ValueError("initial levels must have shape (K, Nx), K = max(k, kz)")
     oy = np.zeros(s.Nx) if want_level else None
     oz = np.zeros(s.Nx) if want_level else None
     rc = lib.orc_solve(ctypes.byref(s),

@@ -19,6 +19,8 @@ LIB_PATH = os.path.join(_HERE, "libbsde.so")
 BSDE_DRIVER = {"LIN_SIN": 0, "BS": 1, "LB": 2, "EX1": 3, "EX2": 4}
 BSDE_TERMINAL = {"SIN": 0, "CALL_LOG": 1, "LOGISTIC": 2, "LNSIN": 3}
 BSDE_PRECISION = {"fp64": 0, "fp32c": 1}
+BSDE_INIT = {"EXACT": 0, "ONESTEP": 1}
+BSDE_ZFORM = {"EZ": 0, "EYDW": 1}
 
 BSDE_OK = 0
 BSDE_WARN_NOCONV = 1
@@ -44,6 +46,8 @@ class bsde_problem(ctypes.Structure):
         ("sigma", ctypes.c_double), ("R", ctypes.c_double),
         ("delta", ctypes.c_double), ("lb_sign", ctypes.c_double),
         ("strike", ctypes.c_double), ("picard_tol", ctypes.c_double),
+        ("k_z", ctypes.c_int32), ("z_form", ctypes.c_int32),
+        ("init_mode", ctypes.c_int32), ("init_substeps", ctypes.c_int32),
     ]
 
 
@@ -157,7 +161,17 @@ def make_problem(p: dict, precision: str = "fp64") -> bsde_problem:
     if s.sigma == 0.0:
         s.sigma = 1.0
     s.picard_tol = float(p.get("picard_tol", 1e-12))
+    s.k_z = int(p.get("kz", 0))
+    s.z_form = int(p.get("zform", 0))
+    mode = p.get("init_mode", 0)
+    s.init_mode = BSDE_INIT[mode] if isinstance(mode, str) else int(mode)
+    s.init_substeps = int(p.get("init_substeps", 0))
     return s
+
+
+def levels_K(p: dict) -> int:
+    """K = max(K_y, K_z): initial levels and levels read per step (Eq. 16)."""
+    return max(int(p["k"]), int(p.get("kz", 0)) or int(p["k"]))
 
 
 # --- thin wrappers with the C names ----------------------------------------
@@ -273,8 +287,9 @@ class Solver:
         return bsde_plan_launches(self.plan)
 
     def solve(self, init=None, want_level: bool = False, stream=None) -> dict:
-        """init: None (closed-form start) or (init_y, init_z), each (k, Nx)
-        float64 host arrays or device tensors (row m = level N - m)."""
+        """init: None (the problem's start: closed form or one-step start-up)
+        or (init_y, init_z), each (K, Nx), K = max(k, kz), float64 host
+        arrays or device tensors (row m = level N - m)."""
         import torch
         if stream is None:
             stream = torch.cuda.current_stream(self.device)

@@ -55,10 +55,24 @@ class DeviceGuard {
 
 using namespace bsde;
 
+namespace bsde {
+// One backward run on the workspace: its constants, level ring and node
+// tables.  A plan has the main run and, for the one-step start-up, the run of
+// the 1-step scheme.
+struct Run {
+  Params P;
+  Ring64 r64;
+  Ring32 r32;
+  const NodeF64 *t64;
+  const PairF32 *tp;
+};
+}  // namespace bsde
+
 struct bsde_plan_s {
   bsde_problem prob;
   Params P;
   Layout lay;
+  bsde::Run run, sub;  // main loop; start-up (valid when has_startup(prob))
   int device;
   unsigned char *ws;
   size_t ws_bytes;
@@ -113,59 +127,144 @@ static void launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned block, 
 }
 
 template <int PREC, int DRV>
-static void launch_step(bsde_plan_t *pl, cudaStream_t s, int n) {
-  const Params &P = pl->P;
+static void launch_step(bsde_plan_t *pl, const Run &R, cudaStream_t s, int n) {
+  const Params &P = R.P;
   const unsigned threads = unsigned(kStepTP * P.G);
   const unsigned blocks = unsigned((P.Nx + kStepTP - 1) / kStepTP);
   const int kL = P.k * P.L;
   Stats *st = reinterpret_cast<Stats *>(pl->ws + pl->lay.stats);
   if (PREC == BSDE_FP64) {
     const size_t sm = sizeof(NodeF64) * kL + sizeof(double) * 2 * P.G * kStepTP;
-    launch_pdl(k_step64<DRV>, blocks, threads, sm, s, P, pl->dc64,
-               reinterpret_cast<double4_32a *>(pl->ws + pl->lay.ring64),
-               reinterpret_cast<const NodeF64 *>(pl->ws + pl->lay.table), n, st);
+    launch_pdl(k_step64<DRV>, blocks, threads, sm, s, P, pl->dc64, R.r64.ring, R.t64, n, st);
   } else {
     const size_t sm = step32_smem(P.G, P.k * P.Lp);
-    launch_pdl(k_step32<DRV>, blocks, threads, sm, s, P, pl->dc32,
-               ring32(pl->ws + pl->lay.ringA, pl->ws + pl->lay.ringB, P),
-               reinterpret_cast<const PairF32 *>(pl->ws + pl->lay.ptable), n, st);
+    launch_pdl(k_step32<DRV>, blocks, threads, sm, s, P, pl->dc32, R.r32, R.tp, n, st);
   }
 }
 
 template <int PREC>
-static void launch_step_any(bsde_plan_t *pl, cudaStream_t s, int n) {
-  switch (pl->P.driver) {
-    case BSDE_DRIVER_LIN_SIN: launch_step<PREC, BSDE_DRIVER_LIN_SIN>(pl, s, n); break;
-    case BSDE_DRIVER_BS: launch_step<PREC, BSDE_DRIVER_BS>(pl, s, n); break;
-    case BSDE_DRIVER_LB: launch_step<PREC, BSDE_DRIVER_LB>(pl, s, n); break;
-    case BSDE_DRIVER_EX1: launch_step<PREC, BSDE_DRIVER_EX1>(pl, s, n); break;
-    default: launch_step<PREC, BSDE_DRIVER_EX2>(pl, s, n); break;
+static void launch_step_any(bsde_plan_t *pl, const Run &R, cudaStream_t s, int n) {
+  switch (R.P.driver) {
+    case BSDE_DRIVER_LIN_SIN: launch_step<PREC, BSDE_DRIVER_LIN_SIN>(pl, R, s, n); break;
+    case BSDE_DRIVER_BS: launch_step<PREC, BSDE_DRIVER_BS>(pl, R, s, n); break;
+    case BSDE_DRIVER_LB: launch_step<PREC, BSDE_DRIVER_LB>(pl, R, s, n); break;
+    case BSDE_DRIVER_EX1: launch_step<PREC, BSDE_DRIVER_EX1>(pl, R, s, n); break;
+    default: launch_step<PREC, BSDE_DRIVER_EX2>(pl, R, s, n); break;
   }
 }
 
 template <int PREC>
-static int64_t enqueue_spline(bsde_plan_t *pl, cudaStream_t s, int slot) {
-  const Params &P = pl->P;
-  Ring64 r64{reinterpret_cast<double4_32a *>(pl->ws + pl->lay.ring64)};
-  const Ring32 r32 = ring32(pl->ws + pl->lay.ringA, pl->ws + pl->lay.ringB, P);
+static int64_t enqueue_spline(const Run &R, cudaStream_t s, int slot) {
+  const Params &P = R.P;
   constexpr int TS = SplineLaunch<PREC>::TS;
   const unsigned blocks = unsigned((P.Nx - 2 + TS - 1) / TS);
-  launch_pdl(k_spline<PREC>, blocks, unsigned(SplineLaunch<PREC>::NT), 0, s, P, r64, r32, slot);
+  launch_pdl(k_spline<PREC>, blocks, unsigned(SplineLaunch<PREC>::NT), 0, s, P, R.r64, R.r32,
+             slot);
   return 1;
+}
+
+// Views of the workspace for the main run and the start-up run (their
+// Params as upload_tables left them).
+static void bind_runs(bsde_plan_t *pl) {
+  unsigned char *ws = pl->ws;
+  const Layout &L = pl->lay;
+  Run &R = pl->run;
+  R.P = pl->P;
+  R.r64 = Ring64{reinterpret_cast<double4_32a *>(ws + L.ring64)};
+  R.r32 = ring32(ws + L.ringA, ws + L.ringB, R.P);
+  R.t64 = reinterpret_cast<const NodeF64 *>(ws + L.table);
+  R.tp = reinterpret_cast<const PairF32 *>(ws + L.ptable);
+  Run &Q = pl->sub;
+  if (has_startup(pl->prob)) {
+    Q.r64 = Ring64{reinterpret_cast<double4_32a *>(ws + L.sub_ring64)};
+    Q.r32 = ring32(ws + L.sub_ringA, ws + L.sub_ringB, Q.P);
+    Q.t64 = reinterpret_cast<const NodeF64 *>(ws + L.sub_table);
+    Q.tp = reinterpret_cast<const PairF32 *>(ws + L.sub_ptable);
+  }
+}
+
+// Node tables of the plan's runs, built on the host (the work split needs the
+// device's resident thread count) into host_buf and copied to the workspace
+// on `s`; the caller keeps host_buf alive until the copies are done.
+struct HostTables {
+  NodeF64 t64[kMaxK * kMaxL], s64[kMaxL];
+  NodeF32 t32[kMaxK * kMaxL], s32[kMaxL];
+  PairF32 tp[kMaxK * kMaxL], sp[kMaxL];
+};
+static int upload_tables(bsde_plan_t *pl, HostTables &h, cudaStream_t s) {
+  const long resident = resident_step_threads(pl->device);
+  build_tables(pl->P, h.t64, h.t32, h.tp, 4, kMaxGroups, resident);
+  const bool sub = has_startup(pl->prob);
+  if (sub) {
+    pl->sub.P = startup_params(pl->P, pl->prob.init_substeps);
+    build_tables(pl->sub.P, h.s64, h.s32, h.sp, 4, kMaxGroups, resident);
+  }
+  pl->run.P = pl->P;
+  const Params &P = pl->P;
+  const Layout &L = pl->lay;
+  if (P.precision == BSDE_FP64) {
+    BSDE_CUDA_TRY(cudaMemcpyAsync(pl->ws + L.table, h.t64, sizeof(NodeF64) * P.k * P.L,
+                                  cudaMemcpyHostToDevice, s));
+    if (sub)
+      BSDE_CUDA_TRY(cudaMemcpyAsync(pl->ws + L.sub_table, h.s64, sizeof(NodeF64) * P.L,
+                                    cudaMemcpyHostToDevice, s));
+  } else {
+    BSDE_CUDA_TRY(cudaMemcpyAsync(pl->ws + L.ptable, h.tp, sizeof(PairF32) * P.k * P.Lp,
+                                  cudaMemcpyHostToDevice, s));
+    if (sub)
+      BSDE_CUDA_TRY(cudaMemcpyAsync(pl->ws + L.sub_ptable, h.sp,
+                                    sizeof(PairF32) * pl->sub.P.Lp, cudaMemcpyHostToDevice, s));
+  }
+  return BSDE_OK;
+}
+
+// The one-step start-up (Section 3.1 step 2): the 1-step scheme from the
+// closed-form level N down K-1 levels of the main grid, S of its steps each;
+// level N and every S-th level after it go to row m of the staging area, from
+// which the main loop imports its K initial levels.
+template <int PREC>
+static int64_t enqueue_startup(bsde_plan_t *pl, cudaStream_t s, double *sy, double *sz) {
+  const Run &Q = pl->sub;
+  const Params &P1 = Q.P;
+  const int64_t nx = P1.Nx;
+  const int S = pl->prob.init_substeps, K = pl->P.k;
+  const unsigned eb = unsigned((nx + 255) / 256 < 4096 ? (nx + 255) / 256 : 4096);
+  int64_t launches = 0;
+  k_init_closed<PREC><<<eb, 256, 0, s>>>(P1, Q.r64, Q.r32, 0);
+  launches += 1 + enqueue_spline<PREC>(Q, s, P1.N % P1.nslot);
+  k_export<PREC><<<eb, 256, 0, s>>>(P1, Q.r64, Q.r32, sy, sz, P1.N % P1.nslot);
+  ++launches;
+  for (int q = 1; q <= (K - 1) * S; ++q) {
+    const int n1 = P1.N - q;
+    launch_step_any<PREC>(pl, Q, s, n1);
+    launches += 1 + enqueue_spline<PREC>(Q, s, n1 % P1.nslot);
+    if (q % S == 0) {
+      const int m = q / S;
+      k_export<PREC><<<eb, 256, 0, s>>>(P1, Q.r64, Q.r32, sy + m * nx, sz + m * nx,
+                                        n1 % P1.nslot);
+      ++launches;
+    }
+  }
+  return launches;
 }
 
 // The whole solve as one stream-ordered sequence (captured into a graph).
 template <int PREC>
 static int64_t enqueue_solve(bsde_plan_t *pl, cudaStream_t s, bool imported) {
   const Params &P = pl->P;
-  Ring64 r64{reinterpret_cast<double4_32a *>(pl->ws + pl->lay.ring64)};
-  const Ring32 r32 = ring32(pl->ws + pl->lay.ringA, pl->ws + pl->lay.ringB, P);
+  const Run &R = pl->run;
+  const Ring64 r64 = R.r64;
+  const Ring32 r32 = R.r32;
   Stats *st = reinterpret_cast<Stats *>(pl->ws + pl->lay.stats);
   double *sy = reinterpret_cast<double *>(pl->ws + pl->lay.stage);
   double *sz = sy + int64_t(P.k) * P.Nx;
   int64_t launches = 0;
   k_reset_stats<<<1, 32, 0, s>>>(st);
   ++launches;
+  if (!imported && has_startup(pl->prob)) {
+    launches += enqueue_startup<PREC>(pl, s, sy, sz);
+    imported = true;
+  }
   const unsigned eb = unsigned((P.Nx + 255) / 256 < 4096 ? (P.Nx + 255) / 256 : 4096);
   for (int m = 0; m < P.k; ++m) {
     if (imported)
@@ -173,12 +272,12 @@ static int64_t enqueue_solve(bsde_plan_t *pl, cudaStream_t s, bool imported) {
     else
       k_init_closed<PREC><<<eb, 256, 0, s>>>(P, r64, r32, m);
     ++launches;
-    launches += enqueue_spline<PREC>(pl, s, (P.N - m) % P.nslot);
+    launches += enqueue_spline<PREC>(R, s, (P.N - m) % P.nslot);
   }
   for (int n = P.N - P.k; n >= 0; --n) {
-    launch_step_any<PREC>(pl, s, n);
+    launch_step_any<PREC>(pl, R, s, n);
     ++launches;
-    launches += enqueue_spline<PREC>(pl, s, n % P.nslot);
+    launches += enqueue_spline<PREC>(R, s, n % P.nslot);
   }
   k_readout<PREC><<<1, 32, 0, s>>>(P, r64, r32, 0, st);
   k_export<PREC><<<eb, 256, 0, s>>>(P, r64, r32, sy, sy + P.Nx, 0);
@@ -238,31 +337,20 @@ int bsde_plan(const bsde_problem *p, void *dev_workspace, size_t bytes, bsde_pla
   pl->ws = static_cast<unsigned char *>(dev_workspace);
   pl->ws_bytes = bytes;
   driver_coefs(P, pl->dc64, pl->dc32);
-  // node table: built on the host, copied once into the workspace
-  const int kL = P.k * P.L;
-  NodeF64 *t64 = new (std::nothrow) NodeF64[kL];
-  NodeF32 *t32 = new (std::nothrow) NodeF32[kL];
-  PairF32 *tp = new (std::nothrow) PairF32[kL];
-  if (!t64 || !t32 || !tp) {
-    delete[] t64;
-    delete[] t32;
-    delete[] tp;
+  // node tables: built on the host, copied once into the workspace
+  HostTables *h = new (std::nothrow) HostTables;
+  if (!h) {
     delete pl;
     return fail(BSDE_ENOMEM, "table allocation");
   }
-  build_tables(pl->P, t64, t32, tp, 4, kMaxGroups, resident_step_threads(pl->device));
-  cudaError_t e;
-  if (P.precision == BSDE_FP64) {
-    e = cudaMemcpy(pl->ws + lay.table, t64, sizeof(NodeF64) * kL, cudaMemcpyHostToDevice);
-  } else {
-    e = cudaMemcpy(pl->ws + lay.table, t32, sizeof(NodeF32) * kL, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-      e = cudaMemcpy(pl->ws + lay.ptable, tp, sizeof(PairF32) * P.k * pl->P.Lp,
-                     cudaMemcpyHostToDevice);
+  int rc = upload_tables(pl, *h, nullptr);
+  cudaError_t e = rc ? cudaErrorUnknown : cudaStreamSynchronize(nullptr);
+  delete h;
+  if (rc) {
+    delete pl;
+    return rc;
   }
-  delete[] t64;
-  delete[] t32;
-  delete[] tp;
+  bind_runs(pl);
   if (e == cudaSuccess) e = cudaMallocHost(&pl->host_stats, sizeof(Stats));
   if (e != cudaSuccess) {
     delete pl;
@@ -338,12 +426,12 @@ int bsde_enqueue_level(bsde_plan_t *pl, void *stream, int n, int parts) {
   DeviceGuard guard(pl->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (parts & 1) {
-    if (pl->P.precision == BSDE_FP64) launch_step_any<BSDE_FP64>(pl, s, n);
-    else launch_step_any<BSDE_FP32C>(pl, s, n);
+    if (pl->P.precision == BSDE_FP64) launch_step_any<BSDE_FP64>(pl, pl->run, s, n);
+    else launch_step_any<BSDE_FP32C>(pl, pl->run, s, n);
   }
   if (parts & 2) {
-    if (pl->P.precision == BSDE_FP64) enqueue_spline<BSDE_FP64>(pl, s, n % pl->P.nslot);
-    else enqueue_spline<BSDE_FP32C>(pl, s, n % pl->P.nslot);
+    if (pl->P.precision == BSDE_FP64) enqueue_spline<BSDE_FP64>(pl->run, s, n % pl->P.nslot);
+    else enqueue_spline<BSDE_FP32C>(pl->run, s, n % pl->P.nslot);
   }
   BSDE_CUDA_TRY(cudaGetLastError());
   return BSDE_OK;
@@ -360,9 +448,15 @@ void bsde_free(bsde_plan_t *pl) {
 
 int64_t bsde_plan_launches(const bsde_plan_t *pl) {
   if (!pl) return 0;
-  // kernels in one solve (identical for both starts)
+  // kernels in one solve without caller levels (with them the start-up, if
+  // any, is not run; the rest is the same)
   const Params &P = pl->P;
-  return 1 + int64_t(P.k) * 2 + int64_t(P.N - P.k + 1) * 2 + 2;
+  int64_t n = 1 + int64_t(P.k) * 2 + int64_t(P.N - P.k + 1) * 2 + 2;
+  if (has_startup(pl->prob)) {
+    const int64_t steps = int64_t(P.k - 1) * pl->prob.init_substeps;
+    n += 3 + 2 * steps + (P.k - 1);
+  }
+  return n;
 }
 
 const char *bsde_strerror(int code) {
@@ -456,21 +550,11 @@ extern "C" int bsde_solve_noalloc(const bsde_problem *p, void *stream, const dou
   pl.ws_bytes = BSDE_NOALLOC_MAX_BYTES;
   driver_coefs(pl.P, pl.dc64, pl.dc32);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  HostTables tabs;  // on this stack frame (about 100 KB)
+  int rc2 = upload_tables(&pl, tabs, s);
+  if (rc2) return rc2;
+  bind_runs(&pl);
   const Params &P = pl.P;
-  const int kL = P.k * P.L;
-  NodeF64 t64[kMaxK * kMaxL];
-  NodeF32 t32[kMaxK * kMaxL];
-  PairF32 tpr[kMaxK * kMaxL];
-  build_tables(pl.P, t64, t32, tpr, 4, kMaxGroups, resident_step_threads(pl.device));
-  if (P.precision == BSDE_FP64) {
-    BSDE_CUDA_TRY(cudaMemcpyAsync(pl.ws + pl.lay.table, t64, sizeof(NodeF64) * kL,
-                                  cudaMemcpyHostToDevice, s));
-  } else {
-    BSDE_CUDA_TRY(cudaMemcpyAsync(pl.ws + pl.lay.table, t32, sizeof(NodeF32) * kL,
-                                  cudaMemcpyHostToDevice, s));
-    BSDE_CUDA_TRY(cudaMemcpyAsync(pl.ws + pl.lay.ptable, tpr, sizeof(PairF32) * P.k * P.Lp,
-                                  cudaMemcpyHostToDevice, s));
-  }
   // the host tables live on this stack frame: wait for the copies
   BSDE_CUDA_TRY(cudaStreamSynchronize(s));
   double *sy = reinterpret_cast<double *>(pl.ws + pl.lay.stage);
@@ -535,9 +619,11 @@ static int batch_layout(int n, const bsde_problem *ps, BatchLayout &L) {
   L.ringB.resize(n);
   for (int i = 0; i < n; ++i) {
     const bsde_problem &p = ps[i];
-    if (validate(p) || p.precision != BSDE_FP32C) return BSDE_EINVAL;
-    const size_t nx = size_t(p.Nx), ns = size_t(p.k + 1);
-    L.ptable[i] = off; off = up(off + size_t(p.k) * ((p.L + 1) / 2) * sizeof(PairF32));
+    // batches start from the closed form (no one-step start-up)
+    if (validate(p) || p.precision != BSDE_FP32C || has_startup(p)) return BSDE_EINVAL;
+    const size_t K = size_t(problem_K(p));
+    const size_t nx = size_t(p.Nx), ns = K + 1;
+    L.ptable[i] = off; off = up(off + K * ((p.L + 1) / 2) * sizeof(PairF32));
     L.ringA[i] = off; off = up(off + ns * nx * 16);
     L.ringB[i] = off; off = up(off + ns * nx * (16 + 8));
   }
@@ -734,7 +820,7 @@ int bsde_solve_batch(bsde_batch_t *b, void *stream, bsde_result *results) {
     std::memcpy(&d, &bits, sizeof(d));
     r.picard_resid_max = d;
     r.picard_iters_max = st.iters_max;
-    r.levels_done = b->probs[i].N - b->probs[i].k + 1;
+    r.levels_done = b->probs[i].N - problem_K(b->probs[i]) + 1;
     r.status = st.nonconv ? BSDE_WARN_NOCONV : BSDE_OK;
     if (r.status != BSDE_OK) worst = r.status;
   }
@@ -814,7 +900,7 @@ namespace bsde {
 
 static size_t request_bytes(const bsde_problem &p) {
   auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
-  const size_t nx = size_t(p.Nx), ns = size_t(p.k + 1);
+  const size_t nx = size_t(p.Nx), ns = size_t(problem_K(p) + 1);
   return up(ns * nx * 16) + up(ns * nx * (16 + 8));
 }
 
@@ -853,7 +939,8 @@ extern "C" {
 
 int bsde_request_bytes(const bsde_problem *p, size_t *bytes) {
   if (!p || !bytes) return fail(BSDE_EINVAL, "null argument");
-  if (validate(*p) || p->precision != BSDE_FP32C) return fail(BSDE_EINVAL, "invalid request");
+  if (validate(*p) || p->precision != BSDE_FP32C || has_startup(*p))
+    return fail(BSDE_EINVAL, "invalid request");
   *bytes = request_bytes(*p);
   return BSDE_OK;
 }
@@ -958,7 +1045,8 @@ int bsde_server_submit(bsde_server_t *s, const bsde_problem *p, int *slot) {
   if (!s->running) return fail(BSDE_EINVAL, "server not running");
   if (__atomic_load_n(&s->ctl->stopped, __ATOMIC_ACQUIRE))
     return fail(BSDE_ETIMEOUT, "server stopped: its idle limit passed; poll, stop and start it again");
-  if (validate(*p) || p->precision != BSDE_FP32C) return fail(BSDE_EINVAL, "invalid request");
+  if (validate(*p) || p->precision != BSDE_FP32C || has_startup(*p))
+    return fail(BSDE_EINVAL, "invalid request");
   if (s->free_slots.empty()) return BSDE_BUSY;
   const size_t need = request_bytes(*p);
   size_t off = 0;

@@ -10,7 +10,13 @@
 namespace bsde {
 
 int validate(const bsde_problem &p) {
-  if (p.k < 1 || p.k > kMaxK || p.k > p.N || p.N < 1) return BSDE_EINVAL;
+  if (p.k < 1 || p.k > kMaxK || p.k_z < 0 || p.k_z > kMaxK || p.N < 1) return BSDE_EINVAL;
+  if (problem_K(p) > p.N) return BSDE_EINVAL;
+  if (p.z_form != BSDE_ZFORM_EZ && p.z_form != BSDE_ZFORM_EYDW) return BSDE_EINVAL;
+  if (p.init_mode != BSDE_INIT_EXACT && p.init_mode != BSDE_INIT_ONESTEP) return BSDE_EINVAL;
+  if (p.init_mode == BSDE_INIT_ONESTEP &&
+      (p.init_substeps < 1 || int64_t(p.N) * p.init_substeps > (int64_t(1) << 30)))
+    return BSDE_EINVAL;
   if (p.Nx < 4 || p.Nx > (int64_t(1) << 30)) return BSDE_EINVAL;
   if (p.L < 1 || p.L > kMaxL) return BSDE_EINVAL;
   if (!(p.T > 0.0) || !(p.x_max > p.x_min)) return BSDE_EINVAL;
@@ -127,14 +133,17 @@ int fill_params(const bsde_problem &p, Params &P) {
   std::memset(&P, 0, sizeof(P));
   P.Nx = p.Nx;
   P.N = p.N;
-  P.k = p.k;
+  P.k = problem_K(p);
+  P.ky = p.k;
+  P.kz = problem_kz(p);
+  P.zform = p.z_form;
   P.L = p.L;
   P.driver = p.driver;
   P.terminal = p.terminal;
   P.precision = p.precision;
   P.smoothing = p.smoothing;
   P.picard_max = p.picard_max;
-  P.nslot = p.k + 1;
+  P.nslot = P.k + 1;
   P.T = p.T;
   P.dt = p.T / p.N;
   P.dx = (p.x_max - p.x_min) / double(p.Nx - 1);
@@ -157,8 +166,13 @@ int fill_params(const bsde_problem &p, Params &P) {
     if ((double)tf > p.picard_tol) tf = std::nextafter(tf, 0.0f);
     P.picard_tol_f = tf;
   }
-  gamma_tables(p.k, P.gy, P.gz);
-  P.h = p.k * P.dt;
+  {
+    // y: Table 1 row K_y; z: Table 2 row K_z; zero beyond
+    double unused[kMaxK + 1];
+    gamma_tables(P.ky, P.gy, unused);
+    gamma_tables(P.kz, unused, P.gz);
+  }
+  P.h = P.ky * P.dt;
   P.hg0 = P.h * P.gy[0];
   P.inv_gz0 = 1.0 / P.gz[0];
   P.inv_dx2_6 = 6.0 / (P.dx * P.dx);
@@ -172,10 +186,29 @@ int fill_params(const bsde_problem &p, Params &P) {
   return BSDE_OK;
 }
 
+bool has_startup(const bsde_problem &p) {
+  return p.init_mode == BSDE_INIT_ONESTEP && problem_K(p) > 1;
+}
+
+Params startup_params(const Params &P, int substeps) {
+  Params Q = P;
+  Q.N = P.N * substeps;
+  Q.dt = P.T / Q.N;  // the time grid t = n' T / (N S): t_{N-m} is n' = (N - m) S
+  Q.k = Q.ky = Q.kz = 1;
+  Q.nslot = 2;
+  for (int j = 0; j <= kMaxK; ++j) Q.gy[j] = Q.gz[j] = 0.0;
+  gamma_tables(1, Q.gy, Q.gz);
+  Q.h = Q.dt;
+  Q.hg0 = Q.h * Q.gy[0];
+  Q.inv_gz0 = 1.0 / Q.gz[0];
+  return Q;
+}
+
 Layout layout_for(const bsde_problem &p) {
   auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
   Layout L{};
-  const size_t nx = size_t(p.Nx), ns = size_t(p.k + 1);
+  const int K = problem_K(p);
+  const size_t nx = size_t(p.Nx), ns = size_t(K + 1);
   size_t off = 0;
   if (p.precision == BSDE_FP64) {
     L.ring64 = off; off = up(off + ns * nx * 32);
@@ -183,9 +216,20 @@ Layout layout_for(const bsde_problem &p) {
     L.ringA = off; off = up(off + ns * nx * 16);
     L.ringB = off; off = up(off + ns * nx * (16 + 8));  // interval records (d, P), Q
   }
-  L.table = off; off = up(off + size_t(p.k) * p.L * (p.precision == BSDE_FP64 ? sizeof(NodeF64) : sizeof(NodeF32)));
-  L.ptable = off; off = up(off + size_t(p.k) * ((p.L + 1) / 2) * sizeof(PairF32));
-  L.stage = off; off = up(off + 2 * size_t(p.k) * nx * 8);
+  const size_t node = p.precision == BSDE_FP64 ? sizeof(NodeF64) : sizeof(NodeF32);
+  L.table = off; off = up(off + size_t(K) * p.L * node);
+  L.ptable = off; off = up(off + size_t(K) * ((p.L + 1) / 2) * sizeof(PairF32));
+  L.stage = off; off = up(off + 2 * size_t(K) * nx * 8);
+  if (has_startup(p)) {
+    if (p.precision == BSDE_FP64) {
+      L.sub_ring64 = off; off = up(off + 2 * nx * 32);
+    } else {
+      L.sub_ringA = off; off = up(off + 2 * nx * 16);
+      L.sub_ringB = off; off = up(off + 2 * nx * (16 + 8));
+    }
+    L.sub_table = off; off = up(off + size_t(p.L) * node);
+    L.sub_ptable = off; off = up(off + size_t((p.L + 1) / 2) * sizeof(PairF32));
+  }
   L.stats = off; off = up(off + sizeof(Stats));
   L.total = off;
   return L;
@@ -254,10 +298,13 @@ void build_tables(Params &P, NodeF64 *t64, NodeF32 *t32, PairF32 *tp, int target
       e.w1 = th;
       e.w2 = c6 * (om * om * om - om);
       e.w3 = c6 * (th * th * th - th);
-      e.cz = wt * ((j == 1 ? 1.0 : 0.0) - P.gz[j]) * P.inv_gz0;
+      // gy[j] = 0 for j > K_y and gz[j] = 0 for j > K_z
+      const bool ez1 = j == 1 && !P.zform;
+      e.cz = wt * ((ez1 ? 1.0 : 0.0) - P.gz[j]) * P.inv_gz0;
       e.cfz = P.gz[j] * wt * dW * P.inv_gz0;
       e.cfy = P.h * P.gy[j] * wt;
-      e.cy = (j == P.k) ? wt : 0.0;
+      e.cy = (j == P.ky) ? wt : 0.0;
+      e.cyz = (j == 1 && P.zform) ? wt * dW / P.dt * P.inv_gz0 : 0.0;
       if (e.shift < smin) smin = e.shift;
       if (e.shift > smax) smax = e.shift;
       const int idx = (j - 1) * P.L + l;
@@ -275,6 +322,8 @@ void build_tables(Params &P, NodeF64 *t64, NodeF32 *t32, PairF32 *tp, int target
         f.cfy = (float)e.cfy;
         f.cyh = (float)e.cy;
         f.cyl = (float)(e.cy - (double)f.cyh);
+        f.cyzh = (float)e.cyz;
+        f.cyzl = (float)(e.cyz - (double)f.cyzh);
         t32[idx] = f;
       }
     }
@@ -306,6 +355,9 @@ void build_tables(Params &P, NodeF64 *t64, NodeF32 *t32, PairF32 *tp, int target
         pr.nch[1] = -pr.ch[1];
         pr.ncl[0] = -(na.cyl * half);
         pr.ncl[1] = -(na.czl * half);
+        // node b's y weight is -cyz (opposite DeltaW); the middle node has 0
+        pr.cyz[0] = na.cyzh;
+        pr.cyz[1] = na.cyzl;
         tp[(j - 1) * P.Lp + q] = pr;
       }
     }

@@ -23,15 +23,18 @@ constexpr int kSplineHead = 16;   // FP32C: pivots of the spline LU are constant
 // x_i + a_x j dt + b_x sqrt(2 j dt) a_l sits in cell i + shift at relative
 // position theta; w0..w3 are the spline weights of v_c, v_{c+1}, M_c, M_{c+1}.
 // The expectations of Eq. 20 are folded into per-node coefficients, so that
-// a thread keeps two sums per point:
-//   z^n = sum_jl cz_jl z^_jl + sum_jl cfz_jl F_jl
-//   A   = sum_l  cy_l  y^_kl + sum_jl cfy_jl F_jl      (y^n = A + k dt gy_0 f(t_n, y^n, z^n))
+// a thread keeps two sums per point (j = 1..K, K = max(K_y, K_z)):
+//   z^n = sum_jl cz_jl z^_jl + sum_jl cfz_jl F_jl [+ sum_l cyz_l y^_1l]
+//   A   = sum_l  cy_l  y^_{K_y}l + sum_jl cfy_jl F_jl  (y^n = A + K_y dt gy_0 f(t_n, y^n, z^n))
 // with wt = omega_l / sqrt(pi) (Eq. 21), DeltaW_jl = sqrt(2 j dt) a_l,
+// gy from Table 1 row K_y and gz from Table 2 row K_z (zero beyond them),
 // cz = wt (delta_{j1} - gz_j) / gz_0, cfz = gz_j wt DeltaW_jl / gz_0,
-// cy = wt (j = k only), cfy = k dt gy_j wt.
+// cy = wt (j = K_y only), cfy = K_y dt gy_j wt.  In the E[y DeltaW] z form
+// the delta_{j1} term moves from z^ to y^: cz = -wt gz_j / gz_0 and
+// cyz = wt DeltaW_1l / (dt gz_0) at j = 1 (zero otherwise).
 struct NodeF64 {
   int32_t shift, pad;
-  double w0, w1, w2, w3, cz, cfz, cfy, cy;
+  double w0, w1, w2, w3, cz, cfz, cfy, cy, cyz;
 };
 
 // FP32C entry: the same coefficients, with cz and cy split into float
@@ -39,8 +42,7 @@ struct NodeF64 {
 struct NodeF32 {
   int32_t shift;
   float w0, w1, w2, w3;
-  float czh, czl, cfz, cfy, cyh, cyl;
-  float pad;
+  float czh, czl, cfz, cfy, cyh, cyl, cyzh, cyzl;
 };
 
 // FP32C pair entry: Gauss-Hermite nodes l and L-1-l (a_{L-1-l} = -a_l) share
@@ -54,29 +56,39 @@ struct NodeF32 {
 // lane pairs (cy, cz): hi parts, and negated hi and lo parts, which let the
 // error terms be formed by fused multiply-adds alone.  Five float4:
 // (shift_a, shift_b, cfz, cfy), (th_a, th_a, ka_a, ka_a),
-// (th_b, th_b, ka_b, ka_b), (cyh, czh, -cyh, -czh), (-cyl, -czl, 0, 0);
+// (th_b, th_b, ka_b, ka_b), (cyh, czh, -cyh, -czh), (-cyl, -czl, cyzh, cyzl);
 // th = theta, ka = -theta (1 - theta) dx^2 / 6 (the spline value is
 // v_c + theta d + ka (P + theta Q) on the interval records).  cy is zero for
-// j < k.
+// j != K_y.  cyz (hi, lo) is node a's weight of y^ in the z sum (E[y DeltaW]
+// z form, j = 1; node b's is -cyz): the pair adds cyz (y^_a - y^_b).
 struct PairF32 {
   int32_t shift_a, shift_b;
   float cfz, cfy;
   float tha[2], kaa[2], thb[2], kab[2];
-  float ch[2], nch[2], ncl[2], pad[2];
+  float ch[2], nch[2], ncl[2], cyz[2];
 };
 constexpr int kPairVec = int(sizeof(PairF32) / 16);  // float4 per entry
 
-// Everything a kernel needs to know about one problem.
+// K_z of a problem (0 in the struct means K_z = k) and K = max(K_y, K_z),
+// the number of later levels one backward step reads (Eq. 16).
+inline int problem_kz(const bsde_problem &p) { return p.k_z > 0 ? p.k_z : p.k; }
+inline int problem_K(const bsde_problem &p) {
+  return p.k > problem_kz(p) ? p.k : problem_kz(p);
+}
+
+// Everything a kernel needs to know about one problem.  k is K (levels per
+// step, ring of k + 1 slots); ky, kz the steps of the y and z lines.
 struct Params {
   int64_t Nx;
   int32_t N, k, L, driver, terminal, precision, smoothing, picard_max, nslot;
+  int32_t ky, kz, zform, pad_;
   double T, dt, dx, x_min, x_max, x0, a_x, b_x;
   double r, mu, sigma, R, delta, lb_sign, strike;
   double picard_tol;
   float picard_tol_f;  // the largest float <= picard_tol (FP32 Picard test)
   double gy[kMaxK + 1], gz[kMaxK + 1];
-  double h;       // k dt
-  double hg0;     // k dt gy_0 (weight of the implicit term)
+  double h;       // K_y dt
+  double hg0;     // K_y dt gy_0 (weight of the implicit term)
   double inv_gz0; // 1 / gz_0
   double inv_dx2_6; // 6 / dx^2
   double invd[kInvPivots];
@@ -91,9 +103,12 @@ struct Layout {
   size_t ring64;   // FP64: double4 (y, M_y, z, M_z) x nslot x Nx
   size_t ringA;    // FP32C: float4 (y_hi, y_lo, z_hi, z_lo) x nslot x Nx
   size_t ringB;    // FP32C: interval records, float4 (d, P) then float2 Q, x nslot x Nx
-  size_t table;    // node table (k L entries)
-  size_t ptable;   // FP32C pair table (k ceil(L/2) entries)
-  size_t stage;    // 2 x k x Nx doubles: imported initial levels / exported level 0
+  size_t table;    // node table (K L entries)
+  size_t ptable;   // FP32C pair table (K ceil(L/2) entries)
+  size_t stage;    // 2 x K x Nx doubles: imported initial levels / exported level 0
+  // one-step start-up (init_mode ONESTEP, K > 1): a ring of two slots and the
+  // node tables of the 1-step scheme; unused otherwise
+  size_t sub_ring64, sub_ringA, sub_ringB, sub_table, sub_ptable;
   size_t stats;    // Stats
   size_t total;
 };
@@ -110,6 +125,11 @@ struct Stats {
 // Host-side planning (bsde_host.cpp).
 int validate(const bsde_problem &p);
 int fill_params(const bsde_problem &p, Params &P);
+// Whether a solve of p without caller levels runs the one-step start-up, and
+// the Params of that start-up: K_y = K_z = 1, N S steps of dt / S on the same
+// grid and nodes (Section 3.1 step 2).
+bool has_startup(const bsde_problem &p);
+Params startup_params(const Params &P, int substeps);
 Layout layout_for(const bsde_problem &p);
 int gauss_hermite(int L, double *nodes, double *weights);
 int gamma_tables(int k, double *gy, double *gz);

@@ -553,11 +553,13 @@ __device__ __forceinline__ void node_cells(int ii, int shift, int last, int &c0,
   }
 }
 
+// yj: this level is n + K_y (E[y^] enters A); zf: the E[y DeltaW] z form's
+// y^ term (j = 1).
 template <int DRV, bool CLAMP>
 __device__ __forceinline__ void nodes64(const DrvC<double> &dc, const double4_32a *__restrict__ lev,
                                         const NodeF64 *row, int l0, int l1, int ii, int last,
-                                        double tj, double et, double emt, bool lastj, double &Zs,
-                                        double &Ys) {
+                                        double tj, double et, double emt, bool yj, bool zf,
+                                        double &Zs, double &Ys) {
 #pragma unroll 4
   for (int l = l0; l < l1; ++l) {
     const NodeF64 &e = row[l];
@@ -570,7 +572,8 @@ __device__ __forceinline__ void nodes64(const DrvC<double> &dc, const double4_32
     const double F = driver<DRV>(dc, tj, et, emt, yh, zh);
     Zs += e.cz * zh + e.cfz * F;
     Ys += e.cfy * F;
-    if (lastj) Ys += e.cy * yh;
+    if (yj) Ys += e.cy * yh;
+    if (zf) Zs += e.cyz * yh;
   }
 }
 
@@ -598,10 +601,11 @@ __global__ void __launch_bounds__(kStepTP * kMaxGroups)
     const double et = exp(tj * tj), emt = exp(-tj * tj);
     const NodeF64 *row = tab + (j - 1) * P.L;
     const bool interior = i0 + P.smin[j - 1] >= 0 && i0 + kStepTP + P.smax[j - 1] <= last;
+    const bool yj = j == P.ky, zf = P.zform && j == 1;
     if (interior)
-      nodes64<DRV, false>(dc, lev, row, l0, l1, ii, last, tj, et, emt, j == P.k, Zs, Ys);
+      nodes64<DRV, false>(dc, lev, row, l0, l1, ii, last, tj, et, emt, yj, zf, Zs, Ys);
     else
-      nodes64<DRV, true>(dc, lev, row, l0, l1, ii, last, tj, et, emt, j == P.k, Zs, Ys);
+      nodes64<DRV, true>(dc, lev, row, l0, l1, ii, last, tj, et, emt, yj, zf, Zs, Ys);
   }
   part[(0 * P.G + g) * kStepTP + tp] = Zs;
   part[(1 * P.G + g) * kStepTP + tp] = Ys;
@@ -694,6 +698,19 @@ __device__ __forceinline__ void comp_acc2(float2 &S, float2 &C, float2 ch, float
   C = f2sub(f2add(C, err), nt);
 }
 
+// One lane of comp_acc2: S += ch*hi exactly, C += the rounding errors plus
+// ch*del + cl*hi.
+__device__ __forceinline__ void comp_acc1(float &S, float &C, float ch, float cl, float hi,
+                                          float del) {
+  const float p = __fmul_rn(ch, hi);
+  const float e = __fmaf_rn(ch, hi, -p);
+  const float sn = __fadd_rn(S, p);
+  const float bp = __fsub_rn(sn, S);
+  const float err = __fadd_rn(__fsub_rn(S, __fsub_rn(sn, bp)), __fsub_rn(p, bp));
+  S = sn;
+  C = __fadd_rn(C, __fadd_rn(err, __fmaf_rn(ch, del, __fmaf_rn(cl, hi, e))));
+}
+
 __device__ __forceinline__ void two_sum_into(float &S, float &C, float x) {
   const float s = __fadd_rn(S, x);
   const float bp = __fsub_rn(s, S);
@@ -735,8 +752,9 @@ __device__ __forceinline__ void node_value(const float4 &a, const float4 &bq, co
 
 // The arithmetic of one node pair (see PairF32 for the entry e0..e4), given
 // the level data of the two nodes' cells.  S, C: compensated (y, z) sums;
-// Fz, Fy: driver terms.
-template <int DRV>
+// Fz, Fy: driver terms.  ZF: the E[y DeltaW] z form's term cyz (y^_a - y^_b)
+// joins the z sum (compensated, the difference formed exactly by TwoSum).
+template <int DRV, bool ZF = false>
 __device__ __forceinline__ void pair_math(const DrvC<float> &dc, float tj, float et, float emt,
                                           const float4 &e0, const float4 &e1, const float4 &e2,
                                           const float4 &e3, const float4 &e4, const float4 &aa,
@@ -755,6 +773,12 @@ __device__ __forceinline__ void pair_math(const DrvC<float> &dc, float tj, float
   float2 hs, he;
   two_sum2(ha, hb, hs, he);
   comp_acc2(S, C, hi2(e3), lo2(e3), hi2(e4), hs, f2add(f2add(da, db), he));
+  if constexpr (ZF) {
+    float dh = 0.f, dl = 0.f;
+    dh = ha.x;
+    two_sum_into(dh, dl, -hb.x);
+    comp_acc1(S.y, C.y, e4.z, e4.w, dh, __fadd_rn(dl, __fsub_rn(da.x, db.x)));
+  }
 }
 
 // Accumulators of one point: compensated (y, z) sums and the driver terms.
@@ -765,7 +789,7 @@ struct Acc32 {
 
 // One group's node pairs for point ii, level data loaded directly from
 // global memory (L1/L2).  With CLAMP false every cell must lie on the grid.
-template <int DRV, bool CLAMP, bool COH>
+template <int DRV, bool CLAMP, bool COH, bool ZF = false>
 __device__ __forceinline__ void pairs32(const DrvC<float> &dc, Ring32 r, int64_t off,
                                         const PairF32 *row, int q0, int q1, int ii, int last,
                                         float tj, float et, float emt, Acc32 &acc) {
@@ -783,8 +807,8 @@ __device__ __forceinline__ void pairs32(const DrvC<float> &dc, Ring32 r, int64_t
     const float4 aa = ldl<COH>(A + ca), ab = ldl<COH>(B + ca), ba = ldl<COH>(A + cb),
                  bb = ldl<COH>(B + cb);
     const float2 ac = ldl<COH>(Cq + ca), bc = ldl<COH>(Cq + cb);
-    pair_math<DRV>(dc, tj, et, emt, e0, e1, e2, e3, e4, aa, ab, ac, ba, bb, bc, acc.S, acc.C,
-                   acc.Fz, acc.Fy);
+    pair_math<DRV, ZF>(dc, tj, et, emt, e0, e1, e2, e3, e4, aa, ab, ac, ba, bb, bc, acc.S,
+                       acc.C, acc.Fz, acc.Fy);
   }
 }
 
@@ -916,7 +940,10 @@ __device__ __forceinline__ void step_tile32(const Params &P, const DrvC<float> &
     float tj, et, emt;
     level_time<DRV>(P, n + w.j, tj, et, emt);
     const PairF32 *row = tab + (w.j - 1) * P.Lp;
-    if (w.interior)
+    if (P.zform && w.j == 1)  // the E[y DeltaW] z form (clamping always on)
+      pairs32<DRV, true, COH, true>(dc, r32, off, row, w.q0, w.q1, i0 + tp, last, tj, et, emt,
+                                    acc);
+    else if (w.interior)
       pairs32<DRV, false, COH>(dc, r32, off, row, w.q0, w.q1, i0 + tp, last, tj, et, emt, acc);
     else  // cells clamp onto the grid, so points past the end are harmless
       pairs32<DRV, true, COH>(dc, r32, off, row, w.q0, w.q1, i0 + tp, last, tj, et, emt, acc);

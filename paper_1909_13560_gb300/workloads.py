@@ -127,18 +127,24 @@ def config5_arrivals(rate: float = 2000.0, duration: float = 10.0,
     return out
 
 
+def levels_K(p: dict) -> int:
+    """K = max(K_y, K_z) (Eq. 16): initial levels, and levels read per step."""
+    return max(int(p["k"]), int(p.get("kz", 0)) or int(p["k"]))
+
+
 def gp_steps(p: dict) -> int:
-    """Grid-point time steps of one solve: Nx * (N - k + 1) levels computed."""
-    return int(p["Nx"]) * (int(p["N"]) - int(p["k"]) + 1)
+    """Grid-point time steps of one solve: Nx * (N - K + 1) levels computed
+    (the one-step start-up, when asked for, is not counted)."""
+    return int(p["Nx"]) * (int(p["N"]) - levels_K(p) + 1)
 
 
 def initial_levels(p: dict):
-    """Host arrays (k, Nx) of the k initial levels N, N-1, ..., N-k+1 from the
+    """Host arrays (K, Nx) of the K initial levels N, N-1, ..., N-K+1 from the
     closed-form solution of the problem (the exact start), with the level-N
     call payoff replaced by its cell average when smoothing is on.  This is
     input data for callers that pass their own levels through host memory."""
     from scipy.special import ndtr
-    k, Nx, N = int(p["k"]), int(p["Nx"]), int(p["N"])
+    k, Nx, N = levels_K(p), int(p["Nx"]), int(p["N"])
     dx = (p["x_max"] - p["x_min"]) / (Nx - 1)
     x = p["x_min"] + dx * np.arange(Nx)
     dt = p["T"] / N

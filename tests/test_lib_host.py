@@ -114,3 +114,47 @@ def test_workspace_bytes_scale_with_ring():
     # plus the interval record (d, P) and Q
     assert ns * nx * 32 <= b64 < ns * nx * 32 + (8 << 20)
     assert ns * nx * 40 <= b32 < ns * nx * 40 + (8 << 20)
+
+
+@pytest.mark.parametrize("bad", [dict(kz=7), dict(kz=-1), dict(kz=6, N=5), dict(zform=2),
+                                 dict(init_mode=2), dict(init_mode=1, init_substeps=0),
+                                 dict(init_mode=1, init_substeps=1 << 25)])
+def test_invalid_variants_rejected(bad):
+    p = W.sin_problem()
+    p.update(bad)
+    with pytest.raises(B.BsdeError) as ei:
+        B.bsde_workspace_bytes(B.make_problem(p))
+    assert ei.value.code == B.BSDE_EINVAL
+
+
+def test_workspace_bytes_of_the_variants():
+    """K_z widens the ring to max(k, kz) + 1 slots; the one-step start-up adds
+    a ring of two slots (and its small node tables), the z form nothing."""
+    p = W.call_problem(Nx=1 << 16, N=64, k=2)
+    for prec, per_node in (("fp64", 32), ("fp32c", 40)):
+        base = B.bsde_workspace_bytes(B.make_problem(p, prec))
+        wide = B.bsde_workspace_bytes(B.make_problem(dict(p, kz=5), prec))
+        zf = B.bsde_workspace_bytes(B.make_problem(dict(p, zform=1), prec))
+        one = B.bsde_workspace_bytes(B.make_problem(dict(p, init_mode="ONESTEP",
+                                                         init_substeps=4), prec))
+        nx = p["Nx"]
+        assert zf == base
+        # 3 more ring slots and 3 more rows of the staging area (2 x 8 B per node)
+        assert wide - base >= 3 * nx * (per_node + 16)
+        assert 2 * nx * per_node <= one - base < 2 * nx * per_node + (1 << 16)
+        # K = 1 has nothing to start up
+        k1 = dict(p, k=1)
+        assert (B.bsde_workspace_bytes(B.make_problem(dict(k1, init_mode="ONESTEP",
+                                                           init_substeps=4), prec))
+                == B.bsde_workspace_bytes(B.make_problem(k1, prec)))
+
+
+def test_batch_and_server_reject_the_startup():
+    p = dict(W.call_problem(Nx=1024, N=32, k=3), init_mode="ONESTEP", init_substeps=2)
+    with pytest.raises(B.BsdeError):
+        B.bsde_batch_workspace_bytes([p])
+    n = ctypes.c_size_t()
+    assert B.load().bsde_request_bytes(ctypes.byref(B.make_problem(p, "fp32c")),
+                                       ctypes.byref(n)) == B.BSDE_EINVAL
+    # the variants without a start-up are accepted
+    B.bsde_batch_workspace_bytes([dict(p, init_mode="EXACT", kz=4, zform=1)])

@@ -39,9 +39,16 @@ def test_picard_fixed_point_of_a_linear_driver(k):
     assert np.max(np.abs(got["z"])) < 1e-13
 
 
-def _mp_scheme(k, Nx, N, L, x_lim, T, mp):
-    """Eq. 20-21 for f = y/2 - z, g = sin(x + T), X = W, at mp precision.
-    Returns level 0 (y, z) at the grid points."""
+def _mp_scheme(k, Nx, N, L, x_lim, T, mp, kz=None, zform=0, start=None, stop=0,
+               return_all=False):
+    """Eq. 20-21 for f = y/2 - z, g = sin(x + T), X = W, at mp precision, with
+    K_y = k and K_z = kz (default k; Eq. 16: K = max(K_y, K_z) levels), the
+    z line's first term E[z^{n+1}] or (zform) E[y^{n+1} DeltaW_1] / dt, and
+    the K initial levels from `start` ({level: (ys, zs)}) or the closed form.
+    Runs levels N-K down to `stop`; returns level `stop` (y, z) at the grid
+    points, or every level ({level: (ys, zs)}) with return_all."""
+    kz = k if kz is None else kz
+    K = max(k, kz)
     dt = mp.mpf(T) / N
     xs = [mp.mpf(-x_lim) + 2 * mp.mpf(x_lim) * i / (Nx - 1) for i in range(Nx)]
     dx = xs[1] - xs[0]
@@ -64,7 +71,8 @@ def _mp_scheme(k, Nx, N, L, x_lim, T, mp):
     nodes = sorted(mp.re(z) for z in mp.polyroots(hc[L], maxsteps=200, extraprec=200))
     wts = [2 ** (L - 1) * mp.factorial(L) * mp.sqrt(mp.pi) / (L * L * herm(L - 1, a) ** 2)
            for a in nodes]
-    gy, gz = _gamma_exact(k)
+    gy, _ = _gamma_exact(k)
+    _, gz = _gamma_exact(kz)
     gy = [mp.mpf(g.numerator) / g.denominator for g in gy]
     gz = [mp.mpf(g.numerator) / g.denominator for g in gz]
 
@@ -96,16 +104,19 @@ def _mp_scheme(k, Nx, N, L, x_lim, T, mp):
                 + dx ** 2 / 6 * ((om ** 3 - om) * M[c] + (th ** 3 - th) * M[c + 1]))
 
     lev = {}
-    for m in range(k):
+    for m in range(K):
         t = (N - m) * dt
-        lev[N - m] = ([mp.sin(x + t) for x in xs], [mp.cos(x + t) for x in xs])
+        if start is not None:
+            lev[N - m] = start[N - m]
+        else:
+            lev[N - m] = ([mp.sin(x + t) for x in xs], [mp.cos(x + t) for x in xs])
     spl = {m: (second_derivs(lev[m][0]), second_derivs(lev[m][1])) for m in lev}
     rpi = 1 / mp.sqrt(mp.pi)
-    for n in range(N - k, -1, -1):
+    for n in range(N - K, stop - 1, -1):
         ys, zs = [], []
         for x in xs:
-            Ez, EFdW, EF, Ey = {}, {}, {}, mp.mpf(0)
-            for j in range(1, k + 1):
+            Ez, EFdW, EF, Ey, EyW1 = {}, {}, {}, mp.mpf(0), mp.mpf(0)
+            for j in range(1, K + 1):
                 vy, vz = lev[n + j]
                 My, Mz = spl[n + j]
                 ez = efdw = ef = mp.mpf(0)
@@ -119,8 +130,11 @@ def _mp_scheme(k, Nx, N, L, x_lim, T, mp):
                     ef += w * rpi * F
                     if j == k:
                         Ey += w * rpi * yh
+                    if j == 1:
+                        EyW1 += w * rpi * yh * dW
                 Ez[j], EFdW[j], EF[j] = ez, efdw, ef
-            z = (Ez[1] + sum(gz[j] * (EFdW[j] - Ez[j]) for j in range(1, k + 1))) / gz[0]
+            first = EyW1 / dt if zform else Ez[1]
+            z = (first + sum(gz[j] * (EFdW[j] - Ez[j]) for j in range(1, kz + 1))) / gz[0]
             Ay = Ey + k * dt * sum(gy[j] * EF[j] for j in range(1, k + 1))
             # y = Ay + k dt gy_0 (y/2 - z): the fixed point, exactly
             y = (Ay - k * dt * gy[0] * z) / (1 - k * dt * gy[0] / 2)
@@ -128,7 +142,7 @@ def _mp_scheme(k, Nx, N, L, x_lim, T, mp):
             zs.append(z)
         lev[n] = (ys, zs)
         spl[n] = (second_derivs(ys), second_derivs(zs))
-    return lev[0]
+    return lev if return_all else lev[stop]
 
 
 @pytest.mark.parametrize("k", [1, 2, 3])
@@ -143,4 +157,41 @@ def test_oracle_against_50_digit_scheme(k):
     ez = max(abs(float(a) - b) for a, b in zip(zs, got["z"]))
     # the oracle's Picard iteration stops once |dy| <= 1e-12 (contraction
     # k dt gy_0 / 2 < 0.15 here), and FP64 rounding is ~1e-15
+    assert ey < 1e-12 and ez < 1e-12, (ey, ez)
+
+
+@pytest.mark.parametrize("k,kz,zform", [(1, 2, 0), (2, 3, 0), (3, 1, 0), (1, 1, 1),
+                                        (2, 2, 1), (1, 2, 1)])
+def test_variants_against_50_digit_scheme(k, kz, zform):
+    """K_z != K_y (Eq. 16) and the E[y DeltaW_1] / dt z form, brute force."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    Nx, N, L, x_lim, T = 17, 6, 4, 3.0, 1.0
+    p = W.sin_problem(Nx=Nx, N=N, k=k, L=L, x_lim=x_lim, T=T)
+    p.update(kz=kz, zform=zform)
+    got = O.solve(p, want_level=True)
+    ys, zs = _mp_scheme(k, Nx, N, L, x_lim, T, mp, kz=kz, zform=zform)
+    ey = max(abs(float(a) - b) for a, b in zip(ys, got["y"]))
+    ez = max(abs(float(a) - b) for a, b in zip(zs, got["z"]))
+    assert ey < 1e-12 and ez < 1e-12, (ey, ez)
+
+
+@pytest.mark.parametrize("k,kz,S", [(2, 2, 2), (3, 3, 1), (1, 3, 2)])
+def test_onestep_startup_against_50_digit_scheme(k, kz, S):
+    """Section 3.1 step 2: levels N-1..N-K+1 from the 1-step scheme with step
+    dt / S, then the K-step loop; at 50 digits the start-up is the same
+    scheme run on the finer time grid t = n' T / (N S)."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    Nx, N, L, x_lim, T = 17, 6, 4, 3.0, 1.0
+    K = max(k, kz)
+    p = W.sin_problem(Nx=Nx, N=N, k=k, L=L, x_lim=x_lim, T=T)
+    p.update(kz=kz, init_mode="ONESTEP", init_substeps=S)
+    got = O.solve(p, want_level=True)
+    fine = _mp_scheme(1, Nx, N * S, L, x_lim, T, mp, stop=N * S - (K - 1) * S,
+                      return_all=True)
+    start = {N - m: fine[(N - m) * S] for m in range(K)}
+    ys, zs = _mp_scheme(k, Nx, N, L, x_lim, T, mp, kz=kz, start=start)
+    ey = max(abs(float(a) - b) for a, b in zip(ys, got["y"]))
+    ez = max(abs(float(a) - b) for a, b in zip(zs, got["z"]))
     assert ey < 1e-12 and ez < 1e-12, (ey, ez)
