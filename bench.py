@@ -149,6 +149,59 @@ def _golden():
         return {}
 
 
+def _golden_variants():
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "config2_oracle.json")) as fh:
+            return json.load(fh).get("variants", [])
+    except OSError:
+        return []
+
+
+def measure_variants(args, dev, stream, flush):
+    """The scheme's variants on the config2 workload (K_z != K_y, the E[y dW]
+    z form, the one-step start-up), each solve timed alone with CUDA events
+    (L2 flushed before each, outside the events) and compared with the FP64
+    oracle's value stored for it."""
+    import torch
+    from paper_1909_13560_gb300 import bsde as B
+    from paper_1909_13560_gb300 import workloads as W
+    sp = stream.cuda_stream
+    rows = []
+    for g in _golden_variants():
+        f = dict(g["fields"])
+        p = W.config2(k=f.pop("k"))
+        p.update(f)
+        s = B.Solver(p, args.precision, device=dev)
+        for _ in range(3):
+            flush.zero_()
+            B.bsde_solve(s.plan, sp, want_result=False)
+        torch.cuda.synchronize(dev)
+        ms = 0.0
+        for _ in range(max(1, args.steps)):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            B.bsde_solve(s.plan, sp, want_result=False)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms += e0.elapsed_time(e1)
+        ms /= max(1, args.steps)
+        r = B.bsde_result_fetch(s.plan, sp)
+        K = W.levels_K(p)
+        startup = p["Nx"] * (K - 1) * int(p.get("init_substeps", 0)) if p.get("init_mode") else 0
+        tol = (1e-12 if args.precision == "fp64" else 1e-6) * max(1.0, abs(g["y0"]))
+        rows.append({"name": g["name"], "fields": g["fields"], "ms_per_solve": ms,
+                     "gp_steps_per_s": W.gp_steps(p) / (ms / 1000.0),
+                     "startup_gp_steps": startup, "launches": s.launches,
+                     "y0": r.y0, "z0": r.z0, "err_y0_vs_oracle": abs(r.y0 - g["y0"]),
+                     "err_z0_vs_oracle": abs(r.z0 - g["z0"]),
+                     "within_tol": abs(r.y0 - g["y0"]) <= tol,
+                     "err_y0_vs_exact": abs(r.y0 - g["exact_y0"]),
+                     "err_z0_vs_exact": abs(r.z0 - g["exact_z0"])})
+        s.close()
+    return rows
+
+
 def _dist_init(world):
     if world > 1:
         import torch.distributed as dist
@@ -376,6 +429,10 @@ def run_ours(args, rank, world, local_rank):
     e_dt = _max_over_ranks(dist, time.perf_counter() - e_t0)
     e2e_value = world * units_per_step * args.steps / e_dt
 
+    variants = None
+    if not c3 and not args.no_variants:
+        variants = measure_variants(args, dev, stream, flush)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(max(1, args.cpu_levels // 8) if c3 else args.cpu_levels,
@@ -428,6 +485,13 @@ def run_ours(args, rank, world, local_rank):
         }
         if cpu is not None:
             line["cpu_baseline"] = cpu
+        if variants is not None:
+            line["variants"] = {
+                "workload": "config2 with the scheme's variants (Eq. 16 K_z != K_y; the "
+                            "E[y dW]/dt z form; the one-step start-up of Section 3.1 step 2)",
+                "gate": "|y0 - stored FP64 oracle| <= 1e-6 max(1, |y0|) (FP32C), "
+                        "1e-12 max(1, |y0|) (FP64)",
+                "rows": variants}
         print(json.dumps(line), flush=True)
     for s in solvers:
         s.close()
@@ -628,6 +692,8 @@ def main():
     ap.add_argument("--cpu-levels", type=int, default=64)
     ap.add_argument("--ref-levels", type=int, default=12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="config2: skip the timing of the scheme's variants")
     ap.add_argument("--autotune", action="store_true",
                     help="config4: pick the batch configuration by timing (else cluster 1, 4 groups)")
     args = ap.parse_args()

@@ -160,3 +160,20 @@ def test_variants_in_a_batch_equal_single_solves(B):
 def test_batch_rejects_the_startup(B):
     with pytest.raises(B.BsdeError):
         B.BatchSolver([ONESTEP["ex1_k3_S4"]])
+
+
+@pytest.mark.parametrize("name,fields", [("ky1_kz2", dict(k=1, kz=2)),
+                                         ("k1_zform", dict(k=1, zform=1)),
+                                         ("k2_onestep_S8", dict(k=2, init_mode="ONESTEP",
+                                                                init_substeps=8))])
+def test_config2_full_size_variants(B, name, fields):
+    """The benchmark workload (Nx = 65536, N = 256, L = 16) with the variants
+    the benchmark times: whole level 0 against the oracle in both
+    precisions."""
+    f = dict(fields)
+    p = W.config2(k=f.pop("k"))
+    p.update(f)
+    ref = O.solve(p, threads=THREADS, want_level=True)
+    for prec in ("fp64", "fp32c"):
+        got = B.solve(p, prec, want_level=True)
+        _cmp(got, ref, TOL[prec], f"config2 {name} {prec}")
