@@ -20,6 +20,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
+_SRC2 = os.path.join(_HERE, "oracle2d.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -46,6 +47,34 @@ class _Problem(ctypes.Structure):
     ]
 
 
+class _Problem2(ctypes.Structure):
+    _fields_ = [
+        ("driver", ctypes.c_int), ("terminal", ctypes.c_int),
+        ("picard_max", ctypes.c_int), ("pad", ctypes.c_int),
+        ("T", ctypes.c_double), ("x1_min", ctypes.c_double), ("x1_max", ctypes.c_double),
+        ("x2_min", ctypes.c_double), ("x2_max", ctypes.c_double),
+        ("x01", ctypes.c_double), ("x02", ctypes.c_double),
+        ("a1", ctypes.c_double), ("a2", ctypes.c_double), ("b11", ctypes.c_double),
+        ("b21", ctypes.c_double), ("b22", ctypes.c_double),
+        ("alpha", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
+        ("picard_tol", ctypes.c_double),
+        ("Nx1", ctypes.c_longlong), ("Nx2", ctypes.c_longlong),
+        ("N", ctypes.c_int), ("k", ctypes.c_int), ("L", ctypes.c_int), ("pad2", ctypes.c_int),
+    ]
+
+
+class _Result2(ctypes.Structure):
+    _fields_ = [
+        ("y0", ctypes.c_double), ("z0", ctypes.c_double * 2),
+        ("picard_resid_max", ctypes.c_double), ("levels_done", ctypes.c_longlong),
+        ("status", ctypes.c_int), ("picard_iters_max", ctypes.c_int),
+    ]
+
+
+DRIVERS2 = {"LINEAR": 0}
+TERMINALS2 = {"SIN_SUM": 0, "SPREAD_LOG": 1}
+
+
 class _Result(ctypes.Structure):
     _fields_ = [
         ("y0", ctypes.c_double), ("z0", ctypes.c_double),
@@ -59,11 +88,12 @@ def build(force: bool = False) -> str:
     contraction, OpenMP over grid points)."""
     with _lock:
         if (not force and os.path.exists(_LIB)
-                and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+                and os.path.getmtime(_LIB) >= max(os.path.getmtime(_SRC),
+                                                  os.path.getmtime(_SRC2))):
             return _LIB
         tmp = _LIB + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-               "-fno-fast-math", "-fopenmp", _SRC, "-o", tmp, "-lm"]
+               "-fno-fast-math", "-fopenmp", _SRC, _SRC2, "-o", tmp, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
         return _LIB
@@ -92,6 +122,14 @@ def _load():
         lib.orc_onestep_levels.argtypes = [P(_Problem), P(d), P(d), P(_Result),
                                            ctypes.c_int]
         lib.orc_max_threads.restype = ctypes.c_int
+        lib.orc2_derivatives.argtypes = [ctypes.c_longlong, ctypes.c_longlong, P(d), P(d),
+                                         P(d), P(d)]
+        lib.orc2_interp.argtypes = [P(_Problem2), P(d), P(d), P(d), P(d), d, d]
+        lib.orc2_interp.restype = d
+        lib.orc2_exact.argtypes = [P(_Problem2), d, d, d, P(d), P(d)]
+        lib.orc2_init_levels.argtypes = [P(_Problem2), P(d), P(d), P(d)]
+        lib.orc2_solve.argtypes = [P(_Problem2), P(d), P(d), P(d), ctypes.c_longlong,
+                                   P(d), P(d), P(d), P(_Result2), ctypes.c_int]
         _lib = lib
     return _lib
 
@@ -266,3 +304,89 @@ def solve(p: dict, init_y=None, init_z=None, levels: int = 0, threads: int = 1,
 
 def max_threads() -> int:
     return int(_load().orc_max_threads())
+
+
+# --- two space dimensions (oracle2d.c) --------------------------------------
+
+def _problem2(p: dict) -> _Problem2:
+    s = _Problem2()
+    s.driver = DRIVERS2[p["driver"]]
+    s.terminal = TERMINALS2[p["terminal"]]
+    s.picard_max = int(p.get("picard_max", 30))
+    for f in ("T", "x1_min", "x1_max", "x2_min", "x2_max", "x01", "x02", "a1", "a2",
+              "b11", "b21", "b22", "alpha", "beta1", "beta2"):
+        setattr(s, f, float(p[f]))
+    s.picard_tol = float(p.get("picard_tol", 1e-12))
+    s.Nx1, s.Nx2 = int(p["Nx1"]), int(p["Nx2"])
+    s.N, s.k, s.L = int(p["N"]), int(p["k"]), int(p["L"])
+    return s
+
+
+def derivatives2(v: np.ndarray):
+    """Scaled fourth-order finite-difference derivatives (fx, fy, fxy) of a
+    field v of shape (Nx2, Nx1) (x1 fastest)."""
+    lib = _load()
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    fx, fy, fxy = np.zeros_like(v), np.zeros_like(v), np.zeros_like(v)
+    if lib.orc2_derivatives(v.shape[1], v.shape[0], _dptr(v), _dptr(fx), _dptr(fy),
+                            _dptr(fxy)) != 0:
+        raise ValueError("a line needs at least 5 points")
+    return fx, fy, fxy
+
+
+def interp2(p: dict, v, fx, fy, fxy, X1: float, X2: float) -> float:
+    lib = _load()
+    s = _problem2(p)
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (v, fx, fy, fxy)]
+    return lib.orc2_interp(ctypes.byref(s), *[_dptr(a) for a in arrs], float(X1), float(X2))
+
+
+def exact2(p: dict, t: float, x1: float, x2: float):
+    lib = _load()
+    s = _problem2(p)
+    u = ctypes.c_double()
+    z = (ctypes.c_double * 2)()
+    if lib.orc2_exact(ctypes.byref(s), t, x1, x2, ctypes.byref(u), z) != 0:
+        raise ValueError("no closed form")
+    return u.value, (z[0], z[1])
+
+
+def init_levels2(p: dict):
+    lib = _load()
+    s = _problem2(p)
+    shape = (s.k, s.Nx2, s.Nx1)
+    iy, iz1, iz2 = np.zeros(shape), np.zeros(shape), np.zeros(shape)
+    if lib.orc2_init_levels(ctypes.byref(s), _dptr(iy), _dptr(iz1), _dptr(iz2)) != 0:
+        raise ValueError("no closed form")
+    return iy, iz1, iz2
+
+
+def solve2(p: dict, init=None, levels: int = 0, threads: int = 1,
+           want_level: bool = False) -> dict:
+    """The two-dimensional backward loop.  init: None (closed form) or
+    (y, z1, z2), each (k, Nx2, Nx1).  Returns y0, z0 = (z1, z2) at (x01, x02)
+    and, if asked, the last level's fields of shape (Nx2, Nx1)."""
+    lib = _load()
+    s = _problem2(p)
+    res = _Result2()
+    ptrs = [None, None, None]
+    keep = []
+    if init is not None:
+        for q, a in enumerate(init):
+            a = np.ascontiguousarray(a, dtype=np.float64)
+            if a.shape != (s.k, s.Nx2, s.Nx1):
+                raise ValueError("initial levels must have shape (k, Nx2, Nx1)")
+            keep.append(a)
+            ptrs[q] = _dptr(a)
+    outs = [np.zeros((s.Nx2, s.Nx1)) for _ in range(3)] if want_level else [None] * 3
+    rc = lib.orc2_solve(ctypes.byref(s), ptrs[0], ptrs[1], ptrs[2], int(levels),
+                        *[(_dptr(o) if o is not None else None) for o in outs],
+                        ctypes.byref(res), int(threads))
+    if rc != 0:
+        raise ValueError(f"oracle rejected the problem (rc={rc})")
+    out = {"y0": res.y0, "z0": (res.z0[0], res.z0[1]), "status": res.status,
+           "picard_iters_max": res.picard_iters_max,
+           "picard_resid_max": res.picard_resid_max, "levels_done": res.levels_done}
+    if want_level:
+        out["y"], out["z1"], out["z2"] = outs
+    return out

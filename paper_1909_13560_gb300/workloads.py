@@ -183,3 +183,39 @@ def initial_levels(p: dict):
                     u, ux = a - K * math.exp(-r * tau) * ndtr(d1 - sq), a
         ys[m], zs[m] = u, p["b_x"] * ux
     return ys, zs
+
+
+# --- two space dimensions (Section 5, Examples 4 and 5) ----------------------
+
+def ex4_problem(M: int = 128, N: int = 8, k: int = 3, L: int = 8, x_lim: float = 8.0) -> dict:
+    """Example 4 (Eq. 34-35): f = y - z A, A = (1/2, 1/2)^T, g = sin(x1 + x2 + T),
+    X = W in two dimensions, x in [-x_lim, x_lim]^2 with M intervals per
+    dimension; exact (y_0, z_0) = (0, (1, 1))."""
+    return dict(driver="LINEAR", terminal="SIN_SUM", T=1.0,
+                x1_min=-x_lim, x1_max=x_lim, x2_min=-x_lim, x2_max=x_lim, x01=0.0, x02=0.0,
+                a1=0.0, a2=0.0, b11=1.0, b21=0.0, b22=1.0,
+                alpha=1.0, beta1=-0.5, beta2=-0.5,
+                Nx1=M + 1, Nx2=M + 1, N=N, k=k, L=L, picard_max=30, picard_tol=1e-12)
+
+
+def ex5_problem(M: int = 128, N: int = 8, k: int = 3, L: int = 8, width: float = 8.0,
+                S0=(100.0, 100.0), sigma=(0.25, 0.3), rho: float = 0.0, r: float = 0.05,
+                mu=(0.1, 0.1), T: float = 1.0) -> dict:
+    """Example 5 (Eq. 36-37): zero-strike spread option (S1 - S2)^+ in log
+    prices x = ln S, dX = (mu - sigma^2/2) dt + A dW with A the Cholesky factor
+    [[s1, 0], [rho s2, s2 sqrt(1 - rho^2)]], f = -(r y + z A^{-1} M^T),
+    M = mu - r; x in ln S0 +- width with M intervals per dimension.  T = 1:
+    the paper's printed solution (15.48076, (14.4350, -12.6779)) is the
+    Margrabe value at T = 1, which its text states as 0.1."""
+    s1, s2 = sigma
+    b11, b21, b22 = s1, rho * s2, s2 * math.sqrt(1.0 - rho * rho)
+    m1, m2 = mu[0] - r, mu[1] - r
+    # theta = A^{-1} M^T (A lower triangular)
+    th1 = m1 / b11
+    th2 = (m2 - b21 * th1) / b22
+    c1, c2 = math.log(S0[0]), math.log(S0[1])
+    return dict(driver="LINEAR", terminal="SPREAD_LOG", T=T,
+                x1_min=c1 - width, x1_max=c1 + width, x2_min=c2 - width, x2_max=c2 + width,
+                x01=c1, x02=c2, a1=mu[0] - 0.5 * s1 * s1, a2=mu[1] - 0.5 * s2 * s2,
+                b11=b11, b21=b21, b22=b22, alpha=-r, beta1=-th1, beta2=-th2,
+                Nx1=M + 1, Nx2=M + 1, N=N, k=k, L=L, picard_max=30, picard_tol=1e-12)
