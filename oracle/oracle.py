@@ -330,7 +330,7 @@ def derivatives2(v: np.ndarray):
     fx, fy, fxy = np.zeros_like(v), np.zeros_like(v), np.zeros_like(v)
     if lib.orc2_derivatives(v.shape[1], v.shape[0], _dptr(v), _dptr(fx), _dptr(fy),
                             _dptr(fxy)) != 0:
-        raise ValueError("a line needs at least 5 points")
+        raise ValueError("a line needs at least 6 points")
     return fx, fy, fxy
 
 

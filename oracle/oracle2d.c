@@ -62,7 +62,7 @@ static const double ORC2_PI = 3.14159265358979323846;
 
 static int orc2_check(const orc2_problem *p) {
   if (p->k < 1 || p->k > 6 || p->k > p->N) return -1;
-  if (p->Nx1 < 5 || p->Nx2 < 5 || p->L < 1 || p->L > 64) return -1;
+  if (p->Nx1 < 6 || p->Nx2 < 6 || p->L < 1 || p->L > 64) return -1;
   if (!(p->x1_max > p->x1_min) || !(p->x2_max > p->x2_min) || !(p->T > 0.0)) return -1;
   if (p->driver != ORC2_DRV_LINEAR) return -1;
   if (p->terminal < 0 || p->terminal > 1) return -1;
@@ -70,7 +70,7 @@ static int orc2_check(const orc2_problem *p) {
 }
 
 /* ---- fourth-order finite differences along one line ---------------------- */
-/* d[i] ~ h f'(x_i) (scaled by the spacing) for a line of n >= 5 values with
+/* d[i] ~ h f'(x_i) (scaled by the spacing) for a line of n >= 6 values with
  * stride s: central (f_{i-2} - 8 f_{i-1} + 8 f_{i+1} - f_{i+2}) / 12 where
  * it fits, forward (-25 f_i + 48 f_{i+1} - 36 f_{i+2} + 16 f_{i+3} - 3 f_{i+4}) / 12
  * at i = 0, 1 and its mirror image (backward) at i = n-2, n-1. */
@@ -94,7 +94,7 @@ static void orc2_fd_line(long long n, const double *f, long long s, double *d, l
  * fy = dx2 dv/dx2, fxy = dx1 dx2 d2v/dx1dx2 (x1 operator applied to fy). */
 int orc2_derivatives(long long n1, long long n2, const double *v, double *fx, double *fy,
                      double *fxy) {
-  if (n1 < 5 || n2 < 5) return -1;
+  if (n1 < 6 || n2 < 6) return -1;
   for (long long i2 = 0; i2 < n2; ++i2) orc2_fd_line(n1, v + i2 * n1, 1, fx + i2 * n1, 1);
   for (long long i1 = 0; i1 < n1; ++i1) orc2_fd_line(n2, v + i1, n1, fy + i1, n1);
   for (long long i2 = 0; i2 < n2; ++i2) orc2_fd_line(n1, fy + i2 * n1, 1, fxy + i2 * n1, 1);

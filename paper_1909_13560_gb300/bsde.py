@@ -51,6 +51,35 @@ class bsde_problem(ctypes.Structure):
     ]
 
 
+class bsde2_problem(ctypes.Structure):
+    _fields_ = [
+        ("driver", ctypes.c_int32), ("terminal", ctypes.c_int32),
+        ("precision", ctypes.c_int32), ("picard_max", ctypes.c_int32),
+        ("N", ctypes.c_int32), ("k", ctypes.c_int32), ("L", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("Nx1", ctypes.c_int64), ("Nx2", ctypes.c_int64),
+        ("T", ctypes.c_double), ("x1_min", ctypes.c_double), ("x1_max", ctypes.c_double),
+        ("x2_min", ctypes.c_double), ("x2_max", ctypes.c_double),
+        ("x01", ctypes.c_double), ("x02", ctypes.c_double),
+        ("a1", ctypes.c_double), ("a2", ctypes.c_double), ("b11", ctypes.c_double),
+        ("b21", ctypes.c_double), ("b22", ctypes.c_double),
+        ("alpha", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
+        ("picard_tol", ctypes.c_double),
+    ]
+
+
+class bsde2_result(ctypes.Structure):
+    _fields_ = [
+        ("y0", ctypes.c_double), ("z0", ctypes.c_double * 2),
+        ("picard_resid_max", ctypes.c_double), ("status", ctypes.c_int32),
+        ("picard_iters_max", ctypes.c_int32), ("levels_done", ctypes.c_int64),
+    ]
+
+
+BSDE2_DRIVER = {"LINEAR": 0}
+BSDE2_TERMINAL = {"SIN_SUM": 0, "SPREAD_LOG": 1}
+
+
 class bsde_batch_config(ctypes.Structure):
     _fields_ = [("cluster", ctypes.c_int32), ("target_groups", ctypes.c_int32),
                 ("reserved", ctypes.c_int32 * 6)]
@@ -73,7 +102,9 @@ _SYMBOLS = ("bsde_workspace_bytes", "bsde_plan", "bsde_solve", "bsde_result_fetc
             "bsde_batch_get_config", "bsde_batch_autotune", "bsde_solve_batch", "bsde_batch_free",
             "bsde_request_bytes", "bsde_server_workspace_bytes", "bsde_server_create",
             "bsde_server_start", "bsde_server_submit", "bsde_server_poll", "bsde_server_stop",
-            "bsde_server_free", "bsde_l2_read_probe")
+            "bsde_server_free", "bsde_l2_read_probe",
+            "bsde2_workspace_bytes", "bsde2_plan", "bsde2_solve", "bsde2_result_fetch",
+            "bsde2_enqueue_level", "bsde2_plan_launches", "bsde2_free")
 
 
 def load(path: str = LIB_PATH):
@@ -124,6 +155,16 @@ def load(path: str = LIB_PATH):
     lib.bsde_server_free.argtypes = [vp]
     lib.bsde_server_free.restype = None
     lib.bsde_l2_read_probe.argtypes = [vp, ctypes.c_size_t, ctypes.c_int, ctypes.c_int, vp, vp]
+    lib.bsde2_workspace_bytes.argtypes = [P(bsde2_problem), P(ctypes.c_size_t)]
+    lib.bsde2_plan.argtypes = [P(bsde2_problem), vp, ctypes.c_size_t, P(vp)]
+    lib.bsde2_solve.argtypes = [vp, vp, vp, vp, vp, ctypes.c_int, vp, vp, vp, ctypes.c_int,
+                                P(bsde2_result)]
+    lib.bsde2_result_fetch.argtypes = [vp, vp, P(bsde2_result)]
+    lib.bsde2_enqueue_level.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int]
+    lib.bsde2_plan_launches.argtypes = [vp]
+    lib.bsde2_plan_launches.restype = ctypes.c_int64
+    lib.bsde2_free.argtypes = [vp]
+    lib.bsde2_free.restype = None
     _lib = lib
     return lib
 
@@ -520,3 +561,123 @@ def l2_read_bandwidth(mib: int = 48, reps: int = 40, device=None) -> float:
     e1.record(stream)
     torch.cuda.synchronize(dev)
     return buf.numel() * 4 * reps / (e0.elapsed_time(e1) / 1e3) / 1e9
+
+
+# --- two space dimensions (include/bsde2d.h) ---------------------------------
+
+def make_problem2(p: dict) -> bsde2_problem:
+    s = bsde2_problem()
+    s.driver = BSDE2_DRIVER[p["driver"]]
+    s.terminal = BSDE2_TERMINAL[p["terminal"]]
+    s.precision = BSDE_PRECISION["fp64"]
+    s.picard_max = int(p.get("picard_max", 30))
+    s.N, s.k, s.L = int(p["N"]), int(p["k"]), int(p["L"])
+    s.Nx1, s.Nx2 = int(p["Nx1"]), int(p["Nx2"])
+    for f in ("T", "x1_min", "x1_max", "x2_min", "x2_max", "x01", "x02", "a1", "a2",
+              "b11", "b21", "b22", "alpha", "beta1", "beta2"):
+        setattr(s, f, float(p[f]))
+    s.picard_tol = float(p.get("picard_tol", 1e-12))
+    return s
+
+
+def bsde2_workspace_bytes(prob: bsde2_problem) -> int:
+    n = ctypes.c_size_t()
+    _check(load().bsde2_workspace_bytes(ctypes.byref(prob), ctypes.byref(n)),
+           "bsde2_workspace_bytes")
+    return int(n.value)
+
+
+class Solver2:
+    """One two-dimensional problem, one device workspace, one plan."""
+
+    def __init__(self, problem: dict, device=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("the BSDE solver needs a CUDA device (no CPU fallback)")
+        self.problem = dict(problem)
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self._prob = make_problem2(problem)
+        self.ws_bytes = bsde2_workspace_bytes(self._prob)
+        with torch.cuda.device(self.device):
+            self.workspace = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=self.device)
+            self._base = (self.workspace.data_ptr() + 255) // 256 * 256
+            h = ctypes.c_void_p()
+            _check(load().bsde2_plan(ctypes.byref(self._prob), ctypes.c_void_p(self._base),
+                                     self.ws_bytes, ctypes.byref(h)), "bsde2_plan")
+            self.plan = h.value
+
+    @property
+    def launches(self) -> int:
+        return int(load().bsde2_plan_launches(ctypes.c_void_p(self.plan)))
+
+    def enqueue(self, stream: int) -> None:
+        """Enqueue one solve from the closed-form start; no wait, no result."""
+        _check(load().bsde2_solve(ctypes.c_void_p(self.plan), ctypes.c_void_p(stream),
+                                  None, None, None, 0, None, None, None, 0, None),
+               "bsde2_solve")
+
+    def fetch(self, stream: int) -> dict:
+        r = bsde2_result()
+        rc = load().bsde2_result_fetch(ctypes.c_void_p(self.plan), ctypes.c_void_p(stream),
+                                       ctypes.byref(r))
+        if rc < 0:
+            _check(rc, "bsde2_result_fetch")
+        return self._dict(r)
+
+    @staticmethod
+    def _dict(r) -> dict:
+        return {"y0": r.y0, "z0": (r.z0[0], r.z0[1]), "status": r.status,
+                "picard_iters_max": r.picard_iters_max,
+                "picard_resid_max": r.picard_resid_max, "levels_done": r.levels_done}
+
+    def enqueue_level(self, stream: int, n: int, parts: int = 1) -> None:
+        _check(load().bsde2_enqueue_level(ctypes.c_void_p(self.plan), ctypes.c_void_p(stream),
+                                          int(n), int(parts)), "bsde2_enqueue_level")
+
+    def solve(self, init=None, want_level: bool = False, stream=None) -> dict:
+        """init: None (closed-form start) or (y, z1, z2), each (k, Nx2, Nx1)
+        float64 host arrays (row m = level N - m, x1 fastest)."""
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        p = self.problem
+        shape = (int(p["Nx2"]), int(p["Nx1"]))
+        ins = [None, None, None]
+        keep = []
+        if init is not None:
+            for q, a in enumerate(init):
+                a = np.ascontiguousarray(a, dtype=np.float64)
+                keep.append(a)
+                ins[q] = ctypes.c_void_p(a.ctypes.data)
+        outs = [np.zeros(shape) for _ in range(3)] if want_level else None
+        r = bsde2_result()
+        rc = load().bsde2_solve(ctypes.c_void_p(self.plan), ctypes.c_void_p(stream.cuda_stream),
+                                *ins, 1 if init is not None else 0,
+                                *([ctypes.c_void_p(o.ctypes.data) for o in outs] if outs
+                                  else [None, None, None]),
+                                1, ctypes.byref(r))
+        if rc < 0:
+            _check(rc, "bsde2_solve")
+        out = self._dict(r)
+        if want_level:
+            out["y"], out["z1"], out["z2"] = outs
+        return out
+
+    def close(self) -> None:
+        if getattr(self, "plan", None):
+            load().bsde2_free(ctypes.c_void_p(self.plan))
+            self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve2(problem: dict, init=None, want_level: bool = False) -> dict:
+    s = Solver2(problem)
+    try:
+        return s.solve(init=init, want_level=want_level)
+    finally:
+        s.close()

@@ -9,7 +9,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libbsde.so")
 SOURCES = ["bsde_cuda.cu", "bsde_host.cpp"]
-HEADERS = ["bsde_internal.h", "bsde_kernels.cuh", "bsde_batch.cuh", "bsde_server.cuh"]
+HEADERS = ["bsde_internal.h", "bsde_kernels.cuh", "bsde_batch.cuh", "bsde_server.cuh",
+           "bsde2d.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -26,6 +27,7 @@ def _stale() -> bool:
     t = os.path.getmtime(LIB)
     deps = [os.path.join(CSRC, f) for f in SOURCES + HEADERS]
     deps.append(os.path.join(HERE, "..", "include", "bsde.h"))
+    deps.append(os.path.join(HERE, "..", "include", "bsde2d.h"))
     deps.append(os.path.abspath(__file__))
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 

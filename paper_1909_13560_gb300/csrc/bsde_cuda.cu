@@ -1148,3 +1148,8 @@ void bsde_server_free(bsde_server_t *s) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Two space dimensions (include/bsde2d.h)
+// ---------------------------------------------------------------------------
+#include "bsde2d.cuh"

@@ -87,7 +87,9 @@ __device__ void closed_form(const Params &P, double t, double x, bool smooth_lev
         r = P.r - P.lb_sign * (P.R - P.r);
         dl = 0.0;
       }
-      const double S = exp(x), tau = P.T - t;
+      // rounded separately (no contraction with the caller's t = n dt): at
+      // the terminal level tau is exactly 0 and the payoff branch is taken
+      const double S = exp(x), tau = __dsub_rn(P.T, t);
       if (tau <= 0.0) {
         u = S > K ? S - K : 0.0;
         ux = S > K ? S : 0.0;
@@ -181,7 +183,7 @@ __device__ __forceinline__ void init_point(const Params &P, Ring64 r64, Ring32 r
                                            int64_t i) {
   const int level = P.N - m;
   const int64_t off = int64_t(level % P.nslot) * P.Nx;
-  const double t = level * P.dt;
+  const double t = __dmul_rn(double(level), P.dt);
   const bool smooth = (m == 0) && P.smoothing && P.terminal == BSDE_TERMINAL_CALL_LOG;
   const double x = P.x_min + double(i) * P.dx;
   double u, z;

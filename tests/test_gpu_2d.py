@@ -1,0 +1,126 @@
+"""Parity of the two-dimensional CUDA path (include/bsde2d.h, through the C
+ABI) with the 2-D FP64 oracle, and the paper's Table 9 at full size.
+
+Tolerance: FP64, |GPU - oracle| <= 1e-12 max(1, max |level value|) (only the
+summation order, the grouping of the bicubic sums and FMA contraction
+differ).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1909_13560_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+THREADS = max(1, os.cpu_count() or 1)
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1909_13560_gb300 import bsde
+    bsde.load()
+    return bsde
+
+
+def _cmp(got, ref, what, tol=TOL):
+    msgs = []
+    for f in ("y", "z1", "z2"):
+        scale = max(1.0, float(np.max(np.abs(ref[f]))))
+        e = float(np.max(np.abs(got[f] - ref[f])))
+        msgs.append(f"max|d{f}|={e:.3e}")
+        assert e <= tol * scale, (what, f, e)
+    e0 = max(abs(got["y0"] - ref["y0"]), abs(got["z0"][0] - ref["z0"][0]),
+             abs(got["z0"][1] - ref["z0"][1]))
+    print(f"{what}: {' '.join(msgs)} |d(y0,z0)|={e0:.3e}")
+    scale0 = max(1.0, abs(ref["y0"]), abs(ref["z0"][0]), abs(ref["z0"][1]))
+    assert e0 <= tol * scale0
+    assert got["levels_done"] == ref["levels_done"]
+    assert got["picard_iters_max"] <= ref["picard_iters_max"] + 2
+
+
+def _with(p, **kw):
+    q = dict(p)
+    q.update(kw)
+    return q
+
+
+CASES = {
+    "ex4_k1": W.ex4_problem(M=64, N=8, k=1),
+    "ex4_k3": W.ex4_problem(M=96, N=8, k=3),
+    "ex4_k6": W.ex4_problem(M=80, N=8, k=6),
+    "ex5_k2": W.ex5_problem(M=72, N=8, k=2, width=2.0),
+    "ex5_corr_k3": W.ex5_problem(M=60, N=6, k=3, width=2.0, rho=0.5),
+    "ragged_L5": _with(W.ex4_problem(M=50, N=6, k=2, L=5), Nx1=77, Nx2=45, x1_max=6.0),
+    "drift_L3": _with(W.ex4_problem(M=40, N=10, k=4, L=3, x_lim=3.0), a1=0.3, a2=-0.2,
+                      b11=0.8, b21=0.3, b22=0.6),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_2d_parity(B, name):
+    p = CASES[name]
+    ref = O.solve2(p, threads=THREADS, want_level=True)
+    got = B.solve2(p, want_level=True)
+    _cmp(got, ref, name)
+
+
+def test_2d_imported_levels_and_polynomial_exactness(B):
+    """Caller levels through host memory: a quadratic terminal with f = 0 and
+    a correlated forward process, exact to rounding inside the box (as in the
+    oracle's pin), and equal to the oracle everywhere."""
+    a1, a2, b11, b21, b22 = 0.2, -0.3, 0.7, 0.25, 0.5
+    p = _with(W.ex4_problem(M=64, N=8, k=3), alpha=0.0, beta1=0.0, beta2=0.0, a1=a1, a2=a2,
+              b11=b11, b21=b21, b22=b22)
+    x1 = np.linspace(p["x1_min"], p["x1_max"], p["Nx1"])
+    X1, X2 = np.meshgrid(x1, np.linspace(p["x2_min"], p["x2_max"], p["Nx2"]))
+    dt = p["T"] / p["N"]
+    c11, c12, c22 = b11 * b11, b11 * b21, b21 * b21 + b22 * b22
+
+    def u(tau):
+        m1, m2 = X1 + a1 * tau, X2 + a2 * tau
+        return m1 ** 2 + m1 * m2 - 2 * m2 ** 2 + tau * (c11 + c12 - 2 * c22)
+
+    def z(tau):
+        m1, m2 = X1 + a1 * tau, X2 + a2 * tau
+        u1, u2 = 2 * m1 + m2, m1 - 4 * m2
+        return u1 * b11 + u2 * b21, u2 * b22
+
+    init = (np.array([u(m * dt) for m in range(3)]),
+            np.array([z(m * dt)[0] for m in range(3)]),
+            np.array([z(m * dt)[1] for m in range(3)]))
+    ref = O.solve2(p, init=init, threads=THREADS, want_level=True)
+    got = B.Solver2(p).solve(init=init, want_level=True)
+    _cmp(got, ref, "imported quadratic", tol=1e-11)
+    inner = (np.abs(X1) < 3) & (np.abs(X2) < 3)
+    assert np.max(np.abs(got["y"] - u(p["T"]))[inner]) < 1e-10
+
+
+def test_2d_repeat_solves_are_bitwise_identical(B):
+    s = B.Solver2(W.ex4_problem(M=48, N=8, k=3))
+    a = s.solve(want_level=True)
+    b = s.solve(want_level=True)
+    assert np.array_equal(a["y"], b["y"]) and np.array_equal(a["z1"], b["z1"])
+    assert s.launches == 1 + 2 * 3 + 2 * (8 - 3 + 1) + 2
+    s.close()
+
+
+@pytest.mark.parametrize("K,N,M,ye,ze", [(6, 64, 1024, 8.00e-07, 2.32e-06),
+                                         (3, 32, 512, 9.72e-06, 2.79e-05)])
+def test_2d_paper_table9_at_full_size(B, K, N, M, ye, ze):
+    """Example 4 at the paper's largest sizes (Table 9, Section 5): the
+    printed errors of (y_0, z_0) (z as the Euclidean norm of the error
+    vector), three digits."""
+    r = B.solve2(W.ex4_problem(M=M, N=N, k=K))
+    ey = abs(r["y0"])
+    ez = math.hypot(r["z0"][0] - 1.0, r["z0"][1] - 1.0)
+    print(f"Table 9 K={K} N={N} M={M}: y err {ey:.3e} (paper {ye:.2e}), z err {ez:.3e} (paper {ze:.2e})")
+    assert ey == pytest.approx(ye, rel=0.02)
+    assert ez == pytest.approx(ze, rel=0.02)

@@ -158,3 +158,43 @@ def test_batch_and_server_reject_the_startup():
                                        ctypes.byref(n)) == B.BSDE_EINVAL
     # the variants without a start-up are accepted
     B.bsde_batch_workspace_bytes([dict(p, init_mode="EXACT", kz=4, zform=1)])
+
+
+def test_binding_2d_structs_match_header_layout(tmp_path):
+    import subprocess
+    src = tmp_path / "probe2.c"
+    fp = [f for f, _ in B.bsde2_problem._fields_]
+    fr = [f for f, _ in B.bsde2_result._fields_]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "bsde2d.h"', 'int main(void){',
+             'printf("%zu %zu\\n", sizeof(bsde2_problem), sizeof(bsde2_result));']
+    lines += [f'printf("%zu\\n", offsetof(bsde2_problem, {f}));' for f in fp]
+    lines += [f'printf("%zu\\n", offsetof(bsde2_result, {f}));' for f in fr]
+    lines += ['return 0;}']
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "probe2"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    vals = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True,
+                                            text=True).stdout.split()]
+    assert vals[0] == ctypes.sizeof(B.bsde2_problem)
+    assert vals[1] == ctypes.sizeof(B.bsde2_result)
+    for f, o in zip(fp + fr, vals[2:]):
+        cls = B.bsde2_problem if f in fp else B.bsde2_result
+        assert getattr(cls, f).offset == o, f
+
+
+@pytest.mark.parametrize("bad", [dict(k=7), dict(k=9, N=8), dict(Nx1=5), dict(L=0), dict(L=17),
+                                 dict(x01=9.0), dict(T=0.0), dict(picard_max=0)])
+def test_invalid_2d_problems_rejected(bad):
+    p = W.ex4_problem()
+    p.update(bad)
+    with pytest.raises(B.BsdeError) as ei:
+        B.bsde2_workspace_bytes(B.make_problem2(p))
+    assert ei.value.code == B.BSDE_EINVAL
+
+
+def test_2d_workspace_bytes():
+    p = W.ex4_problem(M=1024, N=64, k=6)
+    b = B.bsde2_workspace_bytes(B.make_problem2(p))
+    np_ = 1025 * 1025
+    # ring 7 x 3 x 32 B, new values 24 B, staging 6 x 24 B per point
+    assert 7 * 96 * np_ + 24 * np_ + 6 * 24 * np_ <= b < (7 * 96 + 24 + 6 * 24) * np_ + (1 << 20)

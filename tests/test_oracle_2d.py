@@ -183,7 +183,7 @@ def test_example5_converges_to_margrabe():
 
 
 def test_invalid_2d_problems_rejected():
-    for bad in (dict(k=7), dict(k=9, N=8), dict(Nx1=4), dict(L=0), dict(driver="X")):
+    for bad in (dict(k=7), dict(k=9, N=8), dict(Nx1=5), dict(L=0), dict(driver="X")):
         p = W.ex4_problem()
         p.update(bad)
         with pytest.raises((ValueError, KeyError)):
