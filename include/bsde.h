@@ -55,19 +55,40 @@ enum {
   BSDE_DRIVER_LB = 2,      /* f = -(r y + (mu - r) z / sigma)
                               + lb_sign (R - r) min(y - z/sigma, 0): borrowing rate */
   BSDE_DRIVER_EX1 = 3,     /* f = -y^3 + 5/2 y^2 - 3/2 y                (Eq. 22)     */
-  BSDE_DRIVER_EX2 = 4      /* f = (e^{t^2} - 4ty - 3e^{t^2 - y e^{-t^2}}
+  BSDE_DRIVER_EX2 = 4,     /* f = (e^{t^2} - 4ty - 3e^{t^2 - y e^{-t^2}}
                               + z^2 e^{-t^2}) / 2                       (Eq. 24)     */
+  BSDE_DRIVER_SHORT_RATE = 5 /* f = -x y: discounting at the short rate x, the
+                              forward state where f is evaluated (the zero-coupon
+                              bond; FP64, general forward path only)               */
+};
+
+/* forward process: a(x) dt + b(x) dW, advanced from the grid point by one
+ * Euler step over j dt (the general Markovian X of Section 1) */
+enum {
+  BSDE_FORWARD_CONST = 0, /* a = a_x, b = b_x (exact; the constant-shift kernels)  */
+  BSDE_FORWARD_AFFINE = 1 /* a = a_x + a_1 x, b = b_x + b_1 x (FP64; the node
+                             positions are computed per point).  With an
+                             x-dependent a or b only z_form = EYDW with k_z = 1
+                             is consistent: Eq. 20's E[z^{n+1}] relies on the
+                             identity E[y DeltaW] = dt E[z] of constant
+                             coefficients, and its z misses the drift's slope   */
 };
 
 /* terminal ids: g and, for the closed-form start, the exact solution u(t, x)
- * with z = b_x u_x */
+ * with z = b(x) u_x */
 enum {
   BSDE_TERMINAL_SIN = 0,      /* g = sin(x + T); u = sin(x + t)             (Eq. 35) */
   BSDE_TERMINAL_CALL_LOG = 1, /* g = (e^x - strike)^+, x = ln S; u = Black-Scholes
                                  call with dividend yield delta (Eq. 31; for LB
                                  the rate r - lb_sign (R - r), no dividend)          */
   BSDE_TERMINAL_LOGISTIC = 2, /* g = e^{x+T}/(e^{x+T}+1)                    (Eq. 23) */
-  BSDE_TERMINAL_LNSIN = 3     /* g = ln(sin x + 3) e^{T^2}                  (Eq. 25) */
+  BSDE_TERMINAL_LNSIN = 3,    /* g = ln(sin x + 3) e^{T^2}                  (Eq. 25) */
+  BSDE_TERMINAL_ONE = 4,      /* g = 1; u = the Vasicek bond price A e^{-B x} for
+                                 SHORT_RATE with AFFINE a_1 < 0, b_1 = 0
+                                 (kappa = -a_1, theta = a_x / kappa, sigma = b_x)   */
+  BSDE_TERMINAL_CALL_PRICE = 5 /* g = (x - strike)^+ in the price x = S; u =
+                                 Black-Scholes with volatility b_1 for AFFINE
+                                 a_x = b_x = 0 (geometric Brownian motion)          */
 };
 
 /* arithmetic of the bulk (interpolation, driver at the nodes, quadrature) */
@@ -106,7 +127,10 @@ enum {
   BSDE_EINVAL = -1,     /* bad problem: k or k_z outside 1..6, max(k, k_z) > N,
                            Nx < 4, L outside 1..64, x0 outside [x_min, x_max],
                            unknown id or mode, T <= 0, init_substeps < 1 or
-                           N init_substeps > 2^30 with ONESTEP                    */
+                           N init_substeps > 2^30 with ONESTEP, the general
+                           forward path (AFFINE, SHORT_RATE, ONE, CALL_PRICE)
+                           outside FP64 or a terminal whose closed form needs
+                           a forward process the problem does not have         */
   BSDE_ENOSPC = -2,     /* workspace smaller than bsde_workspace_bytes()          */
   BSDE_ECUDA = -3,      /* a CUDA call failed (detail in bsde_last_error())       */
   BSDE_ENOMEM = -4,     /* host allocation failed                                 */
@@ -136,6 +160,9 @@ typedef struct bsde_problem {
   int32_t z_form;     /* BSDE_ZFORM_*                                          */
   int32_t init_mode;  /* BSDE_INIT_*                                           */
   int32_t init_substeps; /* ONESTEP: 1-step scheme steps per dt, >= 1          */
+  int32_t forward;    /* BSDE_FORWARD_*                                        */
+  int32_t reserved;   /* 0                                                     */
+  double a_1, b_1;    /* AFFINE: slopes of a(x) and b(x)                       */
 } bsde_problem;
 
 typedef struct bsde_result {

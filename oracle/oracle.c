@@ -55,9 +55,10 @@
 
 /* ---- problem description (layout mirrored by oracle/oracle.py) ---------- */
 enum { ORC_DRV_LIN_SIN = 0, ORC_DRV_BS = 1, ORC_DRV_LB = 2, ORC_DRV_EX1 = 3,
-       ORC_DRV_EX2 = 4 };
+       ORC_DRV_EX2 = 4, ORC_DRV_SHORT_RATE = 5 };
 enum { ORC_TERM_SIN = 0, ORC_TERM_CALL_LOG = 1, ORC_TERM_LOGISTIC = 2,
-       ORC_TERM_LNSIN = 3 };
+       ORC_TERM_LNSIN = 3, ORC_TERM_ONE = 4, ORC_TERM_CALL_PRICE = 5 };
+enum { ORC_FWD_CONST = 0, ORC_FWD_AFFINE = 1 };
 
 typedef struct {
   int driver, terminal, smoothing, picard_max;
@@ -71,6 +72,9 @@ typedef struct {
   int zform;          /* 0: E[z^{n+1}] in the z line (Eq. 20); 1: E[y DW]/dt */
   int init_mode;      /* 0: closed-form levels; 1: one-step start-up        */
   int init_substeps;  /* start-up steps per dt (init_mode 1)                */
+  int forward;        /* 0: a_x, b_x constant; 1: a_x + a_1 x, b_x + b_1 x  */
+  int pad_f;
+  double a_1, b_1;
 } orc_problem;
 
 enum { ORC_INIT_EXACT = 0, ORC_INIT_ONESTEP = 1 };
@@ -78,6 +82,15 @@ enum { ORC_INIT_EXACT = 0, ORC_INIT_ONESTEP = 1 };
 static int orc_kz(const orc_problem *p) { return p->kz > 0 ? p->kz : p->k; }
 /* K = max(K_y, K_z): the levels one step reads (Eq. 16) */
 static int orc_K(const orc_problem *p) { return p->k > orc_kz(p) ? p->k : orc_kz(p); }
+
+/* Coefficients of the forward process at x: constant, or affine in x (the
+ * general Markovian X of Section 1, advanced by one Euler step over j dt). */
+static double orc_fwd_a(const orc_problem *p, double x) {
+  return p->forward == ORC_FWD_AFFINE ? p->a_x + p->a_1 * x : p->a_x;
+}
+static double orc_fwd_b(const orc_problem *p, double x) {
+  return p->forward == ORC_FWD_AFFINE ? p->b_x + p->b_1 * x : p->b_x;
+}
 
 typedef struct {
   double y0, z0;
@@ -250,8 +263,10 @@ double orc_interp(long long n, double x_min, double dx, const double *v,
  *          g(x) = sin(x + T) (u_t + u_xx/2 + f = 0 holds exactly);
  * BS:      Eq. 29 with constant r, mu, sigma and dividend yield delta;
  * LB:      Eq. 29 plus the borrowing-rate term lb_sign*(R-r)*min(y - z/sigma, 0);
- * EX1:     Eq. 22;  EX2: Eq. 24. */
-double orc_driver(const orc_problem *p, double t, double y, double z) {
+ * EX1:     Eq. 22;  EX2: Eq. 24;
+ * SHORT_RATE: f = -x y, discounting at the short rate x (the forward
+ *          state at the point where f is evaluated; the zero-coupon bond). */
+double orc_driver(const orc_problem *p, double t, double x, double y, double z) {
   switch (p->driver) {
     case ORC_DRV_LIN_SIN:
       return 0.5 * y - z;
@@ -268,12 +283,14 @@ double orc_driver(const orc_problem *p, double t, double y, double z) {
       double e = exp(t * t);
       return 0.5 * (e - 4.0 * t * y - 3.0 * exp(t * t - y * exp(-t * t)) + z * z * exp(-t * t));
     }
+    case ORC_DRV_SHORT_RATE:
+      return -x * y;
     default:
       return 0.0;
   }
 }
 
-/* ---- closed-form solutions u(t,x) and z = b_x * du/dx ------------------- */
+/* ---- closed-form solutions u(t,x) and z = b(x) du/dx -------------------- */
 static double orc_ncdf(double x) { return 0.5 * erfc(-x / sqrt(2.0)); }
 
 /* Black-Scholes call with dividend yield in log price x = ln S (Eq. 31 with
@@ -314,6 +331,36 @@ int orc_exact(const orc_problem *p, double t, double x, double *u, double *z) {
       ux = e / ((e + 1.0) * (e + 1.0));
       break;
     }
+    case ORC_TERM_ONE: {
+      /* zero-coupon bond under the Vasicek short rate dX = kappa (theta - X)
+       * dt + sigma dW (forward AFFINE with a_1 = -kappa < 0, a_x = kappa
+       * theta, b_1 = 0, sigma = b_x) and f = -x y:
+       * P = exp(ln A - B x), B = (1 - e^{-kappa tau}) / kappa,
+       * ln A = (theta - sigma^2 / (2 kappa^2)) (B - tau) - sigma^2 B^2 / (4 kappa) */
+      double tau = p->T - t;
+      if (tau <= 0.0) { *u = 1.0; ux = 0.0; break; }
+      if (p->forward != ORC_FWD_AFFINE || !(p->a_1 < 0.0) || p->b_1 != 0.0) return -1;
+      double kap = -p->a_1, th = p->a_x / kap, sg = p->b_x;
+      double B = -expm1(-kap * tau) / kap;
+      double lnA = (th - sg * sg / (2.0 * kap * kap)) * (B - tau) - sg * sg * B * B / (4.0 * kap);
+      *u = exp(lnA - B * x);
+      ux = -B * *u;
+      break;
+    }
+    case ORC_TERM_CALL_PRICE: {
+      /* call (x - K)^+ in the price x = S itself, geometric Brownian motion
+       * dX = a_1 X dt + b_1 X dW: Black-Scholes with volatility b_1 and the
+       * driver's rate and dividend yield */
+      double r = p->r, dlt = p->delta, tau = p->T - t, sg = p->b_1, K = p->strike;
+      if (p->driver == ORC_DRV_LB) { r = p->r - p->lb_sign * (p->R - p->r); dlt = 0.0; }
+      if (x <= 0.0) { *u = 0.0; ux = 0.0; break; }
+      if (tau <= 0.0) { *u = x > K ? x - K : 0.0; ux = x > K ? 1.0 : 0.0; break; }
+      double sq = sg * sqrt(tau);
+      double d1 = (log(x / K) + (r - dlt + 0.5 * sg * sg) * tau) / sq, d2 = d1 - sq;
+      *u = x * exp(-dlt * tau) * orc_ncdf(d1) - K * exp(-r * tau) * orc_ncdf(d2);
+      ux = exp(-dlt * tau) * orc_ncdf(d1);
+      break;
+    }
     case ORC_TERM_LNSIN: { /* Eq. 25 */
       double e = exp(t * t);
       *u = log(sin(x) + 3.0) * e;
@@ -323,7 +370,7 @@ int orc_exact(const orc_problem *p, double t, double x, double *u, double *z) {
     default:
       return -1;
   }
-  *z = p->b_x * ux;
+  *z = orc_fwd_b(p, x) * ux;
   return 0;
 }
 
@@ -346,6 +393,18 @@ static void orc_call_cell_average(double x, double dx, double K, double bx,
   }
 }
 
+/* Cell average of the call payoff (s - K)^+ in the price and of b(s) times
+ * its derivative, b(s) = b_x + b_1 s, over [x - dx/2, x + dx/2]. */
+static void orc_call_price_cell_average(const orc_problem *p, double x, double dx,
+                                        double *u, double *z) {
+  double a = x - 0.5 * dx, b = x + 0.5 * dx, K = p->strike;
+  if (b <= K) { *u = 0.0; *z = 0.0; return; }
+  double lo = a > K ? a : K;
+  /* int_lo^b (s - K) ds and int_lo^b (b_x + b_1 s) ds */
+  *u = 0.5 * ((b - K) * (b - K) - (lo - K) * (lo - K)) / dx;
+  *z = (p->b_x * (b - lo) + 0.5 * p->b_1 * (b * b - lo * lo)) / dx;
+}
+
 /* K initial levels: row m (0 <= m < K) holds level N-m (Section 3.1 step 2,
  * read as the closed form at t_{N-m}). */
 int orc_init_levels(const orc_problem *p, double *init_y, double *init_z) {
@@ -357,6 +416,8 @@ int orc_init_levels(const orc_problem *p, double *init_y, double *init_z) {
       double x = p->x_min + (double)i * dx, u, z;
       if (m == 0 && p->smoothing && p->terminal == ORC_TERM_CALL_LOG)
         orc_call_cell_average(x, dx, p->strike, p->b_x, &u, &z);
+      else if (m == 0 && p->smoothing && p->terminal == ORC_TERM_CALL_PRICE)
+        orc_call_price_cell_average(p, x, dx, &u, &z);
       else if (orc_exact(p, t, x, &u, &z) != 0)
         return -1;
       init_y[(size_t)m * p->Nx + i] = u;
@@ -374,7 +435,9 @@ static int orc_check(const orc_problem *p) {
     return -1;
   if (p->Nx < 4 || p->L < 1 || p->L > 128) return -1;
   if (!(p->x_max > p->x_min) || !(p->T > 0.0)) return -1;
-  if (p->driver < 0 || p->driver > 4) return -1;
+  if (p->driver < 0 || p->driver > 5) return -1;
+  if (p->terminal < 0 || p->terminal > 5) return -1;
+  if (p->forward < 0 || p->forward > 1) return -1;
   return 0;
 }
 
@@ -397,10 +460,12 @@ static void orc_point_expectations(const orc_problem *p, int n, long long i,
     double ez = 0.0, ef = 0.0, efw = 0.0, ey = 0.0, eyw = 0.0;
     for (int l = 0; l < p->L; ++l) {
       double dW = sq * gh_a[l];
-      double X = xi + p->a_x * j * dt + p->b_x * dW;
+      /* one Euler step of the forward process over j dt (exact for
+       * constant coefficients) */
+      double X = xi + orc_fwd_a(p, xi) * j * dt + orc_fwd_b(p, xi) * dW;
       double yh = orc_interp(p->Nx, p->x_min, dx, ly[j - 1], lmy[j - 1], X);
       double zh = orc_interp(p->Nx, p->x_min, dx, lz[j - 1], lmz[j - 1], X);
-      double F = orc_driver(p, tj, yh, zh);
+      double F = orc_driver(p, tj, X, yh, zh);
       double w = gh_w[l] * rpi;
       ez += w * zh;
       ef += w * F;
@@ -566,11 +631,12 @@ int orc_solve(const orc_problem *p, const double *init_y, const double *init_z,
       double sf = 0.0;
       for (int j = 1; j <= ky; ++j) sf += gy[j] * e[5 * (j - 1) + 1];
       double A = e[5 * (ky - 1) + 3] + h * sf;
+      const double xi = p->x_min + (double)i * dx;
       double y = yprev[i];
       double d = 0.0;
       int it = 0;
       while (it < p->picard_max) {
-        double yn1 = A + h * gy[0] * orc_driver(p, tn, y, z);
+        double yn1 = A + h * gy[0] * orc_driver(p, tn, xi, y, z);
         d = fabs(yn1 - y);
         y = yn1;
         ++it;

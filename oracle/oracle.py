@@ -25,8 +25,9 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-DRIVERS = {"LIN_SIN": 0, "BS": 1, "LB": 2, "EX1": 3, "EX2": 4}
-TERMINALS = {"SIN": 0, "CALL_LOG": 1, "LOGISTIC": 2, "LNSIN": 3}
+DRIVERS = {"LIN_SIN": 0, "BS": 1, "LB": 2, "EX1": 3, "EX2": 4, "SHORT_RATE": 5}
+TERMINALS = {"SIN": 0, "CALL_LOG": 1, "LOGISTIC": 2, "LNSIN": 3, "ONE": 4, "CALL_PRICE": 5}
+FORWARDS = {"CONST": 0, "AFFINE": 1}
 INIT_MODES = {"EXACT": 0, "ONESTEP": 1}
 
 
@@ -44,6 +45,8 @@ class _Problem(ctypes.Structure):
         ("Nx", ctypes.c_longlong), ("N", ctypes.c_int), ("k", ctypes.c_int),
         ("L", ctypes.c_int), ("kz", ctypes.c_int), ("zform", ctypes.c_int),
         ("init_mode", ctypes.c_int), ("init_substeps", ctypes.c_int),
+        ("forward", ctypes.c_int), ("pad_f", ctypes.c_int),
+        ("a_1", ctypes.c_double), ("b_1", ctypes.c_double),
     ]
 
 
@@ -111,7 +114,7 @@ def _load():
         lib.orc_spline.argtypes = [ctypes.c_longlong, d, P(d), P(d)]
         lib.orc_interp.argtypes = [ctypes.c_longlong, d, d, P(d), P(d), d]
         lib.orc_interp.restype = d
-        lib.orc_driver.argtypes = [P(_Problem), d, d, d]
+        lib.orc_driver.argtypes = [P(_Problem), d, d, d, d]
         lib.orc_driver.restype = d
         lib.orc_exact.argtypes = [P(_Problem), d, d, P(d), P(d)]
         lib.orc_init_levels.argtypes = [P(_Problem), P(d), P(d)]
@@ -161,6 +164,10 @@ def _problem(p: dict) -> _Problem:
     mode = p.get("init_mode", 0)
     s.init_mode = INIT_MODES[mode] if isinstance(mode, str) else int(mode)
     s.init_substeps = int(p.get("init_substeps", 0))
+    fwd = p.get("forward", "CONST")
+    s.forward = FORWARDS[fwd] if isinstance(fwd, str) else int(fwd)
+    s.a_1 = float(p.get("a_1", 0.0))
+    s.b_1 = float(p.get("b_1", 0.0))
     return s
 
 
@@ -204,10 +211,10 @@ def interp(v: np.ndarray, M: np.ndarray, x_min: float, dx: float, X: float) -> f
     return lib.orc_interp(len(v), x_min, dx, _dptr(v), _dptr(M), float(X))
 
 
-def driver(p: dict, t: float, y: float, z: float) -> float:
+def driver(p: dict, t: float, y: float, z: float, x: float = 0.0) -> float:
     lib = _load()
     s = _problem(p)
-    return lib.orc_driver(ctypes.byref(s), t, y, z)
+    return lib.orc_driver(ctypes.byref(s), t, x, y, z)
 
 
 def exact(p: dict, t: float, x: float):

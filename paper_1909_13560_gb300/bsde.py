@@ -16,8 +16,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libbsde.so")
 
-BSDE_DRIVER = {"LIN_SIN": 0, "BS": 1, "LB": 2, "EX1": 3, "EX2": 4}
-BSDE_TERMINAL = {"SIN": 0, "CALL_LOG": 1, "LOGISTIC": 2, "LNSIN": 3}
+BSDE_DRIVER = {"LIN_SIN": 0, "BS": 1, "LB": 2, "EX1": 3, "EX2": 4, "SHORT_RATE": 5}
+BSDE_TERMINAL = {"SIN": 0, "CALL_LOG": 1, "LOGISTIC": 2, "LNSIN": 3, "ONE": 4, "CALL_PRICE": 5}
+BSDE_FORWARD = {"CONST": 0, "AFFINE": 1}
 BSDE_PRECISION = {"fp64": 0, "fp32c": 1}
 BSDE_INIT = {"EXACT": 0, "ONESTEP": 1}
 BSDE_ZFORM = {"EZ": 0, "EYDW": 1}
@@ -48,6 +49,8 @@ class bsde_problem(ctypes.Structure):
         ("strike", ctypes.c_double), ("picard_tol", ctypes.c_double),
         ("k_z", ctypes.c_int32), ("z_form", ctypes.c_int32),
         ("init_mode", ctypes.c_int32), ("init_substeps", ctypes.c_int32),
+        ("forward", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("a_1", ctypes.c_double), ("b_1", ctypes.c_double),
     ]
 
 
@@ -207,6 +210,10 @@ def make_problem(p: dict, precision: str = "fp64") -> bsde_problem:
     mode = p.get("init_mode", 0)
     s.init_mode = BSDE_INIT[mode] if isinstance(mode, str) else int(mode)
     s.init_substeps = int(p.get("init_substeps", 0))
+    fwd = p.get("forward", "CONST")
+    s.forward = BSDE_FORWARD[fwd] if isinstance(fwd, str) else int(fwd)
+    s.a_1 = float(p.get("a_1", 0.0))
+    s.b_1 = float(p.get("b_1", 0.0))
     return s
 
 

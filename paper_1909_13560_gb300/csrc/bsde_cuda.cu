@@ -135,8 +135,13 @@ static void launch_step(bsde_plan_t *pl, const Run &R, cudaStream_t s, int n) {
   Stats *st = reinterpret_cast<Stats *>(pl->ws + pl->lay.stats);
   if (PREC == BSDE_FP64) {
     const size_t sm = sizeof(NodeF64) * kL + sizeof(double) * 2 * P.G * kStepTP;
-    launch_pdl(k_step64<DRV>, blocks, threads, sm, s, P, pl->dc64, R.r64.ring, R.t64, n, st);
-  } else {
+    if (P.general)
+      launch_pdl(k_step64_gen<DRV>, blocks, threads, sm, s, P, pl->dc64, R.r64.ring, R.t64, n,
+                 st);
+    else if constexpr (DRV != BSDE_DRIVER_SHORT_RATE)
+      launch_pdl(k_step64<DRV>, blocks, threads, sm, s, P, pl->dc64, R.r64.ring, R.t64, n, st);
+  } else if constexpr (DRV != BSDE_DRIVER_SHORT_RATE) {
+    // (the general path is FP64 only: validate() rejects it in FP32C)
     const size_t sm = step32_smem(P.G, P.k * P.Lp);
     launch_pdl(k_step32<DRV>, blocks, threads, sm, s, P, pl->dc32, R.r32, R.tp, n, st);
   }
@@ -149,6 +154,7 @@ static void launch_step_any(bsde_plan_t *pl, const Run &R, cudaStream_t s, int n
     case BSDE_DRIVER_BS: launch_step<PREC, BSDE_DRIVER_BS>(pl, R, s, n); break;
     case BSDE_DRIVER_LB: launch_step<PREC, BSDE_DRIVER_LB>(pl, R, s, n); break;
     case BSDE_DRIVER_EX1: launch_step<PREC, BSDE_DRIVER_EX1>(pl, R, s, n); break;
+    case BSDE_DRIVER_SHORT_RATE: launch_step<PREC, BSDE_DRIVER_SHORT_RATE>(pl, R, s, n); break;
     default: launch_step<PREC, BSDE_DRIVER_EX2>(pl, R, s, n); break;
   }
 }

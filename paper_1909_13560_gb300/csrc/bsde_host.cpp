@@ -21,8 +21,21 @@ int validate(const bsde_problem &p) {
   if (p.L < 1 || p.L > kMaxL) return BSDE_EINVAL;
   if (!(p.T > 0.0) || !(p.x_max > p.x_min)) return BSDE_EINVAL;
   if (!(p.x0 >= p.x_min && p.x0 <= p.x_max)) return BSDE_EINVAL;
-  if (p.driver < BSDE_DRIVER_LIN_SIN || p.driver > BSDE_DRIVER_EX2) return BSDE_EINVAL;
-  if (p.terminal < BSDE_TERMINAL_SIN || p.terminal > BSDE_TERMINAL_LNSIN) return BSDE_EINVAL;
+  if (p.driver < BSDE_DRIVER_LIN_SIN || p.driver > BSDE_DRIVER_SHORT_RATE) return BSDE_EINVAL;
+  if (p.terminal < BSDE_TERMINAL_SIN || p.terminal > BSDE_TERMINAL_CALL_PRICE) return BSDE_EINVAL;
+  if (p.forward != BSDE_FORWARD_CONST && p.forward != BSDE_FORWARD_AFFINE) return BSDE_EINVAL;
+  const bool general = problem_general(p) || p.terminal == BSDE_TERMINAL_ONE ||
+                       p.terminal == BSDE_TERMINAL_CALL_PRICE;
+  if (general && p.precision != BSDE_FP64) return BSDE_EINVAL;
+  // terminals whose closed form (initial levels, and the start-up's level N)
+  // needs a particular forward process
+  if (p.terminal == BSDE_TERMINAL_ONE &&
+      !(p.forward == BSDE_FORWARD_AFFINE && p.a_1 < 0.0 && p.b_1 == 0.0))
+    return BSDE_EINVAL;
+  if (p.terminal == BSDE_TERMINAL_CALL_PRICE &&
+      !(p.forward == BSDE_FORWARD_AFFINE && p.a_x == 0.0 && p.b_x == 0.0 && p.b_1 > 0.0 &&
+        p.x_min > 0.0))
+    return BSDE_EINVAL;
   if (p.precision != BSDE_FP64 && p.precision != BSDE_FP32C) return BSDE_EINVAL;
   if (p.picard_max < 1 || !(p.picard_tol >= 0.0)) return BSDE_EINVAL;
   if ((p.driver == BSDE_DRIVER_BS || p.driver == BSDE_DRIVER_LB) && p.sigma == 0.0) return BSDE_EINVAL;
@@ -137,6 +150,9 @@ int fill_params(const bsde_problem &p, Params &P) {
   P.ky = p.k;
   P.kz = problem_kz(p);
   P.zform = p.z_form;
+  P.general = problem_general(p) ? 1 : 0;
+  P.a_1 = p.forward == BSDE_FORWARD_AFFINE ? p.a_1 : 0.0;
+  P.b_1 = p.forward == BSDE_FORWARD_AFFINE ? p.b_1 : 0.0;
   P.L = p.L;
   P.driver = p.driver;
   P.terminal = p.terminal;
@@ -305,6 +321,7 @@ void build_tables(Params &P, NodeF64 *t64, NodeF32 *t32, PairF32 *tp, int target
       e.cfy = P.h * P.gy[j] * wt;
       e.cy = (j == P.ky) ? wt : 0.0;
       e.cyz = (j == 1 && P.zform) ? wt * dW / P.dt * P.inv_gz0 : 0.0;
+      e.dW = dW;
       if (e.shift < smin) smin = e.shift;
       if (e.shift > smax) smax = e.shift;
       const int idx = (j - 1) * P.L + l;

@@ -35,6 +35,7 @@ constexpr int kSplineHead = 16;   // FP32C: pivots of the spline LU are constant
 struct NodeF64 {
   int32_t shift, pad;
   double w0, w1, w2, w3, cz, cfz, cfy, cy, cyz;
+  double dW;  // DeltaW_jl (the general forward path places its nodes per point)
 };
 
 // FP32C entry: the same coefficients, with cz and cy split into float
@@ -75,13 +76,20 @@ inline int problem_kz(const bsde_problem &p) { return p.k_z > 0 ? p.k_z : p.k; }
 inline int problem_K(const bsde_problem &p) {
   return p.k > problem_kz(p) ? p.k : problem_kz(p);
 }
+// The general forward path: node positions per point (affine a, b) or a
+// driver that reads the forward state.
+inline bool problem_general(const bsde_problem &p) {
+  return p.forward == BSDE_FORWARD_AFFINE || p.driver == BSDE_DRIVER_SHORT_RATE;
+}
 
 // Everything a kernel needs to know about one problem.  k is K (levels per
 // step, ring of k + 1 slots); ky, kz the steps of the y and z lines.
 struct Params {
   int64_t Nx;
   int32_t N, k, L, driver, terminal, precision, smoothing, picard_max, nslot;
-  int32_t ky, kz, zform, pad_;
+  int32_t ky, kz, zform, general;  // general: per-point node positions (AFFINE
+                                   // forward or an x-dependent driver), FP64
+  double a_1, b_1;                 // AFFINE slopes of a(x), b(x)
   double T, dt, dx, x_min, x_max, x0, a_x, b_x;
   double r, mu, sigma, R, delta, lb_sign, strike;
   double picard_tol;

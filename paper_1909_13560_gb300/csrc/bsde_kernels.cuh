@@ -106,12 +106,59 @@ __device__ void closed_form(const Params &P, double t, double x, bool smooth_lev
     const double e = exp(x + t);
     u = e / (e + 1.0);
     ux = e / ((e + 1.0) * (e + 1.0));
-  } else {
+  } else if (P.terminal == BSDE_TERMINAL_LNSIN) {
     const double e = exp(t * t);
     u = log(sin(x) + 3.0) * e;
     ux = e * cos(x) / (sin(x) + 3.0);
+  } else if (P.terminal == BSDE_TERMINAL_ONE) {
+    // the Vasicek bond: kappa = -a_1, theta = a_x / kappa, sigma = b_x
+    const double tau = __dsub_rn(P.T, t);
+    if (tau <= 0.0) {
+      u = 1.0;
+      ux = 0.0;
+    } else {
+      const double kap = -P.a_1, th = P.a_x / kap, sg = P.b_x;
+      const double B = -expm1(-kap * tau) / kap;
+      const double lnA = (th - sg * sg / (2.0 * kap * kap)) * (B - tau) - sg * sg * B * B / (4.0 * kap);
+      u = exp(lnA - B * x);
+      ux = -B * u;
+    }
+  } else {
+    // call in the price x = S under geometric Brownian motion (volatility b_1)
+    const double K = P.strike, tau = __dsub_rn(P.T, t), sg = P.b_1;
+    double r = P.r, dl = P.delta;
+    if (P.driver == BSDE_DRIVER_LB) {
+      r = P.r - P.lb_sign * (P.R - P.r);
+      dl = 0.0;
+    }
+    if (smooth_level) {
+      // averages over [x - dx/2, x + dx/2] of (s - K)^+ and of b(s) 1{s > K}
+      const double a = x - 0.5 * P.dx, b = x + 0.5 * P.dx;
+      if (b <= K) {
+        u = 0.0;
+        z = 0.0;
+      } else {
+        const double lo = a > K ? a : K;
+        u = 0.5 * ((b - K) * (b - K) - (lo - K) * (lo - K)) / P.dx;
+        z = (P.b_x * (b - lo) + 0.5 * P.b_1 * (b * b - lo * lo)) / P.dx;
+      }
+      return;
+    }
+    if (x <= 0.0) {
+      u = 0.0;
+      ux = 0.0;
+    } else if (tau <= 0.0) {
+      u = x > K ? x - K : 0.0;
+      ux = x > K ? 1.0 : 0.0;
+    } else {
+      const double sq = sg * sqrt(tau);
+      const double d1 = (log(x / K) + (r - dl + 0.5 * sg * sg) * tau) / sq, d2 = d1 - sq;
+      u = x * exp(-dl * tau) * ncdf(d1) - K * exp(-r * tau) * ncdf(d2);
+      ux = exp(-dl * tau) * ncdf(d1);
+    }
   }
-  z = P.b_x * ux;
+  // z = b(x) u_x (b constant unless the forward process is AFFINE)
+  z = (P.b_x + P.b_1 * x) * ux;
 }
 
 // ---------------------------------------------------------------------------
@@ -184,7 +231,9 @@ __device__ __forceinline__ void init_point(const Params &P, Ring64 r64, Ring32 r
   const int level = P.N - m;
   const int64_t off = int64_t(level % P.nslot) * P.Nx;
   const double t = __dmul_rn(double(level), P.dt);
-  const bool smooth = (m == 0) && P.smoothing && P.terminal == BSDE_TERMINAL_CALL_LOG;
+  const bool smooth = (m == 0) && P.smoothing &&
+                      (P.terminal == BSDE_TERMINAL_CALL_LOG ||
+                       P.terminal == BSDE_TERMINAL_CALL_PRICE);
   const double x = P.x_min + double(i) * P.dx;
   double u, z;
   closed_form(P, t, x, smooth, u, z);
@@ -628,6 +677,109 @@ __global__ void __launch_bounds__(kStepTP * kMaxGroups)
     double y = ring[int64_t((n + 1) % P.nslot) * P.Nx + ii].x;
     while (it < P.picard_max) {
       const double y1 = A + P.hg0 * driver<DRV>(dc, tn, etn, emtn, y, z);
+      d = fabs(y1 - y);
+      y = y1;
+      ++it;
+      if (d <= P.picard_tol) break;
+    }
+    ring[int64_t(n % P.nslot) * P.Nx + ii] = make_double4_32a(y, 0.0, z, 0.0);
+  }
+  record_picard(st, active, it, d, P.picard_tol);
+}
+
+// ---------------------------------------------------------------------------
+// The general forward path (FP64): the forward process is advanced from the
+// grid point by one Euler step, X = x_i + a(x_i) j dt + b(x_i) DeltaW_jl with
+// a, b affine in x, so a node's position, cell and spline weights depend on
+// the point; the driver may read X (SHORT_RATE).  Otherwise as k_step64:
+// same groups, same table weights (cz, cfz, cfy, cy, cyz), same Picard tail.
+// ---------------------------------------------------------------------------
+template <int DRV>
+__device__ __forceinline__ double driver_x(const DrvC<double> &dc, double t, double et,
+                                           double emt, double x, double y, double z) {
+  if constexpr (DRV == BSDE_DRIVER_SHORT_RATE)
+    return -rmul(x, y);
+  else
+    return driver<DRV>(dc, t, et, emt, y, z);
+}
+
+template <int DRV>
+__global__ void __launch_bounds__(kStepTP * kMaxGroups)
+    k_step64_gen(const Params P, const DrvC<double> dc, double4_32a *__restrict__ ring,
+                 const NodeF64 *__restrict__ table, int n, Stats *st) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int kL = P.k * P.L;
+  NodeF64 *tab = reinterpret_cast<NodeF64 *>(smem_raw);
+  double *part = reinterpret_cast<double *>(smem_raw + sizeof(NodeF64) * kL);  // [2][G][TP]
+  for (int t = threadIdx.x; t < kL; t += blockDim.x) tab[t] = table[t];
+  __syncthreads();
+  wait_predecessor();
+
+  const int tp = threadIdx.x % kStepTP, g = threadIdx.x / kStepTP;
+  const int j = g / P.S + 1, lc = g % P.S;
+  const int l0 = lc * P.Lg, l1 = l0 + P.Lg < P.L ? l0 + P.Lg : P.L;
+  const int ii = blockIdx.x * kStepTP + tp;
+  const int last = int(P.Nx - 1);
+  const double xi = P.x_min + double(ii) * P.dx;
+  double Zs = 0.0, Ys = 0.0;
+  if (ii <= last) {
+    const double4_32a *lev = ring + int64_t((n + j) % P.nslot) * P.Nx;
+    const double tj = __dmul_rn(double(n + j), P.dt);
+    const double et = exp(tj * tj), emt = exp(-tj * tj);
+    const NodeF64 *row = tab + (j - 1) * P.L;
+    const bool yj = j == P.ky, zf = P.zform && j == 1;
+    const double ax = P.a_x + P.a_1 * xi, bx = P.b_x + P.b_1 * xi;
+    const double drift = ax * double(j) * P.dt;
+    const double c6 = P.dx * P.dx / 6.0;
+#pragma unroll 2
+    for (int l = l0; l < l1; ++l) {
+      const NodeF64 &e = row[l];
+      const double X = xi + drift + bx * e.dW;
+      const double s = (X - P.x_min) / P.dx;
+      double yh, zh;
+      if (s <= 0.0) {  // off the grid: the end values (Section 3.2)
+        const double4_32a a = lev[0];
+        yh = a.x;
+        zh = a.z;
+      } else if (s >= double(last)) {
+        const double4_32a a = lev[last];
+        yh = a.x;
+        zh = a.z;
+      } else {
+        int c = int(floor(s));
+        c = c > last - 1 ? last - 1 : c;
+        const double th = s - double(c), om = 1.0 - th;
+        const double w2 = c6 * (om * om * om - om), w3 = c6 * (th * th * th - th);
+        const double4_32a a = lev[c], b = lev[c + 1];
+        yh = om * a.x + th * b.x + (w2 * a.y + w3 * b.y);
+        zh = om * a.z + th * b.z + (w2 * a.w + w3 * b.w);
+      }
+      const double F = driver_x<DRV>(dc, tj, et, emt, X, yh, zh);
+      Zs += e.cz * zh + e.cfz * F;
+      Ys += e.cfy * F;
+      if (yj) Ys += e.cy * yh;
+      if (zf) Zs += e.cyz * yh;
+    }
+  }
+  part[(0 * P.G + g) * kStepTP + tp] = Zs;
+  part[(1 * P.G + g) * kStepTP + tp] = Ys;
+  __syncthreads();
+  if (g != 0) return;
+
+  const bool active = ii <= last;
+  int it = 0;
+  double d = 0.0;
+  if (active) {
+    double z = 0.0, A = 0.0;
+    for (int q = 0; q < P.G; ++q) {
+      z += part[(0 * P.G + q) * kStepTP + tp];
+      A += part[(1 * P.G + q) * kStepTP + tp];
+    }
+    const double tn = __dmul_rn(double(n), P.dt);
+    const double etn = exp(tn * tn), emtn = exp(-tn * tn);
+    double y = ring[int64_t((n + 1) % P.nslot) * P.Nx + ii].x;
+    while (it < P.picard_max) {
+      const double y1 = A + P.hg0 * driver_x<DRV>(dc, tn, etn, emtn, xi, y, z);
       d = fabs(y1 - y);
       y = y1;
       ++it;

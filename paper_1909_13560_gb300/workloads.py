@@ -219,3 +219,36 @@ def ex5_problem(M: int = 128, N: int = 8, k: int = 3, L: int = 8, width: float =
                 x01=c1, x02=c2, a1=mu[0] - 0.5 * s1 * s1, a2=mu[1] - 0.5 * s2 * s2,
                 b11=b11, b21=b21, b22=b22, alpha=-r, beta1=-th1, beta2=-th2,
                 Nx1=M + 1, Nx2=M + 1, N=N, k=k, L=L, picard_max=30, picard_tol=1e-12)
+
+
+# --- general forward processes (Euler; Section 1's general Markovian X) -----
+
+def vasicek_problem(kappa: float = 0.8, theta: float = 0.04, sigma: float = 0.02,
+                    r0: float = 0.03, T: float = 2.0, Nx: int = 2049, N: int = 64, k: int = 3,
+                    L: int = 16, width_sd: float = 8.0) -> dict:
+    """Zero-coupon bond under the Vasicek short rate dX = kappa (theta - X) dt
+    + sigma dW: f = -x y, g = 1, forward AFFINE (a(x) = kappa theta - kappa x,
+    b = sigma); closed form A(tau) exp(-B(tau) x).  Grid: theta +- width_sd
+    times the stationary standard deviation sigma / sqrt(2 kappa), widened to
+    contain r0."""
+    sd = sigma / math.sqrt(2.0 * kappa)
+    lo, hi = min(theta, r0) - width_sd * sd, max(theta, r0) + width_sd * sd
+    return dict(driver="SHORT_RATE", terminal="ONE", forward="AFFINE", T=T,
+                x_min=lo, x_max=hi, x0=r0, a_x=kappa * theta, a_1=-kappa, b_x=sigma, b_1=0.0,
+                Nx=Nx, N=N, k=k, L=L, smoothing=0, picard_max=30, picard_tol=1e-12)
+
+
+def gbm_call_problem(S0: float = 100.0, strike: float = 100.0, r: float = 0.03,
+                     mu: float = 0.05, sigma: float = 0.2, T: float = 1.0, Nx: int = 4097,
+                     N: int = 64, k: int = 3, L: int = 16, width_sd: float = 6.0,
+                     smoothing: int = 1) -> dict:
+    """Black-Scholes call with the stock price itself as the grid variable:
+    dS = mu S dt + sigma S dW (forward AFFINE with a(x) = mu x, b(x) = sigma x,
+    advanced by Euler), f = -(r y + (mu - r) z / sigma), g = (x - K)^+.
+    Grid: S0 exp(+-width_sd sigma sqrt(T)) (price space, positive)."""
+    w = width_sd * sigma * math.sqrt(T)
+    return dict(driver="BS", terminal="CALL_PRICE", forward="AFFINE", T=T,
+                x_min=S0 * math.exp(-w), x_max=S0 * math.exp(w), x0=S0,
+                a_x=0.0, a_1=mu, b_x=0.0, b_1=sigma, r=r, mu=mu, sigma=sigma, delta=0.0,
+                strike=strike, Nx=Nx, N=N, k=k, L=L, smoothing=smoothing, picard_max=30,
+                picard_tol=1e-12)

@@ -198,3 +198,26 @@ def test_2d_workspace_bytes():
     np_ = 1025 * 1025
     # ring 7 x 3 x 32 B, new values 24 B, staging 6 x 24 B per point
     assert 7 * 96 * np_ + 24 * np_ + 6 * 24 * np_ <= b < (7 * 96 + 24 + 6 * 24) * np_ + (1 << 20)
+
+
+@pytest.mark.parametrize("bad", [
+    dict(W.vasicek_problem(), precision_fp32c=True),
+    dict(W.vasicek_problem(), a_1=0.1),
+    dict(W.vasicek_problem(), b_1=0.01),
+    dict(W.vasicek_problem(), forward="CONST"),
+    dict(W.gbm_call_problem(), x_min=-1.0),
+    dict(W.gbm_call_problem(), b_x=0.1),
+    dict(W.sin_problem(), forward=2),
+])
+def test_invalid_general_forward_problems_rejected(bad):
+    p = dict(bad)
+    prec = "fp32c" if p.pop("precision_fp32c", False) else "fp64"
+    with pytest.raises(B.BsdeError) as ei:
+        B.bsde_workspace_bytes(B.make_problem(p, prec))
+    assert ei.value.code == B.BSDE_EINVAL
+
+
+def test_general_forward_problems_accepted():
+    for p in (W.vasicek_problem(), W.gbm_call_problem(),
+              dict(W.sin_problem(), driver="SHORT_RATE")):
+        assert B.bsde_workspace_bytes(B.make_problem(p, "fp64")) > 0
