@@ -790,6 +790,180 @@ def _ex4_levels(p):
     return ys, zs, zs.copy()
 
 
+def flops_per_gp_step_general(k: int, L: int) -> float:
+    """Algorithmic FP64 flops of one grid-point step on the general forward
+    path: per node the Euler position (2 FMA), cell and theta (sub, div,
+    floor, sub), the four spline weights (~8), the two spline values (2 x 6),
+    the driver (~3) and the weighted sums (~6); per point ~10 Picard
+    iterations."""
+    return k * L * (4 + 4 + 8 + 12 + 3 + 6) + 10 * 6
+
+
+def run_general(args, rank, world, local_rank):
+    """The general forward path (affine coefficients, Euler) in FP64 at the
+    benchmark's grid size: the Vasicek bond (short-rate driver f = -x y,
+    K_y = 2, K_z = 1 with the E[y dW]/dt z form) and the Black-Scholes call in
+    the price (geometric Brownian motion, K = 3); Nx = 65536, N = 256, L = 16.
+    One step = one solve of each."""
+    import torch
+    from paper_1909_13560_gb300 import bsde as B
+    from paper_1909_13560_gb300 import workloads as W
+    dist = _dist_init(world)
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    probs = {"vasicek_k2_kz1_ydw": dict(W.vasicek_problem(Nx=65536, N=256, k=2), kz=1, zform=1),
+             "gbm_price_call_k3": W.gbm_call_problem(Nx=65536, N=256, k=3)}
+    solvers = {n: B.Solver(p, "fp64", device=dev) for n, p in probs.items()}
+    units = sum(W.gp_steps(p) for p in probs.values())
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def one_step():
+        for s in solvers.values():
+            B.bsde_solve(s.plan, sp, want_result=False)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        one_step()
+    torch.cuda.synchronize(dev)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        if not uuid.startswith("GPU-"):
+            uuid = "GPU-" + uuid
+    except Exception:
+        uuid = None
+    _barrier(dist)
+    torch.cuda.synchronize(dev)
+    with ClockSampler(uuid) as clk:
+        w0 = time.perf_counter()
+        for i in range(args.steps):
+            flush.zero_()
+            starts[i].record(stream)
+            one_step()
+            ends[i].record(stream)
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - w0
+    _barrier(dist)
+    ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+    ms_max = _max_over_ranks(dist, ms)
+    value = world * units * args.steps / (ms_max / 1000.0)
+    rows = []
+    kern_ms = kern_flops = 0.0
+    for name, p in probs.items():
+        s = solvers[name]
+        r = B.bsde_result_fetch(s.plan, sp)
+        if p["terminal"] == "ONE":
+            u, ux = W.vasicek_bond(p, 0.0, p["x0"])
+        else:
+            u, ux = W.price_call(p, 0.0, p["x0"])
+        u, z = float(u), float((p["b_x"] + p["b_1"] * p["x0"]) * ux)
+        # the step kernel of level 0, replayed from a graph
+        B.bsde_enqueue_level(s.plan, sp, 0, 1)
+        torch.cuda.synchronize(dev)
+        g = torch.cuda.CUDAGraph()
+        cap = torch.cuda.Stream(dev)
+        with torch.cuda.graph(g, stream=cap):
+            for _ in range(20):
+                B.bsde_enqueue_level(s.plan, cap.cuda_stream, 0, 1)
+        g.replay()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.replay()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        avg = e0.elapsed_time(e1) / 20
+        del g
+        K = W.levels_K(p)
+        nlev = p["N"] - K + 1
+        kern_ms += avg * nlev
+        kern_flops += flops_per_gp_step_general(K, p["L"]) * p["Nx"] * nlev
+        rows.append({"name": name, "y0": r.y0, "z0": r.z0, "exact_y0": u, "exact_z0": z,
+                     "err_y0_vs_exact": abs(r.y0 - u), "err_z0_vs_exact": abs(r.z0 - z),
+                     "step_launch_us": 1000.0 * avg, "launches": s.launches})
+    peaks = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = _alu_peak_tflops("fp64", sm_max)
+    achieved = kern_flops / (kern_ms / 1000.0) / 1e12
+
+    # end to end: caller levels from pinned host memory, level 0 and the
+    # result back, every step
+    host = {}
+    h2d = d2h = 0
+    for name, p in probs.items():
+        iy, iz = W.initial_levels(p)
+        ty, tz = torch.from_numpy(iy).pin_memory(), torch.from_numpy(iz).pin_memory()
+        oy = torch.empty(p["Nx"], dtype=torch.float64).pin_memory()
+        oz = torch.empty(p["Nx"], dtype=torch.float64).pin_memory()
+        host[name] = (ty, tz, oy, oz)
+        h2d += (ty.numel() + tz.numel()) * 8
+        d2h += (oy.numel() + oz.numel()) * 8 + 40
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for name, s in solvers.items():
+            ty, tz, oy, oz = host[name]
+            B.bsde_solve(s.plan, sp, ty.data_ptr(), tz.data_ptr(), True, oy.data_ptr(),
+                         oz.data_ptr(), True)
+    torch.cuda.synchronize(dev)
+    e_dt = _max_over_ranks(dist, time.perf_counter() - t0)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import oracle as O
+        threads = os.cpu_count() or 1
+        lv = 32
+        c0 = time.perf_counter()
+        cu = 0
+        for p in probs.values():
+            rr = O.solve(p, levels=lv, threads=threads)
+            cu += p["Nx"] * rr["levels_done"]
+        cdt = time.perf_counter() - c0
+        cpu = {"value": cu / cdt, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"both problems, first {lv} backward levels each, {threads} host "
+                         f"threads, {cdt:.1f} s"}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "general: forward process by Euler with affine a(x), b(x); "
+                                   "Vasicek bond (kappa=.8, theta=.04, sigma=.02, r0=.03, T=2, "
+                                   "f = -x y, K_y=2, K_z=1, E[y dW]/dt z form) and the call in "
+                                   "the price under GBM (S0=K=100, r=.03, mu=.05, sigma=.2, "
+                                   "T=1, K=3); Nx=65536, N=256, L=16, FP64; one solve each per "
+                                   "step",
+                       "Nx": 65536, "N": 256, "L": 16,
+                       "l2": "flushed between steps (256 MiB write, outside the timed events)",
+                       "parallelism": f"{world} independent replica(s)"},
+            "accuracy": {"gate": "errors against the closed forms (Euler forward: first "
+                                 "order in dt)", "rows": rows},
+            "roofline": {"kernel": "k_step64_gen", "bound": "alu", "achieved": achieved,
+                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": None,
+                         "peak_source": f"derived: 152 SMs x 2 FP64 FMA units x 2 flop x {sm_max:.0f} MHz",
+                         "flop_per_gp_step": {n: flops_per_gp_step_general(W.levels_K(p), p["L"])
+                                              for n, p in probs.items()}},
+            "e2e": {"value": world * units * args.steps / e_dt, "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": sum(s.launches for s in solvers.values()) * args.steps,
+            "clocks": clk.summary(),
+            "wall_s_timed_region": wall,
+        }
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    for s in solvers.values():
+        s.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def run_serving(args, rank, world, local_rank):
     """config5: Poisson arrivals of pricing requests served by the persistent
     continuous-batching kernel; one step = the whole arrival sequence."""
@@ -856,7 +1030,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp32c", "fp64"], default="fp32c")
-    ap.add_argument("--workload", choices=["config2", "config3", "config4", "config5", "ex4_2d"],
+    ap.add_argument("--workload", choices=["config2", "config3", "config4", "config5", "ex4_2d",
+                                           "general"],
                     default="config2",
                     help="config2: the Black-Scholes solves k = 1..6 (default); "
                          "config3: the lending/borrowing call at Nx=2^20, N=1024, k=4; "
@@ -888,6 +1063,8 @@ def main():
         run_serving(args, rank, world, local_rank)
     elif args.workload == "ex4_2d":
         run_2d(args, rank, world, local_rank)
+    elif args.workload == "general":
+        run_general(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

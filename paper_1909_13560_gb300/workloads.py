@@ -160,6 +160,10 @@ def initial_levels(p: dict):
         elif term == "LNSIN":
             e = math.exp(t * t)
             u, ux = np.log(np.sin(x) + 3) * e, e * np.cos(x) / (np.sin(x) + 3)
+        elif term == "ONE":
+            u, ux = vasicek_bond(p, t, x)
+        elif term == "CALL_PRICE":
+            u, ux = price_call(p, t, x, smooth=(m == 0 and bool(p.get("smoothing", 0))))
         else:
             K = p["strike"]
             if m == 0 and p.get("smoothing", 0):
@@ -181,8 +185,60 @@ def initial_levels(p: dict):
                     d1 = (np.log(S / K) + (r - dl + 0.5 * sig * sig) * tau) / sq
                     a = S * math.exp(-dl * tau) * ndtr(d1)
                     u, ux = a - K * math.exp(-r * tau) * ndtr(d1 - sq), a
-        ys[m], zs[m] = u, p["b_x"] * ux
+        bx = p["b_x"] + (p.get("b_1", 0.0) * x if p.get("forward", "CONST") == "AFFINE" else 0.0)
+        ys[m], zs[m] = u, bx * ux
+        if term == "CALL_PRICE" and m == 0 and p.get("smoothing", 0):
+            zs[m] = price_call_z_average(p, x)
     return ys, zs
+
+
+def vasicek_bond(p: dict, t: float, x):
+    """Zero-coupon bond price A(tau) exp(-B(tau) x) and its x-derivative under
+    dX = kappa (theta - X) dt + sigma dW (kappa = -a_1, theta = a_x / kappa,
+    sigma = b_x)."""
+    tau = p["T"] - t
+    x = np.asarray(x, dtype=np.float64)
+    if tau <= 0:
+        return np.ones_like(x), np.zeros_like(x)
+    kap = -p["a_1"]
+    th, sg = p["a_x"] / kap, p["b_x"]
+    B = -math.expm1(-kap * tau) / kap
+    lnA = (th - sg * sg / (2 * kap * kap)) * (B - tau) - sg * sg * B * B / (4 * kap)
+    u = np.exp(lnA - B * x)
+    return u, -B * u
+
+
+def price_call(p: dict, t: float, x, smooth: bool = False):
+    """Black-Scholes call in the price x = S (volatility b_1) and its
+    x-derivative; with smooth, the level-N cell averages of the payoff over
+    [x - dx/2, x + dx/2]."""
+    from scipy.special import ndtr
+    x = np.asarray(x, dtype=np.float64)
+    K, tau, sg = p["strike"], p["T"] - t, p["b_1"]
+    r, dl = p.get("r", 0.0), p.get("delta", 0.0)
+    if smooth:
+        dx = (p["x_max"] - p["x_min"]) / (int(p["Nx"]) - 1)
+        a, b = x - dx / 2, x + dx / 2
+        lo = np.maximum(a, K)
+        u = np.where(b <= K, 0.0, 0.5 * ((b - K) ** 2 - (lo - K) ** 2) / dx)
+        return u, np.zeros_like(x)
+    if tau <= 0:
+        return np.maximum(x - K, 0.0), (x > K).astype(np.float64)
+    sq = sg * math.sqrt(tau)
+    with np.errstate(divide="ignore"):
+        d1 = (np.log(np.maximum(x, 1e-300) / K) + (r - dl + 0.5 * sg * sg) * tau) / sq
+    u = x * math.exp(-dl * tau) * ndtr(d1) - K * math.exp(-r * tau) * ndtr(d1 - sq)
+    return np.where(x > 0, u, 0.0), np.where(x > 0, math.exp(-dl * tau) * ndtr(d1), 0.0)
+
+
+def price_call_z_average(p: dict, x):
+    """Level-N cell average of b(s) 1{s > K}, b(s) = b_x + b_1 s."""
+    dx = (p["x_max"] - p["x_min"]) / (int(p["Nx"]) - 1)
+    K = p["strike"]
+    a, b = x - dx / 2, x + dx / 2
+    lo = np.maximum(a, K)
+    z = (p["b_x"] * (b - lo) + 0.5 * p["b_1"] * (b * b - lo * lo)) / dx
+    return np.where(b <= K, 0.0, z)
 
 
 # --- two space dimensions (Section 5, Examples 4 and 5) ----------------------
