@@ -964,6 +964,89 @@ def run_general(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def run_decomp(args, rank, world, local_rank):
+    """One large problem decomposed into slabs (the lending/borrowing call of
+    config3 at full size, Nx = 2^20, N = 1024, K = 2, FP32C): solved as one
+    plan and as 2, 4 and 8 slabs with halo exchange after every step, all
+    slabs on this GPU (LocalTransport).  Reports each layout's time, the halo
+    overhead (extra points computed) and the exchange volume per level, and
+    the agreement of y0 with the one-plan solve.  One step = one solve of the
+    largest layout."""
+    import torch
+    from paper_1909_13560_gb300 import bsde as B
+    from paper_1909_13560_gb300 import decomp
+    from paper_1909_13560_gb300 import workloads as W
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    p = W.config3(k=2)
+    units = W.gp_steps(p)
+    halo = decomp.halo_width(p)
+    ref = B.solve(p, "fp32c")
+    rows = []
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        if not uuid.startswith("GPU-"):
+            uuid = "GPU-" + uuid
+    except Exception:
+        uuid = None
+    parts_list = (2, 4, 8)
+    with ClockSampler(uuid) as clk:
+        for parts in parts_list:
+            for _ in range(1):
+                decomp.solve_sharded(p, parts, "fp32c")  # warm-up (plans, graphs)
+            torch.cuda.synchronize(dev)
+            ms = 0.0
+            for _ in range(max(1, args.steps)):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                got = decomp.solve_sharded(p, parts, "fp32c")
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                ms += e0.elapsed_time(e1)
+            ms /= max(1, args.steps)
+            lay = got["slabs"]
+            extra = sum(sl["local"][1] - sl["local"][0] for sl in lay) - p["Nx"]
+            rows.append({"parts": parts, "ms_per_solve": ms, "gp_steps_per_s": units / (ms / 1000.0),
+                         "halo": halo, "extra_points_frac": extra / p["Nx"],
+                         "exchange_bytes_per_level": 2 * (parts - 1) * halo * 16,
+                         "y0": got["y0"], "dy0_vs_one_plan": abs(got["y0"] - ref["y0"])})
+    s1 = B.Solver(p, "fp32c", device=dev)
+    s1.solve()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    B.bsde_solve(s1.plan, stream.cuda_stream, want_result=False)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    one_ms = e0.elapsed_time(e1)
+    launches = s1.launches
+    s1.close()
+    if rank == 0:
+        last = rows[-1]
+        line = {
+            "metric": METRIC, "value": last["gp_steps_per_s"], "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": 1, "ms_per_step": last["ms_per_solve"],
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "decomp: lending/borrowing call (config3 parameters) at full "
+                                   "size Nx=2^20, N=1024, K=2, L=16, FP32C, one problem as 8 "
+                                   "slabs with halo exchange every level, all slabs on one GPU "
+                                   "(launched level by level from the host)",
+                       "Nx": p["Nx"], "N": p["N"], "k": 2, "halo": halo},
+            "one_plan": {"ms_per_solve": one_ms, "gp_steps_per_s": units / (one_ms / 1000.0),
+                         "y0": ref["y0"], "launches": launches},
+            "layouts": rows,
+            "accuracy": {"gate": "|y0(slabs) - y0(one plan)| <= 1e-6 max(1, |y0|)",
+                         "within_tol": all(r["dy0_vs_one_plan"] <= 1e-6 * max(1.0, abs(ref["y0"]))
+                                           for r in rows)},
+            "gpu_launches": None,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+
+
 def run_serving(args, rank, world, local_rank):
     """config5: Poisson arrivals of pricing requests served by the persistent
     continuous-batching kernel; one step = the whole arrival sequence."""
@@ -1031,7 +1114,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp32c", "fp64"], default="fp32c")
     ap.add_argument("--workload", choices=["config2", "config3", "config4", "config5", "ex4_2d",
-                                           "general"],
+                                           "general", "decomp"],
                     default="config2",
                     help="config2: the Black-Scholes solves k = 1..6 (default); "
                          "config3: the lending/borrowing call at Nx=2^20, N=1024, k=4; "
@@ -1065,6 +1148,8 @@ def main():
         run_2d(args, rank, world, local_rank)
     elif args.workload == "general":
         run_general(args, rank, world, local_rank)
+    elif args.workload == "decomp":
+        run_decomp(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

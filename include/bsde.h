@@ -219,6 +219,36 @@ BSDE_API int bsde_result_fetch(bsde_plan_t *plan, void *stream, bsde_result *res
  * way.  Used to time the kernels one by one. */
 BSDE_API int bsde_enqueue_level(bsde_plan_t *plan, void *stream, int n, int parts);
 
+/* Level-by-level driving, for a grid decomposed over several plans (each
+ * plan one slab of the grid with a halo; see the package's decomposition
+ * driver).  A solve is then:
+ *   bsde_enqueue_start(plan, stream, init_y, init_z, init_on_host);
+ *   for n = N-K down to 0:
+ *     bsde_enqueue_level(plan, stream, n, 1);   -- the step writes level n
+ *     (replace the halo part of level n's value records)
+ *     bsde_enqueue_level(plan, stream, n, 2);   -- the spline of level n
+ *   bsde_enqueue_finish(plan, stream, out_y, out_z, out_on_host);
+ *   bsde_result_fetch(plan, stream, &result);
+ * bsde_enqueue_start: the stats reset, the start-up if any and the K initial
+ *   levels with their splines; init_y/init_z as in bsde_solve (the call waits
+ *   for the stream when they are host memory).
+ * bsde_enqueue_finish: readout of level 0 at x0, its export (to out_y/out_z
+ *   if given, host or device memory as out_on_host says; the call waits for
+ *   host copies) and the statistics for bsde_result_fetch. */
+BSDE_API int bsde_enqueue_start(bsde_plan_t *plan, void *stream, const double *init_y,
+                                const double *init_z, int init_on_host);
+BSDE_API int bsde_enqueue_finish(bsde_plan_t *plan, void *stream, double *out_y,
+                                 double *out_z, int out_on_host);
+
+/* Device address of level n's per-point value records in the plan's ring
+ * (valid for the levels the ring holds at the time of use) and their size:
+ * FP64 32-byte records (y, M_y, z, M_z) as doubles, FP32C 16-byte records
+ * (y_hi, z_hi, y_lo, z_lo) as floats, value = hi + lo; record i belongs to
+ * grid point i.  The spline part (M, and the FP32C interval records) is
+ * recomputed by the spline launch, so a halo exchange copies these records
+ * between the step and the spline launches of a level. */
+BSDE_API int bsde_level_records(bsde_plan_t *plan, int n, void **records, size_t *record_bytes);
+
 /* Release the plan's host resources and graphs (not the workspace). */
 BSDE_API void bsde_free(bsde_plan_t *plan);
 

@@ -107,7 +107,8 @@ _SYMBOLS = ("bsde_workspace_bytes", "bsde_plan", "bsde_solve", "bsde_result_fetc
             "bsde_server_start", "bsde_server_submit", "bsde_server_poll", "bsde_server_stop",
             "bsde_server_free", "bsde_l2_read_probe",
             "bsde2_workspace_bytes", "bsde2_plan", "bsde2_solve", "bsde2_result_fetch",
-            "bsde2_enqueue_level", "bsde2_plan_launches", "bsde2_free")
+            "bsde2_enqueue_level", "bsde2_plan_launches", "bsde2_free",
+            "bsde_enqueue_start", "bsde_enqueue_finish", "bsde_level_records")
 
 
 def load(path: str = LIB_PATH):
@@ -168,6 +169,9 @@ def load(path: str = LIB_PATH):
     lib.bsde2_plan_launches.restype = ctypes.c_int64
     lib.bsde2_free.argtypes = [vp]
     lib.bsde2_free.restype = None
+    lib.bsde_enqueue_start.argtypes = [vp, vp, vp, vp, ctypes.c_int]
+    lib.bsde_enqueue_finish.argtypes = [vp, vp, vp, vp, ctypes.c_int]
+    lib.bsde_level_records.argtypes = [vp, ctypes.c_int, P(vp), P(ctypes.c_size_t)]
     _lib = lib
     return lib
 

@@ -254,13 +254,11 @@ static int64_t enqueue_startup(bsde_plan_t *pl, cudaStream_t s, double *sy, doub
   return launches;
 }
 
-// The whole solve as one stream-ordered sequence (captured into a graph).
 template <int PREC>
-static int64_t enqueue_solve(bsde_plan_t *pl, cudaStream_t s, bool imported) {
+static int64_t enqueue_start(bsde_plan_t *pl, cudaStream_t s, bool imported) {
+  // stats reset, the start-up if any, the K initial levels and their splines
   const Params &P = pl->P;
   const Run &R = pl->run;
-  const Ring64 r64 = R.r64;
-  const Ring32 r32 = R.r32;
   Stats *st = reinterpret_cast<Stats *>(pl->ws + pl->lay.stats);
   double *sy = reinterpret_cast<double *>(pl->ws + pl->lay.stage);
   double *sz = sy + int64_t(P.k) * P.Nx;
@@ -274,21 +272,40 @@ static int64_t enqueue_solve(bsde_plan_t *pl, cudaStream_t s, bool imported) {
   const unsigned eb = unsigned((P.Nx + 255) / 256 < 4096 ? (P.Nx + 255) / 256 : 4096);
   for (int m = 0; m < P.k; ++m) {
     if (imported)
-      k_import<PREC><<<eb, 256, 0, s>>>(P, r64, r32, sy, sz, m);
+      k_import<PREC><<<eb, 256, 0, s>>>(P, R.r64, R.r32, sy, sz, m);
     else
-      k_init_closed<PREC><<<eb, 256, 0, s>>>(P, r64, r32, m);
+      k_init_closed<PREC><<<eb, 256, 0, s>>>(P, R.r64, R.r32, m);
     ++launches;
     launches += enqueue_spline<PREC>(R, s, (P.N - m) % P.nslot);
   }
+  return launches;
+}
+
+template <int PREC>
+static int64_t enqueue_finish(bsde_plan_t *pl, cudaStream_t s) {
+  // readout of level 0 at x0 and its export to the staging area
+  const Params &P = pl->P;
+  const Run &R = pl->run;
+  Stats *st = reinterpret_cast<Stats *>(pl->ws + pl->lay.stats);
+  double *sy = reinterpret_cast<double *>(pl->ws + pl->lay.stage);
+  const unsigned eb = unsigned((P.Nx + 255) / 256 < 4096 ? (P.Nx + 255) / 256 : 4096);
+  k_readout<PREC><<<1, 32, 0, s>>>(P, R.r64, R.r32, 0, st);
+  k_export<PREC><<<eb, 256, 0, s>>>(P, R.r64, R.r32, sy, sy + P.Nx, 0);
+  return 2;
+}
+
+// The whole solve as one stream-ordered sequence (captured into a graph).
+template <int PREC>
+static int64_t enqueue_solve(bsde_plan_t *pl, cudaStream_t s, bool imported) {
+  const Params &P = pl->P;
+  const Run &R = pl->run;
+  int64_t launches = enqueue_start<PREC>(pl, s, imported);
   for (int n = P.N - P.k; n >= 0; --n) {
     launch_step_any<PREC>(pl, R, s, n);
     ++launches;
     launches += enqueue_spline<PREC>(R, s, n % P.nslot);
   }
-  k_readout<PREC><<<1, 32, 0, s>>>(P, r64, r32, 0, st);
-  k_export<PREC><<<eb, 256, 0, s>>>(P, r64, r32, sy, sy + P.Nx, 0);
-  launches += 2;
-  return launches;
+  return launches + enqueue_finish<PREC>(pl, s);
 }
 
 static int build_graph(bsde_plan_t *pl, int which) {
@@ -440,6 +457,68 @@ int bsde_enqueue_level(bsde_plan_t *pl, void *stream, int n, int parts) {
     else enqueue_spline<BSDE_FP32C>(pl->run, s, n % pl->P.nslot);
   }
   BSDE_CUDA_TRY(cudaGetLastError());
+  return BSDE_OK;
+}
+
+int bsde_enqueue_start(bsde_plan_t *pl, void *stream, const double *init_y, const double *init_z,
+                       int init_on_host) {
+  if (!pl) return fail(BSDE_EINVAL, "null plan");
+  if ((init_y == nullptr) != (init_z == nullptr))
+    return fail(BSDE_EINVAL, "init_y and init_z must both be given or both be NULL");
+  DeviceGuard guard(pl->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const Params &P = pl->P;
+  if (init_y) {
+    double *sy = reinterpret_cast<double *>(pl->ws + pl->lay.stage);
+    double *sz = sy + int64_t(P.k) * P.Nx;
+    const size_t lev_bytes = size_t(P.k) * size_t(P.Nx) * sizeof(double);
+    const cudaMemcpyKind kind = init_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    BSDE_CUDA_TRY(cudaMemcpyAsync(sy, init_y, lev_bytes, kind, s));
+    BSDE_CUDA_TRY(cudaMemcpyAsync(sz, init_z, lev_bytes, kind, s));
+  }
+  if (P.precision == BSDE_FP64)
+    enqueue_start<BSDE_FP64>(pl, s, init_y != nullptr);
+  else
+    enqueue_start<BSDE_FP32C>(pl, s, init_y != nullptr);
+  BSDE_CUDA_TRY(cudaGetLastError());
+  if (init_y && init_on_host) BSDE_CUDA_TRY(cudaStreamSynchronize(s));
+  return BSDE_OK;
+}
+
+int bsde_enqueue_finish(bsde_plan_t *pl, void *stream, double *out_y, double *out_z,
+                        int out_on_host) {
+  if (!pl) return fail(BSDE_EINVAL, "null plan");
+  DeviceGuard guard(pl->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const Params &P = pl->P;
+  if (P.precision == BSDE_FP64)
+    enqueue_finish<BSDE_FP64>(pl, s);
+  else
+    enqueue_finish<BSDE_FP32C>(pl, s);
+  BSDE_CUDA_TRY(cudaGetLastError());
+  const double *sy = reinterpret_cast<const double *>(pl->ws + pl->lay.stage);
+  const size_t out_bytes = size_t(P.Nx) * sizeof(double);
+  const cudaMemcpyKind okind = out_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (out_y) BSDE_CUDA_TRY(cudaMemcpyAsync(out_y, sy, out_bytes, okind, s));
+  if (out_z) BSDE_CUDA_TRY(cudaMemcpyAsync(out_z, sy + P.Nx, out_bytes, okind, s));
+  BSDE_CUDA_TRY(cudaMemcpyAsync(pl->host_stats, pl->ws + pl->lay.stats, sizeof(Stats),
+                                cudaMemcpyDeviceToHost, s));
+  if ((out_y || out_z) && out_on_host) BSDE_CUDA_TRY(cudaStreamSynchronize(s));
+  return BSDE_OK;
+}
+
+int bsde_level_records(bsde_plan_t *pl, int n, void **records, size_t *record_bytes) {
+  if (!pl || !records || !record_bytes) return fail(BSDE_EINVAL, "null argument");
+  const Params &P = pl->P;
+  if (n < 0 || n > P.N) return fail(BSDE_EINVAL, "level out of range");
+  const size_t slot = size_t(n % P.nslot);
+  if (P.precision == BSDE_FP64) {
+    *records = pl->ws + pl->lay.ring64 + slot * size_t(P.Nx) * 32;
+    *record_bytes = 32;
+  } else {
+    *records = pl->ws + pl->lay.ringA + slot * size_t(P.Nx) * 16;
+    *record_bytes = 16;
+  }
   return BSDE_OK;
 }
 

@@ -1,0 +1,227 @@
+"""Domain decomposition of one 1-D problem over several plans: each plan owns
+a slab of the grid and keeps a halo wide enough that its owned points never
+see the slab's ends.
+
+Per backward level every slab runs its step kernel, the halo part of the new
+level's value records is replaced by the neighbours' owned values, and every
+slab runs its spline kernel.  The halo is the reach of the Gauss-Hermite
+nodes (the largest cell shift of any (j, l), plus the right cell of a node)
+plus a margin over which the spline's end condition at the slab's end decays
+below double precision (the LU recurrences of tridiag(1, 4, 1) contract by
+2 - sqrt 3 per node: 40 nodes give 1e-23).  The initial levels come from the
+closed form (or the caller's levels) on every slab's whole local grid, so they
+need no exchange.
+
+Two transports move the halo records:
+  * LocalTransport: all slabs on one device, copies between their
+    workspaces on one stream (the exchange the multi-GPU run does, with the
+    wire replaced by device copies);
+  * DistTransport: one slab per rank of torch.distributed, point-to-point
+    send/recv of the edge records to the neighbouring ranks between launches
+    (NCCL on GPUs; gloo carries the same protocol on CPU tensors in the
+    tests).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+
+import numpy as np
+
+from . import bsde as B
+
+MARGIN = 40  # spline margin in grid nodes
+
+
+def node_reach(problem: dict) -> int:
+    """Largest |cell index offset| a node of any (j, l) reaches from its grid
+    point, counting the right cell node: max over j <= K, l of
+    max(|floor(o)|, |floor(o) + 1|), o = (a_x j dt + b_x sqrt(2 j dt) a_l) / dx."""
+    if problem.get("forward", "CONST") not in ("CONST", 0):
+        raise ValueError("the decomposition needs a constant-coefficient forward process")
+    K = B.levels_K(problem)
+    L = int(problem["L"])
+    a = (ctypes.c_double * L)()
+    w = (ctypes.c_double * L)()
+    B._check(B.load().bsde_gauss_hermite(L, a, w), "bsde_gauss_hermite")
+    dt = float(problem["T"]) / int(problem["N"])
+    dx = (float(problem["x_max"]) - float(problem["x_min"])) / (int(problem["Nx"]) - 1)
+    reach = 0
+    for j in range(1, K + 1):
+        for l in range(L):
+            o = (float(problem["a_x"]) * j * dt + float(problem["b_x"]) * math.sqrt(2.0 * j * dt) * a[l]) / dx
+            f = math.floor(o)
+            reach = max(reach, abs(f), abs(f + 1))
+    return int(reach)
+
+
+def halo_width(problem: dict) -> int:
+    return node_reach(problem) + MARGIN
+
+
+def slabs(Nx: int, parts: int, halo: int):
+    """Owned ranges [own_lo, own_hi) split evenly, local ranges [lo, hi) with
+    the halo clipped to the grid.  Every owned range must be at least `halo`
+    wide, so that a halo comes from the immediate neighbours only."""
+    if parts < 1:
+        raise ValueError("parts >= 1")
+    out = []
+    for r in range(parts):
+        own_lo = r * Nx // parts
+        own_hi = (r + 1) * Nx // parts
+        if parts > 1 and own_hi - own_lo < halo:
+            raise ValueError(f"slab {r} owns {own_hi - own_lo} points, fewer than the halo {halo}")
+        out.append({"own": (own_lo, own_hi), "local": (max(0, own_lo - halo), min(Nx, own_hi + halo))})
+    return out
+
+
+def slab_problem(problem: dict, lo: int, hi: int) -> dict:
+    """The problem restricted to grid points [lo, hi) (same spacing; the
+    readout point clamped into the slab)."""
+    Nx = int(problem["Nx"])
+    dx = (float(problem["x_max"]) - float(problem["x_min"])) / (Nx - 1)
+    q = dict(problem)
+    q["x_min"] = float(problem["x_min"]) + lo * dx
+    q["x_max"] = float(problem["x_min"]) + (hi - 1) * dx
+    q["Nx"] = hi - lo
+    q["x0"] = min(max(float(problem["x0"]), q["x_min"]), q["x_max"])
+    return q
+
+
+def _records(solver, n: int):
+    """(uint8 tensor view of level n's value records, record size) of a
+    Solver: a slice of its workspace tensor."""
+    vp = ctypes.c_void_p()
+    rb = ctypes.c_size_t()
+    B._check(B.load().bsde_level_records(ctypes.c_void_p(solver.plan), int(n), ctypes.byref(vp),
+                                         ctypes.byref(rb)), "bsde_level_records")
+    off = int(vp.value) - solver.workspace.data_ptr()
+    nb = int(solver.problem["Nx"]) * int(rb.value)
+    return solver.workspace[off:off + nb], int(rb.value)
+
+
+class LocalTransport:
+    """All slabs in this process on one device: halo records copied between
+    the slabs' workspaces on the solve's stream."""
+
+    def exchange(self, solvers, layout, n: int) -> None:
+        views = [_records(s, n) for s in solvers]
+        for r, sl in enumerate(layout):
+            lo, hi = sl["local"]
+            own_lo, own_hi = sl["own"]
+            dst, rb = views[r]
+            if r > 0 and lo < own_lo:  # left halo from slab r - 1
+                src, _ = views[r - 1]
+                slo = layout[r - 1]["local"][0]
+                dst[(0) * rb:(own_lo - lo) * rb].copy_(src[(lo - slo) * rb:(own_lo - slo) * rb])
+            if r < len(layout) - 1 and own_hi < hi:  # right halo from slab r + 1
+                src, _ = views[r + 1]
+                slo = layout[r + 1]["local"][0]
+                dst[(own_hi - lo) * rb:(hi - lo) * rb].copy_(src[(own_hi - slo) * rb:(hi - slo) * rb])
+
+
+class DistTransport:
+    """One slab per rank: the edge records go to the neighbouring ranks by
+    point-to-point send/recv between launches.  `stage` moves device records
+    through host memory for backends without device tensors (gloo)."""
+
+    def __init__(self, dist, stage_on_host: bool = False):
+        self.dist = dist
+        self.stage_on_host = stage_on_host
+
+    def exchange_views(self, rank: int, layout, view, rb: int) -> None:
+        """Exchange halos of this rank's records `view` (uint8, local grid)."""
+        d = self.dist
+        lo, hi = layout[rank]["local"]
+        own_lo, own_hi = layout[rank]["own"]
+        world = len(layout)
+        ops, recvs = [], []
+
+        def buf(t):
+            return t.cpu() if self.stage_on_host else t
+
+        if rank > 0:
+            # my first owned records -> left neighbour's right halo; its last
+            # owned records -> my left halo
+            nl = layout[rank - 1]["local"][1] - own_lo
+            send = buf(view[(own_lo - lo) * rb:(own_lo - lo + nl) * rb].contiguous())
+            recv = buf(view[0:(own_lo - lo) * rb].clone())
+            ops += [d.P2POp(d.isend, send, rank - 1), d.P2POp(d.irecv, recv, rank - 1)]
+            recvs.append((recv, 0, (own_lo - lo) * rb))
+        if rank < world - 1:
+            nr = own_hi - layout[rank + 1]["local"][0]
+            send = buf(view[(own_hi - lo - nr) * rb:(own_hi - lo) * rb].contiguous())
+            recv = buf(view[(own_hi - lo) * rb:(hi - lo) * rb].clone())
+            ops += [d.P2POp(d.isend, send, rank + 1), d.P2POp(d.irecv, recv, rank + 1)]
+            recvs.append((recv, (own_hi - lo) * rb, (hi - lo) * rb))
+        if ops:
+            for req in d.batch_isend_irecv(ops):
+                req.wait()
+        for recv, a, b in recvs:
+            view[a:b].copy_(recv.to(view.device) if self.stage_on_host else recv)
+
+
+def solve_sharded(problem: dict, parts: int, precision: str = "fp64", device=None,
+                  want_level: bool = False, init=None) -> dict:
+    """Solve one problem as `parts` slabs on one device (LocalTransport).
+    Returns y0, z0 (from the slab that owns x0), the merged Picard statistics
+    and, if asked, the assembled level 0."""
+    import torch
+    if problem.get("init_mode", 0) not in (0, "EXACT") and B.levels_K(problem) > 1:
+        raise ValueError("the decomposition starts from the closed form or caller levels")
+    Nx = int(problem["Nx"])
+    layout = slabs(Nx, parts, halo_width(problem))
+    subs = [slab_problem(problem, *sl["local"]) for sl in layout]
+    solvers = [B.Solver(q, precision, device=device) for q in subs]
+    dev = solvers[0].device
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    lib = B.load()
+    keep = []
+    for s, sl in zip(solvers, layout):
+        iy = iz = None
+        if init is not None:
+            lo, hi = sl["local"]
+            iy = np.ascontiguousarray(init[0][:, lo:hi], dtype=np.float64)
+            iz = np.ascontiguousarray(init[1][:, lo:hi], dtype=np.float64)
+            keep += [iy, iz]
+        B._check(lib.bsde_enqueue_start(ctypes.c_void_p(s.plan), ctypes.c_void_p(sp),
+                                        iy.ctypes.data if iy is not None else None,
+                                        iz.ctypes.data if iz is not None else None,
+                                        1 if iy is not None else 0), "bsde_enqueue_start")
+    K = B.levels_K(problem)
+    tr = LocalTransport()
+    for n in range(int(problem["N"]) - K, -1, -1):
+        for s in solvers:
+            B.bsde_enqueue_level(s.plan, sp, n, 1)
+        tr.exchange(solvers, layout, n)
+        for s in solvers:
+            B.bsde_enqueue_level(s.plan, sp, n, 2)
+    outs = []
+    for s, q in zip(solvers, subs):
+        oy = np.zeros(int(q["Nx"]))
+        oz = np.zeros(int(q["Nx"]))
+        B._check(lib.bsde_enqueue_finish(ctypes.c_void_p(s.plan), ctypes.c_void_p(sp),
+                                         oy.ctypes.data, oz.ctypes.data, 1), "bsde_enqueue_finish")
+        outs.append((oy, oz))
+    res = [B.bsde_result_fetch(s.plan, sp) for s in solvers]
+    x0 = float(problem["x0"])
+    dx = (float(problem["x_max"]) - float(problem["x_min"])) / (Nx - 1)
+    g0 = min(int(math.floor((x0 - float(problem["x_min"])) / dx)), Nx - 1)
+    owner = next(r for r, sl in enumerate(layout) if sl["own"][0] <= g0 < sl["own"][1])
+    out = {"y0": res[owner].y0, "z0": res[owner].z0,
+           "picard_iters_max": max(r.picard_iters_max for r in res),
+           "picard_resid_max": max(r.picard_resid_max for r in res),
+           "levels_done": res[owner].levels_done, "slabs": layout}
+    if want_level:
+        y = np.zeros(Nx)
+        z = np.zeros(Nx)
+        for (oy, oz), sl in zip(outs, layout):
+            lo = sl["local"][0]
+            a, b = sl["own"]
+            y[a:b] = oy[a - lo:b - lo]
+            z[a:b] = oz[a - lo:b - lo]
+        out["y"], out["z"] = y, z
+    for s in solvers:
+        s.close()
+    return out
