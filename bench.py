@@ -612,6 +612,15 @@ def run_batch(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def flops_per_gp_step_2d32(k: int, L: int) -> float:
+    """FP32C 2-D: per tensor node 15 weight products, per field three value
+    increments (3 ops each) and 15 FMA, a compensated accumulation (~10) for
+    the three fields, the driver (3) and the three driver sums (3); counted as
+    operations (an FMA as 2 flop); per point the group sums and Picard."""
+    per_node = 15 + 3 * (9 + 15 * 2) + 3 * 10 + 3 * 2 + 3 * 2
+    return k * L * L * per_node + 9 * 6 + 10 * 6
+
+
 def flops_per_gp_step_2d(k: int, L: int) -> float:
     """Algorithmic FP64 flops of one 2-D grid-point step: per tensor node three
     bicubic values (12 FMA each), the linear driver (2 FMA + 1 mul) and the
@@ -624,7 +633,8 @@ def flops_per_gp_step_2d(k: int, L: int) -> float:
 def run_2d(args, rank, world, local_rank):
     """Example 4 (Eq. 34-35) at the paper's largest configuration (Table 9:
     K = 6, N = 64, M = 1024 intervals per dimension on [-8, 8]^2, L = 8 per
-    dimension), FP64; one step = one whole solve."""
+    dimension), in --precision (FP32C by default, FP64 on request); one step =
+    one whole solve."""
     import torch
     from paper_1909_13560_gb300 import bsde as B
     from paper_1909_13560_gb300 import workloads as W
@@ -635,7 +645,8 @@ def run_2d(args, rank, world, local_rank):
     sp = stream.cuda_stream
     K, N, M, L = 6, 64, 1024, 8
     p = W.ex4_problem(M=M, N=N, k=K, L=L)
-    s = B.Solver2(p, device=dev)
+    prec = args.precision
+    s = B.Solver2(p, device=dev, precision=prec)
     np_ = p["Nx1"] * p["Nx2"]
     units = np_ * (N - K + 1)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -693,8 +704,9 @@ def run_2d(args, rank, world, local_rank):
         del g
     peaks = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = _alu_peak_tflops("fp64", sm_max)
-    step_flops = flops_per_gp_step_2d(K, L) * np_
+    peak = _alu_peak_tflops(prec, sm_max)
+    fpg = flops_per_gp_step_2d(K, L) if prec == "fp64" else flops_per_gp_step_2d32(K, L)
+    step_flops = fpg * np_
     achieved = step_flops / (times["k2_step"] / 1000.0) / 1e12
     # derivative kernel: reads the new values (24 B) and writes the ring
     # records (96 B) per point
@@ -740,11 +752,12 @@ def run_2d(args, rank, world, local_rank):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic",
+            "dtype": "f64" if prec == "fp64" else "f32", "data": "synthetic",
             "config": {"workload": "ex4_2d: two-dimensional Example 4 (f = y - (z1+z2)/2, "
                                    "g = sin(x1+x2+T), X = W), x in [-8,8]^2, M=1024 intervals "
                                    "per dimension (1025^2 points), N=64, K=6, L=8 per dimension "
-                                   "(64 tensor nodes), FP64; one solve per step",
+                                   f"(64 tensor nodes), {prec.upper()}; one solve per step",
+                       "precision": prec,
                        "Nx1": p["Nx1"], "Nx2": p["Nx2"], "N": N, "k": K, "L": L,
                        "l2": "flushed between steps (256 MiB write, outside the timed events); "
                              "the level ring (700 MB) is HBM-resident",
@@ -754,10 +767,14 @@ def run_2d(args, rank, world, local_rank):
                          "err_y0": ey, "err_z0_norm": ez,
                          "within_tol": abs(ey - 8.00e-7) <= 0.02 * 8.00e-7
                          and abs(ez - 2.32e-6) <= 0.02 * 2.32e-6},
-            "roofline": {"kernel": "k2_step", "bound": "alu", "achieved": achieved, "peak": peak,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                         "peak_source": f"derived: 152 SMs x 2 FP64 FMA units x 2 flop x {sm_max:.0f} MHz",
-                         "flop_per_gp_step": flops_per_gp_step_2d(K, L),
+                         "kernel": "k2_step" if prec == "fp64" else "k2_step32",
+                         "peak_source": (f"derived: 152 SMs x 2 FP64 FMA units x 2 flop x {sm_max:.0f} MHz"
+                                         if prec == "fp64" else
+                                         f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz"),
+                         "flop_per_gp_step": fpg,
+                         "l1_bytes_per_gp_step": K * L * L * (384 if prec == "fp64" else 256),
                          "step_launch_ms": times["k2_step"],
                          "deriv": {"kernel": "k2_deriv", "bound": "hbm", "achieved": der_gbs,
                                    "peak": hbm, "unit": "GB/s", "frac": der_gbs / hbm,

@@ -52,7 +52,10 @@ enum {
 
 typedef struct bsde2_problem {
   int32_t driver, terminal;
-  int32_t precision;  /* BSDE_FP64 (the only precision of the 2-D path)           */
+  int32_t precision;  /* BSDE_FP64, or BSDE_FP32C: level values as float pairs,
+                         derivatives as floats, the bicubic increment over the
+                         cell's corner value in FP32, compensated sums, Picard
+                         on the increment in FP32 (derivatives computed in FP64) */
   int32_t picard_max; /* Picard iteration cap (paper: 30)                         */
   int32_t N, k, L;    /* time steps, steps of the scheme (1..min(6, N)), GH nodes
                          per dimension (1..16)                                    */
@@ -80,7 +83,8 @@ typedef struct bsde2_plan_s bsde2_plan_t;
  * grid point (96 B), one plane of new values (24 B per point), the node
  * table, a staging area of 3 k planes and the statistics.  BSDE_EINVAL for a
  * bad problem (k outside 1..min(6, N), Nx1 or Nx2 < 6, L outside 1..16, x0
- * outside the box, unknown id, precision other than FP64, T <= 0). */
+ * outside the box, unknown id or precision, T <= 0).  FP32C keeps one 64-byte
+ * record per point and level instead of 96 bytes. */
 BSDE_API int bsde2_workspace_bytes(const bsde2_problem *p, size_t *bytes);
 
 /* Validate *p, build the node table on the host (per (j, l1, l2): the cell

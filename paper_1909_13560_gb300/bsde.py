@@ -576,11 +576,11 @@ def l2_read_bandwidth(mib: int = 48, reps: int = 40, device=None) -> float:
 
 # --- two space dimensions (include/bsde2d.h) ---------------------------------
 
-def make_problem2(p: dict) -> bsde2_problem:
+def make_problem2(p: dict, precision: str = "fp64") -> bsde2_problem:
     s = bsde2_problem()
     s.driver = BSDE2_DRIVER[p["driver"]]
     s.terminal = BSDE2_TERMINAL[p["terminal"]]
-    s.precision = BSDE_PRECISION["fp64"]
+    s.precision = BSDE_PRECISION[precision]
     s.picard_max = int(p.get("picard_max", 30))
     s.N, s.k, s.L = int(p["N"]), int(p["k"]), int(p["L"])
     s.Nx1, s.Nx2 = int(p["Nx1"]), int(p["Nx2"])
@@ -601,13 +601,14 @@ def bsde2_workspace_bytes(prob: bsde2_problem) -> int:
 class Solver2:
     """One two-dimensional problem, one device workspace, one plan."""
 
-    def __init__(self, problem: dict, device=None):
+    def __init__(self, problem: dict, device=None, precision: str = "fp64"):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("the BSDE solver needs a CUDA device (no CPU fallback)")
         self.problem = dict(problem)
+        self.precision = precision
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
-        self._prob = make_problem2(problem)
+        self._prob = make_problem2(problem, precision)
         self.ws_bytes = bsde2_workspace_bytes(self._prob)
         with torch.cuda.device(self.device):
             self.workspace = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=self.device)
@@ -686,8 +687,8 @@ class Solver2:
             pass
 
 
-def solve2(problem: dict, init=None, want_level: bool = False) -> dict:
-    s = Solver2(problem)
+def solve2(problem: dict, init=None, want_level: bool = False, precision: str = "fp64") -> dict:
+    s = Solver2(problem, precision=precision)
     try:
         return s.solve(init=init, want_level=want_level)
     finally:

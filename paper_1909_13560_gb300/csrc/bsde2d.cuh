@@ -13,14 +13,15 @@ constexpr int kDerTX = 32, kDerTY = 8, kDerH = 4;  // derivative tile and halo
 
 struct Params2 {
   int64_t Nx1, Nx2, Np;
-  int32_t N, k, L, LL, nslot, picard_max, terminal, pad;
+  int32_t N, k, L, LL, nslot, picard_max, terminal, precision;
+  float picard_tol_f, alpha_f, beta1_f, beta2_f, hg0_f, pad_f[3];
   double T, dt, dx1, dx2, x1_min, x1_max, x2_min, x2_max, x01, x02;
   double a1, a2, b11, b21, b22, alpha, beta1, beta2, picard_tol;
   double gy[kMaxK + 1], gz[kMaxK + 1];
   double h, hg0;
   // work split: S chunks of Lg nodes per j, G = k S groups per point;
   // per j the range of cell shifts in each dimension (clamp-free fast path)
-  int32_t S, Lg, G, pad2;
+  int32_t S, Lg, G, LLp;  // LLp = ceil(L^2 / 2) mirror pairs (FP32C)
   int32_t s1min[kMaxK], s1max[kMaxK], s2min[kMaxK], s2max[kMaxK];
 };
 
@@ -37,6 +38,41 @@ struct Node2 {
   double h1[4], h2[4];
   double cz, cfz1, cfz2, cfy, cy;
 };
+
+// FP32C pair entry (112 B): tensor nodes a = (l1, l2) and b = (L-1-l1,
+// L-1-l2) mirror each other (DeltaW_b = -DeltaW_a, equal weight), so the pair
+// is processed together: the two values' hi parts are added exactly before
+// one compensated product, and the driver terms enter as cfz (F_a - F_b) and
+// cfy (F_a + F_b), whose FP32 rounding scales with the small difference
+// rather than with F.  Per node the cell shift and the Hermite basis of theta
+// in each dimension; weights as floats (cz, cy split hi + lo).  The middle
+// node of an odd L pairs with itself at half weight.
+struct Node2f {
+  int32_t s1a, s2a, s1b, s2b;
+  float h1a[4], h2a[4], h1b[4], h2b[4];
+  float czh, czl, cyh, cyl;
+  float cfz1, cfz2, cfy, pad;
+};
+
+// FP32C level record of a grid point (64 B, four float4): the three fields'
+// values as float pairs hi + lo and their scaled derivatives as floats
+//   V0 = (y_hi, z1_hi, z2_hi, y_lo)       V1 = (z1_lo, z2_lo, y_fx, z1_fx)
+//   V2 = (z2_fx, y_fy, z1_fy, z2_fy)      V3 = (y_fxy, z1_fxy, z2_fxy, 0)
+// The ring keeps the four float4 of a record in four planes of Np entries
+// per level (a warp's 16-byte loads of one plane are then contiguous).
+struct Rec2f {
+  float4 v0, v1, v2, v3;
+};
+struct Lev2f {
+  const float4 *p0, *p1, *p2, *p3;
+};
+__host__ __device__ inline Lev2f lev2f(const float4 *ring, int64_t Np, int slot) {
+  const float4 *b = ring + int64_t(slot) * 4 * Np;
+  return Lev2f{b, b + Np, b + 2 * Np, b + 3 * Np};
+}
+__device__ __forceinline__ Rec2f load_rec(const Lev2f &L, int64_t q) {
+  return Rec2f{L.p0[q], L.p1[q], L.p2[q], L.p3[q]};
+}
 
 struct Stats2 {
   Stats s;       // y0 and the Picard statistics (z0 holds z1)
@@ -340,6 +376,365 @@ __global__ void k2_reset_stats(Stats2 *s) {
 }
 
 // ---------------------------------------------------------------------------
+// FP32C form of the 2-D path.  A bicubic value is kept as hi_00 + del: the
+// corner (c1, c2)'s value hi part plus, in FP32, the increments of the other
+// corners' values over it (the value weights sum to one), the corner's lo
+// part and the derivative terms -- all of size dx |grad v|, so their
+// rounding is far below that of the value.  The expectations take the exact
+// product of the weight's hi part with hi_00 (FMA error term) and add it by
+// TwoSum (comp_acc1); the driver terms are summed in plain FP32; z^n and A
+// are formed as float pairs and y^n by Picard on the increment, as in the 1-D
+// FP32C step.  Derivatives of a new level come from the FP64 values.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kDerTX * kDerTY)
+    k2_deriv32(const Params2 P, const double *__restrict__ V, float4 *__restrict__ ring,
+               int slot) {
+  constexpr int W = kDerTX + 2 * kDerH, H = kDerTY + 2 * kDerH;
+  __shared__ double sv[H][W];
+  __shared__ double sy[kDerTY][W];
+  wait_predecessor();
+  const int x0 = blockIdx.x * kDerTX, y0 = blockIdx.y * kDerTY;
+  const int n1 = int(P.Nx1), n2 = int(P.Nx2);
+  const int tid = threadIdx.x;
+  // one point per thread (kDerTX * kDerTY threads)
+  const int r = tid / kDerTX, c = tid % kDerTX;
+  const int i1 = x0 + c, i2 = y0 + r;
+  double val[3], fx[3], fy[3], fxy[3];
+  for (int f = 0; f < 3; ++f) {
+    const double *v = V + int64_t(f) * P.Np;
+    for (int e = tid; e < H * W; e += blockDim.x) {
+      const int rr = e / W, cc = e % W;
+      int g2 = y0 - kDerH + rr, g1 = x0 - kDerH + cc;
+      g2 = g2 < 0 ? 0 : (g2 >= n2 ? n2 - 1 : g2);
+      g1 = g1 < 0 ? 0 : (g1 >= n1 ? n1 - 1 : g1);
+      sv[rr][cc] = v[int64_t(g2) * n1 + g1];
+    }
+    __syncthreads();
+    for (int e = tid; e < kDerTY * W; e += blockDim.x) {
+      const int rr = e / W, cc = e % W;
+      const int j2 = y0 + rr;
+      sy[rr][cc] = j2 < n2 ? fd4(&sv[rr + kDerH][cc], W, j2, n2) : 0.0;
+    }
+    __syncthreads();
+    val[f] = fx[f] = fy[f] = fxy[f] = 0.0;
+    if (i1 < n1 && i2 < n2) {
+      val[f] = sv[r + kDerH][c + kDerH];
+      fx[f] = fd4(&sv[r + kDerH][c + kDerH], 1, i1, n1);
+      fy[f] = sy[r][c + kDerH];
+      fxy[f] = fd4(&sy[r][c + kDerH], 1, i1, n1);
+    }
+    __syncthreads();
+  }
+  if (i1 < n1 && i2 < n2) {
+    float hi[3], lo[3];
+    for (int f = 0; f < 3; ++f) {
+      hi[f] = __double2float_rn(val[f]);
+      lo[f] = __double2float_rn(__dsub_rn(val[f], double(hi[f])));
+    }
+    float4 *b = ring + int64_t(slot) * 4 * P.Np + int64_t(i2) * n1 + i1;
+    b[0] = make_float4(hi[0], hi[1], hi[2], lo[0]);
+    b[P.Np] = make_float4(lo[1], lo[2], float(fx[0]), float(fx[1]));
+    b[2 * P.Np] = make_float4(float(fx[2]), float(fy[0]), float(fy[1]), float(fy[2]));
+    b[3 * P.Np] = make_float4(float(fxy[0]), float(fxy[1]), float(fxy[2]), 0.f);
+  }
+}
+
+// hi_00 and del of one field from the four corner records (see Rec2f);
+// w: W10 W01 W11 | X00 X10 X01 X11 | Y00 Y10 Y01 Y11 | Z00 Z10 Z01 Z11
+__device__ __forceinline__ void field2f(float h00, float l00, float h10, float l10, float h01,
+                                        float l01, float h11, float l11, float4 fx, float4 fy,
+                                        float4 fxy, const float *w, float &hi, float &del) {
+  const float d10 = __fadd_rn(__fsub_rn(h10, h00), __fsub_rn(l10, l00));
+  const float d01 = __fadd_rn(__fsub_rn(h01, h00), __fsub_rn(l01, l00));
+  const float d11 = __fadd_rn(__fsub_rn(h11, h00), __fsub_rn(l11, l00));
+  float s = l00;
+  s = __fmaf_rn(d10, w[0], s);
+  s = __fmaf_rn(d01, w[1], s);
+  s = __fmaf_rn(d11, w[2], s);
+  s = __fmaf_rn(fx.x, w[3], s);
+  s = __fmaf_rn(fx.y, w[4], s);
+  s = __fmaf_rn(fx.z, w[5], s);
+  s = __fmaf_rn(fx.w, w[6], s);
+  s = __fmaf_rn(fy.x, w[7], s);
+  s = __fmaf_rn(fy.y, w[8], s);
+  s = __fmaf_rn(fy.z, w[9], s);
+  s = __fmaf_rn(fy.w, w[10], s);
+  s = __fmaf_rn(fxy.x, w[11], s);
+  s = __fmaf_rn(fxy.y, w[12], s);
+  s = __fmaf_rn(fxy.z, w[13], s);
+  s = __fmaf_rn(fxy.w, w[14], s);
+  hi = h00;
+  del = s;
+}
+
+struct Acc2f {
+  float Sy, Cy, S1, C1, S2, C2, Fy, F1, F2, FyC;  // Fy + FyC: the y driver terms (TwoSum)
+};
+
+// The bicubic value (hi, del) of the three fields at one node, from its cell
+// shift and Hermite basis (clamped onto the box in CLAMP mode).
+template <bool CLAMP>
+__device__ __forceinline__ void node2f_values(const Params2 &P, const Lev2f &lev,
+                                              int i1, int i2, int s1, int s2, const float *h1in,
+                                              const float *h2in, float *hi, float *del) {
+  const int n1 = int(P.Nx1), n2 = int(P.Nx2);
+  int c1 = i1 + s1, c2 = i2 + s2;
+  float h1[4], h2[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    h1[u] = h1in[u];
+    h2[u] = h2in[u];
+  }
+  if (CLAMP) {
+    if (c1 < 0 || c1 > n1 - 2) {
+      const bool lo = c1 < 0;
+      c1 = lo ? 0 : n1 - 2;
+      h1[0] = lo ? 1.f : 0.f;
+      h1[1] = lo ? 0.f : 1.f;
+      h1[2] = h1[3] = 0.f;
+    }
+    if (c2 < 0 || c2 > n2 - 2) {
+      const bool lo = c2 < 0;
+      c2 = lo ? 0 : n2 - 2;
+      h2[0] = lo ? 1.f : 0.f;
+      h2[1] = lo ? 0.f : 1.f;
+      h2[2] = h2[3] = 0.f;
+    }
+  }
+  float w[15];
+  w[0] = h1[1] * h2[0];
+  w[1] = h1[0] * h2[1];
+  w[2] = h1[1] * h2[1];
+  w[3] = h1[2] * h2[0];
+  w[4] = h1[3] * h2[0];
+  w[5] = h1[2] * h2[1];
+  w[6] = h1[3] * h2[1];
+  w[7] = h1[0] * h2[2];
+  w[8] = h1[1] * h2[2];
+  w[9] = h1[0] * h2[3];
+  w[10] = h1[1] * h2[3];
+  w[11] = h1[2] * h2[2];
+  w[12] = h1[3] * h2[2];
+  w[13] = h1[2] * h2[3];
+  w[14] = h1[3] * h2[3];
+  const int64_t q00 = int64_t(c2) * n1 + c1;
+  const Rec2f A = load_rec(lev, q00), Bq = load_rec(lev, q00 + 1), C = load_rec(lev, q00 + n1),
+              D = load_rec(lev, q00 + n1 + 1);
+  field2f(A.v0.x, A.v0.w, Bq.v0.x, Bq.v0.w, C.v0.x, C.v0.w, D.v0.x, D.v0.w,
+          make_float4(A.v1.z, Bq.v1.z, C.v1.z, D.v1.z), make_float4(A.v2.y, Bq.v2.y, C.v2.y, D.v2.y),
+          make_float4(A.v3.x, Bq.v3.x, C.v3.x, D.v3.x), w, hi[0], del[0]);
+  field2f(A.v0.y, A.v1.x, Bq.v0.y, Bq.v1.x, C.v0.y, C.v1.x, D.v0.y, D.v1.x,
+          make_float4(A.v1.w, Bq.v1.w, C.v1.w, D.v1.w), make_float4(A.v2.z, Bq.v2.z, C.v2.z, D.v2.z),
+          make_float4(A.v3.y, Bq.v3.y, C.v3.y, D.v3.y), w, hi[1], del[1]);
+  field2f(A.v0.z, A.v1.y, Bq.v0.z, Bq.v1.y, C.v0.z, C.v1.y, D.v0.z, D.v1.y,
+          make_float4(A.v2.x, Bq.v2.x, C.v2.x, D.v2.x), make_float4(A.v2.w, Bq.v2.w, C.v2.w, D.v2.w),
+          make_float4(A.v3.z, Bq.v3.z, C.v3.z, D.v3.z), w, hi[2], del[2]);
+}
+
+template <bool CLAMP>
+__device__ __forceinline__ void nodes2f(const Params2 &P, const Lev2f &lev,
+                                        const Node2f *row, int q0, int q1, int i1, int i2,
+                                        bool yj, Acc2f &a) {
+#pragma unroll 1
+  for (int q = q0; q < q1; ++q) {
+    const Node2f &e = row[q];
+    float ha[3], da[3], hb[3], db[3];
+    node2f_values<CLAMP>(P, lev, i1, i2, e.s1a, e.s2a, e.h1a, e.h2a, ha, da);
+    node2f_values<CLAMP>(P, lev, i1, i2, e.s1b, e.s2b, e.h1b, e.h2b, hb, db);
+    const float Fa = __fmaf_rn(P.alpha_f, __fadd_rn(ha[0], da[0]),
+                               __fmaf_rn(P.beta1_f, __fadd_rn(ha[1], da[1]),
+                                         __fmul_rn(P.beta2_f, __fadd_rn(ha[2], da[2]))));
+    const float Fb = __fmaf_rn(P.alpha_f, __fadd_rn(hb[0], db[0]),
+                               __fmaf_rn(P.beta1_f, __fadd_rn(hb[1], db[1]),
+                                         __fmul_rn(P.beta2_f, __fadd_rn(hb[2], db[2]))));
+    // F_a - F_b of the linear driver from the fields' differences: the hi
+    // parts of neighbouring values subtract exactly, so the difference keeps
+    // the accuracy of its small size rather than inheriting F's rounding
+    float dv[3];
+#pragma unroll
+    for (int f = 0; f < 3; ++f) dv[f] = __fadd_rn(__fsub_rn(ha[f], hb[f]), __fsub_rn(da[f], db[f]));
+    const float dF = __fmaf_rn(P.alpha_f, dv[0], __fmaf_rn(P.beta1_f, dv[1], __fmul_rn(P.beta2_f, dv[2])));
+    a.F1 = __fmaf_rn(e.cfz1, dF, a.F1);
+    a.F2 = __fmaf_rn(e.cfz2, dF, a.F2);
+    // sum k dt gy_j E[f] reaches O(k dt |f|): accumulated with its error
+    two_sum_into(a.Fy, a.FyC, __fmul_rn(e.cfy, __fadd_rn(Fa, Fb)));
+    // the pair's hi parts summed exactly, then one compensated product
+    float hs, he;
+#pragma unroll
+    for (int f = 1; f < 3; ++f) {
+      hs = ha[f];
+      he = 0.f;
+      two_sum_into(hs, he, hb[f]);
+      const float dd = __fadd_rn(__fadd_rn(da[f], db[f]), he);
+      if (f == 1)
+        comp_acc1(a.S1, a.C1, e.czh, e.czl, hs, dd);
+      else
+        comp_acc1(a.S2, a.C2, e.czh, e.czl, hs, dd);
+    }
+    if (yj) {
+      hs = ha[0];
+      he = 0.f;
+      two_sum_into(hs, he, hb[0]);
+      comp_acc1(a.Sy, a.Cy, e.cyh, e.cyl, hs, __fadd_rn(__fadd_rn(da[0], db[0]), he));
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kStep2TP * kMaxGroups, 2)
+    k2_step32(const Params2 P, const float4 *__restrict__ ring, double *__restrict__ V,
+              const Node2f *__restrict__ table, int n, Stats *st) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int kLL = P.k * P.LLp;
+  Node2f *tab = reinterpret_cast<Node2f *>(smem_raw);
+  float *part = reinterpret_cast<float *>(tab + kLL);  // [10][G][kStep2TP]
+  {
+    const float4 *src = reinterpret_cast<const float4 *>(table);
+    float4 *dst = reinterpret_cast<float4 *>(tab);
+    const int nv = kLL * int(sizeof(Node2f) / 16);
+    for (int t = threadIdx.x; t < nv; t += blockDim.x) dst[t] = src[t];
+  }
+  __syncthreads();
+  wait_predecessor();
+  const int tp = threadIdx.x % kStep2TP, g = threadIdx.x / kStep2TP;
+  const int64_t q0p = int64_t(blockIdx.x) * kStep2TP;
+  const int64_t qq = q0p + tp;
+  const bool active = qq < P.Np;
+  const int n1 = int(P.Nx1), n2 = int(P.Nx2);
+  Acc2f a{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  // the Picard start y^{n+1} of this thread's point, loaded early
+  float prev_h = 0.f, prev_l = 0.f;
+  if (g == 0 && active) {
+    const float4 v0 = lev2f(ring, P.Np, (n + 1) % P.nslot).p0[qq];
+    prev_h = v0.x;
+    prev_l = v0.w;
+  }
+  if (active) {
+    const int j = g / P.S + 1, lc = g % P.S;
+    const int a0 = lc * P.Lg, a1 = a0 + P.Lg < P.LLp ? a0 + P.Lg : P.LLp;
+    const int i1 = int(qq % n1), i2 = int(qq / n1);
+    const int64_t qe = (q0p + kStep2TP <= P.Np ? q0p + kStep2TP : P.Np) - 1;
+    const int r0 = int(q0p / n1), r1 = int(qe / n1);
+    const int cmin = r0 == r1 ? int(q0p % n1) : 0, cmax = r0 == r1 ? int(qe % n1) : n1 - 1;
+    const bool interior = cmin + P.s1min[j - 1] >= 0 && cmax + P.s1max[j - 1] <= n1 - 2 &&
+                          r0 + P.s2min[j - 1] >= 0 && r1 + P.s2max[j - 1] <= n2 - 2;
+    const Lev2f lev = lev2f(ring, P.Np, (n + j) % P.nslot);
+    const Node2f *row = tab + (j - 1) * P.LLp;
+    if (interior)
+      nodes2f<false>(P, lev, row, a0, a1, i1, i2, j == P.k, a);
+    else
+      nodes2f<true>(P, lev, row, a0, a1, i1, i2, j == P.k, a);
+  }
+  const int G = P.G, gs = G * kStep2TP, o = g * kStep2TP + tp;
+  part[0 * gs + o] = a.Sy;
+  part[1 * gs + o] = a.Cy;
+  part[2 * gs + o] = a.S1;
+  part[3 * gs + o] = a.C1;
+  part[4 * gs + o] = a.S2;
+  part[5 * gs + o] = a.C2;
+  part[6 * gs + o] = a.Fy;
+  part[7 * gs + o] = a.F1;
+  part[8 * gs + o] = a.F2;
+  part[9 * gs + o] = a.FyC;
+  __syncthreads();
+  if (g != 0) return;
+  int it = 0;
+  float d = 0.f;
+  if (active) {
+    float yS = 0.f, yC = 0.f, z1S = 0.f, z1C = 0.f, z2S = 0.f, z2C = 0.f, fy = 0.f, f1 = 0.f,
+          f2 = 0.f, fyC = 0.f;
+    for (int u = 0; u < G; ++u) {
+      const int ou = u * kStep2TP + tp;
+      two_sum_into(yS, yC, part[0 * gs + ou]);
+      yC = __fadd_rn(yC, part[1 * gs + ou]);
+      two_sum_into(z1S, z1C, part[2 * gs + ou]);
+      z1C = __fadd_rn(z1C, part[3 * gs + ou]);
+      two_sum_into(z2S, z2C, part[4 * gs + ou]);
+      z2C = __fadd_rn(z2C, part[5 * gs + ou]);
+      two_sum_into(fy, fyC, part[6 * gs + ou]);
+      fyC = __fadd_rn(fyC, part[9 * gs + ou]);
+      f1 = __fadd_rn(f1, part[7 * gs + ou]);
+      f2 = __fadd_rn(f2, part[8 * gs + ou]);
+    }
+    // z_d = S + (C + F) and A = S + (C + F) as exact float pairs
+    float z1h = z1S, z1l = 0.f, z2h = z2S, z2l = 0.f, Ah = yS, Al = 0.f;
+    two_sum_into(z1h, z1l, __fadd_rn(z1C, f1));
+    two_sum_into(z2h, z2l, __fadd_rn(z2C, f2));
+    two_sum_into(Ah, Al, fy);
+    two_sum_into(Ah, Al, __fadd_rn(yC, fyC));
+    const float zlin = __fmaf_rn(P.beta1_f, z1h, __fmul_rn(P.beta2_f, z2h));
+    // Picard on the increment delta = y^n - A: delta = hg0 f(A + delta, z)
+    float dl = __fadd_rn(__fsub_rn(prev_h, Ah), __fsub_rn(prev_l, Al));
+    float dpp = __int_as_float(0x7fc00000);
+    while (it < P.picard_max) {
+      const float dn = __fmul_rn(P.hg0_f, __fmaf_rn(P.alpha_f, __fadd_rn(Ah, dl), zlin));
+      ++it;
+      d = fabsf(__fsub_rn(dn, dl));
+      const bool cyc = dn == dpp;
+      dpp = dl;
+      dl = dn;
+      if (cyc) d = 0.f;
+      if (d <= P.picard_tol_f) break;
+    }
+    V[qq] = double(Ah) + (double(Al) + double(dl));
+    V[P.Np + qq] = double(z1h) + double(z1l);
+    V[2 * P.Np + qq] = double(z2h) + double(z2l);
+  }
+  record_picard(st, active, it, double(d), P.picard_tol);
+}
+
+__device__ double interp2_point32(const Params2 &P, const Lev2f &lev, int field, double X1,
+                                  double X2) {
+  auto locate = [](double X, double xmin, double xmax, double dx, int64_t n, int64_t &c,
+                   double &th) {
+    X = X < xmin ? xmin : (X > xmax ? xmax : X);
+    const double s = (X - xmin) / dx;
+    int64_t q = int64_t(floor(s));
+    q = q < 0 ? 0 : (q > n - 2 ? n - 2 : q);
+    c = q;
+    th = s - double(q);
+  };
+  int64_t c1, c2;
+  double t1, t2, h1[4], h2[4];
+  locate(X1, P.x1_min, P.x1_max, P.dx1, P.Nx1, c1, t1);
+  locate(X2, P.x2_min, P.x2_max, P.dx2, P.Nx2, c2, t2);
+  hermite4(t1, h1);
+  hermite4(t2, h2);
+  auto rec = [&](int64_t q) {
+    const Rec2f R = load_rec(lev, q);
+    double4_32a o;
+    if (field == 0) {
+      o = make_double4_32a(double(R.v0.x) + double(R.v0.w), R.v1.z, R.v2.y, R.v3.x);
+    } else if (field == 1) {
+      o = make_double4_32a(double(R.v0.y) + double(R.v1.x), R.v1.w, R.v2.z, R.v3.y);
+    } else {
+      o = make_double4_32a(double(R.v0.z) + double(R.v1.y), R.v2.x, R.v2.w, R.v3.z);
+    }
+    return o;
+  };
+  const int64_t b = c2 * P.Nx1 + c1;
+  return bicubic(rec(b), rec(b + 1), rec(b + P.Nx1), rec(b + P.Nx1 + 1), h1, h2);
+}
+
+__global__ void k2_readout32(const Params2 P, const float4 *ring, int slot, Stats2 *st) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const Lev2f lev = lev2f(ring, P.Np, slot);
+  st->s.y0 = interp2_point32(P, lev, 0, P.x01, P.x02);
+  st->s.z0 = interp2_point32(P, lev, 1, P.x01, P.x02);
+  st->z0b = interp2_point32(P, lev, 2, P.x01, P.x02);
+}
+
+__global__ void k2_export32(const Params2 P, const float4 *ring, int slot, double *out) {
+  const Lev2f lev = lev2f(ring, P.Np, slot);
+  for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < P.Np;
+       q += int64_t(gridDim.x) * blockDim.x) {
+    const Rec2f R = load_rec(lev, q);
+    out[q] = double(R.v0.x) + double(R.v0.w);
+    out[P.Np + q] = double(R.v0.y) + double(R.v1.x);
+    out[2 * P.Np + q] = double(R.v0.z) + double(R.v1.y);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Host side: validation, constants, layout.
 // ---------------------------------------------------------------------------
 struct Layout2 {
@@ -358,7 +753,7 @@ static int validate2(const bsde2_problem &p) {
   if (p.driver != BSDE2_DRIVER_LINEAR) return BSDE_EINVAL;
   if (p.terminal != BSDE2_TERMINAL_SIN_SUM && p.terminal != BSDE2_TERMINAL_SPREAD_LOG)
     return BSDE_EINVAL;
-  if (p.precision != BSDE_FP64) return BSDE_EINVAL;
+  if (p.precision != BSDE_FP64 && p.precision != BSDE_FP32C) return BSDE_EINVAL;
   if (p.picard_max < 1 || !(p.picard_tol >= 0.0)) return BSDE_EINVAL;
   return BSDE_OK;
 }
@@ -368,13 +763,49 @@ static Layout2 layout2(const bsde2_problem &p) {
   const size_t np = size_t(p.Nx1) * size_t(p.Nx2), ns = size_t(p.k + 1);
   Layout2 L{};
   size_t off = 0;
-  L.ring = off; off = up(off + ns * 3 * np * 32);
+  // FP64: 3 fields x 32-byte records per point; FP32C: four float4 planes
+  L.ring = off; off = up(off + ns * np * (p.precision == BSDE_FP64 ? 96 : sizeof(Rec2f)));
   L.vals = off; off = up(off + 3 * np * 8);
   L.table = off; off = up(off + size_t(p.k) * p.L * p.L * sizeof(Node2));
   L.stage = off; off = up(off + 3 * size_t(p.k) * np * 8);
   L.stats = off; off = up(off + sizeof(Stats2));
   L.total = off;
   return L;
+}
+
+// The FP32C pair table from the FP64 node table: pair q of level j joins
+// nodes q and L^2 - 1 - q ((l1, l2) and (L-1-l1, L-1-l2)); the middle node
+// of an odd L is a pair with itself at half weight.
+static void build_pairs2f(const Params2 &P, const std::vector<Node2> &tab,
+                          std::vector<Node2f> &out) {
+  out.assign(size_t(P.k) * P.LLp, Node2f{});
+  for (int j = 0; j < P.k; ++j) {
+    for (int q = 0; q < P.LLp; ++q) {
+      const Node2 &a = tab[size_t(j) * P.LL + q];
+      const Node2 &b = tab[size_t(j) * P.LL + (P.LL - 1 - q)];
+      const double half = (q == P.LL - 1 - q) ? 0.5 : 1.0;
+      Node2f f{};
+      f.s1a = a.s1;
+      f.s2a = a.s2;
+      f.s1b = b.s1;
+      f.s2b = b.s2;
+      for (int u = 0; u < 4; ++u) {
+        f.h1a[u] = float(a.h1[u]);
+        f.h2a[u] = float(a.h2[u]);
+        f.h1b[u] = float(b.h1[u]);
+        f.h2b[u] = float(b.h2[u]);
+      }
+      const double cz = a.cz * half, cy = a.cy * half;
+      f.czh = float(cz);
+      f.czl = float(cz - double(f.czh));
+      f.cyh = float(cy);
+      f.cyl = float(cy - double(f.cyh));
+      f.cfz1 = float(a.cfz1);  // node b's is -cfz (opposite DeltaW); 0 for the middle
+      f.cfz2 = float(a.cfz2);
+      f.cfy = float(a.cfy * half);
+      out[size_t(j) * P.LLp + q] = f;
+    }
+  }
 }
 
 static void plan2_constants(const bsde2_problem &p, Params2 &P, std::vector<Node2> &tab,
@@ -409,18 +840,31 @@ static void plan2_constants(const bsde2_problem &p, Params2 &P, std::vector<Node
   P.beta1 = p.beta1;
   P.beta2 = p.beta2;
   P.picard_tol = p.picard_tol;
+  P.precision = p.precision;
+  {
+    // |d| <= tol for a float d is exactly |d| <= the largest float <= tol
+    float tf = (float)p.picard_tol;
+    if ((double)tf > p.picard_tol) tf = std::nextafter(tf, 0.0f);
+    P.picard_tol_f = tf;
+  }
   gamma_tables(p.k, P.gy, P.gz);
   P.h = p.k * P.dt;
   P.hg0 = P.h * P.gy[0];
+  P.alpha_f = float(P.alpha);
+  P.beta1_f = float(P.beta1);
+  P.beta2_f = float(P.beta2);
+  P.hg0_f = float(P.hg0);
   // work split as in 1-D: >= 4 groups per point, at most kMaxGroups, no
   // more threads per level than the GPU holds at once when that is known
+  P.LLp = (P.LL + 1) / 2;
+  const int units = P.precision == BSDE_FP32C ? P.LLp : P.LL;
   int S = (4 + P.k - 1) / P.k;
   if (S * P.k > kMaxGroups) S = kMaxGroups / P.k;
-  if (S > P.LL) S = P.LL;
+  if (S > units) S = units;
   while (S > 1 && resident_threads > 0 && long(P.Np) * P.k * S > resident_threads) --S;
   if (S < 1) S = 1;
   P.S = S;
-  P.Lg = (P.LL + S - 1) / S;
+  P.Lg = (units + S - 1) / S;
   P.G = P.k * S;
   double a[kMaxL2], w[kMaxL2];
   gauss_hermite(p.L, a, w);
@@ -474,9 +918,21 @@ struct bsde2_plan_s {
 
 namespace bsde {
 
+static size_t step32_2d_smem(const Params2 &P) {
+  return sizeof(Node2f) * size_t(P.k) * P.LLp + sizeof(float) * 10 * size_t(P.G) * kStep2TP;
+}
+
 static void launch2_step(bsde2_plan_t *pl, cudaStream_t s, int n) {
   const Params2 &P = pl->P;
   const unsigned blocks = unsigned((P.Np + kStep2TP - 1) / kStep2TP);
+  if (P.precision == BSDE_FP32C) {
+    launch_pdl(k2_step32, blocks, unsigned(kStep2TP * P.G), step32_2d_smem(P), s, P,
+               reinterpret_cast<const float4 *>(pl->ws + pl->lay.ring),
+               reinterpret_cast<double *>(pl->ws + pl->lay.vals),
+               reinterpret_cast<const Node2f *>(pl->ws + pl->lay.table), n,
+               reinterpret_cast<Stats *>(pl->ws + pl->lay.stats));
+    return;
+  }
   launch_pdl(k2_step, blocks, unsigned(kStep2TP * P.G), 0, s, P,
              reinterpret_cast<const double4_32a *>(pl->ws + pl->lay.ring),
              reinterpret_cast<double *>(pl->ws + pl->lay.vals),
@@ -495,8 +951,13 @@ static void launch2_deriv(bsde2_plan_t *pl, cudaStream_t s, int slot) {
   lc.stream = s;
   lc.attrs = at;
   lc.numAttrs = 1;
-  cudaLaunchKernelEx(&lc, k2_deriv, P, reinterpret_cast<const double *>(pl->ws + pl->lay.vals),
-                     reinterpret_cast<double4_32a *>(pl->ws + pl->lay.ring), slot);
+  if (P.precision == BSDE_FP32C)
+    cudaLaunchKernelEx(&lc, k2_deriv32, P,
+                       reinterpret_cast<const double *>(pl->ws + pl->lay.vals),
+                       reinterpret_cast<float4 *>(pl->ws + pl->lay.ring), slot);
+  else
+    cudaLaunchKernelEx(&lc, k2_deriv, P, reinterpret_cast<const double *>(pl->ws + pl->lay.vals),
+                       reinterpret_cast<double4_32a *>(pl->ws + pl->lay.ring), slot);
 }
 
 static int64_t enqueue2_solve(bsde2_plan_t *pl, cudaStream_t s, bool imported) {
@@ -522,9 +983,16 @@ static int64_t enqueue2_solve(bsde2_plan_t *pl, cudaStream_t s, bool imported) {
     launch2_deriv(pl, s, n % P.nslot);
     launches += 2;
   }
-  k2_readout<<<1, 32, 0, s>>>(P, ring, 0, st);
-  // level 0 into the staging area (its first 3 planes)
-  k2_export<<<eb, 256, 0, s>>>(P, ring, 0, reinterpret_cast<double *>(pl->ws + pl->lay.stage));
+  double *out = reinterpret_cast<double *>(pl->ws + pl->lay.stage);
+  if (P.precision == BSDE_FP32C) {
+    const float4 *r32 = reinterpret_cast<const float4 *>(pl->ws + pl->lay.ring);
+    k2_readout32<<<1, 32, 0, s>>>(P, r32, 0, st);
+    k2_export32<<<eb, 256, 0, s>>>(P, r32, 0, out);
+  } else {
+    k2_readout<<<1, 32, 0, s>>>(P, ring, 0, st);
+    // level 0 into the staging area (its first 3 planes)
+    k2_export<<<eb, 256, 0, s>>>(P, ring, 0, out);
+  }
   launches += 2;
   return launches;
 }
@@ -594,8 +1062,19 @@ int bsde2_plan(const bsde2_problem *p, void *dev_workspace, size_t bytes, bsde2_
   pl->ws = static_cast<unsigned char *>(dev_workspace);
   std::vector<Node2> tab;
   plan2_constants(*p, pl->P, tab, resident_step_threads(pl->device));
-  cudaError_t e = cudaMemcpy(pl->ws + lay.table, tab.data(), sizeof(Node2) * tab.size(),
-                             cudaMemcpyHostToDevice);
+  cudaError_t e;
+  if (p->precision == BSDE_FP32C) {
+    std::vector<Node2f> t32;
+    build_pairs2f(pl->P, tab, t32);
+    e = cudaMemcpy(pl->ws + lay.table, t32.data(), sizeof(Node2f) * t32.size(),
+                   cudaMemcpyHostToDevice);
+    const size_t sm = step32_2d_smem(pl->P);
+    if (e == cudaSuccess && sm > 48 * 1024)
+      e = cudaFuncSetAttribute(k2_step32, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+  } else {
+    e = cudaMemcpy(pl->ws + lay.table, tab.data(), sizeof(Node2) * tab.size(),
+                   cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess) e = cudaMallocHost(&pl->host_stats, sizeof(Stats2));
   if (e != cudaSuccess) {
     delete pl;
