@@ -192,6 +192,7 @@ int fill_params(const bsde_problem &p, Params &P) {
   P.hg0 = P.h * P.gy[0];
   P.inv_gz0 = 1.0 / P.gz[0];
   P.inv_dx2_6 = 6.0 / (P.dx * P.dx);
+  P.inv_dx = 1.0 / P.dx;
   // LU pivots of tridiag(1, 4, 1): d_0 = 4, d_m = 4 - 1/d_{m-1}; they reach
   // 2 + sqrt(3) to double precision long before m = 64.
   double d = 4.0;

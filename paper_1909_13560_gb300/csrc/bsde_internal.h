@@ -99,6 +99,10 @@ struct Params {
   double hg0;     // K_y dt gy_0 (weight of the implicit term)
   double inv_gz0; // 1 / gz_0
   double inv_dx2_6; // 6 / dx^2
+  double inv_dx;    // 1 / dx (the general path's cell position: a multiply, not
+                    // a divide; it may move a node that lands within rounding
+                    // of a grid node to the neighbouring cell, where the spline
+                    // has the same value to rounding)
   double invd[kInvPivots];
   // work split of the step kernels: S l-chunks of Lg nodes per j, G = k S
   // groups per point; shift range per j (for the clamp-free fast path)

@@ -735,7 +735,7 @@ __global__ void __launch_bounds__(kStepTP * kMaxGroups)
     for (int l = l0; l < l1; ++l) {
       const NodeF64 &e = row[l];
       const double X = xi + drift + bx * e.dW;
-      const double s = (X - P.x_min) / P.dx;
+      const double s = (X - P.x_min) * P.inv_dx;
       double yh, zh;
       if (s <= 0.0) {  // off the grid: the end values (Section 3.2)
         const double4_32a a = lev[0];
