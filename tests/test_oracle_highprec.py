@@ -40,13 +40,16 @@ def test_picard_fixed_point_of_a_linear_driver(k):
 
 
 def _mp_scheme(k, Nx, N, L, x_lim, T, mp, kz=None, zform=0, start=None, stop=0,
-               return_all=False):
+               return_all=False, general=None):
     """Eq. 20-21 for f = y/2 - z, g = sin(x + T), X = W, at mp precision, with
     K_y = k and K_z = kz (default k; Eq. 16: K = max(K_y, K_z) levels), the
     z line's first term E[z^{n+1}] or (zform) E[y^{n+1} DeltaW_1] / dt, and
     the K initial levels from `start` ({level: (ys, zs)}) or the closed form.
     Runs levels N-K down to `stop`; returns level `stop` (y, z) at the grid
-    points, or every level ({level: (ys, zs)}) with return_all."""
+    points, or every level ({level: (ys, zs)}) with return_all.
+    general = (a0, a1, b0, b1): the forward process advanced by one Euler step,
+    X = x + (a0 + a1 x) j dt + (b0 + b1 x) DeltaW, with the short-rate driver
+    f = -X y (implicit step y = A / (1 + k dt gy_0 x))."""
     kz = k if kz is None else kz
     K = max(k, kz)
     dt = mp.mpf(T) / N
@@ -122,9 +125,14 @@ def _mp_scheme(k, Nx, N, L, x_lim, T, mp, kz=None, zform=0, start=None, stop=0,
                 ez = efdw = ef = mp.mpf(0)
                 for a, w in zip(nodes, wts):
                     dW = mp.sqrt(2 * j * dt) * a
-                    yh = interp(vy, My, x + dW)
-                    zh = interp(vz, Mz, x + dW)
-                    F = yh / 2 - zh
+                    if general is None:
+                        X = x + dW
+                    else:
+                        a0, a1, b0, b1 = general
+                        X = x + (a0 + a1 * x) * j * dt + (b0 + b1 * x) * dW
+                    yh = interp(vy, My, X)
+                    zh = interp(vz, Mz, X)
+                    F = yh / 2 - zh if general is None else -X * yh
                     ez += w * rpi * zh
                     efdw += w * rpi * F * dW
                     ef += w * rpi * F
@@ -136,8 +144,12 @@ def _mp_scheme(k, Nx, N, L, x_lim, T, mp, kz=None, zform=0, start=None, stop=0,
             first = EyW1 / dt if zform else Ez[1]
             z = (first + sum(gz[j] * (EFdW[j] - Ez[j]) for j in range(1, kz + 1))) / gz[0]
             Ay = Ey + k * dt * sum(gy[j] * EF[j] for j in range(1, k + 1))
-            # y = Ay + k dt gy_0 (y/2 - z): the fixed point, exactly
-            y = (Ay - k * dt * gy[0] * z) / (1 - k * dt * gy[0] / 2)
+            if general is None:
+                # y = Ay + k dt gy_0 (y/2 - z): the fixed point, exactly
+                y = (Ay - k * dt * gy[0] * z) / (1 - k * dt * gy[0] / 2)
+            else:
+                # y = Ay + k dt gy_0 (-x y)
+                y = Ay / (1 + k * dt * gy[0] * x)
             ys.append(y)
             zs.append(z)
         lev[n] = (ys, zs)
@@ -192,6 +204,37 @@ def test_onestep_startup_against_50_digit_scheme(k, kz, S):
                       return_all=True)
     start = {N - m: fine[(N - m) * S] for m in range(K)}
     ys, zs = _mp_scheme(k, Nx, N, L, x_lim, T, mp, kz=kz, start=start)
+    ey = max(abs(float(a) - b) for a, b in zip(ys, got["y"]))
+    ez = max(abs(float(a) - b) for a, b in zip(zs, got["z"]))
+    assert ey < 1e-12 and ez < 1e-12, (ey, ez)
+
+
+@pytest.mark.parametrize("k,kz,zform", [(1, 1, 1), (2, 1, 1), (2, 2, 0)])
+def test_general_forward_against_50_digit_scheme(k, kz, zform):
+    """The general forward path (affine a, b by one Euler step, the short-rate
+    driver f = -x y), brute force, from the same smooth initial levels."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    Nx, N, L, x_lim, T = 17, 6, 4, 3.0, 1.0
+    a0, a1, b0, b1 = "0.05", "-0.3", "0.2", "0.04"
+    p = W.sin_problem(Nx=Nx, N=N, k=k, L=L, x_lim=x_lim, T=T)
+    # Picard to rounding (the contraction k dt gy_0 |x| reaches 0.25 here, so
+    # the default stop at |dy| <= 1e-12 would leave a few 1e-12)
+    p.update(kz=kz, zform=zform, driver="SHORT_RATE", forward="AFFINE", a_x=float(a0),
+             a_1=float(a1), b_x=float(b0), b_1=float(b1), picard_tol=1e-15)
+    K = max(k, kz)
+    xs = np.linspace(-x_lim, x_lim, Nx)
+    dt = T / N
+    iy = np.array([1.0 + 0.1 * np.sin(xs + (N - m) * dt) for m in range(K)])
+    iz = np.array([0.05 * np.cos(xs - (N - m) * dt) for m in range(K)])
+    got = O.solve(p, iy, iz, want_level=True)
+    xm = [mp.mpf(-x_lim) + 2 * mp.mpf(x_lim) * i / (Nx - 1) for i in range(Nx)]
+    start = {}
+    for m in range(K):
+        # the same doubles the oracle received
+        start[N - m] = ([mp.mpf(float(v)) for v in iy[m]], [mp.mpf(float(v)) for v in iz[m]])
+    ys, zs = _mp_scheme(k, Nx, N, L, x_lim, T, mp, kz=kz, zform=zform, start=start,
+                        general=tuple(mp.mpf(v) for v in (a0, a1, b0, b1)))
     ey = max(abs(float(a) - b) for a, b in zip(ys, got["y"]))
     ez = max(abs(float(a) - b) for a, b in zip(zs, got["z"]))
     assert ey < 1e-12 and ez < 1e-12, (ey, ez)
