@@ -816,9 +816,18 @@ def flops_per_gp_step_general(k: int, L: int) -> float:
     return k * L * (4 + 4 + 8 + 12 + 3 + 6) + 10 * 6
 
 
+def flops_per_gp_step_general32(k: int, L: int) -> float:
+    """FP32C general path, per node (half a pair): the double-float offset
+    (~10), floor and theta (~6), kappa (3), the spline value (3 packed FMA on
+    the (y, z) lanes = 6 lane ops x 2), the driver (~4), and the pair's share
+    of the compensated sums and driver terms (~12); per point ~10 Picard
+    iterations.  Operations, an FMA counted as 2 flop."""
+    return k * L * (10 + 6 + 3 + 12 + 4 + 12) * 2 + 10 * 6
+
+
 def run_general(args, rank, world, local_rank):
-    """The general forward path (affine coefficients, Euler) in FP64 at the
-    benchmark's grid size: the Vasicek bond (short-rate driver f = -x y,
+    """The general forward path (affine coefficients, Euler) in --precision
+    (FP32C by default) at the benchmark's grid size: the Vasicek bond (short-rate driver f = -x y,
     K_y = 2, K_z = 1 with the E[y dW]/dt z form) and the Black-Scholes call in
     the price (geometric Brownian motion, K = 3); Nx = 65536, N = 256, L = 16.
     One step = one solve of each."""
@@ -832,7 +841,8 @@ def run_general(args, rank, world, local_rank):
     sp = stream.cuda_stream
     probs = {"vasicek_k2_kz1_ydw": dict(W.vasicek_problem(Nx=65536, N=256, k=2), kz=1, zform=1),
              "gbm_price_call_k3": W.gbm_call_problem(Nx=65536, N=256, k=3)}
-    solvers = {n: B.Solver(p, "fp64", device=dev) for n, p in probs.items()}
+    prec = args.precision
+    solvers = {n: B.Solver(p, prec, device=dev) for n, p in probs.items()}
     units = sum(W.gp_steps(p) for p in probs.values())
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
@@ -898,13 +908,14 @@ def run_general(args, rank, world, local_rank):
         K = W.levels_K(p)
         nlev = p["N"] - K + 1
         kern_ms += avg * nlev
-        kern_flops += flops_per_gp_step_general(K, p["L"]) * p["Nx"] * nlev
+        fpg = flops_per_gp_step_general if prec == "fp64" else flops_per_gp_step_general32
+        kern_flops += fpg(K, p["L"]) * p["Nx"] * nlev
         rows.append({"name": name, "y0": r.y0, "z0": r.z0, "exact_y0": u, "exact_z0": z,
                      "err_y0_vs_exact": abs(r.y0 - u), "err_z0_vs_exact": abs(r.z0 - z),
                      "step_launch_us": 1000.0 * avg, "launches": s.launches})
     peaks = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = _alu_peak_tflops("fp64", sm_max)
+    peak = _alu_peak_tflops(prec, sm_max)
     achieved = kern_flops / (kern_ms / 1000.0) / 1e12
 
     # end to end: caller levels from pinned host memory, level 0 and the
@@ -948,23 +959,27 @@ def run_general(args, rank, world, local_rank):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic",
+            "dtype": "f64" if prec == "fp64" else "f32", "data": "synthetic",
             "config": {"workload": "general: forward process by Euler with affine a(x), b(x); "
                                    "Vasicek bond (kappa=.8, theta=.04, sigma=.02, r0=.03, T=2, "
                                    "f = -x y, K_y=2, K_z=1, E[y dW]/dt z form) and the call in "
                                    "the price under GBM (S0=K=100, r=.03, mu=.05, sigma=.2, "
-                                   "T=1, K=3); Nx=65536, N=256, L=16, FP64; one solve each per "
-                                   "step",
+                                   f"T=1, K=3); Nx=65536, N=256, L=16, {prec.upper()}; one solve "
+                                   "each per step", "precision": prec,
                        "Nx": 65536, "N": 256, "L": 16,
                        "l2": "flushed between steps (256 MiB write, outside the timed events)",
                        "parallelism": f"{world} independent replica(s)"},
             "accuracy": {"gate": "errors against the closed forms (Euler forward: first "
                                  "order in dt)", "rows": rows},
-            "roofline": {"kernel": "k_step64_gen", "bound": "alu", "achieved": achieved,
+            "roofline": {"kernel": "k_step64_gen" if prec == "fp64" else "k_step32_gen",
+                         "bound": "alu", "achieved": achieved,
                          "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          "traffic": None,
-                         "peak_source": f"derived: 152 SMs x 2 FP64 FMA units x 2 flop x {sm_max:.0f} MHz",
-                         "flop_per_gp_step": {n: flops_per_gp_step_general(W.levels_K(p), p["L"])
+                         "peak_source": (f"derived: 152 SMs x 2 FP64 FMA units x 2 flop x {sm_max:.0f} MHz"
+                                         if prec == "fp64" else
+                                         f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz"),
+                         "flop_per_gp_step": {n: (flops_per_gp_step_general if prec == "fp64"
+                                                  else flops_per_gp_step_general32)(W.levels_K(p), p["L"])
                                               for n, p in probs.items()}},
             "e2e": {"value": world * units * args.steps / e_dt, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

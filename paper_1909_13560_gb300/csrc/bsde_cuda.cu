@@ -140,10 +140,12 @@ static void launch_step(bsde_plan_t *pl, const Run &R, cudaStream_t s, int n) {
                  st);
     else if constexpr (DRV != BSDE_DRIVER_SHORT_RATE)
       launch_pdl(k_step64<DRV>, blocks, threads, sm, s, P, pl->dc64, R.r64.ring, R.t64, n, st);
-  } else if constexpr (DRV != BSDE_DRIVER_SHORT_RATE) {
-    // (the general path is FP64 only: validate() rejects it in FP32C)
+  } else {
     const size_t sm = step32_smem(P.G, P.k * P.Lp);
-    launch_pdl(k_step32<DRV>, blocks, threads, sm, s, P, pl->dc32, R.r32, R.tp, n, st);
+    if (P.general)
+      launch_pdl(k_step32_gen<DRV>, blocks, threads, sm, s, P, pl->dc32, R.r32, R.tp, n, st);
+    else if constexpr (DRV != BSDE_DRIVER_SHORT_RATE)
+      launch_pdl(k_step32<DRV>, blocks, threads, sm, s, P, pl->dc32, R.r32, R.tp, n, st);
   }
 }
 
@@ -705,7 +707,8 @@ static int batch_layout(int n, const bsde_problem *ps, BatchLayout &L) {
   for (int i = 0; i < n; ++i) {
     const bsde_problem &p = ps[i];
     // batches start from the closed form (no one-step start-up)
-    if (validate(p) || p.precision != BSDE_FP32C || has_startup(p)) return BSDE_EINVAL;
+    if (validate(p) || p.precision != BSDE_FP32C || has_startup(p) || problem_general(p))
+      return BSDE_EINVAL;
     const size_t K = size_t(problem_K(p));
     const size_t nx = size_t(p.Nx), ns = K + 1;
     L.ptable[i] = off; off = up(off + K * ((p.L + 1) / 2) * sizeof(PairF32));
@@ -1024,7 +1027,7 @@ extern "C" {
 
 int bsde_request_bytes(const bsde_problem *p, size_t *bytes) {
   if (!p || !bytes) return fail(BSDE_EINVAL, "null argument");
-  if (validate(*p) || p->precision != BSDE_FP32C || has_startup(*p))
+  if (validate(*p) || p->precision != BSDE_FP32C || has_startup(*p) || problem_general(*p))
     return fail(BSDE_EINVAL, "invalid request");
   *bytes = request_bytes(*p);
   return BSDE_OK;
@@ -1130,7 +1133,7 @@ int bsde_server_submit(bsde_server_t *s, const bsde_problem *p, int *slot) {
   if (!s->running) return fail(BSDE_EINVAL, "server not running");
   if (__atomic_load_n(&s->ctl->stopped, __ATOMIC_ACQUIRE))
     return fail(BSDE_ETIMEOUT, "server stopped: its idle limit passed; poll, stop and start it again");
-  if (validate(*p) || p->precision != BSDE_FP32C || has_startup(*p))
+  if (validate(*p) || p->precision != BSDE_FP32C || has_startup(*p) || problem_general(*p))
     return fail(BSDE_EINVAL, "invalid request");
   if (s->free_slots.empty()) return BSDE_BUSY;
   const size_t need = request_bytes(*p);

@@ -24,9 +24,6 @@ int validate(const bsde_problem &p) {
   if (p.driver < BSDE_DRIVER_LIN_SIN || p.driver > BSDE_DRIVER_SHORT_RATE) return BSDE_EINVAL;
   if (p.terminal < BSDE_TERMINAL_SIN || p.terminal > BSDE_TERMINAL_CALL_PRICE) return BSDE_EINVAL;
   if (p.forward != BSDE_FORWARD_CONST && p.forward != BSDE_FORWARD_AFFINE) return BSDE_EINVAL;
-  const bool general = problem_general(p) || p.terminal == BSDE_TERMINAL_ONE ||
-                       p.terminal == BSDE_TERMINAL_CALL_PRICE;
-  if (general && p.precision != BSDE_FP64) return BSDE_EINVAL;
   // terminals whose closed form (initial levels, and the start-up's level N)
   // needs a particular forward process
   if (p.terminal == BSDE_TERMINAL_ONE &&
@@ -294,6 +291,10 @@ void build_tables(Params &P, NodeF64 *t64, NodeF32 *t32, PairF32 *tp, int target
   work_split(P, target_groups, max_groups, resident_threads);
   double a[kMaxL], w[kMaxL];
   cached_rule(P.L, a, w);
+  for (int q = 0; q < P.Lp && q < kMaxL / 2; ++q) {
+    P.gh_hi[q] = float(a[q]);
+    P.gh_lo[q] = float(a[q] - double(P.gh_hi[q]));
+  }
   const double rpi = 1.0 / std::sqrt(M_PI);
   const double c6 = P.dx * P.dx / 6.0;
   for (int j = 1; j <= P.k; ++j) {

@@ -108,6 +108,9 @@ struct Params {
   // groups per point; shift range per j (for the clamp-free fast path)
   int32_t S, Lg, G, Lp;  // Lp = ceil(L/2) pairs; in FP32C the chunks hold Lg pairs
   int32_t smin[kMaxK], smax[kMaxK];
+  // the Gauss-Hermite node of pair q (node q; node L-1-q is its negative) as
+  // a float pair hi + lo, for the FP32C general path's per-point positions
+  float gh_hi[kMaxL / 2], gh_lo[kMaxL / 2];
 };
 
 // Device workspace layout (byte offsets from the workspace base).

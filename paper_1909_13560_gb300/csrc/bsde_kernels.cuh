@@ -694,9 +694,8 @@ __global__ void __launch_bounds__(kStepTP * kMaxGroups)
 // the point; the driver may read X (SHORT_RATE).  Otherwise as k_step64:
 // same groups, same table weights (cz, cfz, cfy, cy, cyz), same Picard tail.
 // ---------------------------------------------------------------------------
-template <int DRV>
-__device__ __forceinline__ double driver_x(const DrvC<double> &dc, double t, double et,
-                                           double emt, double x, double y, double z) {
+template <int DRV, typename T>
+__device__ __forceinline__ T driver_x(const DrvC<T> &dc, T t, T et, T emt, T x, T y, T z) {
   if constexpr (DRV == BSDE_DRIVER_SHORT_RATE)
     return -rmul(x, y);
   else
@@ -1047,8 +1046,9 @@ __device__ __forceinline__ void finish_points32(const Params &P, const DrvC<floa
     level_time<DRV>(P, n, tn, etn, emtn);
     const float hg0 = float(P.hg0);
     float dl = __fsub_rn(prev_y, Ah), dpp = __int_as_float(0x7fc00000);
+    const float xf = float(P.x_min + double(ii) * P.dx);  // x-aware drivers only
     while (it < P.picard_max) {
-      const float dn = hg0 * driver<DRV>(dc, tn, etn, emtn, Ah + dl, zh);
+      const float dn = hg0 * driver_x<DRV>(dc, tn, etn, emtn, xf, Ah + dl, zh);
       ++it;
       d = fabsf(__fsub_rn(dn, dl));
       const bool cyc = dn == dpp;
@@ -1135,6 +1135,134 @@ __global__ void __launch_bounds__(kStepTP * kMaxGroups, 3)
   __syncthreads();
   wait_predecessor();
   step_tile32<DRV, false>(P, dc, r32, tab, part, n, blockIdx.x * kStepTP, st);
+}
+
+// ---------------------------------------------------------------------------
+// The FP32C general forward path: as k_step32, but a node's position is
+// computed per point.  Node q of a pair sits at the offset
+// o = A_j + B_j a_q cells from its grid point (node L-1-q at A_j - B_j a_q),
+// A_j = a(x_i) j dt / dx and B_j = b(x_i) sqrt(2 j dt) / dx formed once per
+// thread in FP64 and split into float pairs, a_q a float pair, so the offset
+// is a float pair accurate to ~1e-10 cells (a plain float would lose 1e-3
+// cells at offsets of thousands of cells); its floor is the cell shift and
+// the remainder theta.  The spline value, the pair arithmetic, the
+// compensated sums and the Picard tail are those of k_step32, with the
+// driver reading the node's position.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void split_pair(double v, float &h, float &l) {
+  h = __double2float_rn(v);
+  l = __double2float_rn(__dsub_rn(v, double(h)));
+}
+
+// o = A + s B a (s = +1 or -1) as a float pair; the cell shift (floor) and
+// theta in [0, 1)
+__device__ __forceinline__ void gen_offset(float Ah, float Al, float Bh, float Bl, float ah,
+                                           float al, float &fl, float &th, float &ol_out) {
+  const float p = __fmul_rn(Bh, ah);
+  const float pe = __fmaf_rn(Bh, ah, -p);                 // exact product error
+  const float t = __fmaf_rn(Bh, al, __fmul_rn(Bl, ah));   // the small cross terms
+  const float s = __fadd_rn(Ah, p);
+  const float bp = __fsub_rn(s, Ah);
+  const float err = __fadd_rn(__fsub_rn(Ah, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+  const float ol = __fadd_rn(err, __fadd_rn(Al, __fadd_rn(pe, t)));
+  fl = floorf(s);
+  float r = __fadd_rn(__fsub_rn(s, fl), ol);  // s - fl is exact
+  if (r < 0.f) {
+    fl = __fsub_rn(fl, 1.f);
+    r = __fadd_rn(r, 1.f);
+  } else if (r >= 1.f) {
+    fl = __fadd_rn(fl, 1.f);
+    r = __fsub_rn(r, 1.f);
+  }
+  th = r;
+  ol_out = __fadd_rn(s, ol);  // the offset, rounded (for the node's position)
+}
+
+template <int DRV>
+__global__ void __launch_bounds__(kStepTP * kMaxGroups, 3)
+    k_step32_gen(const Params P, const DrvC<float> dc, Ring32 r32,
+                 const PairF32 *__restrict__ table, int n, Stats *st) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int kP = P.k * P.Lp;
+  PairF32 *tab = reinterpret_cast<PairF32 *>(smem_raw);
+  float *part = reinterpret_cast<float *>(tab + kP);  // [6][G][kStepTP]
+  {
+    const float4 *src = reinterpret_cast<const float4 *>(table);
+    float4 *dst = reinterpret_cast<float4 *>(tab);
+    for (int t = threadIdx.x; t < kP * kPairVec; t += blockDim.x) dst[t] = src[t];
+  }
+  __syncthreads();
+  wait_predecessor();
+  const int i0 = blockIdx.x * kStepTP;
+  const int tp = threadIdx.x % kStepTP, g = threadIdx.x / kStepTP;
+  const int G = P.G;
+  const int last = int(P.Nx - 1);
+  const int ii = i0 + tp;
+  float prev_y = 0.f;
+  if (threadIdx.x < kStepTP && i0 + int(threadIdx.x) <= last)
+    prev_y = r32.A[int64_t((n + 1) % P.nslot) * P.Nx + i0 + threadIdx.x].x;
+  if (g < G) {
+    const Group32 w = group32(P, g, i0);
+    Acc32 acc{make_float2(0.f, 0.f), make_float2(0.f, 0.f), 0.f, 0.f};
+    if (ii <= last) {
+      const int64_t off = int64_t((n + w.j) % P.nslot) * P.Nx;
+      const float4 *A = r32.A + off;
+      const float4 *Bv = r32.B + off;
+      const float2 *Cq = r32.C + off;
+      float tj, et, emt;
+      level_time<DRV>(P, n + w.j, tj, et, emt);
+      const PairF32 *row = tab + (w.j - 1) * P.Lp;
+      const double xi = P.x_min + double(ii) * P.dx;
+      float Ah, Al, Bh, Bl;
+      split_pair((P.a_x + P.a_1 * xi) * double(w.j) * P.dt * P.inv_dx, Ah, Al);
+      split_pair((P.b_x + P.b_1 * xi) * sqrt(2.0 * double(w.j) * P.dt) * P.inv_dx, Bh, Bl);
+      const float xf = float(xi), dxf = float(P.dx);
+      const float c6 = float(P.dx * P.dx / 6.0);
+#pragma unroll 1
+      for (int q = w.q0; q < w.q1; ++q) {
+        const float4 *te = reinterpret_cast<const float4 *>(row + q);
+        const float4 e0 = te[0], e3 = te[3], e4 = te[4];
+        const float ah = P.gh_hi[q], al = P.gh_lo[q];
+        float fla, tha, oa, flb, thb, ob;
+        gen_offset(Ah, Al, Bh, Bl, ah, al, fla, tha, oa);
+        gen_offset(Ah, Al, Bh, Bl, -ah, -al, flb, thb, ob);
+        int ca = ii + int(fla), cb = ii + int(flb);
+        float kaa = -tha * (1.f - tha) * c6, kab = -thb * (1.f - thb) * c6;
+        // off the grid: the end value (theta = kappa = 0 on the end node)
+        if (ca < 0 || ca >= last) {
+          ca = ca < 0 ? 0 : last;
+          tha = kaa = 0.f;
+        }
+        if (cb < 0 || cb >= last) {
+          cb = cb < 0 ? 0 : last;
+          thb = kab = 0.f;
+        }
+        const float4 aa = A[ca], ab = Bv[ca], ba = A[cb], bb = Bv[cb];
+        const float2 ac = Cq[ca], bc = Cq[cb];
+        float2 ha, da, hb, db;
+        node_value(aa, ab, ac, make_float2(tha, tha), make_float2(kaa, kaa), ha, da);
+        node_value(ba, bb, bc, make_float2(thb, thb), make_float2(kab, kab), hb, db);
+        const float2 va = f2add(ha, da), vb = f2add(hb, db);
+        const float Xa = __fmaf_rn(oa, dxf, xf), Xb = __fmaf_rn(ob, dxf, xf);
+        const float Fa = driver_x<DRV>(dc, tj, et, emt, Xa, va.x, va.y);
+        const float Fb = driver_x<DRV>(dc, tj, et, emt, Xb, vb.x, vb.y);
+        acc.Fz = __fmaf_rn(e0.z, __fsub_rn(Fa, Fb), acc.Fz);
+        acc.Fy = __fmaf_rn(e0.w, __fadd_rn(Fa, Fb), acc.Fy);
+        float2 hs, he;
+        two_sum2(ha, hb, hs, he);
+        comp_acc2(acc.S, acc.C, hi2(e3), lo2(e3), hi2(e4), hs, f2add(f2add(da, db), he));
+        if (P.zform && w.j == 1) {
+          // E[y DeltaW] z form: cyz (y^_a - y^_b) into the z lane
+          float dh = ha.x, dl2 = 0.f;
+          two_sum_into(dh, dl2, -hb.x);
+          comp_acc1(acc.S.y, acc.C.y, e4.z, e4.w, dh, __fadd_rn(dl2, __fsub_rn(da.x, db.x)));
+        }
+      }
+    }
+    store_partials(part, G, g, tp, acc);
+  }
+  __syncthreads();
+  finish_points32<DRV, false>(P, dc, r32.A, part, G, n, i0, st, prev_y);
 }
 
 // ---------------------------------------------------------------------------

@@ -201,7 +201,6 @@ def test_2d_workspace_bytes():
 
 
 @pytest.mark.parametrize("bad", [
-    dict(W.vasicek_problem(), precision_fp32c=True),
     dict(W.vasicek_problem(), a_1=0.1),
     dict(W.vasicek_problem(), b_1=0.01),
     dict(W.vasicek_problem(), forward="CONST"),
@@ -220,4 +219,8 @@ def test_invalid_general_forward_problems_rejected(bad):
 def test_general_forward_problems_accepted():
     for p in (W.vasicek_problem(), W.gbm_call_problem(),
               dict(W.sin_problem(), driver="SHORT_RATE")):
-        assert B.bsde_workspace_bytes(B.make_problem(p, "fp64")) > 0
+        for prec in ("fp64", "fp32c"):
+            assert B.bsde_workspace_bytes(B.make_problem(p, prec)) > 0
+    # batches and the server run the constant-shift kernels only
+    with pytest.raises(B.BsdeError):
+        B.bsde_batch_workspace_bytes([W.vasicek_problem()])
