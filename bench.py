@@ -294,9 +294,17 @@ def run_ours(args, rank, world, local_rank):
     launches_per_step = sum(s.launches for s in solvers)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
+    # the solves of a step are independent: each runs on its own stream,
+    # forked from and joined to the timing stream, so their dependent launch
+    # chains overlap (--sequential: one after another on the timing stream)
+    conc = B.ConcurrentSolves(solvers, dev)
+
     def one_step():
-        for s in solvers:
-            B.bsde_solve(s.plan, sp, want_result=False)
+        if args.sequential:
+            for s in solvers:
+                B.bsde_solve(s.plan, sp, want_result=False)
+        else:
+            conc.enqueue(stream)
 
     for _ in range(args.warmup):
         flush.zero_()
@@ -458,6 +466,10 @@ def run_ours(args, rank, world, local_rank):
                        "precision": args.precision,
                        "l2": "flushed between steps (256 MiB write, outside the timed events); "
                              "within a solve the level ring (<= 15 MB) is L2-resident by design",
+                       "schedule": ("the step's solves one after another on one stream"
+                                    if args.sequential else
+                                    "the step's solves concurrently, one stream each "
+                                    "(forked from and joined to the timing stream)"),
                        "parallelism": f"{world} independent replica(s)"},
             "accuracy": ({"gate": "no oracle at this size: y0 vs the closed form (Black-Scholes "
                                   "at r - (R - r)); the oracle at the reduced size Nx=2^16, N=256 "
@@ -1160,6 +1172,9 @@ def main():
     ap.add_argument("--cpu-levels", type=int, default=64)
     ap.add_argument("--ref-levels", type=int, default=12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sequential", action="store_true",
+                    help="config2/3: run a step's solves one after another on one stream "
+                         "(default: concurrently, one stream each)")
     ap.add_argument("--no-variants", action="store_true",
                     help="config2: skip the timing of the scheme's variants")
     ap.add_argument("--autotune", action="store_true",

@@ -255,6 +255,33 @@ def bsde_solve(plan: int, stream: int, init_y: int = 0, init_z: int = 0,
     return res if want_result else None
 
 
+class ConcurrentSolves:
+    """Independent solves (each its own plan and workspace) run concurrently:
+    every call forks from the caller's stream onto one stream per solver,
+    enqueues each solver's graph there, and joins back, so the dependent
+    launch chains of the solves overlap on the GPU.  Results are read with
+    bsde_result_fetch on the caller's stream afterwards."""
+
+    def __init__(self, solvers, device=None):
+        import torch
+        self.solvers = list(solvers)
+        dev = device if device is not None else self.solvers[0].device
+        self.streams = [torch.cuda.Stream(dev) for _ in self.solvers]
+        self.fork = torch.cuda.Event()
+        self.joins = [torch.cuda.Event() for _ in self.solvers]
+
+    def enqueue(self, stream) -> None:
+        """Enqueue one solve of every solver, ordered after `stream`'s prior
+        work, with `stream` waiting for all of them."""
+        self.fork.record(stream)
+        for s, st, ev in zip(self.solvers, self.streams, self.joins):
+            st.wait_event(self.fork)
+            bsde_solve(s.plan, st.cuda_stream, want_result=False)
+            ev.record(st)
+        for ev in self.joins:
+            stream.wait_event(ev)
+
+
 def bsde_result_fetch(plan: int, stream: int) -> bsde_result:
     res = bsde_result()
     _check(load().bsde_result_fetch(ctypes.c_void_p(plan), ctypes.c_void_p(stream),
