@@ -228,3 +228,20 @@ def test_config3_reduced_size(B, k):
             assert abs(got["z0"] - ref["z0"]) <= 1e-8 * abs(ref["z0"])
         else:
             assert math.isfinite(got["y0"]) and math.isfinite(got["z0"])
+
+
+def test_concurrent_solves_equal_sequential_solves(B):
+    """Independent plans forked onto their own streams (ConcurrentSolves, the
+    benchmark's schedule) give bitwise the results of one-at-a-time solves."""
+    import torch
+    probs = [W.call_problem(Nx=4096, N=32, k=k) for k in (1, 3, 6)]
+    seq = [B.solve(p, "fp32c") for p in probs]
+    solvers = [B.Solver(p, "fp32c") for p in probs]
+    stream = torch.cuda.current_stream()
+    conc = B.ConcurrentSolves(solvers)
+    for _ in range(3):
+        conc.enqueue(stream)
+    for s, r in zip(solvers, seq):
+        got = B.bsde_result_fetch(s.plan, stream.cuda_stream)
+        assert got.y0 == r["y0"] and got.z0 == r["z0"]
+        s.close()
