@@ -31,7 +31,7 @@ constexpr int kBatchSplineTile = kBatchThreads * kSplineChunk;  // 1536 unknowns
 struct alignas(16) BatchSmem {
   InstDesc D;
   PairF32 tab[kMaxK * (kMaxL / 2)];
-  float part[6 * 6 * kStepTP];
+  float part[kPartArrays * kMaxGroups * kStepTP];
   float sr[2][spline_span<BSDE_FP32C>(kBatchSplineTile)];
   float sg[2][spline_span<BSDE_FP32C>(kBatchSplineTile)];
   float sd[2][spline_span<BSDE_FP32C>(kBatchSplineTile)];

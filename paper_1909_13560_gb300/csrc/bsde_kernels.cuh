@@ -913,7 +913,7 @@ __device__ __forceinline__ void pair_math(const DrvC<float> &dc, float tj, float
                                           const float4 &e3, const float4 &e4, const float4 &aa,
                                           const float4 &ab, const float2 &ac, const float4 &ba,
                                           const float4 &bb, const float2 &bc, float2 &S, float2 &C,
-                                          float &Fz, float &Fy) {
+                                          float &Fz, float &Fy, float &FyC) {
   float2 ha, da, hb, db;
   node_value(aa, ab, ac, hi2(e1), lo2(e1), ha, da);
   node_value(ba, bb, bc, hi2(e2), lo2(e2), hb, db);
@@ -921,7 +921,8 @@ __device__ __forceinline__ void pair_math(const DrvC<float> &dc, float tj, float
   const float Fa = driver<DRV>(dc, tj, et, emt, va.x, va.y);
   const float Fb = driver<DRV>(dc, tj, et, emt, vb.x, vb.y);
   Fz = __fmaf_rn(e0.z, __fsub_rn(Fa, Fb), Fz);
-  Fy = __fmaf_rn(e0.w, __fadd_rn(Fa, Fb), Fy);
+  // sum of k dt gy_j f: O(k dt |f|), so accumulated with its rounding error
+  two_sum_into(Fy, FyC, __fmul_rn(e0.w, __fadd_rn(Fa, Fb)));
   // the pair's hi parts summed exactly, then one compensated product
   float2 hs, he;
   two_sum2(ha, hb, hs, he);
@@ -937,7 +938,7 @@ __device__ __forceinline__ void pair_math(const DrvC<float> &dc, float tj, float
 // Accumulators of one point: compensated (y, z) sums and the driver terms.
 struct Acc32 {
   float2 S, C;
-  float Fz, Fy;
+  float Fz, Fy, FyC;  // Fy + FyC: the y driver terms with their rounding error
 };
 
 // One group's node pairs for point ii, level data loaded directly from
@@ -961,7 +962,7 @@ __device__ __forceinline__ void pairs32(const DrvC<float> &dc, Ring32 r, int64_t
                  bb = ldl<COH>(B + cb);
     const float2 ac = ldl<COH>(Cq + ca), bc = ldl<COH>(Cq + cb);
     pair_math<DRV, ZF>(dc, tj, et, emt, e0, e1, e2, e3, e4, aa, ab, ac, ba, bb, bc, acc.S,
-                       acc.C, acc.Fz, acc.Fy);
+                       acc.C, acc.Fz, acc.Fy, acc.FyC);
   }
 }
 
@@ -995,7 +996,7 @@ __device__ __forceinline__ void level_time(const Params &P, int m, float &t, flo
 
 __device__ __forceinline__ void store_partials(float *part, int G, int g, int tp,
                                                const Acc32 &a) {
-  // lanes: y (x), z (y); part is [6][G][kStepTP]
+  // lanes: y (x), z (y); part is [kPartArrays][G][kStepTP]
   const int o = g * kStepTP + tp, gs = G * kStepTP;
   part[0 * gs + o] = a.S.y;
   part[1 * gs + o] = a.C.y;
@@ -1003,6 +1004,7 @@ __device__ __forceinline__ void store_partials(float *part, int G, int g, int tp
   part[3 * gs + o] = a.Fy;
   part[4 * gs + o] = a.S.x;
   part[5 * gs + o] = a.C.x;
+  part[6 * gs + o] = a.FyC;
 }
 
 // The last part of the step for the kStepTP points of a tile, by the threads
@@ -1028,20 +1030,22 @@ __device__ __forceinline__ void finish_points32(const Params &P, const DrvC<floa
   float d = 0.f;
   if (active) {
     const int gs = G * kStepTP;
-    float zS = 0.f, zC = 0.f, yS = 0.f, yC = 0.f, fz = 0.f, fy = 0.f;
+    float zS = 0.f, zC = 0.f, yS = 0.f, yC = 0.f, fz = 0.f, fy = 0.f, fyC = 0.f;
     for (int q = 0; q < G; ++q) {
       const int o = q * kStepTP + tid;
       two_sum_into(zS, zC, part[0 * gs + o]);
       zC = __fadd_rn(zC, part[1 * gs + o]);
       fz = __fadd_rn(fz, part[2 * gs + o]);
-      fy = __fadd_rn(fy, part[3 * gs + o]);
+      two_sum_into(fy, fyC, part[3 * gs + o]);
+      fyC = __fadd_rn(fyC, part[6 * gs + o]);
       two_sum_into(yS, yC, part[4 * gs + o]);
       yC = __fadd_rn(yC, part[5 * gs + o]);
     }
     // z^n = zS + (zC + fz) and A = yS + (yC + fy) as exact float pairs
     float zh = zS, zl = 0.f, Ah = yS, Al = 0.f;
     two_sum_into(zh, zl, __fadd_rn(zC, fz));
-    two_sum_into(Ah, Al, __fadd_rn(yC, fy));
+    two_sum_into(Ah, Al, fy);
+    two_sum_into(Ah, Al, __fadd_rn(yC, fyC));
     float tn, etn, emtn;
     level_time<DRV>(P, n, tn, etn, emtn);
     const float hg0 = float(P.hg0);
@@ -1089,7 +1093,7 @@ __device__ __forceinline__ void step_tile32(const Params &P, const DrvC<float> &
     prev_y = ldl<COH>(r32.A + int64_t((n + 1) % P.nslot) * P.Nx + i0 + threadIdx.x).x;
   if (g < G) {
     const Group32 w = group32(P, g, i0);
-    Acc32 acc{make_float2(0.f, 0.f), make_float2(0.f, 0.f), 0.f, 0.f};
+    Acc32 acc{make_float2(0.f, 0.f), make_float2(0.f, 0.f), 0.f, 0.f, 0.f};
     const int64_t off = int64_t((n + w.j) % P.nslot) * P.Nx;
     float tj, et, emt;
     level_time<DRV>(P, n + w.j, tj, et, emt);
@@ -1115,7 +1119,7 @@ __device__ __forceinline__ void step_tile32(const Params &P, const DrvC<float> &
 // neighbouring CTAs on the SM).
 // ---------------------------------------------------------------------------
 __host__ __device__ inline size_t step32_smem(int G, int kP) {
-  return sizeof(PairF32) * size_t(kP) + sizeof(float) * 6 * size_t(G) * kStepTP;
+  return sizeof(PairF32) * size_t(kP) + sizeof(float) * kPartArrays * size_t(G) * kStepTP;
 }
 
 template <int DRV>
@@ -1125,7 +1129,7 @@ __global__ void __launch_bounds__(kStepTP * kMaxGroups, 3)
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int kP = P.k * P.Lp;
   PairF32 *tab = reinterpret_cast<PairF32 *>(smem_raw);
-  float *part = reinterpret_cast<float *>(tab + kP);  // [6][G][kStepTP]
+  float *part = reinterpret_cast<float *>(tab + kP);  // [kPartArrays][G][kStepTP]
   {
     // the pair table is written once, at plan time
     const float4 *src = reinterpret_cast<const float4 *>(table);
@@ -1185,7 +1189,7 @@ __global__ void __launch_bounds__(kStepTP * kMaxGroups, 3)
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int kP = P.k * P.Lp;
   PairF32 *tab = reinterpret_cast<PairF32 *>(smem_raw);
-  float *part = reinterpret_cast<float *>(tab + kP);  // [6][G][kStepTP]
+  float *part = reinterpret_cast<float *>(tab + kP);  // [kPartArrays][G][kStepTP]
   {
     const float4 *src = reinterpret_cast<const float4 *>(table);
     float4 *dst = reinterpret_cast<float4 *>(tab);
@@ -1203,7 +1207,7 @@ __global__ void __launch_bounds__(kStepTP * kMaxGroups, 3)
     prev_y = r32.A[int64_t((n + 1) % P.nslot) * P.Nx + i0 + threadIdx.x].x;
   if (g < G) {
     const Group32 w = group32(P, g, i0);
-    Acc32 acc{make_float2(0.f, 0.f), make_float2(0.f, 0.f), 0.f, 0.f};
+    Acc32 acc{make_float2(0.f, 0.f), make_float2(0.f, 0.f), 0.f, 0.f, 0.f};
     if (ii <= last) {
       const int64_t off = int64_t((n + w.j) % P.nslot) * P.Nx;
       const float4 *A = r32.A + off;
@@ -1247,7 +1251,7 @@ __global__ void __launch_bounds__(kStepTP * kMaxGroups, 3)
         const float Fa = driver_x<DRV>(dc, tj, et, emt, Xa, va.x, va.y);
         const float Fb = driver_x<DRV>(dc, tj, et, emt, Xb, vb.x, vb.y);
         acc.Fz = __fmaf_rn(e0.z, __fsub_rn(Fa, Fb), acc.Fz);
-        acc.Fy = __fmaf_rn(e0.w, __fadd_rn(Fa, Fb), acc.Fy);
+        two_sum_into(acc.Fy, acc.FyC, __fmul_rn(e0.w, __fadd_rn(Fa, Fb)));
         float2 hs, he;
         two_sum2(ha, hb, hs, he);
         comp_acc2(acc.S, acc.C, hi2(e3), lo2(e3), hi2(e4), hs, f2add(f2add(da, db), he));

@@ -5,8 +5,9 @@ Tolerances (written here, derived in the design notes):
          only the summation order and FMA contraction differ.
   FP32C: |GPU - oracle| <= 2e-7 * max(1, scale).  The driver is evaluated in
          FP32 at every node, so each level carries ~eps32 |f| h of error in y
-         and ~eps32 |f| sqrt(dt) in z (h = k dt); the largest measured case
-         (N = 3, h = 1) reaches 1.4e-7, typical problems 1e-8..5e-8.
+         and ~eps32 |f| sqrt(dt) in z (h = k dt); the y driver terms are summed
+         with their rounding error, and the largest measured cases (N = 1 and
+         N = 3 with h = 1) reach 0.8e-7..1.1e-7, typical problems 1e-8..5e-8.
 Where the scheme itself is unstable (config2 with k >= 4 at Nx = 65536,
 L = 16) it amplifies rounding, and only the FP64 relative agreement that the
 amplification leaves is asserted.
