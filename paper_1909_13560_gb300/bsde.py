@@ -580,7 +580,8 @@ class Server:
 def l2_read_bandwidth(mib: int = 48, reps: int = 40, device=None) -> float:
     """L2 -> SM read bandwidth in GB/s: a buffer that fits in L2, read `reps`
     times by one launch of 16-byte loads (after one warm-up launch), timed
-    with CUDA events on the launching stream."""
+    with CUDA events on the launching stream; the best of five launches (a
+    peak probe: slower launches were disturbed)."""
     import torch
     dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
     props = torch.cuda.get_device_properties(dev)
@@ -592,13 +593,16 @@ def l2_read_bandwidth(mib: int = 48, reps: int = 40, device=None) -> float:
     args = (ctypes.c_void_p(buf.data_ptr()), buf.numel() * 4, 1, grid,
             ctypes.c_void_p(sink.data_ptr()), ctypes.c_void_p(stream.cuda_stream))
     _check(lib.bsde_l2_read_probe(*args), "bsde_l2_read_probe")
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    _check(lib.bsde_l2_read_probe(args[0], args[1], reps, grid, args[4], args[5]),
-           "bsde_l2_read_probe")
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    return buf.numel() * 4 * reps / (e0.elapsed_time(e1) / 1e3) / 1e9
+    best = 0.0
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _check(lib.bsde_l2_read_probe(args[0], args[1], reps, grid, args[4], args[5]),
+               "bsde_l2_read_probe")
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        best = max(best, buf.numel() * 4 * reps / (e0.elapsed_time(e1) / 1e3) / 1e9)
+    return best
 
 
 # --- two space dimensions (include/bsde2d.h) ---------------------------------
