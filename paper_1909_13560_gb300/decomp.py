@@ -122,8 +122,8 @@ class LocalTransport:
 
 class DistTransport:
     """One slab per rank: the edge records go to the neighbouring ranks by
-    point-to-point send/recv between launches.  `stage` moves device records
-    through host memory for backends without device tensors (gloo)."""
+    point-to-point send/recv between launches.  stage_on_host moves device
+    records through host memory for backends without device tensors (gloo)."""
 
     def __init__(self, dist, stage_on_host: bool = False):
         self.dist = dist
@@ -161,67 +161,93 @@ class DistTransport:
             view[a:b].copy_(recv.to(view.device) if self.stage_on_host else recv)
 
 
+class ShardedSolver:
+    """One problem as `parts` slabs on one device (LocalTransport): the slabs'
+    plans are made once; each enqueue() runs the level-by-level loop with a
+    halo exchange after every step, and result() reads the owner's result."""
+
+    def __init__(self, problem: dict, parts: int, precision: str = "fp64", device=None):
+        if problem.get("init_mode", 0) not in (0, "EXACT") and B.levels_K(problem) > 1:
+            raise ValueError("the decomposition starts from the closed form or caller levels")
+        self.problem = dict(problem)
+        self.Nx = int(problem["Nx"])
+        self.layout = slabs(self.Nx, parts, halo_width(problem))
+        self.subs = [slab_problem(problem, *sl["local"]) for sl in self.layout]
+        self.solvers = [B.Solver(q, precision, device=device) for q in self.subs]
+        self.device = self.solvers[0].device
+        self.transport = LocalTransport()
+        x0 = float(problem["x0"])
+        dx = (float(problem["x_max"]) - float(problem["x_min"])) / (self.Nx - 1)
+        g0 = min(int(math.floor((x0 - float(problem["x_min"])) / dx)), self.Nx - 1)
+        self.owner = next(r for r, sl in enumerate(self.layout)
+                          if sl["own"][0] <= g0 < sl["own"][1])
+
+    def enqueue(self, stream, init=None, outs=None, keep=None) -> None:
+        """Enqueue one solve on `stream` (torch stream).  init: None or host
+        arrays (K, Nx) of the caller's levels; outs: None or per slab a pair of
+        host arrays for its local level 0 (the call then waits for them)."""
+        sp = stream.cuda_stream
+        lib = B.load()
+        keep = [] if keep is None else keep
+        for s, sl in zip(self.solvers, self.layout):
+            iy = iz = None
+            if init is not None:
+                lo, hi = sl["local"]
+                iy = np.ascontiguousarray(init[0][:, lo:hi], dtype=np.float64)
+                iz = np.ascontiguousarray(init[1][:, lo:hi], dtype=np.float64)
+                keep += [iy, iz]
+            B._check(lib.bsde_enqueue_start(ctypes.c_void_p(s.plan), ctypes.c_void_p(sp),
+                                            iy.ctypes.data if iy is not None else None,
+                                            iz.ctypes.data if iz is not None else None,
+                                            1 if iy is not None else 0), "bsde_enqueue_start")
+        K = B.levels_K(self.problem)
+        for n in range(int(self.problem["N"]) - K, -1, -1):
+            for s in self.solvers:
+                B.bsde_enqueue_level(s.plan, sp, n, 1)
+            self.transport.exchange(self.solvers, self.layout, n)
+            for s in self.solvers:
+                B.bsde_enqueue_level(s.plan, sp, n, 2)
+        for r, s in enumerate(self.solvers):
+            oy = oz = None
+            if outs is not None:
+                oy, oz = outs[r]
+            B._check(lib.bsde_enqueue_finish(ctypes.c_void_p(s.plan), ctypes.c_void_p(sp),
+                                             oy.ctypes.data if oy is not None else None,
+                                             oz.ctypes.data if oz is not None else None,
+                                             1 if oy is not None else 0), "bsde_enqueue_finish")
+
+    def result(self, stream) -> dict:
+        res = [B.bsde_result_fetch(s.plan, stream.cuda_stream) for s in self.solvers]
+        r0 = res[self.owner]
+        return {"y0": r0.y0, "z0": r0.z0,
+                "picard_iters_max": max(r.picard_iters_max for r in res),
+                "picard_resid_max": max(r.picard_resid_max for r in res),
+                "levels_done": r0.levels_done, "slabs": self.layout}
+
+    def close(self) -> None:
+        for s in self.solvers:
+            s.close()
+
+
 def solve_sharded(problem: dict, parts: int, precision: str = "fp64", device=None,
                   want_level: bool = False, init=None) -> dict:
     """Solve one problem as `parts` slabs on one device (LocalTransport).
     Returns y0, z0 (from the slab that owns x0), the merged Picard statistics
     and, if asked, the assembled level 0."""
     import torch
-    if problem.get("init_mode", 0) not in (0, "EXACT") and B.levels_K(problem) > 1:
-        raise ValueError("the decomposition starts from the closed form or caller levels")
-    Nx = int(problem["Nx"])
-    layout = slabs(Nx, parts, halo_width(problem))
-    subs = [slab_problem(problem, *sl["local"]) for sl in layout]
-    solvers = [B.Solver(q, precision, device=device) for q in subs]
-    dev = solvers[0].device
-    stream = torch.cuda.current_stream(dev)
-    sp = stream.cuda_stream
-    lib = B.load()
-    keep = []
-    for s, sl in zip(solvers, layout):
-        iy = iz = None
-        if init is not None:
-            lo, hi = sl["local"]
-            iy = np.ascontiguousarray(init[0][:, lo:hi], dtype=np.float64)
-            iz = np.ascontiguousarray(init[1][:, lo:hi], dtype=np.float64)
-            keep += [iy, iz]
-        B._check(lib.bsde_enqueue_start(ctypes.c_void_p(s.plan), ctypes.c_void_p(sp),
-                                        iy.ctypes.data if iy is not None else None,
-                                        iz.ctypes.data if iz is not None else None,
-                                        1 if iy is not None else 0), "bsde_enqueue_start")
-    K = B.levels_K(problem)
-    tr = LocalTransport()
-    for n in range(int(problem["N"]) - K, -1, -1):
-        for s in solvers:
-            B.bsde_enqueue_level(s.plan, sp, n, 1)
-        tr.exchange(solvers, layout, n)
-        for s in solvers:
-            B.bsde_enqueue_level(s.plan, sp, n, 2)
-    outs = []
-    for s, q in zip(solvers, subs):
-        oy = np.zeros(int(q["Nx"]))
-        oz = np.zeros(int(q["Nx"]))
-        B._check(lib.bsde_enqueue_finish(ctypes.c_void_p(s.plan), ctypes.c_void_p(sp),
-                                         oy.ctypes.data, oz.ctypes.data, 1), "bsde_enqueue_finish")
-        outs.append((oy, oz))
-    res = [B.bsde_result_fetch(s.plan, sp) for s in solvers]
-    x0 = float(problem["x0"])
-    dx = (float(problem["x_max"]) - float(problem["x_min"])) / (Nx - 1)
-    g0 = min(int(math.floor((x0 - float(problem["x_min"])) / dx)), Nx - 1)
-    owner = next(r for r, sl in enumerate(layout) if sl["own"][0] <= g0 < sl["own"][1])
-    out = {"y0": res[owner].y0, "z0": res[owner].z0,
-           "picard_iters_max": max(r.picard_iters_max for r in res),
-           "picard_resid_max": max(r.picard_resid_max for r in res),
-           "levels_done": res[owner].levels_done, "slabs": layout}
+    ss = ShardedSolver(problem, parts, precision, device)
+    stream = torch.cuda.current_stream(ss.device)
+    outs = [(np.zeros(int(q["Nx"])), np.zeros(int(q["Nx"]))) for q in ss.subs] if want_level else None
+    ss.enqueue(stream, init=init, outs=outs)
+    out = ss.result(stream)
     if want_level:
-        y = np.zeros(Nx)
-        z = np.zeros(Nx)
-        for (oy, oz), sl in zip(outs, layout):
+        y = np.zeros(ss.Nx)
+        z = np.zeros(ss.Nx)
+        for (oy, oz), sl in zip(outs, ss.layout):
             lo = sl["local"][0]
             a, b = sl["own"]
             y[a:b] = oy[a - lo:b - lo]
             z[a:b] = oz[a - lo:b - lo]
         out["y"], out["z"] = y, z
-    for s in solvers:
-        s.close()
+    ss.close()
     return out
