@@ -216,6 +216,21 @@ class ShardedSolver:
                                              oz.ctypes.data if oz is not None else None,
                                              1 if oy is not None else 0), "bsde_enqueue_finish")
 
+    def replay(self, stream) -> None:
+        """One solve from the closed-form start as a CUDA graph: the
+        level-by-level loop (a few launches and copies per slab and level,
+        which the host would otherwise issue one by one) is captured at the
+        first call and replayed on `stream` after that."""
+        import torch
+        if getattr(self, "_graph", None) is None:
+            self._graph = torch.cuda.CUDAGraph()
+            cap = torch.cuda.Stream(self.device)
+            cap.wait_stream(stream)
+            with torch.cuda.graph(self._graph, stream=cap):
+                self.enqueue(cap)
+            stream.wait_stream(cap)
+        self._graph.replay()
+
     def result(self, stream) -> dict:
         res = [B.bsde_result_fetch(s.plan, stream.cuda_stream) for s in self.solvers]
         r0 = res[self.owner]
@@ -225,6 +240,7 @@ class ShardedSolver:
                 "levels_done": r0.levels_done, "slabs": self.layout}
 
     def close(self) -> None:
+        self._graph = None
         for s in self.solvers:
             s.close()
 

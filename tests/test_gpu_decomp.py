@@ -55,3 +55,20 @@ def test_sharded_with_caller_levels(B):
     ref = B.solve(p, "fp64", init=(iy, iz), want_level=True)
     got = decomp.solve_sharded(p, 3, "fp64", want_level=True, init=(iy, iz))
     assert float(np.max(np.abs(got["y"] - ref["y"]))) <= 1e-12 * float(np.max(np.abs(ref["y"])))
+
+
+def test_sharded_graph_replay_equals_direct(B):
+    """The level loop captured into a CUDA graph and replayed gives the
+    directly launched result."""
+    import torch
+    from paper_1909_13560_gb300 import decomp
+    p = W.call_problem(Nx=8192, N=32, k=3)
+    ss = decomp.ShardedSolver(p, 3, "fp32c")
+    stream = torch.cuda.current_stream()
+    ss.enqueue(stream)
+    a = ss.result(stream)
+    ss.replay(stream)
+    ss.replay(stream)
+    b = ss.result(stream)
+    ss.close()
+    assert a["y0"] == b["y0"] and a["z0"] == b["z0"]
