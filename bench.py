@@ -474,6 +474,10 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(max(1, args.cpu_levels // 8) if c3 else args.cpu_levels,
                            os.cpu_count() or 1, args.workload)
+        # and on one host thread, a smaller sample
+        one = cpu_baseline(max(1, args.cpu_levels // 64) if c3 else max(1, args.cpu_levels // 8),
+                           1, args.workload)
+        cpu["single_thread"] = {"value": one["value"], "cores": 1, "sample": one["sample"]}
 
     if rank == 0:
         kname = "k_step32" if args.precision == "fp32c" else "k_step64"
