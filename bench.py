@@ -561,7 +561,9 @@ def run_batch(args, rank, world, local_rank):
     t0 = time.perf_counter()
     bs = B.BatchSolver(probs, device=dev)
     plan_s = time.perf_counter() - t0
-    cfg = bs.autotune() if args.autotune else (bs.set_config(1, 4) or bs.config())
+    # the batch configuration by timing (bsde_batch_autotune, outside the timed
+    # region) unless a fixed one is asked for
+    cfg = (bs.set_config(1, 4) or bs.config()) if args.no_autotune else bs.autotune()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     for _ in range(args.warmup):
         flush.zero_()
@@ -1213,8 +1215,9 @@ def main():
                          "(default: concurrently, one stream each)")
     ap.add_argument("--no-variants", action="store_true",
                     help="config2: skip the timing of the scheme's variants")
-    ap.add_argument("--autotune", action="store_true",
-                    help="config4: pick the batch configuration by timing (else cluster 1, 4 groups)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="config4: a fixed batch configuration (cluster 1, 4 groups) instead "
+                         "of the autotuned one")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
