@@ -580,7 +580,7 @@ __device__ __forceinline__ void nodes2f(const Params2 &P, const Lev2f &lev,
   }
 }
 
-__global__ void __launch_bounds__(kStep2TP * kMaxGroups, 2)
+__global__ void __launch_bounds__(kStep2TP * kMaxGroups, 1)
     k2_step32(const Params2 P, const float4 *__restrict__ ring, double *__restrict__ V,
               const Node2f *__restrict__ table, int n, Stats *st) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
