@@ -64,7 +64,8 @@ struct Run {
   Ring64 r64;
   Ring32 r32;
   const NodeF64 *t64;
-  const PairF32 *tp;
+  const PairF32 *tp;   // FP32C pair table in the workspace
+  PairTab32 tab;       // the same table, passed to k_step32 by value
 };
 }  // namespace bsde
 
@@ -141,11 +142,12 @@ static void launch_step(bsde_plan_t *pl, const Run &R, cudaStream_t s, int n) {
     else if constexpr (DRV != BSDE_DRIVER_SHORT_RATE)
       launch_pdl(k_step64<DRV>, blocks, threads, sm, s, P, pl->dc64, R.r64.ring, R.t64, n, st);
   } else {
-    const size_t sm = step32_smem(P.G, P.k * P.Lp);
     if (P.general)
-      launch_pdl(k_step32_gen<DRV>, blocks, threads, sm, s, P, pl->dc32, R.r32, R.tp, n, st);
+      launch_pdl(k_step32_gen<DRV>, blocks, threads, step32_smem(P.G, P.k * P.Lp), s, P,
+                 pl->dc32, R.r32, R.tp, n, st);
     else if constexpr (DRV != BSDE_DRIVER_SHORT_RATE)
-      launch_pdl(k_step32<DRV>, blocks, threads, sm, s, P, pl->dc32, R.r32, R.tp, n, st);
+      launch_pdl(k_step32<DRV>, blocks, threads, step32_smem(P.G, 0), s, P, pl->dc32, R.r32,
+                 R.tab, n, st);
   }
 }
 
@@ -219,6 +221,8 @@ static int upload_tables(bsde_plan_t *pl, HostTables &h, cudaStream_t s) {
   } else {
     BSDE_CUDA_TRY(cudaMemcpyAsync(pl->ws + L.ptable, h.tp, sizeof(PairF32) * P.k * P.Lp,
                                   cudaMemcpyHostToDevice, s));
+    std::memcpy(pl->run.tab.e, h.tp, sizeof(PairF32) * P.k * P.Lp);
+    if (sub) std::memcpy(pl->sub.tab.e, h.sp, sizeof(PairF32) * pl->sub.P.Lp);
     if (sub)
       BSDE_CUDA_TRY(cudaMemcpyAsync(pl->ws + L.sub_ptable, h.sp,
                                     sizeof(PairF32) * pl->sub.P.Lp, cudaMemcpyHostToDevice, s));

@@ -1076,8 +1076,8 @@ __device__ __forceinline__ void finish_points32(const Params &P, const DrvC<floa
 }
 
 // One tile of kStepTP points of level n with direct loads, called by every
-// thread of the CTA; `tab` (the pair table of the problem) and `part` are in
-// shared memory.  Thread tp of group g accumulates the pairs of group g for
+// thread of the CTA; `tab` is the pair table of the problem (in shared memory
+// or in the kernel's parameters) and `part` is in shared memory.  Thread tp of group g accumulates the pairs of group g for
 // point i0 + tp; threads of groups g >= G idle.  The caller separates
 // consecutive tiles by a barrier (part is reused).
 template <int DRV, bool COH>
@@ -1114,31 +1114,28 @@ __device__ __forceinline__ void step_tile32(const Params &P, const DrvC<float> &
 
 // ---------------------------------------------------------------------------
 // The FP32C step kernel of one level: one CTA per tile of kStepTP points and
-// G groups of kStepTP threads, level data through L1 (the k level windows of
-// the CTA's nodes are reused by neighbouring threads' cells c + 1 and by the
-// neighbouring CTAs on the SM).
+// G groups of kStepTP threads, level data loaded through L1 from the
+// L2-resident ring.  The pair table is a kernel parameter: every thread of a
+// group reads the same entry, so the reads go through the constant cache and
+// leave the L1 data path to the level loads (and no CTA copies the table).
 // ---------------------------------------------------------------------------
 __host__ __device__ inline size_t step32_smem(int G, int kP) {
   return sizeof(PairF32) * size_t(kP) + sizeof(float) * kPartArrays * size_t(G) * kStepTP;
 }
 
+// The pair table of a plan (k Lp entries used) as a kernel parameter.
+struct PairTab32 {
+  PairF32 e[kMaxK * (kMaxL / 2)];
+};
+
 template <int DRV>
 __global__ void __launch_bounds__(kStepTP * kMaxGroups, 3)
-    k_step32(const Params P, const DrvC<float> dc, Ring32 r32, const PairF32 *__restrict__ table,
-             int n, Stats *st) {
+    k_step32(const Params P, const DrvC<float> dc, Ring32 r32,
+             const __grid_constant__ PairTab32 tab, int n, Stats *st) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  const int kP = P.k * P.Lp;
-  PairF32 *tab = reinterpret_cast<PairF32 *>(smem_raw);
-  float *part = reinterpret_cast<float *>(tab + kP);  // [kPartArrays][G][kStepTP]
-  {
-    // the pair table is written once, at plan time
-    const float4 *src = reinterpret_cast<const float4 *>(table);
-    float4 *dst = reinterpret_cast<float4 *>(tab);
-    for (int t = threadIdx.x; t < kP * kPairVec; t += blockDim.x) dst[t] = src[t];
-  }
-  __syncthreads();
+  float *part = reinterpret_cast<float *>(smem_raw);  // [kPartArrays][G][kStepTP]
   wait_predecessor();
-  step_tile32<DRV, false>(P, dc, r32, tab, part, n, blockIdx.x * kStepTP, st);
+  step_tile32<DRV, false>(P, dc, r32, tab.e, part, n, blockIdx.x * kStepTP, st);
 }
 
 // ---------------------------------------------------------------------------
