@@ -816,7 +816,9 @@ def run_2d(args, rank, world, local_rank):
                          and abs(ez - 2.32e-6) <= 0.02 * 2.32e-6},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                         "kernel": "k2_step" if prec == "fp64" else "k2_step32",
+                         # K = 6, L = 8: the 192-entry pair table fits the
+                         # FP32C step's parameters (k2_step32p)
+                         "kernel": "k2_step" if prec == "fp64" else "k2_step32p",
                          "peak_source": (f"derived: 152 SMs x 2 FP64 FMA units x 2 flop x {sm_max:.0f} MHz"
                                          if prec == "fp64" else
                                          f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz"),

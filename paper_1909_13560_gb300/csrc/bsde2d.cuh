@@ -580,21 +580,12 @@ __device__ __forceinline__ void nodes2f(const Params2 &P, const Lev2f &lev,
   }
 }
 
-__global__ void __launch_bounds__(kStep2TP * kMaxGroups, 1)
-    k2_step32(const Params2 P, const float4 *__restrict__ ring, double *__restrict__ V,
-              const Node2f *__restrict__ table, int n, Stats *st) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  const int kLL = P.k * P.LLp;
-  Node2f *tab = reinterpret_cast<Node2f *>(smem_raw);
-  float *part = reinterpret_cast<float *>(tab + kLL);  // [10][G][kStep2TP]
-  {
-    const float4 *src = reinterpret_cast<const float4 *>(table);
-    float4 *dst = reinterpret_cast<float4 *>(tab);
-    const int nv = kLL * int(sizeof(Node2f) / 16);
-    for (int t = threadIdx.x; t < nv; t += blockDim.x) dst[t] = src[t];
-  }
-  __syncthreads();
-  wait_predecessor();
+// One tile of kStep2TP points of level n, by every thread of the CTA: `tab`
+// is the pair table (in shared memory or in the kernel's parameters), `part`
+// the groups' partial sums in shared memory.
+__device__ __forceinline__ void step2_tile32(const Params2 &P, const float4 *__restrict__ ring,
+                                             double *__restrict__ V, const Node2f *tab,
+                                             float *part, int n, Stats *st) {
   const int tp = threadIdx.x % kStep2TP, g = threadIdx.x / kStep2TP;
   const int64_t q0p = int64_t(blockIdx.x) * kStep2TP;
   const int64_t qq = q0p + tp;
@@ -680,6 +671,44 @@ __global__ void __launch_bounds__(kStep2TP * kMaxGroups, 1)
     V[2 * P.Np + qq] = double(z2h) + double(z2l);
   }
   record_picard(st, active, it, double(d), P.picard_tol);
+}
+
+// The FP32C 2-D step with the pair table copied into shared memory by every
+// CTA (tables beyond the parameter capacity below).
+__global__ void __launch_bounds__(kStep2TP * kMaxGroups, 1)
+    k2_step32(const Params2 P, const float4 *__restrict__ ring, double *__restrict__ V,
+              const Node2f *__restrict__ table, int n, Stats *st) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int kLL = P.k * P.LLp;
+  Node2f *tab = reinterpret_cast<Node2f *>(smem_raw);
+  float *part = reinterpret_cast<float *>(tab + kLL);  // [10][G][kStep2TP]
+  {
+    const float4 *src = reinterpret_cast<const float4 *>(table);
+    float4 *dst = reinterpret_cast<float4 *>(tab);
+    const int nv = kLL * int(sizeof(Node2f) / 16);
+    for (int t = threadIdx.x; t < nv; t += blockDim.x) dst[t] = src[t];
+  }
+  __syncthreads();
+  wait_predecessor();
+  step2_tile32(P, ring, V, tab, part, n, st);
+}
+
+// The pair table as a kernel parameter (up to K = 6 with L <= 8, the
+// paper's 2-D settings): a group's threads read the same entry, so it comes
+// through the constant cache and leaves the L1 data path to the level
+// records.
+constexpr int kPairTab2Cap = kMaxK * 32;
+struct PairTab2 {
+  Node2f e[kPairTab2Cap];
+};
+
+__global__ void __launch_bounds__(kStep2TP * kMaxGroups, 1)
+    k2_step32p(const Params2 P, const float4 *__restrict__ ring, double *__restrict__ V,
+               const __grid_constant__ PairTab2 tab, int n, Stats *st) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float *part = reinterpret_cast<float *>(smem_raw);  // [10][G][kStep2TP]
+  wait_predecessor();
+  step2_tile32(P, ring, V, tab.e, part, n, st);
 }
 
 __device__ double interp2_point32(const Params2 &P, const Lev2f &lev, int field, double X1,
@@ -914,6 +943,8 @@ struct bsde2_plan_s {
   cudaGraphExec_t graph[2];  // [closed-form start, imported start]
   int64_t launches;
   bsde::Stats2 *host_stats;  // pinned
+  bool tab_param;            // FP32C: the pair table fits the step's parameters
+  bsde::PairTab2 tab;        // ... and is passed by value (k2_step32p)
 };
 
 namespace bsde {
@@ -925,6 +956,14 @@ static size_t step32_2d_smem(const Params2 &P) {
 static void launch2_step(bsde2_plan_t *pl, cudaStream_t s, int n) {
   const Params2 &P = pl->P;
   const unsigned blocks = unsigned((P.Np + kStep2TP - 1) / kStep2TP);
+  if (P.precision == BSDE_FP32C && pl->tab_param) {
+    launch_pdl(k2_step32p, blocks, unsigned(kStep2TP * P.G),
+               sizeof(float) * 10 * size_t(P.G) * kStep2TP, s, P,
+               reinterpret_cast<const float4 *>(pl->ws + pl->lay.ring),
+               reinterpret_cast<double *>(pl->ws + pl->lay.vals), pl->tab, n,
+               reinterpret_cast<Stats *>(pl->ws + pl->lay.stats));
+    return;
+  }
   if (P.precision == BSDE_FP32C) {
     launch_pdl(k2_step32, blocks, unsigned(kStep2TP * P.G), step32_2d_smem(P), s, P,
                reinterpret_cast<const float4 *>(pl->ws + pl->lay.ring),
@@ -1068,6 +1107,8 @@ int bsde2_plan(const bsde2_problem *p, void *dev_workspace, size_t bytes, bsde2_
     build_pairs2f(pl->P, tab, t32);
     e = cudaMemcpy(pl->ws + lay.table, t32.data(), sizeof(Node2f) * t32.size(),
                    cudaMemcpyHostToDevice);
+    pl->tab_param = t32.size() <= size_t(kPairTab2Cap);
+    if (pl->tab_param) std::memcpy(pl->tab.e, t32.data(), sizeof(Node2f) * t32.size());
     const size_t sm = step32_2d_smem(pl->P);
     if (e == cudaSuccess && sm > 48 * 1024)
       e = cudaFuncSetAttribute(k2_step32, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
