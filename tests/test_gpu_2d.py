@@ -62,6 +62,9 @@ CASES = {
     "ragged_L5": _with(W.ex4_problem(M=50, N=6, k=2, L=5), Nx1=77, Nx2=45, x1_max=6.0),
     "drift_L3": _with(W.ex4_problem(M=40, N=10, k=4, L=3, x_lim=3.0), a1=0.3, a2=-0.2,
                       b11=0.8, b21=0.3, b22=0.6),
+    # 2 x 128 mirror pairs: beyond the parameter table's 192 entries, so the
+    # FP32C step copies its table into shared memory (k2_step32)
+    "ex4_L16_k2": W.ex4_problem(M=96, N=8, k=2, L=16),
 }
 
 
