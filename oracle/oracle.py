@@ -22,6 +22,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _SRC2 = os.path.join(_HERE, "oracle2d.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+# A prebuilt library used in place of liboracle.so (the mutation tests load
+# copies of the oracle with planted mistakes this way).
+_LIB_OVERRIDE = os.environ.get("BSDE_ORACLE_LIB")
 _lock = threading.Lock()
 _lib = None
 
@@ -89,24 +92,30 @@ class _Result(ctypes.Structure):
 def build(force: bool = False) -> str:
     """Compile oracle.c into liboracle.so next to it (plain C, FP64, no FMA
     contraction, OpenMP over grid points)."""
+    if _LIB_OVERRIDE:
+        return _LIB_OVERRIDE
     with _lock:
         if (not force and os.path.exists(_LIB)
                 and os.path.getmtime(_LIB) >= max(os.path.getmtime(_SRC),
                                                   os.path.getmtime(_SRC2))):
             return _LIB
         tmp = _LIB + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-               "-fno-fast-math", "-fopenmp", _SRC, _SRC2, "-o", tmp, "-lm"]
-        subprocess.run(cmd, check=True)
+        compile_library(_SRC, _SRC2, tmp)
         os.replace(tmp, _LIB)
         return _LIB
+
+
+def compile_library(src: str, src2: str, out: str) -> None:
+    """Compile the oracle's two C sources into the shared library `out`."""
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+           "-fno-fast-math", "-fopenmp", src, src2, "-o", out, "-lm"]
+    subprocess.run(cmd, check=True)
 
 
 def _load():
     global _lib
     if _lib is None:
-        build()
-        lib = ctypes.CDLL(_LIB)
+        lib = ctypes.CDLL(build())
         P = ctypes.POINTER
         d = ctypes.c_double
         lib.orc_gauss_hermite.argtypes = [ctypes.c_int, P(d), P(d)]
