@@ -701,6 +701,8 @@ constexpr int kPairTab2Cap = kMaxK * 32;
 struct PairTab2 {
   Node2f e[kPairTab2Cap];
 };
+static_assert(sizeof(Params2) + sizeof(PairTab2) + 32 <= 32764,
+              "k2_step32p parameters exceed the kernel parameter limit");
 
 __global__ void __launch_bounds__(kStep2TP * kMaxGroups, 1)
     k2_step32p(const Params2 P, const float4 *__restrict__ ring, double *__restrict__ V,

@@ -1127,6 +1127,10 @@ __host__ __device__ inline size_t step32_smem(int G, int kP) {
 struct PairTab32 {
   PairF32 e[kMaxK * (kMaxL / 2)];
 };
+// kernel parameters are limited to 32764 bytes
+static_assert(sizeof(Params) + sizeof(DrvC<float>) + sizeof(Ring32) + sizeof(PairTab32) + 16 <=
+                  32764,
+              "k_step32 parameters exceed the kernel parameter limit");
 
 template <int DRV>
 __global__ void __launch_bounds__(kStepTP * kMaxGroups, 3)
