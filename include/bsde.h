@@ -59,15 +59,16 @@ enum {
                               + z^2 e^{-t^2}) / 2                       (Eq. 24)     */
   BSDE_DRIVER_SHORT_RATE = 5 /* f = -x y: discounting at the short rate x, the
                               forward state where f is evaluated (the zero-coupon
-                              bond; FP64, general forward path only)               */
+                              bond; general forward path only)                     */
 };
 
 /* forward process: a(x) dt + b(x) dW, advanced from the grid point by one
  * Euler step over j dt (the general Markovian X of Section 1) */
 enum {
   BSDE_FORWARD_CONST = 0, /* a = a_x, b = b_x (exact; the constant-shift kernels)  */
-  BSDE_FORWARD_AFFINE = 1 /* a = a_x + a_1 x, b = b_x + b_1 x (FP64; the node
-                             positions are computed per point).  With an
+  BSDE_FORWARD_AFFINE = 1 /* a = a_x + a_1 x, b = b_x + b_1 x (the node
+                             positions are computed per point; FP32C keeps
+                             each node's offset as a float pair).  With an
                              x-dependent a or b only z_form = EYDW with k_z = 1
                              is consistent: Eq. 20's E[z^{n+1}] relies on the
                              identity E[y DeltaW] = dt E[z] of constant
@@ -96,9 +97,10 @@ enum {
   BSDE_FP64 = 0,  /* everything in IEEE double                                     */
   BSDE_FP32C = 1  /* levels as float (hi, lo) pairs, FP32 interpolation and driver,
                      compensated (error-free product and sum) accumulation of the
-                     y and z expectations, double for the final combination of
-                     y^n and z^n and the Picard convergence test; spline second
-                     derivatives from exact float differences of the pairs       */
+                     y and z expectations, z^n and the explicit part of y^n as
+                     normalized float pairs, Picard in FP32 on the increment
+                     with an exact convergence test; spline second derivatives
+                     from exact float differences of the pairs                   */
 };
 
 /* first term of the z line of Eq. 20 */
@@ -127,10 +129,9 @@ enum {
   BSDE_EINVAL = -1,     /* bad problem: k or k_z outside 1..6, max(k, k_z) > N,
                            Nx < 4, L outside 1..64, x0 outside [x_min, x_max],
                            unknown id or mode, T <= 0, init_substeps < 1 or
-                           N init_substeps > 2^30 with ONESTEP, the general
-                           forward path (AFFINE, SHORT_RATE, ONE, CALL_PRICE)
-                           outside FP64 or a terminal whose closed form needs
-                           a forward process the problem does not have         */
+                           N init_substeps > 2^30 with ONESTEP, or a terminal
+                           whose closed form needs a forward process the
+                           problem does not have (ONE, CALL_PRICE)              */
   BSDE_ENOSPC = -2,     /* workspace smaller than bsde_workspace_bytes()          */
   BSDE_ECUDA = -3,      /* a CUDA call failed (detail in bsde_last_error())       */
   BSDE_ENOMEM = -4,     /* host allocation failed                                 */
@@ -294,8 +295,9 @@ typedef struct bsde_batch_config {
 
 /* Workspace for the n problems ps[0..n-1] (rings, tables, descriptors,
  * queue, per-problem statistics).  BSDE_EINVAL if any problem is invalid,
- * not BSDE_FP32C or asks for the one-step start-up (batches start from the
- * closed form; K_z and the z form are free). */
+ * not BSDE_FP32C, asks for the one-step start-up or takes the general
+ * forward path (AFFINE or SHORT_RATE): batches run the constant-shift
+ * kernels from the closed form; K_z and the z form are free. */
 BSDE_API int bsde_batch_workspace_bytes(int n, const bsde_problem *ps, size_t *bytes);
 
 /* Plan the batch on dev_workspace (caller-owned, >= bsde_batch_workspace_bytes,
@@ -325,7 +327,8 @@ BSDE_API void bsde_batch_free(bsde_batch_t *b);
  * request is admitted when a slot and enough of the device pool for its
  * level ring are free (admission by footprint), runs on the next free
  * cluster while others are in flight, and frees its slot and memory when
- * polled.  Problems must be BSDE_FP32C with the closed-form start.  A request
+ * polled.  Problems must be BSDE_FP32C with the closed-form start and a
+ * constant forward process (as for batches).  A request
  * gives the same result alone and in any mix (same kernels per tile, same
  * order of operations).  The server's waits for new requests are bounded: a
  * cluster that finds no request for idle_ms milliseconds stops the whole
