@@ -89,7 +89,7 @@ struct Params {
   int64_t Nx;
   int32_t N, k, L, driver, terminal, precision, smoothing, picard_max, nslot;
   int32_t ky, kz, zform, general;  // general: per-point node positions (AFFINE
-                                   // forward or an x-dependent driver), FP64
+                                   // forward or an x-dependent driver)
   double a_1, b_1;                 // AFFINE slopes of a(x), b(x)
   double T, dt, dx, x_min, x_max, x0, a_x, b_x;
   double r, mu, sigma, R, delta, lb_sign, strike;
@@ -117,7 +117,7 @@ struct Params {
 // Device workspace layout (byte offsets from the workspace base).
 struct Layout {
   size_t ring64;   // FP64: double4 (y, M_y, z, M_z) x nslot x Nx
-  size_t ringA;    // FP32C: float4 (y_hi, y_lo, z_hi, z_lo) x nslot x Nx
+  size_t ringA;    // FP32C: float4 (y_hi, z_hi, y_lo, z_lo) x nslot x Nx
   size_t ringB;    // FP32C: interval records, float4 (d, P) then float2 Q, x nslot x Nx
   size_t table;    // node table (K L entries)
   size_t ptable;   // FP32C pair table (K ceil(L/2) entries)
