@@ -815,7 +815,8 @@ def run_2d(args, rank, world, local_rank):
                          "within_tol": abs(ey - 8.00e-7) <= 0.02 * 8.00e-7
                          and abs(ez - 2.32e-6) <= 0.02 * 2.32e-6},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
-                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": None if prec == "fp64" else _traffic("k2_step32p"),
                          # K = 6, L = 8: the 192-entry pair table fits the
                          # FP32C step's parameters (k2_step32p)
                          "kernel": "k2_step" if prec == "fp64" else "k2_step32p",
