@@ -46,6 +46,8 @@ MUTATIONS = [
     ("Picard weight gamma_1 in place of gamma_0", "oracle.c",
      "double yn1 = A + h * gy[0] * orc_driver(p, tn, xi, y, z);",
      "double yn1 = A + h * gy[1] * orc_driver(p, tn, xi, y, z);", PINS),
+    ("cell-averaged payoff: the -d term dropped in the strike's cell", "oracle.c",
+     "*u = K * (expm1(d) - d) / dx;", "*u = K * expm1(d) / dx;", PINS),
     ("2-D: sign of the outer central difference term", "oracle2d.c",
      "+ 8.0 * f[(i + 1) * s] - f[(i + 2) * s]) / 12.0;",
      "+ 8.0 * f[(i + 1) * s] + f[(i + 2) * s]) / 12.0;", PINS_2D),

@@ -223,6 +223,30 @@ def test_closed_forms_solve_the_pde(make):
             assert abs(res) < 1e-5
 
 
+def test_log_price_call_cell_average():
+    """Kreiss smoothing read as cell averages (Section 5, Example 3): level N
+    holds the averages over [x - dx/2, x + dx/2] of the payoff (e^x - K)^+ and
+    of b_X g' = sigma e^x 1{x > ln K}, against a fine midpoint rule; without
+    smoothing it holds the point values."""
+    p = W.call_problem(Nx=41, N=8, k=1, L=8, smoothing=1)
+    iy, iz = O.init_levels(p)
+    dx = (p["x_max"] - p["x_min"]) / (p["Nx"] - 1)
+    x = p["x_min"] + dx * np.arange(p["Nx"])
+    s = (np.arange(2_000_000) + 0.5) / 2_000_000 - 0.5  # the jump at ln K costs ~1/n
+    for i in range(p["Nx"]):
+        xs = x[i] + dx * s
+        ey = np.exp(xs)
+        assert iy[0, i] == pytest.approx(np.mean(np.maximum(ey - p["strike"], 0.0)), abs=2e-6)
+        assert iz[0, i] == pytest.approx(np.mean(p["sigma"] * ey * (xs > math.log(p["strike"]))),
+                                         abs=2e-5)
+    py, pz = O.init_levels(dict(p, smoothing=0))
+    assert np.allclose(py[0], np.maximum(np.exp(x) - p["strike"], 0.0), rtol=0, atol=1e-12)
+    off_kink = np.abs(x - math.log(p["strike"])) > 1e-9  # g' is undefined at the strike
+    assert np.allclose(pz[0][off_kink],
+                       (p["sigma"] * np.exp(x) * (x > math.log(p["strike"])))[off_kink],
+                       rtol=0, atol=1e-12)
+
+
 def test_call_closed_form_solves_the_pde_in_log_price():
     p = W.call_problem(T=1.0, r=0.03, mu=0.05, delta=0.01, sigma=0.2, Nx=5, N=4, k=1)
     h = 1e-4
