@@ -20,6 +20,7 @@ ORACLE_DIR = os.path.join(ROOT, "oracle")
 PINS = "tests/test_oracle_pins.py"
 PINS_2D = "tests/test_oracle_2d.py"
 PINS_GENERAL = "tests/test_oracle_general.py"
+PINS_VARIANTS = "tests/test_oracle_variants.py"
 
 # (name, source file, text, replacement, pin file)
 MUTATIONS = [
@@ -48,6 +49,19 @@ MUTATIONS = [
      "double yn1 = A + h * gy[1] * orc_driver(p, tn, xi, y, z);", PINS),
     ("cell-averaged payoff: the -d term dropped in the strike's cell", "oracle.c",
      "*u = K * (expm1(d) - d) / dx;", "*u = K * expm1(d) / dx;", PINS),
+    ("spline right-hand side 3 (second differences) in place of 6", "oracle.c",
+     "double rhs = 6.0 * (v[q] - 2.0 * v[q + 1] + v[q + 2]) / (dx * dx);",
+     "double rhs = 3.0 * (v[q] - 2.0 * v[q + 1] + v[q + 2]) / (dx * dx);", PINS),
+    ("Gauss-Hermite Newton polish stepping the wrong way", "oracle.c",
+     "a -= pL / d;", "a += pL / d;", PINS),
+    ("one-step start-up with the main step dt instead of dt / S", "oracle.c",
+     "q.N = p->N * S;", "q.N = p->N;", PINS_VARIANTS),
+    ("2-D: the DeltaW components of the z line swapped", "oracle2d.c",
+     "s += gz[j] * (E[j - 1][3 + d] - E[j - 1][d]);",
+     "s += gz[j] * (E[j - 1][4 - d] - E[j - 1][d]);", PINS_2D),
+    ("2-D: sign of a one-sided difference coefficient", "oracle2d.c",
+     "48.0 * f[(i + 1) * s] - 36.0 * f[(i + 2) * s]",
+     "48.0 * f[(i + 1) * s] + 36.0 * f[(i + 2) * s]", PINS_2D),
     ("2-D: sign of the outer central difference term", "oracle2d.c",
      "+ 8.0 * f[(i + 1) * s] - f[(i + 2) * s]) / 12.0;",
      "+ 8.0 * f[(i + 1) * s] + f[(i + 2) * s]) / 12.0;", PINS_2D),
