@@ -660,7 +660,7 @@ __device__ __forceinline__ void step2_tile32(const Params2 &P, const float4 *__r
       const float dn = __fmul_rn(P.hg0_f, __fmaf_rn(P.alpha_f, __fadd_rn(Ah, dl), zlin));
       ++it;
       d = fabsf(__fsub_rn(dn, dl));
-      const bool cyc = dn == dpp;
+      const bool cyc = dn == dpp && picard_cycle_ok(d, __fadd_rn(Ah, dl), dn);
       dpp = dl;
       dl = dn;
       if (cyc) d = 0.f;

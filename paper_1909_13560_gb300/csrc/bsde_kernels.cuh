@@ -795,8 +795,10 @@ __global__ void __launch_bounds__(kStepTP * kMaxGroups)
 // FP32 (|del| ~ dx |y'|, so its rounding is far below that of y).  The z and
 // y sums take the exact product of the coefficient's hi part with hi_c (FMA)
 // and add it by TwoSum into an (S, C) pair; the driver terms, which carry a
-// dt-sized or sqrt(dt)-sized weight, are summed in plain FP32.  The final
-// combination of z^n and A runs in FP64.
+// dt-sized or sqrt(dt)-sized weight, are summed in plain FP32 (the y driver
+// terms with their rounding error).  z^n and the explicit part A of y^n are
+// formed as normalized float pairs, and the Picard iteration runs in FP32 on
+// the increment y^n - A (finish_points32).
 // y and z go through the same arithmetic with the same weights, so it runs on
 // (y, z) lane pairs with packed FP32x2 instructions (one instruction, two
 // correctly rounded results).
@@ -1007,6 +1009,14 @@ __device__ __forceinline__ void store_partials(float *part, int G, int g, int tp
   part[6 * gs + o] = a.FyC;
 }
 
+// Whether a Picard two-cycle (delta^(p+1) == delta^(p-1)) of step d is the
+// rounding of the FP32 iteration and not an oscillation: d within 2^-22 of
+// |y| + |delta| (two to four ulps of the larger), y = A + delta being the
+// argument the FP32 driver sees and delta the increment it returns.
+__device__ __forceinline__ bool picard_cycle_ok(float d, float y, float delta) {
+  return d <= __fmul_rn(__fadd_rn(fabsf(y), fabsf(delta)), 2.384185791015625e-7f);
+}
+
 // The last part of the step for the kStepTP points of a tile, by the threads
 // tid < kStepTP of the CTA (the others pass through; all threads call it):
 // the groups' partial sums are added, z^n and the explicit part A of y^n are
@@ -1017,8 +1027,11 @@ __device__ __forceinline__ void store_partials(float *part, int G, int g, int tp
 // |delta^(p+1) - delta^(p)| <= tol is exact (near convergence the two
 // increments are within a factor two, so their float difference carries no
 // rounding; a float is <= tol exactly when it is <= picard_tol_f).  A
-// two-cycle across a rounding boundary of the FP32 argument is as far as the
-// FP32 driver can resolve, and ends it too.
+// two-cycle whose step is within a couple of ulps of the FP32 argument
+// A + delta or of the increment (picard_cycle_ok) is that argument's rounding
+// flipping between neighbours, as far as the FP32 driver can resolve, and
+// ends it too; a wider cycle is an oscillation of the iteration itself and
+// runs on to picard_max, where it is reported as non-convergence.
 template <int DRV, bool COH>
 __device__ __forceinline__ void finish_points32(const Params &P, const DrvC<float> &dc,
                                                 float4 *__restrict__ ringA, const float *part,
@@ -1055,7 +1068,7 @@ __device__ __forceinline__ void finish_points32(const Params &P, const DrvC<floa
       const float dn = hg0 * driver_x<DRV>(dc, tn, etn, emtn, xf, Ah + dl, zh);
       ++it;
       d = fabsf(__fsub_rn(dn, dl));
-      const bool cyc = dn == dpp;
+      const bool cyc = dn == dpp && picard_cycle_ok(d, __fadd_rn(Ah, dl), dn);
       dpp = dl;
       dl = dn;
       if (cyc) d = 0.f;

@@ -108,6 +108,19 @@ def test_2d_imported_levels_and_polynomial_exactness(B):
     assert np.max(np.abs(got["y"] - u(p["T"]))[inner]) < 1e-10
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_2d_picard_wide_two_cycle_is_reported(B, prec):
+    """Example 5's driver at r = 8 with k = 1, dt = 1/4: the Picard map has
+    slope k dt gy_0 alpha = -1 and alternates between two far-apart values;
+    both precisions report non-convergence, as the oracle does."""
+    p = W.ex5_problem(M=24, N=4, k=1, L=4, r=8.0)
+    ref = O.solve2(p)
+    got = B.Solver2(p, precision=prec).solve()
+    assert ref["status"] == 1
+    assert got["status"] == B.BSDE_WARN_NOCONV, got
+    assert got["picard_iters_max"] == p["picard_max"]
+
+
 def test_2d_repeat_solves_are_bitwise_identical(B):
     s = B.Solver2(W.ex4_problem(M=48, N=8, k=3))
     a = s.solve(want_level=True)

@@ -179,6 +179,28 @@ def test_picard_nonconvergence_is_reported(B):
     assert got["picard_iters_max"] == 1
 
 
+def test_picard_nonconvergence_is_reported_fp32c(B):
+    """The FP32C tail reports a Picard cap it hits, as the FP64 one does."""
+    p = dict(W.ex1_problem(Nx=300, N=10, k=2, L=8), picard_max=1, picard_tol=1e-15)
+    got = B.solve(p, "fp32c")
+    assert got["status"] == B.BSDE_WARN_NOCONV and got["picard_iters_max"] == 1
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_picard_wide_two_cycle_is_reported(B, prec):
+    """With k = 1, dt = 1/4 and the Black-Scholes driver at r = 8 the Picard
+    map delta -> k dt gy_0 f(A + delta, z) has slope k dt gy_0 (-r) = -1: its
+    iterates alternate between two values a whole |2 (delta - delta*)| apart.
+    Such a cycle is no rounding effect, and every precision reports it as
+    non-convergence, as the oracle does (Section 3.1 step 3)."""
+    p = W.call_problem(r=8.0, T=1.0, N=4, k=1, Nx=257, L=8)
+    ref = O.solve(p)
+    got = B.solve(p, prec)
+    assert ref["status"] == 1
+    assert got["status"] == B.BSDE_WARN_NOCONV, got
+    assert got["picard_iters_max"] == p["picard_max"]
+
+
 @pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 6])
 def test_config2_full_size(B, k):
     """Black-Scholes call, Nx = 65536, N = 256, L = 16: the benchmark workload,
