@@ -135,7 +135,8 @@ enum {
   BSDE_ENOSPC = -2,     /* workspace smaller than bsde_workspace_bytes()          */
   BSDE_ECUDA = -3,      /* a CUDA call failed (detail in bsde_last_error())       */
   BSDE_ENOMEM = -4,     /* host allocation failed                                 */
-  BSDE_ETIMEOUT = -5    /* a bounded device-side wait expired                     */
+  BSDE_ETIMEOUT = -5    /* a bounded device-side wait expired (the server's idle
+                           wait; single solves and batches have no device waits) */
 };
 
 /* Problem description (all fields read by bsde_plan; nothing is kept by
@@ -386,7 +387,9 @@ BSDE_API void bsde_server_free(bsde_server_t *s);
  * in device memory (BSDE_NOALLOC_MAX_BYTES per GPU, held by every GPU that
  * loads the library until the process exits).  It launches the kernels one
  * by one and calls no cudaMalloc, cudaMallocHost, cudaFree or any other
- * allocating routine; the plan constants live on the host stack.
+ * allocating routine.  The plan constants and node tables (about 130 KB)
+ * live in a file-scope host buffer, not on the caller's stack; a library
+ * mutex guards it, so calls from several host threads run one at a time.
  *
  * Arguments are those of bsde_plan and bsde_solve (the caller still passes
  * the initial levels, if any, and the output buffers).  The call waits for
@@ -396,7 +399,10 @@ BSDE_API void bsde_server_free(bsde_server_t *s);
  *
  * The first call on each device looks up that device's copy of the array
  * (cudaGetSymbolAddress, with the device current) and caches the address;
- * make that first call before any stream capture on the device.  All calls
+ * make that first call before any stream capture on the device.  The cached
+ * address belongs to the device's primary context: after cudaDeviceReset (or
+ * any reset of that context) this entry point must not be called again in
+ * the same process.  All calls
  * on a device share the one array, which keeps the contents of the last
  * call; every call rewrites what it reads before reading it.  Calls whose GPU
  * work overlaps (different streams, or different host threads, on the same

@@ -399,11 +399,9 @@ static int fill_result(bsde_plan_t *pl, bsde_result *r) {
   r->picard_resid_max = d;
   r->picard_iters_max = s.iters_max;
   r->levels_done = pl->P.N - pl->P.k + 1;
+  // single solves have no device-side waits (only the server's bounded idle
+  // wait sets Stats::timeout), so the status is convergence alone
   r->status = s.nonconv ? BSDE_WARN_NOCONV : BSDE_OK;
-  if (s.timeout) {
-    r->status = BSDE_ETIMEOUT;
-    return fail(BSDE_ETIMEOUT, "a bulk-copy wait in the step kernel gave up");
-  }
   return r->status;
 }
 
@@ -603,9 +601,20 @@ constexpr int kMaxDevices = 64;
 static unsigned char *g_noalloc_addr[kMaxDevices];
 static std::mutex g_noalloc_mu;
 
+// The host side of a no-allocation solve: the plan and its node tables
+// (about 130 KB), kept in this file-scope buffer rather than on the caller's
+// stack, which may be small (a plug-in thread, a musl thread's 128 KB).
+// Guarded by g_noalloc_mu for the whole call.
+struct NoallocHost {
+  bsde_plan_t pl;
+  HostTables tabs;
+  Stats st;
+};
+static NoallocHost g_noalloc_host;
+
+// Called with g_noalloc_mu held.
 static int noalloc_address(int dev, unsigned char **out) {
   if (dev < 0 || dev >= kMaxDevices) return fail(BSDE_EINVAL, "device ordinal out of range");
-  std::lock_guard<std::mutex> lk(g_noalloc_mu);
   if (!g_noalloc_addr[dev]) {
     void *ptr = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&ptr, noalloc_ws);
@@ -626,8 +635,12 @@ extern "C" int bsde_solve_noalloc(const bsde_problem *p, void *stream, const dou
   if (!p) return fail(BSDE_EINVAL, "null problem");
   if ((init_y == nullptr) != (init_z == nullptr))
     return fail(BSDE_EINVAL, "init_y and init_z must both be given or both be NULL");
-  // the plan lives on this stack frame: no host or device allocation
-  bsde_plan_t pl{};
+  // the plan and its tables live in a file-scope buffer: no host or device
+  // allocation, and little of the caller's stack; one call at a time
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  NoallocHost &H = g_noalloc_host;
+  bsde_plan_t &pl = H.pl;
+  pl = bsde_plan_t{};
   if (fill_params(*p, pl.P)) return fail(BSDE_EINVAL, "invalid problem");
   pl.lay = layout_for(*p);
   if (pl.lay.total > BSDE_NOALLOC_MAX_BYTES)
@@ -635,18 +648,17 @@ extern "C" int bsde_solve_noalloc(const bsde_problem *p, void *stream, const dou
                                  " bytes of workspace; the no-allocation workspace holds " +
                                  std::to_string(size_t(BSDE_NOALLOC_MAX_BYTES)));
   pl.prob = *p;
-  cudaGetDevice(&pl.device);
+  BSDE_CUDA_TRY(cudaGetDevice(&pl.device));
   int rc = noalloc_address(pl.device, &pl.ws);
   if (rc) return rc;
   pl.ws_bytes = BSDE_NOALLOC_MAX_BYTES;
   driver_coefs(pl.P, pl.dc64, pl.dc32);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  HostTables tabs;  // on this stack frame (about 100 KB)
-  int rc2 = upload_tables(&pl, tabs, s);
+  int rc2 = upload_tables(&pl, H.tabs, s);
   if (rc2) return rc2;
   bind_runs(&pl);
   const Params &P = pl.P;
-  // the host tables live on this stack frame: wait for the copies
+  // the next call rewrites the host tables: wait for their copies
   BSDE_CUDA_TRY(cudaStreamSynchronize(s));
   double *sy = reinterpret_cast<double *>(pl.ws + pl.lay.stage);
   double *sz = sy + int64_t(P.k) * P.Nx;
@@ -665,12 +677,12 @@ extern "C" int bsde_solve_noalloc(const bsde_problem *p, void *stream, const dou
   const cudaMemcpyKind okind = out_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
   if (out_y) BSDE_CUDA_TRY(cudaMemcpyAsync(out_y, sy, out_bytes, okind, s));
   if (out_z) BSDE_CUDA_TRY(cudaMemcpyAsync(out_z, sy + P.Nx, out_bytes, okind, s));
-  Stats st{};
-  BSDE_CUDA_TRY(cudaMemcpyAsync(&st, pl.ws + pl.lay.stats, sizeof(Stats),
+  H.st = Stats{};
+  BSDE_CUDA_TRY(cudaMemcpyAsync(&H.st, pl.ws + pl.lay.stats, sizeof(Stats),
                                 cudaMemcpyDeviceToHost, s));
   BSDE_CUDA_TRY(cudaStreamSynchronize(s));
   if (!result) return BSDE_OK;
-  pl.host_stats = &st;
+  pl.host_stats = &H.st;
   return fill_result(&pl, result);
 }
 

@@ -73,6 +73,10 @@ def test_noalloc_matches_planned_solve_on_consecutive_calls(B):
     # previous ones, over the array the earlier calls filled
     p3 = W.sin_problem(Nx=700, N=10, k=2, L=8)
     calls.append((p3, "fp64", W.initial_levels(p3)))
+    # the one-step start-up (Section 3.1 step 2): its own node tables and the
+    # sub-run regions of the array
+    p4 = dict(W.call_problem(Nx=1000, N=16, k=3), init_mode="ONESTEP", init_substeps=2)
+    calls.append((p4, "fp32c", None))
     for i, (p, prec, init) in enumerate(calls):
         got = _noalloc(B, p, prec, init)
         ref = B.solve(p, prec, init=init, want_level=True)
