@@ -279,6 +279,18 @@ BSDE_API int bsde_gamma(int k, double *gy, double *gz);
 BSDE_API int bsde_l2_read_probe(const void *buf, size_t bytes, int reps, int grid, void *sink,
                                 void *stream);
 
+/* Measurement helper (no counterpart in the paper): enqueue on `stream` one
+ * launch of `grid` CTAs of 256 threads in which every thread runs 8
+ * independent fused multiply-add chains, 16 x `iters` steps each, and writes
+ * one double into sink[grid * 256] (device memory).  kind 0: FP64 FMA;
+ * 1: FP32 FMA; 2: packed FP32x2 FMA (two FP32 FMAs per instruction).  The
+ * launch's flop count (2 per FMA) goes to *flops (may be NULL).  Timed with
+ * CUDA events, this is the FMA pipe's rate that the step kernels' arithmetic
+ * is measured against.  BSDE_EINVAL for bad arguments (kind outside 0..2,
+ * iters < 1, grid outside 1..65535), BSDE_ECUDA if the launch fails. */
+BSDE_API int bsde_fma_probe(int kind, int iters, int grid, void *sink, void *stream,
+                            int64_t *flops);
+
 /* ---- batched solves ------------------------------------------------------
  * Many independent problems (uneven Nx, N, k, driver, parameters; all
  * precision BSDE_FP32C, closed-form start) solved by one persistent launch:

@@ -105,7 +105,7 @@ _SYMBOLS = ("bsde_workspace_bytes", "bsde_plan", "bsde_solve", "bsde_result_fetc
             "bsde_batch_get_config", "bsde_batch_autotune", "bsde_solve_batch", "bsde_batch_free",
             "bsde_request_bytes", "bsde_server_workspace_bytes", "bsde_server_create",
             "bsde_server_start", "bsde_server_submit", "bsde_server_poll", "bsde_server_stop",
-            "bsde_server_free", "bsde_l2_read_probe",
+            "bsde_server_free", "bsde_l2_read_probe", "bsde_fma_probe",
             "bsde2_workspace_bytes", "bsde2_plan", "bsde2_solve", "bsde2_result_fetch",
             "bsde2_enqueue_level", "bsde2_plan_launches", "bsde2_free",
             "bsde_enqueue_start", "bsde_enqueue_finish", "bsde_level_records")
@@ -159,6 +159,8 @@ def load(path: str = LIB_PATH):
     lib.bsde_server_free.argtypes = [vp]
     lib.bsde_server_free.restype = None
     lib.bsde_l2_read_probe.argtypes = [vp, ctypes.c_size_t, ctypes.c_int, ctypes.c_int, vp, vp]
+    lib.bsde_fma_probe.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp,
+                                   P(ctypes.c_int64)]
     lib.bsde2_workspace_bytes.argtypes = [P(bsde2_problem), P(ctypes.c_size_t)]
     lib.bsde2_plan.argtypes = [P(bsde2_problem), vp, ctypes.c_size_t, P(vp)]
     lib.bsde2_solve.argtypes = [vp, vp, vp, vp, vp, ctypes.c_int, vp, vp, vp, ctypes.c_int,
@@ -602,6 +604,38 @@ def l2_read_bandwidth(mib: int = 48, reps: int = 40, device=None) -> float:
         e1.record(stream)
         torch.cuda.synchronize(dev)
         best = max(best, buf.numel() * 4 * reps / (e0.elapsed_time(e1) / 1e3) / 1e9)
+    return best
+
+
+FMA_KINDS = {"fp64": 0, "fp32": 1, "fp32x2": 2}
+
+
+def fma_peak_tflops(kind: str, iters: int = 4096, device=None) -> float:
+    """The FMA pipe's rate in TFLOP/s (2 flop per FMA): one launch of
+    independent FMA chains on 8 CTAs of 256 threads per SM (after one warm-up
+    launch), timed with CUDA events on the launching stream; the best of
+    five launches.  kind: "fp64", "fp32" or "fp32x2" (packed)."""
+    import torch
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    props = torch.cuda.get_device_properties(dev)
+    grid = 8 * props.multi_processor_count
+    if kind == "fp64":
+        iters = max(1, iters // 32)  # the FP64 pipe is far slower: a launch of similar length
+    sink = torch.zeros(grid * 256, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    lib = load()
+    flops = ctypes.c_int64()
+    args = (FMA_KINDS[kind], iters, grid, ctypes.c_void_p(sink.data_ptr()),
+            ctypes.c_void_p(stream.cuda_stream), ctypes.byref(flops))
+    _check(lib.bsde_fma_probe(*args), "bsde_fma_probe")
+    best = 0.0
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _check(lib.bsde_fma_probe(*args), "bsde_fma_probe")
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        best = max(best, flops.value / (e0.elapsed_time(e1) / 1e3) / 1e12)
     return best
 
 

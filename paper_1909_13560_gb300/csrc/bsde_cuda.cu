@@ -584,6 +584,21 @@ int bsde_l2_read_probe(const void *buf, size_t bytes, int reps, int grid, void *
   return BSDE_OK;
 }
 
+int bsde_fma_probe(int kind, int iters, int grid, void *sink, void *stream, int64_t *flops) {
+  if (!sink || kind < 0 || kind > 2 || iters < 1 || grid < 1 || grid > 65535)
+    return fail(BSDE_EINVAL, "bad probe arguments");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  double *out = static_cast<double *>(sink);
+  const unsigned g = unsigned(grid);
+  if (kind == 0) k_fma_probe<double><<<g, 256, 0, s>>>(iters, out);
+  else if (kind == 1) k_fma_probe<float><<<g, 256, 0, s>>>(iters, out);
+  else k_fma_probe<float2><<<g, 256, 0, s>>>(iters, out);
+  BSDE_CUDA_TRY(cudaGetLastError());
+  if (flops)
+    *flops = int64_t(grid) * 256 * kFmaChains * kFmaUnroll * int64_t(iters) * 2 * (kind == 2 ? 2 : 1);
+  return BSDE_OK;
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------

@@ -1307,6 +1307,55 @@ __global__ void __launch_bounds__(256) k_l2_read(const float4 *__restrict__ buf,
 }
 
 // ---------------------------------------------------------------------------
+// Measurement helper: the FMA pipe's rate.  Every thread runs kFmaChains
+// independent chains a = a * m + c, kFmaUnroll steps each per iteration, and
+// stores the chains' sum into sink (so none is dropped).  T = double (the
+// FP64 pipe), float (scalar FP32) or float2 (packed fma.rn.f32x2, two FP32
+// FMAs per instruction).
+// ---------------------------------------------------------------------------
+constexpr int kFmaChains = 8, kFmaUnroll = 16;
+template <typename T>
+struct FmaProbe;
+template <>
+struct FmaProbe<double> {
+  static __device__ __forceinline__ double fma(double a, double m, double c) { return __fma_rn(a, m, c); }
+  static __device__ __forceinline__ double val(float v) { return double(v); }
+  static __device__ __forceinline__ double sum(double v) { return v; }
+};
+template <>
+struct FmaProbe<float> {
+  static __device__ __forceinline__ float fma(float a, float m, float c) { return __fmaf_rn(a, m, c); }
+  static __device__ __forceinline__ float val(float v) { return v; }
+  static __device__ __forceinline__ double sum(float v) { return double(v); }
+};
+template <>
+struct FmaProbe<float2> {
+  static __device__ __forceinline__ float2 fma(float2 a, float2 m, float2 c) { return f2fma(a, m, c); }
+  static __device__ __forceinline__ float2 val(float v) { return make_float2(v, 0.5f * v); }
+  static __device__ __forceinline__ double sum(float2 v) { return double(v.x) + double(v.y); }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_probe(int iters, double *sink) {
+  using F = FmaProbe<T>;
+  T a[kFmaChains];
+#pragma unroll
+  for (int q = 0; q < kFmaChains; ++q) a[q] = F::val(float(threadIdx.x + q) * 1e-3f);
+  const T m = F::val(0.9999f), c = F::val(1e-4f);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int u = 0; u < kFmaUnroll; ++u) {
+#pragma unroll
+      for (int q = 0; q < kFmaChains; ++q) a[q] = F::fma(a[q], m, c);
+    }
+  }
+  double acc = 0.0;
+#pragma unroll
+  for (int q = 0; q < kFmaChains; ++q) acc += F::sum(a[q]);
+  sink[size_t(blockIdx.x) * blockDim.x + threadIdx.x] = acc;
+}
+
+// ---------------------------------------------------------------------------
 // S4: readout of y^0, z^0 at x0 by the spline (Section 3.1 step 3).
 // ---------------------------------------------------------------------------
 template <int PREC, bool COH = false>
