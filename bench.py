@@ -1,11 +1,16 @@
 #!/usr/bin/env python
 """Benchmark of the multistep BSDE solve: grid-point time steps per second.
 
-One step = the Black-Scholes call workload (log price, S0 = K = 100,
-r = .03, mu = .05, sigma = .2, T = 1, Nx = 65536, N = 256, L = 16) solved
-once for every k = 1..6: sum_k Nx (N - k + 1) grid-point time steps.
+Default workload (config3, the largest single-GPU configuration): the call
+with different lending and borrowing rates (r = .04, R = .06, mu = .06,
+sigma = .2, T = .5, strike 100) in log price, Nx = 2^20, N = 1024, L = 16,
+solved once per step for the configuration's k = 4 and for k = 2.  A solve
+counts towards the value only when it passes the gate (see GATE_TEXT): on
+this grid the scheme itself diverges at k = 4 (the FP64 oracle too), so that
+solve is timed but reported as excluded.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32c|fp64]
+                  [--workload config3|config2|config4|config5|ex4_2d|general|decomp]
   python bench.py --impl reference ...   (the FP64 CPU oracle on the host cores)
 
 Prints one JSON line (rank 0).  Under torchrun each rank solves its own copy
@@ -141,12 +146,54 @@ def _call_price(p):
     return S0 * math.exp(-q * T) * ncdf(d1) - K * math.exp(-r * T) * ncdf(d2)
 
 
-def _golden():
+def _gold_num(v):
+    # non-finite oracle values are stored as text ("nan", "inf", "-inf")
+    return float(v)
+
+
+def _golden(workload: str = "config2"):
+    """The FP64 oracle's stored (y0, z0) per k for a single-solve workload
+    (tests/golden/<workload>_oracle.json, written by the script beside it,
+    which calls only the oracle)."""
     try:
-        with open(os.path.join(ROOT, "tests", "golden", "config2_oracle.json")) as fh:
-            return {r["k"]: r for r in json.load(fh)["rows"]}
+        with open(os.path.join(ROOT, "tests", "golden", f"{workload}_oracle.json")) as fh:
+            rows = json.load(fh)["rows"]
     except OSError:
         return {}
+    out = {}
+    for r in rows:
+        r = dict(r)
+        for f in ("y0", "z0"):
+            r[f] = _gold_num(r[f])
+        out[int(r["k"])] = r
+    return out
+
+
+# The bench gate.  A solve is counted when (1) the scheme itself converges
+# on this grid -- the stored FP64 oracle's y0 and z0 lie within CONV_REL of
+# the closed form -- and (2) its y0 and z0 agree with that oracle within the
+# precision's tolerance, relative to max(1, |value|).
+CONV_REL = 1e-2
+PARITY_REL = {"fp32c": 1e-6, "fp64": 1e-12}
+
+
+def gate(y0: float, z0: float, oracle_y0: float, oracle_z0: float, exact_y0: float,
+         exact_z0: float, precision: str) -> dict:
+    conv = (math.isfinite(oracle_y0) and math.isfinite(oracle_z0)
+            and abs(oracle_y0 - exact_y0) <= CONV_REL * max(1.0, abs(exact_y0))
+            and abs(oracle_z0 - exact_z0) <= CONV_REL * max(1.0, abs(exact_z0)))
+    tol = PARITY_REL[precision]
+    ey, ez = abs(y0 - oracle_y0), abs(z0 - oracle_z0)
+    par = (math.isfinite(y0) and math.isfinite(z0)
+           and ey <= tol * max(1.0, abs(oracle_y0)) and ez <= tol * max(1.0, abs(oracle_z0)))
+    return {"scheme_converges": conv, "within_tol": par, "counted": conv and par,
+            "err_y0_vs_oracle": ey, "err_z0_vs_oracle": ez,
+            "err_y0_vs_exact": abs(y0 - exact_y0), "err_z0_vs_exact": abs(z0 - exact_z0)}
+
+
+GATE_TEXT = ("a solve counts when the stored FP64 oracle's y0 and z0 are within 1% of the "
+             "closed form (the scheme converges on this grid) and the solve's y0 and z0 are "
+             "within 1e-6 (FP32C) or 1e-12 (FP64) x max(1, |value|) of that oracle")
 
 
 def _golden_variants():
@@ -224,49 +271,101 @@ def _barrier(dist):
         dist.barrier()
 
 
-def cpu_baseline(levels: int, threads: int, workload: str = "config2") -> dict:
+C3_KS = (2, 4)
+
+
+def _single_problems(workload: str, ks=None):
+    """The solves of one step of a single-solve workload: config2 (k = 1..6)
+    or config3 at full size (the configuration's k = 4 beside k = 2)."""
+    from paper_1909_13560_gb300 import workloads as W
+    if workload == "config3":
+        return [(k, W.config3(k=k)) for k in (ks or C3_KS)]
+    return [(k, W.config2(k=k)) for k in (ks or KS)]
+
+
+def _workload_text(workload: str, ks) -> str:
+    if workload == "config3":
+        return ("config3: call with lending/borrowing rates (r=.04, R=.06, mu=.06, sigma=.2, "
+                "T=.5, K=100, x in ln100 +- 6 sigma sqrt T), Nx=2^20, N=1024, L=16; one solve "
+                f"per k in {{{','.join(map(str, ks))}}} per step (the configuration's k=4 beside "
+                "k=2)")
+    return ("config2: Black-Scholes call in log price (S0=K=100, r=.03, mu=.05, sigma=.2, T=1, "
+            f"x in ln100 +- 6 sigma), Nx=65536, N=256, L=16; one solve per k in "
+            f"{{{','.join(map(str, ks))}}} per step")
+
+
+def cpu_baseline(levels: int, threads: int, workload: str = "config3") -> dict:
     """The FP64 oracle as it stands, on a bounded sample of the workload: its
     solves, first `levels` backward levels each, `threads` host threads."""
     from oracle import oracle as O
     from paper_1909_13560_gb300 import workloads as W
-    probs = [W.config3()] if workload == "config3" else [W.config2(k=k) for k in KS]
+    probs = _single_problems(workload)
     t0 = time.perf_counter()
     units = 0
-    for p in probs:
+    for _, p in probs:
         r = O.solve(p, levels=levels, threads=threads)
         units += int(p["Nx"]) * int(r["levels_done"])
     dt = time.perf_counter() - t0
-    name = "config3 (Nx=2^20, k=4)" if workload == "config3" else "config2 k=1..6"
+    ks = ",".join(str(k) for k, _ in probs)
     return {"value": units / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{name}, first {levels} backward levels of each solve, "
-                      f"{threads} host threads; {units} grid-point steps in {dt:.2f} s"}
+            "sample": f"{workload} (k={ks}, full grid), first {levels} backward levels of each "
+                      f"solve, {threads} host threads; {units} grid-point steps in {dt:.2f} s"}
 
 
 def run_reference(args, rank, world):
+    """The FP64 CPU oracle on the host cores, on the same workload, metric and
+    unit as our arm; each step a bounded sample (the first --ref-levels
+    backward levels of each of the workload's solves)."""
     if rank != 0:
         return
     threads = os.cpu_count() or 1
-    levels = args.ref_levels
+    wl = args.workload if args.workload in ("config2", "config3") else "config3"
+    levels = args.ref_levels if args.ref_levels else (4 if wl == "config3" else 12)
     for _ in range(args.warmup):
-        cpu_baseline(levels, threads)
+        cpu_baseline(levels, threads, wl)
     t0 = time.perf_counter()
     tot = 0.0
     for _ in range(args.steps):
-        r = cpu_baseline(levels, threads)
+        r = cpu_baseline(levels, threads, wl)
         tot += r["value"]
     wall = time.perf_counter() - t0
     value = tot / args.steps
+    probs = _single_problems(wl)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 * wall / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "config2: Black-Scholes call in log price, Nx=65536, "
-                                   "N=256, k=1..6, L=16", "Nx": 65536, "N": 256, "k": list(KS),
-                       "L": 16, "sample_levels_per_k": levels},
+            "config": {"workload": _workload_text(wl, [k for k, _ in probs]),
+                       "Nx": probs[0][1]["Nx"], "N": probs[0][1]["N"],
+                       "k": [k for k, _ in probs], "L": 16, "sample_levels_per_solve": levels},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": r["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def measured_peaks(dev) -> dict:
+    """FMA-pipe rates measured now by bsde_fma_probe (FP32: the better of the
+    scalar and packed FP32x2 forms; FP64) and the L2 -> SM read bandwidth by
+    bsde_l2_read_probe."""
+    from paper_1909_13560_gb300 import bsde as B
+    f32 = B.fma_peak_tflops("fp32", device=dev)
+    f32x2 = B.fma_peak_tflops("fp32x2", device=dev)
+    return {"fp32_tflops": max(f32, f32x2), "fp32_scalar_tflops": f32, "fp32x2_tflops": f32x2,
+            "fp64_tflops": B.fma_peak_tflops("fp64", device=dev),
+            "l2_read_gbs": B.l2_read_bandwidth(device=dev),
+            "how": "bsde_fma_probe: 8 CTAs x 256 threads per SM, 8 independent FMA chains per "
+                   "thread, best of 5 launches (CUDA events); bsde_l2_read_probe: 48 MiB "
+                   "L2-resident buffer read 40 times with 16-byte loads, best of 5"}
+
+
+def _gpu_uuid(dev):
+    import torch
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        return uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        return None
 
 
 def run_ours(args, rank, world, local_rank):
@@ -276,21 +375,19 @@ def run_ours(args, rank, world, local_rank):
     from paper_1909_13560_gb300 import workloads as W
 
     dist = _dist_init(world)
-    ks = tuple(args.ks)
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream(dev)
     sp = stream.cuda_stream
-    c3 = args.workload == "config3"
-    if c3:
-        # the configuration's k = 4, beside k = 2 (which converges on this
-        # grid; k = 4 diverges as the oracle does at the reduced size)
-        ks = (2, 4) if tuple(args.ks) == KS else ks
-        probs = [W.config3(k=k) for k in ks]
-    else:
-        probs = [W.config2(k=k) for k in ks]
+    wl = args.workload
+    c3 = wl == "config3"
+    ks_arg = None if tuple(args.ks) == KS else tuple(args.ks)
+    probs_k = _single_problems(wl, ks_arg)
+    ks = tuple(k for k, _ in probs_k)
+    probs = [p for _, p in probs_k]
     solvers = [B.Solver(p, args.precision, device=dev) for p in probs]
-    units_per_step = sum(W.gp_steps(p) for p in probs)
+    units = [W.gp_steps(p) for p in probs]
+    units_per_step = sum(units)
     launches_per_step = sum(s.launches for s in solvers)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
@@ -313,16 +410,9 @@ def run_ours(args, rank, world, local_rank):
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    uuid = None
-    try:
-        uuid = str(torch.cuda.get_device_properties(dev).uuid)
-        if not uuid.startswith("GPU-"):
-            uuid = "GPU-" + uuid
-    except Exception:
-        uuid = None
     _barrier(dist)
     torch.cuda.synchronize(dev)
-    with ClockSampler(uuid) as clk:
+    with ClockSampler(_gpu_uuid(dev)) as clk:
         w0 = time.perf_counter()
         for i in range(args.steps):
             flush.zero_()  # L2 flush between steps, outside the events
@@ -334,45 +424,55 @@ def run_ours(args, rank, world, local_rank):
     _barrier(dist)
     ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
     ms_max = _max_over_ranks(dist, ms)
-    value = world * units_per_step * args.steps / (ms_max / 1000.0)
 
-    # results of the last step and their gate against the stored oracle values
-    # (config2), or against the closed form (config3 at full size, where no
-    # oracle run is stored)
-    gold = {} if c3 else _golden()
-    rows = []
-    ok = True
-    for k, p, s in zip(ks, probs, solvers):
+    # the gate: results of the last step against the stored FP64 oracle values
+    gold = _golden(wl)
+    rows, counted = [], []
+    for k, p, s, u in zip(ks, probs, solvers, units):
         r = B.bsde_result_fetch(s.plan, sp)
         g = gold.get(k)
-        if c3:
-            exact = _call_price(p)
-            row = {"k": k, "y0": r.y0, "z0": r.z0, "picard_iters_max": r.picard_iters_max,
-                   "exact_y0": exact, "err_y0_vs_exact": abs(r.y0 - exact),
-                   "diverged": not (abs(r.y0 - exact) <= 1.0)}
-            rows.append(row)
-            continue
-        row = {"k": k, "y0": r.y0, "z0": r.z0, "picard_iters_max": r.picard_iters_max}
+        row = {"k": k, "y0": r.y0, "z0": r.z0, "picard_iters_max": r.picard_iters_max,
+               "gp_steps": u}
         if g:
-            row["err_y0_vs_oracle"] = abs(r.y0 - g["y0"])
-            row["rel_err_y0_vs_oracle"] = abs(r.y0 - g["y0"]) / max(1.0, abs(g["y0"]))
-            row["err_y0_vs_exact"] = abs(r.y0 - g["exact_y0"])
-            # where the scheme itself diverges on this grid (the FP64 oracle is
-            # far from the price), the run follows the oracle's growth and no
-            # absolute tolerance applies: reported, not gated
-            row["diverged"] = not (abs(g["y0"] - g["exact_y0"]) <= 1.0)
-            if not row["diverged"]:
-                tol = (1e-12 if args.precision == "fp64" else 1e-6) * max(1.0, abs(g["y0"]))
-                row["within_tol"] = row["err_y0_vs_oracle"] <= tol
-                ok = ok and row["within_tol"]
+            row.update({"oracle_y0": g["y0"], "oracle_z0": g["z0"], "exact_y0": g["exact_y0"],
+                        "exact_z0": g["exact_z0"]})
+            row.update(gate(r.y0, r.z0, g["y0"], g["z0"], g["exact_y0"], g["exact_z0"],
+                            args.precision))
+        else:
+            row.update({"counted": False, "why": "no stored oracle value for this k"})
         rows.append(row)
+        counted.append(bool(row["counted"]))
+    counted_units = sum(u for u, c in zip(units, counted) if c)
+    value = world * counted_units * args.steps / (ms_max / 1000.0)
+    excluded = [{"k": r["k"], "gp_steps": r["gp_steps"],
+                 "reason": (r.get("why") or
+                            ("the scheme diverges on this grid: the FP64 oracle's "
+                             f"y0 = {r['oracle_y0']:.6g}, z0 = {r['oracle_z0']:.6g} against the "
+                             f"closed form {r['exact_y0']:.6g}, {r['exact_z0']:.6g}"
+                             if not r["scheme_converges"] else
+                             "outside the parity tolerance of the FP64 oracle"))}
+                for r in rows if not r["counted"]]
+
+    # each solve alone (context for the concurrent step)
+    alone_ms = {}
+    for k, s in zip(ks, solvers):
+        tot = 0.0
+        for _ in range(3):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            B.bsde_solve(s.plan, sp, want_result=False)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            tot += e0.elapsed_time(e1)
+        alone_ms[str(k)] = tot / 3
 
     # dominant kernel: the step kernel, re-running level 0 of each plan (its
     # input levels 1..k are resident after the solve).  The repeats are
     # captured in a CUDA graph, so the host's launch overhead does not starve
     # the device; the graph is replayed on the timing stream between events.
     reps = 20
-    kern_ms, kern_flops, step_us = 0.0, 0.0, {}
+    kern_ms, kern_flops, kern_l2, step_us, levels_total = 0.0, 0.0, 0.0, {}, 0
     for k, p, s in zip(ks, probs, solvers):
         B.bsde_enqueue_level(s.plan, sp, 0, 1)
         torch.cuda.synchronize(dev)
@@ -391,28 +491,30 @@ def run_ours(args, rank, world, local_rank):
         avg = e0.elapsed_time(e1) / reps
         step_us[str(k)] = round(1000.0 * avg, 3)
         nlev = p["N"] - k + 1
+        levels_total += nlev
         kern_ms += avg * nlev
         kern_flops += flops_per_gp_step(k, p["L"]) * p["Nx"] * nlev
+        kern_l2 += 40.0 * p["Nx"] * k * p["L"] * nlev
         del graph
-    peaks = _peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = _alu_peak_tflops(args.precision, sm_max)
+    pk = measured_peaks(dev)
+    fp64 = args.precision == "fp64"
+    peak = pk["fp64_tflops"] if fp64 else pk["fp32_tflops"]
     achieved = kern_flops / (kern_ms / 1000.0) / 1e12
     # the FP32C step kernel streams one A record (16 B) and one interval
     # record (24 B) per point and node from L2: its L2 -> SM rate against
     # the L2 read bandwidth measured now by a plain streaming kernel
     l2 = None
-    if args.precision == "fp32c":
-        l2_bytes = sum(40.0 * p["Nx"] * k * p["L"] * (p["N"] - k + 1) for k, p in zip(ks, probs))
-        l2_peak = B.l2_read_bandwidth(device=dev)
-        l2_gbs = l2_bytes / (kern_ms / 1000.0) / 1e9
-        l2 = {"achieved": l2_gbs, "peak": l2_peak, "unit": "GB/s", "frac": l2_gbs / l2_peak,
-              "bytes_per_point_node": 40,
-              "peak_source": "measured in this run: bsde_l2_read_probe, 48 MiB L2-resident "
-                             "buffer read 40 times by 8 CTAs per SM with 16-byte loads"}
+    if not fp64:
+        l2_gbs = kern_l2 / (kern_ms / 1000.0) / 1e9
+        l2 = {"achieved": l2_gbs, "peak": pk["l2_read_gbs"], "unit": "GB/s",
+              "frac": l2_gbs / pk["l2_read_gbs"], "bytes_per_point_node": 40,
+              "peak_source": "measured in this run (bsde_l2_read_probe)"}
 
-    # end to end through the C ABI with host buffers: initial levels copied in
-    # from pinned memory, level 0 and the result read back, every step
+    # end to end through the C ABI with host buffers: bsde_solve takes the
+    # pinned host initial levels and writes level 0 into pinned host memory,
+    # copies included; the solves of a step run concurrently, one host thread
+    # (and stream) each, and the step ends when every result is on the host
+    import threading
     host_in, host_out = [], []
     h2d = d2h = 0
     for p in probs:
@@ -425,46 +527,39 @@ def run_ours(args, rank, world, local_rank):
         host_out.append((oy, oz))
         h2d += ty.numel() * 8 + tz.numel() * 8
         d2h += oy.numel() * 8 + oz.numel() * 8 + 40
-    # device staging for the concurrent schedule: per solve its own stream
-    # copies the pinned host levels in, solves from them, copies level 0 out;
-    # the step ends when every result (level 0 and the statistics) is on the
-    # host
-    dev_bufs = [(torch.empty_like(ty, device=dev), torch.empty_like(tz, device=dev),
-                 torch.empty_like(oy, device=dev), torch.empty_like(oz, device=dev))
-                for (ty, tz), (oy, oz) in zip(host_in, host_out)]
+    e2e_res = [None] * len(solvers)
+
+    def e2e_one(i, st):
+        (ty, tz), (oy, oz) = host_in[i], host_out[i]
+        e2e_res[i] = B.bsde_solve(solvers[i].plan, st.cuda_stream, ty.data_ptr(), tz.data_ptr(),
+                                  True, oy.data_ptr(), oz.data_ptr(), True)
 
     def e2e_step():
         if args.sequential:
-            for s, (ty, tz), (oy, oz) in zip(solvers, host_in, host_out):
-                B.bsde_solve(s.plan, sp, ty.data_ptr(), tz.data_ptr(), True, oy.data_ptr(),
-                             oz.data_ptr(), True)
+            for i in range(len(solvers)):
+                e2e_one(i, stream)
             return
-        conc.fork.record(stream)
-        for s, st, ev, (ty, tz), (oy, oz), (dy, dz, ey, ez) in zip(
-                solvers, conc.streams, conc.joins, host_in, host_out, dev_bufs):
-            st.wait_event(conc.fork)
-            with torch.cuda.stream(st):
-                dy.copy_(ty, non_blocking=True)
-                dz.copy_(tz, non_blocking=True)
-                B.bsde_solve(s.plan, st.cuda_stream, dy.data_ptr(), dz.data_ptr(), False,
-                             ey.data_ptr(), ez.data_ptr(), False, want_result=False)
-                oy.copy_(ey, non_blocking=True)
-                oz.copy_(ez, non_blocking=True)
-            ev.record(st)
-        for ev in conc.joins:
-            stream.wait_event(ev)
-        for s in solvers:
-            B.bsde_result_fetch(s.plan, sp)  # waits for the stream: results on the host
+        th = [threading.Thread(target=e2e_one, args=(i, st))
+              for i, st in enumerate(conc.streams)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
 
+    torch.cuda.synchronize(dev)
     e2e_step()
     _barrier(dist)
-    torch.cuda.synchronize(dev)
     e_t0 = time.perf_counter()
     for _ in range(args.steps):
         e2e_step()
-    torch.cuda.synchronize(dev)
     e_dt = _max_over_ranks(dist, time.perf_counter() - e_t0)
-    e2e_value = world * units_per_step * args.steps / e_dt
+    e2e_counted = 0
+    for k, u, r in zip(ks, units, e2e_res):
+        g = gold.get(k)
+        if g and gate(r.y0, r.z0, g["y0"], g["z0"], g["exact_y0"], g["exact_z0"],
+                      args.precision)["counted"]:
+            e2e_counted += u
+    e2e_value = world * e2e_counted * args.steps / e_dt
 
     variants = None
     if not c3 and not args.no_variants:
@@ -472,58 +567,58 @@ def run_ours(args, rank, world, local_rank):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(max(1, args.cpu_levels // 8) if c3 else args.cpu_levels,
-                           os.cpu_count() or 1, args.workload)
-        # and on one host thread, a smaller sample
-        one = cpu_baseline(max(1, args.cpu_levels // 64) if c3 else max(1, args.cpu_levels // 8),
-                           1, args.workload)
+        lv = max(1, args.cpu_levels // (16 if c3 else 1))
+        cpu = cpu_baseline(lv, os.cpu_count() or 1, wl)
+        one = cpu_baseline(max(1, lv // 8), 1, wl)
         cpu["single_thread"] = {"value": one["value"], "cores": 1, "sample": one["sample"]}
 
     if rank == 0:
-        kname = "k_step32" if args.precision == "fp32c" else "k_step64"
+        kname = "k_step64" if fp64 else "k_step32"
+        tkey = f"{kname}_{wl}"
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if args.precision == "fp32c" else "f64",
+            "dtype": "f64" if fp64 else "f32",
             "data": "synthetic",
-            "config": {"workload": ("config3: call with lending/borrowing rates (r=.04, R=.06, "
-                                    "mu=.06, sigma=.2, T=.5, K=100, x in ln100 +- 6 sigma sqrt T), "
-                                    f"Nx=2^20, N=1024, k={','.join(map(str, ks))} (one solve each per step), L=16")
-                                   if c3 else
-                                   "config2: Black-Scholes call in log price (S0=K=100, "
-                                   "r=.03, mu=.05, sigma=.2, T=1, x in ln100 +- 6 sigma), "
-                                   "Nx=65536, N=256, k=1..6 (one solve each per step), L=16",
+            "config": {"workload": _workload_text(wl, ks),
                        "Nx": probs[0]["Nx"], "N": probs[0]["N"], "k": list(ks), "L": 16,
                        "precision": args.precision,
-                       "l2": "flushed between steps (256 MiB write, outside the timed events); "
-                             "within a solve the level ring (<= 15 MB) is L2-resident by design",
+                       "l2": ("flushed between steps (256 MiB write, outside the timed events); "
+                              "inputs of the timed steps are the level rings, "
+                              + ("210 MB at k = 4, larger than L2" if c3 else
+                                 "<= 18 MB per solve, L2-resident within a solve by design")),
                        "schedule": ("the step's solves one after another on one stream"
                                     if args.sequential else
                                     "the step's solves concurrently, one stream each "
                                     "(forked from and joined to the timing stream)"),
                        "parallelism": f"{world} independent replica(s)"},
-            "accuracy": ({"gate": "no oracle at this size: y0 vs the closed form (Black-Scholes "
-                                  "at r - (R - r)); the oracle at the reduced size Nx=2^16, N=256 "
-                                  "diverges at k=4 as well (tests/test_gpu_parity.py)",
-                          "rows": rows} if c3 else
-                         {"gate": "|y0 - stored FP64 oracle| <= 1e-6 max(1, |y0|) (FP32C) or "
-                                  "1e-12 max(1, |y0|) (FP64) on the k where the scheme converges; "
-                                  "diverged k (k >= 4 on this grid: the oracle itself grows to "
-                                  "1e5..1e7) reported with their relative error",
-                          "all_within_tol": ok, "rows": rows}),
+            "accuracy": {"gate": GATE_TEXT, "oracle": f"tests/golden/{wl}_oracle.json",
+                         "counted_gp_steps_per_step": counted_units,
+                         "all_gp_steps_per_step": units_per_step, "rows": rows},
+            "excluded": excluded,
+            "ungated": {"value": world * units_per_step * args.steps / (ms_max / 1000.0),
+                        "note": "every solve of the step counted, diverged ones included "
+                                "(not the metric)"},
+            "solve_alone_ms": alone_ms,
             "roofline": {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak,
-                         "traffic": _traffic(kname) if args.precision == "fp32c" else None,
-                         "traffic_source": "profiles/dram_traffic.json (ncu, k = 6 launch)",
-                         "peak_source": f"derived: 152 SMs x {'128 FP32 lanes' if args.precision == 'fp32c' else '2 FP64 FMA units'} x 2 flop x {sm_max:.0f} MHz",
+                         "traffic": _traffic(tkey),
+                         "traffic_source": f"profiles/dram_traffic.json[{tkey}] (ncu)",
+                         "peak_source": ("measured in this run: bsde_fma_probe, "
+                                         + ("FP64 FMA" if fp64 else
+                                            "FP32 FMA (better of scalar and packed FP32x2)")
+                                         + " (of measured)"),
                          "flop_per_gp_step": {str(k): flops_per_gp_step(k, 16) for k in ks},
-                         "avg_launch_ms": kern_ms / sum(p['N'] - p['k'] + 1 for p in probs),
+                         "avg_launch_ms": kern_ms / levels_total,
                          "step_launch_us": step_us,
                          "l2": l2},
+            "peaks": pk,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h},
+                    "d2h_bytes_per_step": d2h,
+                    "how": "bsde_solve with pinned host initial levels in and level 0 out, one "
+                           "host thread and stream per solve, gated like value"},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk.summary(),
             "wall_s_timed_region": wall,
@@ -1195,16 +1290,17 @@ def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=None,
-                    help="timed steps (default: 100 for config2, whose step is ~16 ms, so that "
-                         "the clock samples cover the timed region; 40 otherwise)")
+                    help="timed steps (default: 20 for config3, 100 for config2, whose step "
+                         "is ~16 ms, so that the clock samples cover the timed region; 40 "
+                         "otherwise; 10 for the reference arm)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp32c", "fp64"], default="fp32c")
     ap.add_argument("--workload", choices=["config2", "config3", "config4", "config5", "ex4_2d",
                                            "general", "decomp"],
-                    default="config2",
-                    help="config2: the Black-Scholes solves k = 1..6 (default); "
-                         "config3: the lending/borrowing call at Nx=2^20, N=1024, k=4; "
+                    default="config3",
+                    help="config3: the lending/borrowing call at Nx=2^20, N=1024 (k=4 and "
+                         "k=2; the default); config2: the Black-Scholes solves k = 1..6; "
                          "config4: the 4096-instance batch in one persistent launch; "
                          "config5: the serving run (Poisson arrivals, continuous batching)")
     ap.add_argument("--duration", type=float, default=10.0, help="config5: seconds of arrivals")
@@ -1213,7 +1309,9 @@ def main():
                     help="config2: the step counts k to solve (default 1,2,3,4,5,6; a subset "
                          "is for profiling one kernel shape, not a bench line)")
     ap.add_argument("--cpu-levels", type=int, default=64)
-    ap.add_argument("--ref-levels", type=int, default=12)
+    ap.add_argument("--ref-levels", type=int, default=0,
+                    help="reference arm: backward levels per solve in each step's sample "
+                         "(default 4 for config3, 12 for config2)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sequential", action="store_true",
                     help="config2/3: run a step's solves one after another on one stream "
@@ -1228,7 +1326,8 @@ def main():
         args.warmup = 3
     rank = _env_int("RANK", 0)
     if args.steps is None:
-        args.steps = 100 if (args.workload == "config2" and args.impl == "ours") else 40
+        args.steps = {"config2": 100, "config3": 20}.get(args.workload, 40) \
+            if args.impl == "ours" else 10
     world = _env_int("WORLD_SIZE", 1)
     local_rank = _env_int("LOCAL_RANK", 0)
     if args.impl == "reference":

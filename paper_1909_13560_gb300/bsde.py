@@ -404,6 +404,42 @@ class Solver:
             out["z"] = oz
         return out
 
+    def solve_levels(self, levels: int, stream=None) -> dict:
+        """The first `levels` backward levels only (n = N-K down to
+        N-K-levels+1), driven level by level through bsde_enqueue_start and
+        bsde_enqueue_level from the problem's own start; returns the last
+        computed level's y and z (float64 host arrays, read from the plan's
+        ring through bsde_level_records) and its index n."""
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        sp = stream.cuda_stream
+        p = self.problem
+        K = levels_K(p)
+        n_last = int(p["N"]) - K - int(levels) + 1
+        if levels < 1 or n_last < 0:
+            raise ValueError("levels outside 1..N-K+1")
+        lib = load()
+        _check(lib.bsde_enqueue_start(ctypes.c_void_p(self.plan), ctypes.c_void_p(sp), None, None,
+                                      0), "bsde_enqueue_start")
+        for n in range(int(p["N"]) - K, n_last - 1, -1):
+            bsde_enqueue_level(self.plan, sp, n, 3)
+        rec = ctypes.c_void_p()
+        rb = ctypes.c_size_t()
+        _check(lib.bsde_level_records(ctypes.c_void_p(self.plan), n_last, ctypes.byref(rec),
+                                      ctypes.byref(rb)), "bsde_level_records")
+        torch.cuda.synchronize(self.device)
+        nx = int(p["Nx"])
+        off = int(rec.value) - self.workspace.data_ptr()
+        raw = self.workspace[off:off + nx * int(rb.value)]
+        if int(rb.value) == 32:  # FP64 record (y, M_y, z, M_z)
+            v = raw.view(torch.float64).view(nx, 4).cpu().numpy()
+            y, z = v[:, 0].copy(), v[:, 2].copy()
+        else:  # FP32C record (y_hi, z_hi, y_lo, z_lo)
+            v = raw.view(torch.float32).view(nx, 4).cpu().numpy().astype(np.float64)
+            y, z = v[:, 0] + v[:, 2], v[:, 1] + v[:, 3]
+        return {"n": n_last, "y": y, "z": z}
+
     def close(self) -> None:
         if getattr(self, "plan", None):
             bsde_free(self.plan)
