@@ -246,7 +246,7 @@ BSDE_API int bsde_enqueue_finish(bsde_plan_t *plan, void *stream, double *out_y,
  * (valid for the levels the ring holds at the time of use) and their size:
  * FP64 32-byte records (y, M_y, z, M_z) as doubles, FP32C 16-byte records
  * (y_hi, z_hi, y_lo, z_lo) as floats, value = hi + lo; record i belongs to
- * grid point i.  The spline part (M, and the FP32C interval records) is
+ * grid point i.  The spline part (M, in FP32C a separate array) is
  * recomputed by the spline launch, so a halo exchange copies these records
  * between the step and the spline launches of a level. */
 BSDE_API int bsde_level_records(bsde_plan_t *plan, int n, void **records, size_t *record_bytes);

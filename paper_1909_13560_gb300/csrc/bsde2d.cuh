@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(kStep2TP * kMaxGroups)
       d = fabs(y1 - y);
       y = y1;
       ++it;
-      if (d <= P.picard_tol) break;
+      if (d <= P.picard_tol || !isfinite(d)) break;  // a non-finite step cannot converge
     }
     V[qq] = y;
     V[P.Np + qq] = z1;
@@ -664,7 +664,7 @@ __device__ __forceinline__ void step2_tile32(const Params2 &P, const float4 *__r
       dpp = dl;
       dl = dn;
       if (cyc) d = 0.f;
-      if (d <= P.picard_tol_f) break;
+      if (d <= P.picard_tol_f || !isfinite(d)) break;  // a non-finite step cannot converge
     }
     V[qq] = double(Ah) + (double(Al) + double(dl));
     V[P.Np + qq] = double(z1h) + double(z1l);

@@ -34,7 +34,6 @@ struct alignas(16) BatchSmem {
   float part[kPartArrays * kMaxGroups * kStepTP];
   float sr[2][spline_span<BSDE_FP32C>(kBatchSplineTile)];
   float sg[2][spline_span<BSDE_FP32C>(kBatchSplineTile)];
-  float sd[2][spline_span<BSDE_FP32C>(kBatchSplineTile)];
   float sid[kInvPivots];
   int inst;
 };
@@ -72,7 +71,7 @@ __device__ void batch_instance(BatchSmem &sm, unsigned char *ws, Stats *st,
   for (int m = 0; m < P.k; ++m) {
     for (int t = crank; t < nst; t += csize) {
       spline_tile<BSDE_FP32C, kBatchSplineTile, true, kBatchThreads>(
-          P, r64, r32, (P.N - m) % P.nslot, t, nt, sm.sr, sm.sg, sm.sd, sm.sid);
+          P, r64, r32, (P.N - m) % P.nslot, t, nt, sm.sr, sm.sg, sm.sid);
       __syncthreads();
     }
   }
@@ -88,7 +87,7 @@ __device__ void batch_instance(BatchSmem &sm, unsigned char *ws, Stats *st,
     cl.sync();
     for (int t = crank; t < nst; t += csize) {
       spline_tile<BSDE_FP32C, kBatchSplineTile, true, kBatchThreads>(
-          P, r64, r32, n % P.nslot, t, nt, sm.sr, sm.sg, sm.sd, sm.sid);
+          P, r64, r32, n % P.nslot, t, nt, sm.sr, sm.sg, sm.sid);
       __syncthreads();
     }
     cl.sync();

@@ -744,7 +744,7 @@ static int batch_layout(int n, const bsde_problem *ps, BatchLayout &L) {
     const size_t nx = size_t(p.Nx), ns = K + 1;
     L.ptable[i] = off; off = up(off + K * ((p.L + 1) / 2) * sizeof(PairF32));
     L.ringA[i] = off; off = up(off + ns * nx * 16);
-    L.ringB[i] = off; off = up(off + ns * nx * (16 + 8));
+    L.ringB[i] = off; off = up(off + ns * nx * 8);
   }
   L.total = off;
   return BSDE_OK;
@@ -1020,7 +1020,7 @@ namespace bsde {
 static size_t request_bytes(const bsde_problem &p) {
   auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
   const size_t nx = size_t(p.Nx), ns = size_t(problem_K(p) + 1);
-  return up(ns * nx * 16) + up(ns * nx * (16 + 8));
+  return up(ns * nx * 16) + up(ns * nx * 8);
 }
 
 static bool pool_alloc(bsde_server_t *s, size_t bytes, size_t &off) {

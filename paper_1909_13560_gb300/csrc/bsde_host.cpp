@@ -228,7 +228,7 @@ Layout layout_for(const bsde_problem &p) {
     L.ring64 = off; off = up(off + ns * nx * 32);
   } else {
     L.ringA = off; off = up(off + ns * nx * 16);
-    L.ringB = off; off = up(off + ns * nx * (16 + 8));  // interval records (d, P), Q
+    L.ringB = off; off = up(off + ns * nx * 8);  // second derivatives (M_y, M_z)
   }
   const size_t node = p.precision == BSDE_FP64 ? sizeof(NodeF64) : sizeof(NodeF32);
   L.table = off; off = up(off + size_t(K) * p.L * node);
@@ -239,7 +239,7 @@ Layout layout_for(const bsde_problem &p) {
       L.sub_ring64 = off; off = up(off + 2 * nx * 32);
     } else {
       L.sub_ringA = off; off = up(off + 2 * nx * 16);
-      L.sub_ringB = off; off = up(off + 2 * nx * (16 + 8));
+      L.sub_ringB = off; off = up(off + 2 * nx * 8);
     }
     L.sub_table = off; off = up(off + size_t(p.L) * node);
     L.sub_ptable = off; off = up(off + size_t((p.L + 1) / 2) * sizeof(PairF32));

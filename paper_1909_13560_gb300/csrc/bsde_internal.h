@@ -60,7 +60,7 @@ struct NodeF32 {
 // (shift_a, shift_b, cfz, cfy), (th_a, th_a, ka_a, ka_a),
 // (th_b, th_b, ka_b, ka_b), (cyh, czh, -cyh, -czh), (-cyl, -czl, cyzh, cyzl);
 // th = theta, ka = -theta (1 - theta) dx^2 / 6 (the spline value is
-// v_c + theta d + ka (P + theta Q) on the interval records).  cy is zero for
+// v_c + theta d + ka (P + theta Q), see Ring32).  cy is zero for
 // j != K_y.  cyz (hi, lo) is node a's weight of y^ in the z sum (E[y DeltaW]
 // z form, j = 1; node b's is -cyz): the pair adds cyz (y^_a - y^_b).
 struct PairF32 {
@@ -118,7 +118,7 @@ struct Params {
 struct Layout {
   size_t ring64;   // FP64: double4 (y, M_y, z, M_z) x nslot x Nx
   size_t ringA;    // FP32C: float4 (y_hi, z_hi, y_lo, z_lo) x nslot x Nx
-  size_t ringB;    // FP32C: interval records, float4 (d, P) then float2 Q, x nslot x Nx
+  size_t ringB;    // FP32C: float2 (M_y, M_z) x nslot x Nx
   size_t table;    // node table (K L entries)
   size_t ptable;   // FP32C pair table (K ceil(L/2) entries)
   size_t stage;    // 2 x K x Nx doubles: imported initial levels / exported level 0

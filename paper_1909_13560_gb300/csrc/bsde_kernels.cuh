@@ -196,20 +196,18 @@ __device__ __forceinline__ void wait_predecessor() {
 struct Ring64 {
   double4_32a *ring;
 };
-// FP32C level slots: A = (y_hi, z_hi, y_lo, z_lo) per node; per interval
-// [x_c, x_{c+1}] the spline as B = (d_y, d_z, P_y, P_z), C = (Q_y, Q_z) with
-// d = v_{c+1} - v_c, P = 2 M_c + M_{c+1}, Q = M_{c+1} - M_c (zero for the
-// last node), so that the spline value at x_c + theta dx is
-// v_c + theta d + kappa (P + theta Q), kappa = -theta (1 - theta) dx^2 / 6.
-// B and C share one allocation: C follows the nslot Nx records of B.
+// FP32C level slots, per node: A = (y_hi, z_hi, y_lo, z_lo) (value = hi + lo)
+// and M = (M_y, M_z), the natural spline's second derivatives.  The spline
+// value at x_c + theta dx is v_c + theta d + kappa (P + theta Q),
+// kappa = -theta (1 - theta) dx^2 / 6, with d = v_{c+1} - v_c,
+// P = 2 M_c + M_{c+1}, Q = M_{c+1} - M_c formed from nodes c and c + 1
+// (node_value): 24 bytes per node.
 struct Ring32 {
   float4 *A;
-  float4 *B;
-  float2 *C;
+  float2 *M;
 };
-__host__ __device__ inline Ring32 ring32(void *A, void *B, const Params &P) {
-  float4 *b = static_cast<float4 *>(B);
-  return Ring32{static_cast<float4 *>(A), b, reinterpret_cast<float2 *>(b + int64_t(P.nslot) * P.Nx)};
+__host__ __device__ inline Ring32 ring32(void *A, void *M, const Params &) {
+  return Ring32{static_cast<float4 *>(A), static_cast<float2 *>(M)};
 }
 
 __global__ void k_reset_stats(Stats *s) {
@@ -302,7 +300,7 @@ __global__ void k_export(const Params P, Ring64 r64, Ring32 r32, double *sy, dou
 // the tile and its halo, forms r in shared memory, runs the forward sweep of
 // each thread's chunk (warm-up from the left), then the backward sweep
 // (warm-up from the right over the neighbouring chunks' g), all on chip.  In
-// FP32C it then writes the interval records (d, P, Q) of its cells.
+// FP32C it then writes the second derivatives M of its nodes.
 // ---------------------------------------------------------------------------
 template <int PREC>
 struct SplineT;
@@ -327,7 +325,7 @@ __host__ __device__ constexpr int spline_span(int TS) {
 // One tile of TS unknowns of the level in `slot`, by the threads tid < nt of
 // the CTA (all threads of the CTA must call it: it holds barriers); NT is the
 // compile-time thread count the right-hand sides are spread over (nt >= NT).
-// sr, sg, sd: [2][spline_span(TS)] and sid: [kInvPivots] in shared memory;
+// sr, sg: [2][spline_span(TS)] and sid: [kInvPivots] in shared memory;
 // sid must hold the pivots 1/d_m in T before the call.
 // Unknown m is M_{m+1}; the tile is unknowns [a, b), the forward sweep runs
 // over [a, rb) and the backward one over [a, min(b + 1, u)) (one more on the
@@ -337,7 +335,6 @@ __device__ __forceinline__ void spline_tile(const Params &P, Ring64 r64, Ring32 
                                             int tile, int nt,
                                             typename SplineT<PREC>::T (*sr)[spline_span<PREC>(TS)],
                                             typename SplineT<PREC>::T (*sg)[spline_span<PREC>(TS)],
-                                            typename SplineT<PREC>::T (*sd)[spline_span<PREC>(TS)],
                                             const typename SplineT<PREC>::T *sid) {
   using T = typename SplineT<PREC>::T;
   constexpr int W = SplineT<PREC>::W;
@@ -354,9 +351,9 @@ __device__ __forceinline__ void spline_tile(const Params &P, Ring64 r64, Ring32 
   if (a >= u) return;  // uniform over the CTA
   auto bar_sync = [] { __syncthreads(); };
 
-  // right-hand sides r_m (m in [ra, rb)) and, in FP32C, first differences
-  // d_m = v_{m+1} - v_m (m in [ra, rb]), RC consecutive m per thread: the
-  // RC + 2 level values of a chunk are loaded together
+  // right-hand sides r_m (m in [ra, rb)), in FP32C from the first
+  // differences d_m = v_{m+1} - v_m, RC consecutive m per thread: the RC + 2
+  // level values of a chunk are loaded together
   constexpr int RC = (TS + 2 * W + 2 + NT - 1) / NT;
   {
     const int m0 = ra + tid * RC;
@@ -396,10 +393,6 @@ __device__ __forceinline__ void spline_tile(const Params &P, Ring64 r64, Ring32 
           if (m0 + q < rb) {
             sr[0][m0 + q - base] = inv6 * __fsub_rn(dy[q + 1], dy[q]);
             sr[1][m0 + q - base] = inv6 * __fsub_rn(dz[q + 1], dz[q]);
-          }
-          if (m0 + q <= rb) {
-            sd[0][m0 + q - base] = dy[q];
-            sd[1][m0 + q - base] = dz[q];
           }
         }
       }
@@ -509,22 +502,15 @@ __device__ __forceinline__ void spline_tile(const Params &P, Ring64 r64, Ring32 
     }
   } else {
     __syncthreads();
-    // interval records of cells a + 1 .. b (and 0 for the first tile, and the
-    // last node for the last tile); M_0 = M_{Nx-1} = 0 (natural spline)
+    // second derivatives of nodes a + 1 .. b (M_c is unknown c - 1), and of
+    // node 0 for the first tile and node Nx - 1 for the last tile:
+    // M_0 = M_{Nx-1} = 0 (natural spline)
     const int c0 = a == 0 ? 0 : a + 1;
     const int c1 = b == u ? u + 1 : b;  // inclusive
     for (int c = c0 + tid; c <= c1 && tid < nt; c += nt) {
-      float4 rec = make_float4(0.f, 0.f, 0.f, 0.f);
-      float2 q = make_float2(0.f, 0.f);
-      if (c <= u) {
-        const float my0 = c == 0 ? 0.f : sr[0][c - 1 - base], mz0 = c == 0 ? 0.f : sr[1][c - 1 - base];
-        const float my1 = c == u ? 0.f : sr[0][c - base], mz1 = c == u ? 0.f : sr[1][c - base];
-        rec = make_float4(sd[0][c - base], sd[1][c - base], __fmaf_rn(2.f, my0, my1),
-                          __fmaf_rn(2.f, mz0, mz1));
-        q = make_float2(__fsub_rn(my1, my0), __fsub_rn(mz1, mz0));
-      }
-      r32.B[off + c] = rec;
-      r32.C[off + c] = q;
+      const bool end = c == 0 || c == u + 1;
+      r32.M[off + c] = end ? make_float2(0.f, 0.f)
+                           : make_float2(sr[0][c - 1 - base], sr[1][c - 1 - base]);
     }
   }
 }
@@ -544,11 +530,11 @@ __global__ void __launch_bounds__(SplineLaunch<PREC>::NT)
   using T = typename SplineT<PREC>::T;
   constexpr int TS = SplineLaunch<PREC>::TS, NT = SplineLaunch<PREC>::NT;
   constexpr int S = spline_span<PREC>(TS);
-  __shared__ T sr[2][S], sg[2][S], sd[2][S];
+  __shared__ T sr[2][S], sg[2][S];
   __shared__ T sid[kInvPivots];
   if (threadIdx.x < kInvPivots) sid[threadIdx.x] = T(P.invd[threadIdx.x]);
   wait_predecessor();
-  spline_tile<PREC, TS, false, NT>(P, r64, r32, slot, blockIdx.x, blockDim.x, sr, sg, sd, sid);
+  spline_tile<PREC, TS, false, NT>(P, r64, r32, slot, blockIdx.x, blockDim.x, sr, sg, sid);
 }
 
 // ---------------------------------------------------------------------------
@@ -565,7 +551,8 @@ __device__ __forceinline__ void record_picard(Stats *st, bool active, int it, do
     const unsigned long long other = __shfl_xor_sync(full, db, o);
     db = other > db ? other : db;
   }
-  const unsigned nc = __reduce_or_sync(full, (active && d > tol) ? 1u : 0u);
+  // not <= tol: a NaN step (the level overflowed) is non-convergence too
+  const unsigned nc = __reduce_or_sync(full, (active && !(d <= tol)) ? 1u : 0u);
   if ((threadIdx.x & 31) == 0) {
     if (int(itm) > __ldcg(&st->iters_max)) atomicMax(&st->iters_max, int(itm));
     if (db > __ldcg(&st->resid_bits)) atomicMax(&st->resid_bits, db);
@@ -680,7 +667,7 @@ __global__ void __launch_bounds__(kStepTP * kMaxGroups)
       d = fabs(y1 - y);
       y = y1;
       ++it;
-      if (d <= P.picard_tol) break;
+      if (d <= P.picard_tol || !isfinite(d)) break;  // a non-finite step cannot converge
     }
     ring[int64_t(n % P.nslot) * P.Nx + ii] = make_double4_32a(y, 0.0, z, 0.0);
   }
@@ -782,7 +769,7 @@ __global__ void __launch_bounds__(kStepTP * kMaxGroups)
       d = fabs(y1 - y);
       y = y1;
       ++it;
-      if (d <= P.picard_tol) break;
+      if (d <= P.picard_tol || !isfinite(d)) break;  // a non-finite step cannot converge
     }
     ring[int64_t(n % P.nslot) * P.Nx + ii] = make_double4_32a(y, 0.0, z, 0.0);
   }
@@ -896,29 +883,38 @@ __device__ __forceinline__ bool pair_cell(int ii, int shift, int last, int &c) {
   return false;
 }
 
-// (y, z) spline value of one node as hi + del from the level data of its
-// cell c: A = (y_hi, z_hi, y_lo, z_lo) and the interval record B = (d, P),
-// C = Q (see Ring32); th = (theta, theta), ka = (kappa, kappa).
-__device__ __forceinline__ void node_value(const float4 &a, const float4 &bq, const float2 &cq,
-                                           float2 th, float2 ka, float2 &hi, float2 &del) {
-  hi = hi2(a);
-  del = f2fma(ka, f2fma(th, cq, lo2(bq)), f2fma(th, hi2(bq), lo2(a)));
+// (y, z) spline value of one node as hi + del from the level data of the
+// ends of its cell c: node records a0 = A_c, a1 = A_{c+1} (y_hi, z_hi,
+// y_lo, z_lo) and second derivatives m0 = M_c, m1 = M_{c+1} (see Ring32);
+// th = (theta, theta), ka = (kappa, kappa).  d = v_{c+1} - v_c is formed
+// from exact float differences of the pairs (neighbouring hi values differ
+// exactly away from sign changes), as the spline kernel forms its
+// right-hand sides.
+__device__ __forceinline__ void node_value(const float4 &a0, const float4 &a1, const float2 &m0,
+                                           const float2 &m1, float2 th, float2 ka, float2 &hi,
+                                           float2 &del) {
+  hi = hi2(a0);
+  const float2 d = f2add(f2sub(hi2(a1), hi2(a0)), f2sub(lo2(a1), lo2(a0)));
+  const float2 Pc = f2fma(make_float2(2.f, 2.f), m0, m1), Qc = f2sub(m1, m0);
+  del = f2fma(ka, f2fma(th, Qc, Pc), f2fma(th, d, lo2(a0)));
 }
 
 // The arithmetic of one node pair (see PairF32 for the entry e0..e4), given
-// the level data of the two nodes' cells.  S, C: compensated (y, z) sums;
-// Fz, Fy: driver terms.  ZF: the E[y DeltaW] z form's term cyz (y^_a - y^_b)
-// joins the z sum (compensated, the difference formed exactly by TwoSum).
+// the level data of the ends of the two nodes' cells (node a: aa0, aa1,
+// ma0, ma1; node b likewise).  S, C: compensated (y, z) sums; Fz, Fy: driver
+// terms.  ZF: the E[y DeltaW] z form's term cyz (y^_a - y^_b) joins the z
+// sum (compensated, the difference formed exactly by TwoSum).
 template <int DRV, bool ZF = false>
 __device__ __forceinline__ void pair_math(const DrvC<float> &dc, float tj, float et, float emt,
                                           const float4 &e0, const float4 &e1, const float4 &e2,
-                                          const float4 &e3, const float4 &e4, const float4 &aa,
-                                          const float4 &ab, const float2 &ac, const float4 &ba,
-                                          const float4 &bb, const float2 &bc, float2 &S, float2 &C,
-                                          float &Fz, float &Fy, float &FyC) {
+                                          const float4 &e3, const float4 &e4, const float4 &aa0,
+                                          const float4 &aa1, const float2 &ma0, const float2 &ma1,
+                                          const float4 &ba0, const float4 &ba1, const float2 &mb0,
+                                          const float2 &mb1, float2 &S, float2 &C, float &Fz,
+                                          float &Fy, float &FyC) {
   float2 ha, da, hb, db;
-  node_value(aa, ab, ac, hi2(e1), lo2(e1), ha, da);
-  node_value(ba, bb, bc, hi2(e2), lo2(e2), hb, db);
+  node_value(aa0, aa1, ma0, ma1, hi2(e1), lo2(e1), ha, da);
+  node_value(ba0, ba1, mb0, mb1, hi2(e2), lo2(e2), hb, db);
   const float2 va = f2add(ha, da), vb = f2add(hb, db);
   const float Fa = driver<DRV>(dc, tj, et, emt, va.x, va.y);
   const float Fb = driver<DRV>(dc, tj, et, emt, vb.x, vb.y);
@@ -950,8 +946,7 @@ __device__ __forceinline__ void pairs32(const DrvC<float> &dc, Ring32 r, int64_t
                                         const PairF32 *row, int q0, int q1, int ii, int last,
                                         float tj, float et, float emt, Acc32 &acc) {
   const float4 *A = r.A + off;
-  const float4 *B = r.B + off;
-  const float2 *Cq = r.C + off;
+  const float2 *M = r.M + off;
 #pragma unroll 1
   for (int q = q0; q < q1; ++q) {
     const float4 *te = reinterpret_cast<const float4 *>(row + q);
@@ -960,11 +955,15 @@ __device__ __forceinline__ void pairs32(const DrvC<float> &dc, Ring32 r, int64_t
     int ca, cb;
     if (pair_cell<CLAMP>(ii, __float_as_int(e0.x), last, ca)) e1 = make_float4(0.f, 0.f, 0.f, 0.f);
     if (pair_cell<CLAMP>(ii, __float_as_int(e0.y), last, cb)) e2 = make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 aa = ldl<COH>(A + ca), ab = ldl<COH>(B + ca), ba = ldl<COH>(A + cb),
-                 bb = ldl<COH>(B + cb);
-    const float2 ac = ldl<COH>(Cq + ca), bc = ldl<COH>(Cq + cb);
-    pair_math<DRV, ZF>(dc, tj, et, emt, e0, e1, e2, e3, e4, aa, ab, ac, ba, bb, bc, acc.S,
-                       acc.C, acc.Fz, acc.Fy, acc.FyC);
+    // the cell's right end (a clamped node sits on an end node with zero
+    // weights, so its right end is the node itself)
+    const int ca1 = CLAMP && ca == last ? ca : ca + 1, cb1 = CLAMP && cb == last ? cb : cb + 1;
+    const float4 aa0 = ldl<COH>(A + ca), aa1 = ldl<COH>(A + ca1), ba0 = ldl<COH>(A + cb),
+                 ba1 = ldl<COH>(A + cb1);
+    const float2 ma0 = ldl<COH>(M + ca), ma1 = ldl<COH>(M + ca1), mb0 = ldl<COH>(M + cb),
+                 mb1 = ldl<COH>(M + cb1);
+    pair_math<DRV, ZF>(dc, tj, et, emt, e0, e1, e2, e3, e4, aa0, aa1, ma0, ma1, ba0, ba1, mb0,
+                       mb1, acc.S, acc.C, acc.Fz, acc.Fy, acc.FyC);
   }
 }
 
@@ -1072,7 +1071,7 @@ __device__ __forceinline__ void finish_points32(const Params &P, const DrvC<floa
       dpp = dl;
       dl = dn;
       if (cyc) d = 0.f;
-      if (d <= P.picard_tol_f) break;
+      if (d <= P.picard_tol_f || !isfinite(d)) break;  // a non-finite step cannot converge
     }
     // y^n = A + delta, renormalized
     float yh = Ah, yl = Al;
@@ -1225,8 +1224,7 @@ __global__ void __launch_bounds__(kStepTP * kMaxGroups, 3)
     if (ii <= last) {
       const int64_t off = int64_t((n + w.j) % P.nslot) * P.Nx;
       const float4 *A = r32.A + off;
-      const float4 *Bv = r32.B + off;
-      const float2 *Cq = r32.C + off;
+      const float2 *M = r32.M + off;
       float tj, et, emt;
       level_time<DRV>(P, n + w.j, tj, et, emt);
       const PairF32 *row = tab + (w.j - 1) * P.Lp;
@@ -1255,11 +1253,12 @@ __global__ void __launch_bounds__(kStepTP * kMaxGroups, 3)
           cb = cb < 0 ? 0 : last;
           thb = kab = 0.f;
         }
-        const float4 aa = A[ca], ab = Bv[ca], ba = A[cb], bb = Bv[cb];
-        const float2 ac = Cq[ca], bc = Cq[cb];
+        const int ca1 = ca == last ? ca : ca + 1, cb1 = cb == last ? cb : cb + 1;
         float2 ha, da, hb, db;
-        node_value(aa, ab, ac, make_float2(tha, tha), make_float2(kaa, kaa), ha, da);
-        node_value(ba, bb, bc, make_float2(thb, thb), make_float2(kab, kab), hb, db);
+        node_value(A[ca], A[ca1], M[ca], M[ca1], make_float2(tha, tha), make_float2(kaa, kaa),
+                   ha, da);
+        node_value(A[cb], A[cb1], M[cb], M[cb1], make_float2(thb, thb), make_float2(kab, kab),
+                   hb, db);
         const float2 va = f2add(ha, da), vb = f2add(hb, db);
         const float Xa = __fmaf_rn(oa, dxf, xf), Xb = __fmaf_rn(ob, dxf, xf);
         const float Fa = driver_x<DRV>(dc, tj, et, emt, Xa, va.x, va.y);
@@ -1393,12 +1392,14 @@ __device__ void readout_values(const Params &P, Ring64 r64, Ring32 r32, int slot
     az = om * v[1][0] + th * v[1][1] +
          c6 * ((om * om * om - om) * M[1][0] + (th * th * th - th) * M[1][1]);
   } else {
-    // curvature part kappa (P + theta Q) of the interval record
-    const float4 rb = ldl<COH>(r32.B + off + c);
-    const float2 rq = ldl<COH>(r32.C + off + c);
+    // curvature part kappa (P + theta Q), P and Q formed in FP32 from the
+    // nodes' second derivatives as the step kernels form them
+    const float2 m0 = ldl<COH>(r32.M + off + c), m1 = ldl<COH>(r32.M + off + c + 1);
+    const float Py = __fmaf_rn(2.f, m0.x, m1.x), Pz = __fmaf_rn(2.f, m0.y, m1.y);
+    const float Qy = __fsub_rn(m1.x, m0.x), Qz = __fsub_rn(m1.y, m0.y);
     const double ka = -c6 * th * om;
-    ay = om * v[0][0] + th * v[0][1] + ka * (double(rb.z) + th * double(rq.x));
-    az = om * v[1][0] + th * v[1][1] + ka * (double(rb.w) + th * double(rq.y));
+    ay = om * v[0][0] + th * v[0][1] + ka * (double(Py) + th * double(Qy));
+    az = om * v[1][0] + th * v[1][1] + ka * (double(Pz) + th * double(Qz));
   }
 }
 

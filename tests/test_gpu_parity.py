@@ -314,6 +314,11 @@ def test_config3_full_size_k4_first_levels(B, prec):
     assert not (abs(g["y0"] - g["exact_y0"]) <= 1.0)  # the scheme diverges on this grid
     _cmp_levels(B, W.config3(k=4), prec, TOL64 if prec == "fp64" else TOL32,
                 f"config3 full k=4 {prec}")
+    # the whole solve: the growth ends the Picard iteration unconverged (in
+    # FP32C the levels overflow to NaN), reported as the oracle reports it
+    got = B.solve(W.config3(k=4), prec)
+    print(f"config3 full k=4 {prec}: y0 {got['y0']:.6g} status {got['status']}")
+    assert g["status"] == 1 and got["status"] == B.BSDE_WARN_NOCONV
 
 
 def test_concurrent_solves_equal_sequential_solves(B):

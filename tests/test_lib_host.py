@@ -111,9 +111,9 @@ def test_workspace_bytes_scale_with_ring():
     b32 = B.bsde_workspace_bytes(B.make_problem(p, "fp32c"))
     nx, ns = p["Nx"], p["k"] + 1
     # FP64: (y, M_y, z, M_z) per node; FP32C: (y_hi, z_hi, y_lo, z_lo) per node
-    # plus the interval record (d, P) and Q
+    # plus the second derivatives (M_y, M_z)
     assert ns * nx * 32 <= b64 < ns * nx * 32 + (8 << 20)
-    assert ns * nx * 40 <= b32 < ns * nx * 40 + (8 << 20)
+    assert ns * nx * 24 <= b32 < ns * nx * 24 + (8 << 20)
 
 
 @pytest.mark.parametrize("bad", [dict(kz=7), dict(kz=-1), dict(kz=6, N=5), dict(zform=2),
@@ -131,7 +131,7 @@ def test_workspace_bytes_of_the_variants():
     """K_z widens the ring to max(k, kz) + 1 slots; the one-step start-up adds
     a ring of two slots (and its small node tables), the z form nothing."""
     p = W.call_problem(Nx=1 << 16, N=64, k=2)
-    for prec, per_node in (("fp64", 32), ("fp32c", 40)):
+    for prec, per_node in (("fp64", 32), ("fp32c", 24)):
         base = B.bsde_workspace_bytes(B.make_problem(p, prec))
         wide = B.bsde_workspace_bytes(B.make_problem(dict(p, kz=5), prec))
         zf = B.bsde_workspace_bytes(B.make_problem(dict(p, zform=1), prec))
