@@ -134,18 +134,6 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def _call_price(p):
-    """Closed-form price of the call (Black-Scholes; the lending/borrowing
-    driver at rate r - s (R - r), since its min() is active for a call)."""
-    import math
-    r = p["r"] - (p["lb_sign"] * (p["R"] - p["r"]) if p["driver"] == "LB" else 0.0)
-    S0, K, sig, T, q = math.exp(p["x0"]), p["strike"], p["sigma"], p["T"], p.get("delta", 0.0)
-    d1 = (math.log(S0 / K) + (r - q + 0.5 * sig * sig) * T) / (sig * math.sqrt(T))
-    d2 = d1 - sig * math.sqrt(T)
-    ncdf = lambda x: 0.5 * math.erfc(-x / math.sqrt(2.0))
-    return S0 * math.exp(-q * T) * ncdf(d1) - K * math.exp(-r * T) * ncdf(d2)
-
-
 def _gold_num(v):
     # non-finite oracle values are stored as text ("nan", "inf", "-inf")
     return float(v)
@@ -639,9 +627,26 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def _golden4():
+    """The FP64 oracle's (y0, z0) and the closed form for every config4
+    instance (tests/golden/config4_oracle.json, in the order of
+    workloads.config4())."""
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "config4_oracle.json")) as fh:
+            d = json.load(fh)
+    except OSError:
+        return None
+    return [[_gold_num(v) for v in r[:4]] for r in d["rows"]]
+
+
 def run_batch(args, rank, world, local_rank):
-    """config4: 4096 Black-Scholes problems of uneven Nx, N, k, one persistent
-    launch per step (FP32C)."""
+    """config4: 4096 Black-Scholes problems of uneven Nx, N, k.  The value is
+    the FP32C batch (one persistent launch per step); beside it the plain
+    FP64 form, one bsde_solve per instance launched concurrently over a pool
+    of streams.  Both are gated per instance against the stored FP64 oracle
+    values, and only the instances that pass in both arms are counted."""
+    # more hardware work queues for the FP64 arm's many concurrent streams
+    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     import torch
     from paper_1909_13560_gb300 import bsde as B
     from paper_1909_13560_gb300 import workloads as W
@@ -650,9 +655,11 @@ def run_batch(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
     probs = W.config4()
-    units_per_step = sum(W.gp_steps(p) for p in probs)
-    flops_per_step = sum(flops_per_gp_step(p["k"], p["L"]) * W.gp_steps(p) for p in probs)
+    units = [W.gp_steps(p) for p in probs]
+    units_per_step = sum(units)
+    flops_per_step = sum(flops_per_gp_step(p["k"], p["L"]) * u for p, u in zip(probs, units))
     t0 = time.perf_counter()
     bs = B.BatchSolver(probs, device=dev)
     plan_s = time.perf_counter() - t0
@@ -666,16 +673,9 @@ def run_batch(args, rank, world, local_rank):
     torch.cuda.synchronize(dev)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    uuid = None
-    try:
-        uuid = str(torch.cuda.get_device_properties(dev).uuid)
-        if not uuid.startswith("GPU-"):
-            uuid = "GPU-" + uuid
-    except Exception:
-        uuid = None
     _barrier(dist)
     torch.cuda.synchronize(dev)
-    with ClockSampler(uuid) as clk:
+    with ClockSampler(_gpu_uuid(dev)) as clk:
         for i in range(args.steps):
             flush.zero_()
             starts[i].record(stream)
@@ -685,15 +685,64 @@ def run_batch(args, rank, world, local_rank):
     _barrier(dist)
     ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
     ms_max = _max_over_ranks(dist, ms)
-    value = world * units_per_step * args.steps / (ms_max / 1000.0)
-    res = bs.solve()
-    exact = []
-    from scipy.special import ndtr
-    for p in probs:
-        sq = p["sigma"] * math.sqrt(p["T"])
-        d1 = (math.log(100.0 / p["strike"]) + (p["r"] + 0.5 * p["sigma"] ** 2) * p["T"]) / sq
-        exact.append(100.0 * ndtr(d1) - p["strike"] * math.exp(-p["r"] * p["T"]) * ndtr(d1 - sq))
-    errs = sorted(abs(r["y0"] - e) for r, e in zip(res, exact))
+    res32 = bs.solve()
+
+    gold = _golden4()
+    if gold is None or len(gold) != len(probs):
+        raise RuntimeError("tests/golden/config4_oracle.json is missing or stale")
+    g32 = [gate(r["y0"], r["z0"], *g, "fp32c") for r, g in zip(res32, gold)]
+
+    # the plain FP64 per-instance form: one plan per instance, its solves
+    # launched round robin over a pool of streams forked from the timing
+    # stream and joined back
+    fp64 = None
+    if not args.no_fp64_arm:
+        solvers = [B.Solver(p, "fp64", device=dev) for p in probs]
+        pool = [torch.cuda.Stream(dev) for _ in range(32)]
+        fork, joins = torch.cuda.Event(), [torch.cuda.Event() for _ in pool]
+
+        def fp64_step():
+            fork.record(stream)
+            for st in pool:
+                st.wait_event(fork)
+            for i, s in enumerate(solvers):
+                B.bsde_solve(s.plan, pool[i % len(pool)].cuda_stream, want_result=False)
+            for st, ev in zip(pool, joins):
+                ev.record(st)
+                stream.wait_event(ev)
+
+        for _ in range(args.warmup):  # the first one also captures each plan's graph
+            flush.zero_()
+            fp64_step()
+        torch.cuda.synchronize(dev)
+        steps64 = max(1, args.fp64_steps)
+        e_ms = 0.0
+        for _ in range(steps64):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fp64_step()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            e_ms += e0.elapsed_time(e1)
+        e_ms = _max_over_ranks(dist, e_ms)
+        res64 = [B.bsde_result_fetch(s.plan, sp) for s in solvers]
+        g64 = [gate(r.y0, r.z0, *g, "fp64") for r, g in zip(res64, gold)]
+        for s in solvers:
+            s.close()
+        del solvers
+        fp64 = {"ms_per_step": e_ms / steps64, "steps": steps64, "g": g64,
+                "launches_per_step": None}
+
+    both = [a["counted"] and (fp64 is None or b["counted"])
+            for a, b in zip(g32, fp64["g"] if fp64 else g32)]
+    counted_units = sum(u for u, c in zip(units, both) if c)
+    value = world * counted_units * args.steps / (ms_max / 1000.0)
+    diverged = sum(1 for a in g32 if not a["scheme_converges"])
+    e32 = sorted(a["err_y0_vs_oracle"] / max(1.0, abs(g[0]))
+                 for a, g in zip(g32, gold) if a["scheme_converges"])
+    ex = sorted(a["err_y0_vs_exact"] for a in g32 if a["scheme_converges"])
+
     # end to end: plan the batch from host problem descriptions (tables and
     # descriptors copied in), solve, read every result back
     e_t0 = time.perf_counter()
@@ -701,9 +750,11 @@ def run_batch(args, rank, world, local_rank):
         bs.close()
         bs = B.BatchSolver(probs, device=dev)
         bs.set_config(cfg["cluster"], cfg["target_groups"])
-        bs.solve()
+        eres = bs.solve()
     torch.cuda.synchronize(dev)
     e_dt = _max_over_ranks(dist, time.perf_counter() - e_t0)
+    e_counted = sum(u for u, r, g, b in zip(units, eres, gold, both)
+                    if b and gate(r["y0"], r["z0"], *g, "fp32c")["counted"])
     h2d = sum(1024 + 64 * p["k"] * ((p["L"] + 1) // 2) for p in probs) + 4 * len(probs)
     d2h = 32 * len(probs)
     cpu = None
@@ -713,16 +764,14 @@ def run_batch(args, rank, world, local_rank):
         c0 = time.perf_counter()
         cu = 0
         for p in probs[:: max(1, len(probs) // 24)]:
-            r = O.solve(p, threads=threads)
+            O.solve(p, threads=threads)
             cu += W.gp_steps(p)
         cdt = time.perf_counter() - c0
         cpu = {"value": cu / cdt, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"every {max(1, len(probs) // 24)}th problem of config4 "
                          f"({cu} grid-point steps, {cdt:.1f} s)"}
     if rank == 0:
-        peaks = _peaks()
-        sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-        peak = _alu_peak_tflops("fp32c", sm_max)
+        pk = measured_peaks(dev)
         achieved = flops_per_step / (ms_max / args.steps / 1000.0) / 1e12
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -731,21 +780,47 @@ def run_batch(args, rank, world, local_rank):
             "data": "synthetic",
             "config": {"workload": "config4: 4096 Black-Scholes calls, seed 13560, K~U[70,130], "
                                    "sigma~U[.1,.5], T~U[.25,2], r~U[0,.05], Nx in 2^10..2^14, "
-                                   "N in 32..256, k~U{1..6}, L=16; one persistent launch",
+                                   "N in 32..256, k~U{1..6}, L=16; FP32C, one persistent launch",
                        "instances": len(probs), "batch_config": cfg, "plan_s": plan_s,
                        "l2": "flushed between steps (256 MiB write)",
                        "parallelism": f"{world} independent replica(s)"},
-            "accuracy": {"gate": "|y0 - Black-Scholes closed form| over the batch",
-                         "median": errs[len(errs) // 2], "p90": errs[int(0.9 * len(errs))],
-                         "max": errs[-1]},
-            "roofline": {"kernel": "k_batch32", "bound": "alu", "achieved": achieved, "peak": peak,
-                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                         "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz"},
-            "e2e": {"value": world * units_per_step * args.steps / e_dt, "unit": UNIT,
+            "accuracy": {"gate": GATE_TEXT + "; an instance counts only when it passes in both "
+                                             "the FP32C batch and the FP64 per-instance arm",
+                         "oracle": "tests/golden/config4_oracle.json",
+                         "instances_counted": sum(both),
+                         "instances_diverged": diverged,
+                         "instances_fp32c_outside_tol": sum(1 for a in g32 if a["scheme_converges"]
+                                                            and not a["within_tol"]),
+                         "counted_gp_steps_per_step": counted_units,
+                         "all_gp_steps_per_step": units_per_step,
+                         "fp32c_rel_err_y0_vs_oracle": {"median": e32[len(e32) // 2],
+                                                        "max": e32[-1]} if e32 else None,
+                         "err_y0_vs_exact": {"median": ex[len(ex) // 2],
+                                             "p90": ex[int(0.9 * len(ex))],
+                                             "max": ex[-1]} if ex else None},
+            "ungated": {"value": world * units_per_step * args.steps / (ms_max / 1000.0),
+                        "note": "every instance counted, diverged ones included (not the metric)"},
+            "roofline": {"kernel": "k_batch32", "bound": "alu", "achieved": achieved,
+                         "peak": pk["fp32_tflops"], "unit": "TFLOP/s",
+                         "frac": achieved / pk["fp32_tflops"], "traffic": None,
+                         "peak_source": "measured in this run: bsde_fma_probe, FP32 FMA (of "
+                                        "measured)"},
+            "peaks": pk,
+            "e2e": {"value": world * e_counted * args.steps / e_dt, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": 2 * args.steps,
             "clocks": clk.summary(),
         }
+        if fp64 is not None:
+            fv = world * counted_units * fp64["steps"] / (fp64["ms_per_step"] * fp64["steps"] / 1000.0)
+            line["fp64_per_instance"] = {
+                "value": fv, "unit": UNIT, "ms_per_step": fp64["ms_per_step"],
+                "steps": fp64["steps"],
+                "how": "one FP64 plan per instance (bsde_plan/bsde_solve, one CUDA graph per "
+                       "solve), the 4096 solves launched round robin over 32 streams, CUDA "
+                       "events around the whole set; same instances counted as the FP32C value",
+                "instances_within_tol": sum(1 for b in fp64["g"] if b["counted"]),
+                "fp32c_batch_over_fp64": value / fv if fv > 0 else None}
         if cpu is not None:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
@@ -1227,9 +1302,35 @@ def run_decomp(args, rank, world, local_rank):
         print(json.dumps(line), flush=True)
 
 
+def _closed_form_call(p):
+    """Closed-form price and z of a config5 request at t = 0 (Black-Scholes;
+    the lending/borrowing driver at the rate r - s (R - r), since its min()
+    is active everywhere for a call)."""
+    r = p["r"] - (p["lb_sign"] * (p["R"] - p["r"]) if p["driver"] == "LB" else 0.0)
+    S0, K, sig, T = math.exp(p["x0"]), p["strike"], p["sigma"], p["T"]
+    sq = sig * math.sqrt(T)
+    d1 = (math.log(S0 / K) + (r + 0.5 * sig * sig) * T) / sq
+    ncdf = lambda x: 0.5 * math.erfc(-x / math.sqrt(2.0))
+    price = S0 * ncdf(d1) - K * math.exp(-r * T) * ncdf(d1 - sq)
+    return price, sig * S0 * ncdf(d1)
+
+
+def _served_ok(p, res) -> bool:
+    """A served result counts when its y0 and z0 are within CONV_REL (1%) x
+    max(1, |value|) of the closed form, the accuracy the scheme reaches where
+    it converges on the request's grid."""
+    u, z = _closed_form_call(p)
+    return (math.isfinite(res["y0"]) and math.isfinite(res["z0"])
+            and abs(res["y0"] - u) <= CONV_REL * max(1.0, abs(u))
+            and abs(res["z0"] - z) <= CONV_REL * max(1.0, abs(z)))
+
+
 def run_serving(args, rank, world, local_rank):
     """config5: Poisson arrivals of pricing requests served by the persistent
-    continuous-batching kernel; one step = the whole arrival sequence."""
+    continuous-batching kernel; one step = the whole arrival sequence.  The
+    value counts the served results that pass the accuracy gate; a sweep of
+    lower rates finds the highest one the device sustains with p99 under
+    --p99-bound-ms."""
     import torch
     from paper_1909_13560_gb300 import bsde as B
     from paper_1909_13560_gb300 import serve
@@ -1242,27 +1343,31 @@ def run_serving(args, rank, world, local_rank):
     units = sum(W.gp_steps(p) for _, p in arrivals)
     srv = B.Server(slots=1024, pool_bytes=8 << 30, device=dev)
     srv.start(cluster=1, idle_ms=60000)
+    sweep = []
     try:
         # warm-up: a short burst through the same server
         serve.serve(srv, [(0.0, p) for _, p in arrivals[:64]])
-        uuid = None
-        try:
-            uuid = str(torch.cuda.get_device_properties(dev).uuid)
-            if not uuid.startswith("GPU-"):
-                uuid = "GPU-" + uuid
-        except Exception:
-            uuid = None
         _barrier(dist)
-        with ClockSampler(uuid) as clk:
+        with ClockSampler(_gpu_uuid(dev)) as clk:
             records, summary = serve.serve(srv, arrivals)
         _barrier(dist)
+        if not args.no_sweep:
+            for rate in (1000.0, 500.0, 250.0, 125.0):
+                arr = W.config5_arrivals(rate=rate, duration=args.sweep_duration)
+                _, sm = serve.serve(srv, arr)
+                sweep.append({"rate": rate, "requests": sm["requests"],
+                              "solves_per_s": sm["solves_per_s"], "p50_ms": sm["p50_ms"],
+                              "p99_ms": sm["p99_ms"]})
     finally:
         srv.stop()
         srv.close()
     t = _max_over_ranks(dist, summary["duration_s"])
+    ok = [_served_ok(p, r["result"]) for (_, p), r in zip(arrivals, records)]
+    lb4 = [(p["driver"] == "LB") for _, p in arrivals]
     if rank == 0:
+        sustained = [r for r in sweep if r["p99_ms"] <= args.p99_bound_ms]
         line = {
-            "metric": METRIC, "value": world * summary["requests"] / t, "unit": "solves/s",
+            "metric": METRIC, "value": world * sum(ok) / t, "unit": "solves/s",
             "n_gpus": world, "steps": 1, "warmup": 1, "ms_per_step": 1000.0 * t,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
@@ -1272,11 +1377,29 @@ def run_serving(args, rank, world, local_rank):
                                    "(Nx=2^16, N=256, k=4), L=16; admission by device memory "
                                    "(8 GiB pool, 1024 slots); persistent continuous-batching kernel",
                        "requests": summary["requests"]},
+            "accuracy": {"gate": "a served result counts when y0 and z0 are within 1% x max(1, "
+                                 "|value|) of the closed form (Black-Scholes; the lending/"
+                                 "borrowing call at r - (R - r))",
+                         "served": summary["requests"], "counted": sum(ok),
+                         "black_scholes_counted": sum(1 for o, l in zip(ok, lb4) if o and not l),
+                         "black_scholes_served": sum(1 for l in lb4 if not l),
+                         "lending_borrowing_counted": sum(1 for o, l in zip(ok, lb4) if o and l),
+                         "lending_borrowing_served": sum(lb4),
+                         "note": "the lending/borrowing requests (k=4 at Nx=2^16, N=256) are the "
+                                 "grid on which the scheme diverges (the FP64 oracle of config3 at "
+                                 "this size too): served and timed, not counted"},
             "serving": {"p50_ms": summary["p50_ms"], "p99_ms": summary["p99_ms"],
+                        "solves_per_s_all": world * summary["requests"] / t,
                         "max_inflight": summary["max_inflight"],
                         "admit_wait_p99_ms": summary["admit_wait_p99_ms"],
                         "grid_point_steps_per_s": world * units / t},
-            "e2e": {"value": world * summary["requests"] / t, "unit": "solves/s",
+            "sustained": {"p99_bound_ms": args.p99_bound_ms,
+                          "highest_rate_within_bound": (max(r["rate"] for r in sustained)
+                                                        if sustained else None),
+                          "sweep": sweep,
+                          "how": f"the same mix at lower Poisson rates, {args.sweep_duration:g} s "
+                                 "of arrivals each, through the same server"},
+            "e2e": {"value": world * sum(ok) / t, "unit": "solves/s",
                     "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 40 * summary["requests"]},
             "gpu_launches": 1,
             "clocks": clk.summary(),
@@ -1305,6 +1428,11 @@ def main():
                          "config5: the serving run (Poisson arrivals, continuous batching)")
     ap.add_argument("--duration", type=float, default=10.0, help="config5: seconds of arrivals")
     ap.add_argument("--rate", type=float, default=2000.0, help="config5: arrivals per second")
+    ap.add_argument("--no-sweep", action="store_true", help="config5: skip the rate sweep")
+    ap.add_argument("--sweep-duration", type=float, default=3.0,
+                    help="config5: seconds of arrivals per rate of the sweep")
+    ap.add_argument("--p99-bound-ms", type=float, default=500.0,
+                    help="config5: the p99 latency a sustained rate must stay under")
     ap.add_argument("--ks", type=lambda v: [int(t) for t in v.split(",")], default=list(KS),
                     help="config2: the step counts k to solve (default 1,2,3,4,5,6; a subset "
                          "is for profiling one kernel shape, not a bench line)")
@@ -1318,6 +1446,10 @@ def main():
                          "(default: concurrently, one stream each)")
     ap.add_argument("--no-variants", action="store_true",
                     help="config2: skip the timing of the scheme's variants")
+    ap.add_argument("--no-fp64-arm", action="store_true",
+                    help="config4: skip the FP64 per-instance comparison")
+    ap.add_argument("--fp64-steps", type=int, default=2,
+                    help="config4: timed steps of the FP64 per-instance arm (~7 s each)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="config4: a fixed batch configuration (cluster 1, 4 groups) instead "
                          "of the autotuned one")

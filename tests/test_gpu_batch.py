@@ -108,17 +108,53 @@ def test_batch_rejects_fp64_problems(B):
     assert ei.value.code == B.BSDE_EINVAL
 
 
-def test_config4_sample_matches_closed_form(B):
-    """A seeded sample of the 4096-instance Black-Scholes batch: every price
-    within the scheme's accuracy of the closed form."""
+def _stored_config4():
+    import json
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        "config4_oracle.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        return [[float(v) for v in r[:4]] for r in json.load(fh)["rows"]]
+
+
+def test_config4_sample_against_oracle(B):
+    """The first 64 instances of the 4096-instance Black-Scholes batch (seed
+    13560) in one persistent launch.  Where the scheme converges on an
+    instance's grid (the FP64 oracle's y0 and z0 within 1% of the closed
+    form, the bench's criterion) the batch's y0 and z0 agree with the oracle
+    within the FP32C tolerance.  Where it diverges (k >= 3 on grids far finer
+    than the Gauss-Hermite node spacing) the instance is counted and left
+    out, as the bench leaves it out of its value; such solves are covered by
+    the first-levels parity of single solves, which the batch equals bit for
+    bit (test_batch_equals_single_solves).  The live oracle also reproduces
+    the values stored for the bench's gate."""
     probs = W.config4(count=64)
     bs = B.BatchSolver(probs)
     res = bs.solve()
     bs.close()
-    errs = []
-    for p, r in zip(probs, res):
-        u, _ = O.exact(p, 0.0, p["x0"])
-        errs.append(abs(r["y0"] - u))
-    errs = np.array(errs)
-    print("config4 sample |y0 - exact|: median %.2e max %.2e" % (np.median(errs), errs.max()))
-    assert np.all(np.isfinite(errs))
+    stored = _stored_config4()
+    conv = div = 0
+    worst = 0.0
+    for i, (p, r) in enumerate(zip(probs, res)):
+        ref = O.solve(p, threads=THREADS, want_level=True)
+        u, z = O.exact(p, 0.0, p["x0"])
+        ok = (np.isfinite(ref["y0"]) and abs(ref["y0"] - u) <= 1e-2 * max(1.0, abs(u))
+              and abs(ref["z0"] - z) <= 1e-2 * max(1.0, abs(z)))
+        if stored is not None:
+            # written on another host: its libm may differ from this one's by an ulp
+            assert abs(stored[i][2] - u) <= 1e-13 * max(1.0, abs(u))
+            if ok:
+                assert abs(stored[i][0] - ref["y0"]) <= 1e-10 * max(1.0, abs(ref["y0"]))
+        if not ok:
+            div += 1
+            continue
+        conv += 1
+        scale = max(1.0, float(np.max(np.abs(ref["y"]))))
+        zscale = max(1.0, float(np.max(np.abs(ref["z"]))))
+        ey, ez = abs(r["y0"] - ref["y0"]) / scale, abs(r["z0"] - ref["z0"]) / zscale
+        worst = max(worst, ey, ez)
+        assert ey <= TOL32 and ez <= TOL32, (i, p["Nx"], p["N"], p["k"], r["y0"], ref["y0"])
+    print(f"config4 sample: {conv} converging instances within {worst:.2e} of the oracle, "
+          f"{div} diverging on their grids")
+    assert conv >= 32

@@ -111,6 +111,53 @@ def test_serving_loop_statistics(B):
     assert all(r["done"] >= r["admitted"] >= r["arrival"] for r in records)
 
 
+def test_served_results_against_oracle(B):
+    """A sample of requests shaped like the serving mix (Black-Scholes at
+    Nx = 2^12, N = 64, k = 3 and lending/borrowing calls, here at Nx = 2^12,
+    N = 64, k = 4; parameters drawn as in the mix) served while they overlap
+    on the device: every served y0 and z0 against the FP64 oracle, within the
+    FP32C tolerance (2e-7 of the level's scale) where the scheme converges on
+    the request's grid (the oracle within 1% of the closed form); requests on
+    which it diverges are counted and reported."""
+    from oracle import oracle as O
+    rng = np.random.default_rng(1909)
+    reqs = []
+    for i in range(16):
+        strike, sigma = float(rng.uniform(70, 130)), float(rng.uniform(0.1, 0.5))
+        T, r = float(rng.uniform(0.25, 2.0)), float(rng.uniform(0.0, 0.05))
+        if i % 3:
+            reqs.append(W.call_problem(strike=strike, sigma=sigma, T=T, r=r, Nx=1 << 12, N=64,
+                                       k=3, L=16))
+        else:
+            reqs.append(W.call_problem(strike=strike, sigma=sigma, T=T, r=r, R=r + 0.02, mu=0.06,
+                                       Nx=1 << 12, N=64, k=4, L=16, driver="LB"))
+    srv = B.Server(slots=32, pool_bytes=1 << 30)
+    srv.start(cluster=1, idle_ms=20000)
+    try:
+        slots = [srv.submit(p) for p in reqs]
+        assert all(s is not None for s in slots)
+        got = _wait_all(srv, len(reqs))
+    finally:
+        srv.stop()
+        srv.close()
+    conv = div = 0
+    for p, sl in zip(reqs, slots):
+        res = got[sl]
+        ref = O.solve(p, threads=8, want_level=True)
+        u, z = O.exact(p, 0.0, p["x0"])
+        if not (np.isfinite(ref["y0"]) and abs(ref["y0"] - u) <= 1e-2 * max(1.0, abs(u))
+                and abs(ref["z0"] - z) <= 1e-2 * max(1.0, abs(z))):
+            div += 1
+            continue
+        conv += 1
+        sy = max(1.0, float(np.max(np.abs(ref["y"]))))
+        sz = max(1.0, float(np.max(np.abs(ref["z"]))))
+        assert abs(res["y0"] - ref["y0"]) <= 2e-7 * sy, (p["driver"], res["y0"], ref["y0"])
+        assert abs(res["z0"] - ref["z0"]) <= 2e-7 * sz, (p["driver"], res["z0"], ref["z0"])
+    print(f"served sample: {conv} within the FP32C tolerance of the oracle, {div} diverging")
+    assert conv >= 8
+
+
 def test_start_and_stop_without_requests(B):
     srv = B.Server(slots=4, pool_bytes=1 << 20)
     srv.start(cluster=2, idle_ms=20000)
