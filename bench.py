@@ -40,6 +40,12 @@ KS = (1, 2, 3, 4, 5, 6)
 FLOP_NODE = 7 + 7 + 3 + 6
 
 
+# Algorithmic L2 -> SM bytes per point and node of the FP32C step kernel: the
+# value record (y_hi, z_hi, y_lo, z_lo) and the second derivatives (M_y, M_z)
+# of the node's cell's left end.
+L2_BYTES_NODE = 16 + 8
+
+
 def flops_per_gp_step(k: int, L: int) -> float:
     return k * L * FLOP_NODE + 2 * L + 4 * k + 12
 
@@ -482,20 +488,21 @@ def run_ours(args, rank, world, local_rank):
         levels_total += nlev
         kern_ms += avg * nlev
         kern_flops += flops_per_gp_step(k, p["L"]) * p["Nx"] * nlev
-        kern_l2 += 40.0 * p["Nx"] * k * p["L"] * nlev
+        kern_l2 += L2_BYTES_NODE * p["Nx"] * k * p["L"] * nlev
         del graph
     pk = measured_peaks(dev)
     fp64 = args.precision == "fp64"
     peak = pk["fp64_tflops"] if fp64 else pk["fp32_tflops"]
     achieved = kern_flops / (kern_ms / 1000.0) / 1e12
-    # the FP32C step kernel streams one A record (16 B) and one interval
-    # record (24 B) per point and node from L2: its L2 -> SM rate against
-    # the L2 read bandwidth measured now by a plain streaming kernel
+    # the FP32C step kernel reads, per point and node, the value record
+    # (16 B) and the second derivatives (8 B) of its cell's left node from L2
+    # (the right node's are the next lane's, an L1 hit): its L2 -> SM rate
+    # against the L2 read bandwidth measured now by a plain streaming kernel
     l2 = None
     if not fp64:
         l2_gbs = kern_l2 / (kern_ms / 1000.0) / 1e9
         l2 = {"achieved": l2_gbs, "peak": pk["l2_read_gbs"], "unit": "GB/s",
-              "frac": l2_gbs / pk["l2_read_gbs"], "bytes_per_point_node": 40,
+              "frac": l2_gbs / pk["l2_read_gbs"], "bytes_per_point_node": L2_BYTES_NODE,
               "peak_source": "measured in this run (bsde_l2_read_probe)"}
 
     # end to end through the C ABI with host buffers: bsde_solve takes the

@@ -121,6 +121,17 @@ enum {
                             nodes and z form (Section 3.1 step 2)                */
 };
 
+/* FP32C step kernel of a single solve with a constant forward process.  Both
+ * forms run the same node pairs in the same order of operations, so their
+ * results are bitwise equal; they differ in how threads share a point. */
+enum {
+  BSDE_STEP_AUTO = 0,    /* flat when the grid alone fills the GPU's resident
+                            threads twice, grouped otherwise                     */
+  BSDE_STEP_GROUPED = 1, /* a CTA of 64 points x G groups of threads (j, pair
+                            chunk), partial sums combined in shared memory       */
+  BSDE_STEP_FLAT = 2     /* one thread per point runs all G groups in turn       */
+};
+
 /* return codes */
 enum {
   BSDE_OK = 0,
@@ -163,7 +174,7 @@ typedef struct bsde_problem {
   int32_t init_mode;  /* BSDE_INIT_*                                           */
   int32_t init_substeps; /* ONESTEP: 1-step scheme steps per dt, >= 1          */
   int32_t forward;    /* BSDE_FORWARD_*                                        */
-  int32_t reserved;   /* 0                                                     */
+  int32_t step_kernel; /* BSDE_STEP_*: the FP32C constant-shift step kernel    */
   double a_1, b_1;    /* AFFINE: slopes of a(x) and b(x)                       */
 } bsde_problem;
 

@@ -21,6 +21,7 @@ BSDE_TERMINAL = {"SIN": 0, "CALL_LOG": 1, "LOGISTIC": 2, "LNSIN": 3, "ONE": 4, "
 BSDE_FORWARD = {"CONST": 0, "AFFINE": 1}
 BSDE_PRECISION = {"fp64": 0, "fp32c": 1}
 BSDE_INIT = {"EXACT": 0, "ONESTEP": 1}
+BSDE_STEP = {"AUTO": 0, "GROUPED": 1, "FLAT": 2}
 BSDE_ZFORM = {"EZ": 0, "EYDW": 1}
 
 BSDE_OK = 0
@@ -49,7 +50,7 @@ class bsde_problem(ctypes.Structure):
         ("strike", ctypes.c_double), ("picard_tol", ctypes.c_double),
         ("k_z", ctypes.c_int32), ("z_form", ctypes.c_int32),
         ("init_mode", ctypes.c_int32), ("init_substeps", ctypes.c_int32),
-        ("forward", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("forward", ctypes.c_int32), ("step_kernel", ctypes.c_int32),
         ("a_1", ctypes.c_double), ("b_1", ctypes.c_double),
     ]
 
@@ -220,6 +221,8 @@ def make_problem(p: dict, precision: str = "fp64") -> bsde_problem:
     s.forward = BSDE_FORWARD[fwd] if isinstance(fwd, str) else int(fwd)
     s.a_1 = float(p.get("a_1", 0.0))
     s.b_1 = float(p.get("b_1", 0.0))
+    sk = p.get("step_kernel", 0)
+    s.step_kernel = BSDE_STEP[sk] if isinstance(sk, str) else int(sk)
     return s
 
 

@@ -145,9 +145,14 @@ static void launch_step(bsde_plan_t *pl, const Run &R, cudaStream_t s, int n) {
     if (P.general)
       launch_pdl(k_step32_gen<DRV>, blocks, threads, step32_smem(P.G, P.k * P.Lp), s, P,
                  pl->dc32, R.r32, R.tp, n, st);
-    else if constexpr (DRV != BSDE_DRIVER_SHORT_RATE)
-      launch_pdl(k_step32<DRV>, blocks, threads, step32_smem(P.G, 0), s, P, pl->dc32, R.r32,
-                 R.tab, n, st);
+    else if constexpr (DRV != BSDE_DRIVER_SHORT_RATE) {
+      if (P.flat)
+        launch_pdl(k_step32f<DRV>, unsigned((P.Nx + kFlatTP - 1) / kFlatTP), unsigned(kFlatTP),
+                   0, s, P, pl->dc32, R.r32, R.tab, n, st);
+      else
+        launch_pdl(k_step32<DRV>, blocks, threads, step32_smem(P.G, 0), s, P, pl->dc32, R.r32,
+                   R.tab, n, st);
+    }
   }
 }
 

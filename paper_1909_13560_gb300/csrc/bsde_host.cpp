@@ -34,6 +34,7 @@ int validate(const bsde_problem &p) {
         p.x_min > 0.0))
     return BSDE_EINVAL;
   if (p.precision != BSDE_FP64 && p.precision != BSDE_FP32C) return BSDE_EINVAL;
+  if (p.step_kernel < BSDE_STEP_AUTO || p.step_kernel > BSDE_STEP_FLAT) return BSDE_EINVAL;
   if (p.picard_max < 1 || !(p.picard_tol >= 0.0)) return BSDE_EINVAL;
   if ((p.driver == BSDE_DRIVER_BS || p.driver == BSDE_DRIVER_LB) && p.sigma == 0.0) return BSDE_EINVAL;
   return BSDE_OK;
@@ -148,6 +149,8 @@ int fill_params(const bsde_problem &p, Params &P) {
   P.kz = problem_kz(p);
   P.zform = p.z_form;
   P.general = problem_general(p) ? 1 : 0;
+  // resolved by the work split when automatic (-1)
+  P.flat = p.step_kernel == BSDE_STEP_FLAT ? 1 : p.step_kernel == BSDE_STEP_GROUPED ? 0 : -1;
   P.a_1 = p.forward == BSDE_FORWARD_AFFINE ? p.a_1 : 0.0;
   P.b_1 = p.forward == BSDE_FORWARD_AFFINE ? p.b_1 : 0.0;
   P.L = p.L;
@@ -265,6 +268,11 @@ static void work_split(Params &P, int target_groups, int max_groups, long reside
   P.S = S;
   P.Lg = (units + S - 1) / S;
   P.G = P.k * S;
+  // automatic: a grid whose points alone fill the resident threads twice
+  // takes the flat kernel (same split, same order of operations)
+  if (P.flat < 0)
+    P.flat = P.precision == BSDE_FP32C && resident_threads > 0 &&
+             long(P.Nx) >= 2 * resident_threads;
 }
 
 // Node tables.  On the uniform grid with a constant-coefficient forward

@@ -108,6 +108,8 @@ struct Params {
   // work split of the step kernels: S l-chunks of Lg nodes per j, G = k S
   // groups per point; shift range per j (for the clamp-free fast path)
   int32_t S, Lg, G, Lp;  // Lp = ceil(L/2) pairs; in FP32C the chunks hold Lg pairs
+  int32_t flat;          // FP32C constant-shift step: one thread runs all G groups of
+                         // its point (k_step32f), for grids of at least two waves
   int32_t smin[kMaxK], smax[kMaxK];
   // the Gauss-Hermite node of pair q (node q; node L-1-q is its negative) as
   // a float pair hi + lo, for the FP32C general path's per-point positions

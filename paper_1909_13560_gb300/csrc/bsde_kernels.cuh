@@ -1031,6 +1031,64 @@ __device__ __forceinline__ bool picard_cycle_ok(float d, float y, float delta) {
 // flipping between neighbours, as far as the FP32 driver can resolve, and
 // ends it too; a wider cycle is an oscillation of the iteration itself and
 // runs on to picard_max, where it is reported as non-convergence.
+// The groups' partial sums of one point, folded in group order: compensated
+// z and y sums (S, C), the z driver terms and the y driver terms with their
+// rounding error.
+struct Sums32 {
+  float zS, zC, fz, fy, fyC, yS, yC;
+};
+__device__ __forceinline__ void fold_group(Sums32 &s, float Sy, float Cy, float Fz, float Fy,
+                                           float Sx, float Cx, float FyC) {
+  two_sum_into(s.zS, s.zC, Sy);
+  s.zC = __fadd_rn(s.zC, Cy);
+  s.fz = __fadd_rn(s.fz, Fz);
+  two_sum_into(s.fy, s.fyC, Fy);
+  s.fyC = __fadd_rn(s.fyC, FyC);
+  two_sum_into(s.yS, s.yC, Sx);
+  s.yC = __fadd_rn(s.yC, Cx);
+}
+
+// z^n, A and the Picard iteration for point ii from its folded sums (see
+// finish_points32); stores (y^n, z^n), returns the last step and the
+// iteration count in it.
+template <int DRV>
+__device__ __forceinline__ float finish_point32(const Params &P, const DrvC<float> &dc,
+                                                float4 *__restrict__ ringA, int n, int ii,
+                                                const Sums32 &s, float prev_y, int &it) {
+  float d = 0.f;
+  // z^n = zS + (zC + fz) and A = yS + (yC + fy) as exact float pairs
+  float zh = s.zS, zl = 0.f, Ah = s.yS, Al = 0.f;
+  two_sum_into(zh, zl, __fadd_rn(s.zC, s.fz));
+  two_sum_into(Ah, Al, s.fy);
+  two_sum_into(Ah, Al, __fadd_rn(s.yC, s.fyC));
+  float tn, etn, emtn;
+  level_time<DRV>(P, n, tn, etn, emtn);
+  const float hg0 = float(P.hg0);
+  float dl = __fsub_rn(prev_y, Ah), dpp = __int_as_float(0x7fc00000);
+  const float xf = float(P.x_min + double(ii) * P.dx);  // x-aware drivers only
+  while (it < P.picard_max) {
+    const float dn = hg0 * driver_x<DRV>(dc, tn, etn, emtn, xf, Ah + dl, zh);
+    ++it;
+    d = fabsf(__fsub_rn(dn, dl));
+    const bool cyc = dn == dpp && picard_cycle_ok(d, __fadd_rn(Ah, dl), dn);
+    dpp = dl;
+    dl = dn;
+    if (cyc) d = 0.f;
+    if (d <= P.picard_tol_f || !isfinite(d)) break;  // a non-finite step cannot converge
+  }
+  // y^n = A + delta, renormalized
+  float yh = Ah, yl = Al;
+  two_sum_into(yh, yl, dl);
+  const float sy = __fadd_rn(yh, yl);
+  yl = __fsub_rn(yl, __fsub_rn(sy, yh));
+  yh = sy;
+  const float sz = __fadd_rn(zh, zl);
+  zl = __fsub_rn(zl, __fsub_rn(sz, zh));
+  zh = sz;
+  ringA[int64_t(n % P.nslot) * P.Nx + ii] = make_float4(yh, zh, yl, zl);
+  return d;
+}
+
 template <int DRV, bool COH>
 __device__ __forceinline__ void finish_points32(const Params &P, const DrvC<float> &dc,
                                                 float4 *__restrict__ ringA, const float *part,
@@ -1042,47 +1100,13 @@ __device__ __forceinline__ void finish_points32(const Params &P, const DrvC<floa
   float d = 0.f;
   if (active) {
     const int gs = G * kStepTP;
-    float zS = 0.f, zC = 0.f, yS = 0.f, yC = 0.f, fz = 0.f, fy = 0.f, fyC = 0.f;
+    Sums32 s{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (int q = 0; q < G; ++q) {
       const int o = q * kStepTP + tid;
-      two_sum_into(zS, zC, part[0 * gs + o]);
-      zC = __fadd_rn(zC, part[1 * gs + o]);
-      fz = __fadd_rn(fz, part[2 * gs + o]);
-      two_sum_into(fy, fyC, part[3 * gs + o]);
-      fyC = __fadd_rn(fyC, part[6 * gs + o]);
-      two_sum_into(yS, yC, part[4 * gs + o]);
-      yC = __fadd_rn(yC, part[5 * gs + o]);
+      fold_group(s, part[0 * gs + o], part[1 * gs + o], part[2 * gs + o], part[3 * gs + o],
+                 part[4 * gs + o], part[5 * gs + o], part[6 * gs + o]);
     }
-    // z^n = zS + (zC + fz) and A = yS + (yC + fy) as exact float pairs
-    float zh = zS, zl = 0.f, Ah = yS, Al = 0.f;
-    two_sum_into(zh, zl, __fadd_rn(zC, fz));
-    two_sum_into(Ah, Al, fy);
-    two_sum_into(Ah, Al, __fadd_rn(yC, fyC));
-    float tn, etn, emtn;
-    level_time<DRV>(P, n, tn, etn, emtn);
-    const float hg0 = float(P.hg0);
-    float dl = __fsub_rn(prev_y, Ah), dpp = __int_as_float(0x7fc00000);
-    const float xf = float(P.x_min + double(ii) * P.dx);  // x-aware drivers only
-    while (it < P.picard_max) {
-      const float dn = hg0 * driver_x<DRV>(dc, tn, etn, emtn, xf, Ah + dl, zh);
-      ++it;
-      d = fabsf(__fsub_rn(dn, dl));
-      const bool cyc = dn == dpp && picard_cycle_ok(d, __fadd_rn(Ah, dl), dn);
-      dpp = dl;
-      dl = dn;
-      if (cyc) d = 0.f;
-      if (d <= P.picard_tol_f || !isfinite(d)) break;  // a non-finite step cannot converge
-    }
-    // y^n = A + delta, renormalized
-    float yh = Ah, yl = Al;
-    two_sum_into(yh, yl, dl);
-    const float s = __fadd_rn(yh, yl);
-    yl = __fsub_rn(yl, __fsub_rn(s, yh));
-    yh = s;
-    const float s2 = __fadd_rn(zh, zl);
-    zl = __fsub_rn(zl, __fsub_rn(s2, zh));
-    zh = s2;
-    ringA[int64_t(n % P.nslot) * P.Nx + ii] = make_float4(yh, zh, yl, zl);
+    d = finish_point32<DRV>(P, dc, ringA, n, ii, s, prev_y, it);
   }
   record_picard(st, active, it, double(d), P.picard_tol);
 }
@@ -1152,6 +1176,54 @@ __global__ void __launch_bounds__(kStepTP * kMaxGroups, 3)
   float *part = reinterpret_cast<float *>(smem_raw);  // [kPartArrays][G][kStepTP]
   wait_predecessor();
   step_tile32<DRV, false>(P, dc, r32, tab.e, part, n, blockIdx.x * kStepTP, st);
+}
+
+// ---------------------------------------------------------------------------
+// The FP32C step kernel for grids that fill the GPU several times over: one
+// thread per grid point runs all G groups of its point, in group order, with
+// the grouped kernel's pairs, arithmetic and fold (fold_group), so its
+// results are bitwise those of k_step32 with the same work split.  The group
+// and pair indices are loop counters, uniform across the CTA, so the pair
+// table in the kernel parameters is read by uniform constant loads; there
+// are no shared-memory partial sums and no barrier.
+// ---------------------------------------------------------------------------
+constexpr int kFlatTP = 128;  // grid points (threads) per CTA
+
+template <int DRV>
+__global__ void __launch_bounds__(kFlatTP, 8)
+    k_step32f(const Params P, const DrvC<float> dc, Ring32 r32,
+              const __grid_constant__ PairTab32 tab, int n, Stats *st) {
+  wait_predecessor();
+  const int i0 = blockIdx.x * kFlatTP;
+  const int ii = i0 + int(threadIdx.x);
+  const int last = int(P.Nx - 1);
+  const bool active = ii <= last;
+  float prev_y = 0.f;
+  if (active) prev_y = r32.A[int64_t((n + 1) % P.nslot) * P.Nx + ii].x;
+  Sums32 s{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int g = 0; g < P.G; ++g) {
+    const int j = g / P.S + 1, lc = g % P.S;
+    const int q0 = lc * P.Lg, q1 = q0 + P.Lg < P.Lp ? q0 + P.Lg : P.Lp;
+    // every node cell of every point of the CTA on the grid (points past the
+    // end take the clamping path, whose cells stay on the grid)
+    const bool interior = i0 + P.smin[j - 1] >= 0 && i0 + kFlatTP + P.smax[j - 1] <= last;
+    Acc32 acc{make_float2(0.f, 0.f), make_float2(0.f, 0.f), 0.f, 0.f, 0.f};
+    const int64_t off = int64_t((n + j) % P.nslot) * P.Nx;
+    float tj, et, emt;
+    level_time<DRV>(P, n + j, tj, et, emt);
+    const PairF32 *row = tab.e + (j - 1) * P.Lp;
+    if (P.zform && j == 1)
+      pairs32<DRV, true, false, true>(dc, r32, off, row, q0, q1, ii, last, tj, et, emt, acc);
+    else if (interior)
+      pairs32<DRV, false, false>(dc, r32, off, row, q0, q1, ii, last, tj, et, emt, acc);
+    else
+      pairs32<DRV, true, false>(dc, r32, off, row, q0, q1, ii, last, tj, et, emt, acc);
+    fold_group(s, acc.S.y, acc.C.y, acc.Fz, acc.Fy, acc.S.x, acc.C.x, acc.FyC);
+  }
+  int it = 0;
+  float d = 0.f;
+  if (active) d = finish_point32<DRV>(P, dc, r32.A, n, ii, s, prev_y, it);
+  record_picard(st, active, it, double(d), P.picard_tol);
 }
 
 // ---------------------------------------------------------------------------

@@ -167,6 +167,31 @@ def test_edge_cases(B, name, prec, tol):
     _cmp(got, ref, tol, f"edge {name} {prec}")
 
 
+FLAT_CASES = {
+    "config2_k3": W.config2(k=3),
+    "lb_ragged_k4": W.config3(Nx=100003, N=24, k=4),
+    "sin_zform_k1": dict(W.sin_problem(Nx=1001, N=32, k=1), zform=1),
+    "ex2_odd_L": W.ex2_problem(Nx=777, N=16, k=5, L=7),
+    "kz_ne_k": dict(W.call_problem(Nx=5000, N=32, k=2), kz=3),
+}
+
+
+@pytest.mark.parametrize("name", list(FLAT_CASES))
+def test_flat_step_kernel_equals_grouped_bitwise(B, name):
+    """The FP32C step kernel in its two forms, forced through the problem's
+    step_kernel: grouped (G groups of threads per point, partial sums folded
+    in shared memory) and flat (one thread per point folding its groups in
+    turn).  They run the same node pairs in the same order of operations, so
+    every level-0 value is bitwise equal (ragged grids, clamped nodes, the
+    E[y dW] z form, odd L, K_z != K_y)."""
+    p = FLAT_CASES[name]
+    a = B.solve(dict(p, step_kernel="GROUPED"), "fp32c", want_level=True)
+    b = B.solve(dict(p, step_kernel="FLAT"), "fp32c", want_level=True)
+    assert a["y0"] == b["y0"] and a["z0"] == b["z0"]
+    assert np.array_equal(a["y"], b["y"]) and np.array_equal(a["z"], b["z"])
+    assert a["picard_iters_max"] == b["picard_iters_max"] and a["status"] == b["status"]
+
+
 def test_repeat_solves_are_bitwise_identical(B):
     p = W.call_problem(Nx=4096, N=32, k=4)
     s = B.Solver(p, "fp32c")

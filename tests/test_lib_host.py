@@ -118,7 +118,8 @@ def test_workspace_bytes_scale_with_ring():
 
 @pytest.mark.parametrize("bad", [dict(kz=7), dict(kz=-1), dict(kz=6, N=5), dict(zform=2),
                                  dict(init_mode=2), dict(init_mode=1, init_substeps=0),
-                                 dict(init_mode=1, init_substeps=1 << 25)])
+                                 dict(init_mode=1, init_substeps=1 << 25),
+                                 dict(step_kernel=3), dict(step_kernel=-1)])
 def test_invalid_variants_rejected(bad):
     p = W.sin_problem()
     p.update(bad)
