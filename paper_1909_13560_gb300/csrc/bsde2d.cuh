@@ -670,7 +670,7 @@ __device__ __forceinline__ void step2_tile32(const Params2 &P, const float4 *__r
     V[P.Np + qq] = double(z1h) + double(z1l);
     V[2 * P.Np + qq] = double(z2h) + double(z2l);
   }
-  record_picard(st, active, it, double(d), P.picard_tol);
+  record_picard32(st, active, it, d, P.picard_tol_f);
 }
 
 // The FP32C 2-D step with the pair table copied into shared memory by every

@@ -190,6 +190,7 @@ int fill_params(const bsde_problem &p, Params &P) {
   }
   P.h = P.ky * P.dt;
   P.hg0 = P.h * P.gy[0];
+  P.hg0_f = float(P.hg0);
   P.inv_gz0 = 1.0 / P.gz[0];
   P.inv_dx2_6 = 6.0 / (P.dx * P.dx);
   P.inv_dx = 1.0 / P.dx;
@@ -217,6 +218,7 @@ Params startup_params(const Params &P, int substeps) {
   gamma_tables(1, Q.gy, Q.gz);
   Q.h = Q.dt;
   Q.hg0 = Q.h * Q.gy[0];
+  Q.hg0_f = float(Q.hg0);
   Q.inv_gz0 = 1.0 / Q.gz[0];
   return Q;
 }

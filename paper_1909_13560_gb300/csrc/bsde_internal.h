@@ -95,6 +95,7 @@ struct Params {
   double r, mu, sigma, R, delta, lb_sign, strike;
   double picard_tol;
   float picard_tol_f;  // the largest float <= picard_tol (FP32 Picard test)
+  float hg0_f;         // float(hg0), the FP32 Picard weight
   double gy[kMaxK + 1], gz[kMaxK + 1];
   double h;       // K_y dt
   double hg0;     // K_y dt gy_0 (weight of the implicit term)

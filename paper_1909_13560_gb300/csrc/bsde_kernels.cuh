@@ -560,6 +560,25 @@ __device__ __forceinline__ void record_picard(Stats *st, bool active, int it, do
   }
 }
 
+// The same statistics from the FP32C tails: the test !(d <= picard_tol_f) is
+// exactly !(d <= picard_tol) for a float d, and the maximum of non-negative
+// floats (or NaN) is the maximum of their bit patterns, so the warp reduces
+// 32-bit words and converts its maximum to double once.
+__device__ __forceinline__ void record_picard32(Stats *st, bool active, int it, float d,
+                                                float tol_f) {
+  const unsigned full = 0xffffffffu;
+  const unsigned itm = __reduce_max_sync(full, active ? unsigned(it) : 0u);
+  const unsigned db = __reduce_max_sync(full, active ? __float_as_uint(d) : 0u);
+  const unsigned nc = __reduce_or_sync(full, (active && !(d <= tol_f)) ? 1u : 0u);
+  if ((threadIdx.x & 31) == 0) {
+    const unsigned long long dd =
+        (unsigned long long)__double_as_longlong(double(__uint_as_float(db)));
+    if (int(itm) > __ldcg(&st->iters_max)) atomicMax(&st->iters_max, int(itm));
+    if (dd > __ldcg(&st->resid_bits)) atomicMax(&st->resid_bits, dd);
+    if (nc && !__ldcg(&st->nonconv)) atomicOr(&st->nonconv, 1);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // S3: the step kernels.  A CTA owns kStepTP consecutive grid points and runs
 // G = k S groups of threads over them; group g takes j = g / S + 1 and the
@@ -1063,9 +1082,11 @@ __device__ __forceinline__ float finish_point32(const Params &P, const DrvC<floa
   two_sum_into(Ah, Al, __fadd_rn(s.yC, s.fyC));
   float tn, etn, emtn;
   level_time<DRV>(P, n, tn, etn, emtn);
-  const float hg0 = float(P.hg0);
+  const float hg0 = P.hg0_f;
   float dl = __fsub_rn(prev_y, Ah), dpp = __int_as_float(0x7fc00000);
-  const float xf = float(P.x_min + double(ii) * P.dx);  // x-aware drivers only
+  // the forward state at the point, for x-aware drivers only
+  float xf = 0.f;
+  if constexpr (DRV == BSDE_DRIVER_SHORT_RATE) xf = float(P.x_min + double(ii) * P.dx);
   while (it < P.picard_max) {
     const float dn = hg0 * driver_x<DRV>(dc, tn, etn, emtn, xf, Ah + dl, zh);
     ++it;
@@ -1108,7 +1129,7 @@ __device__ __forceinline__ void finish_points32(const Params &P, const DrvC<floa
     }
     d = finish_point32<DRV>(P, dc, ringA, n, ii, s, prev_y, it);
   }
-  record_picard(st, active, it, double(d), P.picard_tol);
+  record_picard32(st, active, it, d, P.picard_tol_f);
 }
 
 // One tile of kStepTP points of level n with direct loads, called by every
@@ -1223,7 +1244,7 @@ __global__ void __launch_bounds__(kFlatTP, 8)
   int it = 0;
   float d = 0.f;
   if (active) d = finish_point32<DRV>(P, dc, r32.A, n, ii, s, prev_y, it);
-  record_picard(st, active, it, double(d), P.picard_tol);
+  record_picard32(st, active, it, d, P.picard_tol_f);
 }
 
 // ---------------------------------------------------------------------------
