@@ -1349,7 +1349,7 @@ def run_serving(args, rank, world, local_rank):
     arrivals = W.config5_arrivals(rate=args.rate, duration=args.duration)
     units = sum(W.gp_steps(p) for _, p in arrivals)
     srv = B.Server(slots=1024, pool_bytes=8 << 30, device=dev)
-    srv.start(cluster=1, idle_ms=60000)
+    srv.start(cluster=args.server_cluster, idle_ms=60000)
     sweep = []
     try:
         # warm-up: a short burst through the same server
@@ -1382,7 +1382,8 @@ def run_serving(args, rank, world, local_rank):
                                    f"{args.duration:g} s (seed 1909), 70% Black-Scholes "
                                    "(Nx=2^12, N=64, k=3), 30% lending/borrowing calls "
                                    "(Nx=2^16, N=256, k=4), L=16; admission by device memory "
-                                   "(8 GiB pool, 1024 slots); persistent continuous-batching kernel",
+                                   "(8 GiB pool, 1024 slots); persistent continuous-batching kernel, "
+                                   f"{args.server_cluster} CTA(s) per request",
                        "requests": summary["requests"]},
             "accuracy": {"gate": "a served result counts when y0 and z0 are within 1% x max(1, "
                                  "|value|) of the closed form (Black-Scholes; the lending/"
@@ -1436,6 +1437,8 @@ def main():
     ap.add_argument("--duration", type=float, default=10.0, help="config5: seconds of arrivals")
     ap.add_argument("--rate", type=float, default=2000.0, help="config5: arrivals per second")
     ap.add_argument("--no-sweep", action="store_true", help="config5: skip the rate sweep")
+    ap.add_argument("--server-cluster", type=int, default=8, choices=(1, 2, 4, 8),
+                    help="config5: CTAs per cluster of the serving kernel (one request each)")
     ap.add_argument("--sweep-duration", type=float, default=3.0,
                     help="config5: seconds of arrivals per rate of the sweep")
     ap.add_argument("--p99-bound-ms", type=float, default=500.0,
