@@ -568,7 +568,9 @@ def run_ours(args, rank, world, local_rank):
         cpu["single_thread"] = {"value": one["value"], "cores": 1, "sample": one["sample"]}
 
     if rank == 0:
-        kname = "k_step64" if fp64 else "k_step32"
+        # FP32C at config3's size runs the flat step kernel (the grid fills
+        # the resident threads more than twice), config2 the grouped one
+        kname = "k_step64" if fp64 else ("k_step32f" if c3 else "k_step32")
         tkey = f"{kname}_{wl}"
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
