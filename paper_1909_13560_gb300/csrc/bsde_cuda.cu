@@ -168,13 +168,25 @@ static void launch_step_any(bsde_plan_t *pl, const Run &R, cudaStream_t s, int n
   }
 }
 
+template <int PREC, bool BIG>
+static void launch_spline(const Run &R, cudaStream_t s, int slot) {
+  const Params &P = R.P;
+  constexpr int TS = SplineLaunch<PREC, BIG>::TS;
+  const unsigned blocks = unsigned((P.Nx - 2 + TS - 1) / TS);
+  launch_pdl(k_spline<PREC, BIG>, blocks, unsigned(SplineLaunch<PREC, BIG>::NT), 0, s, P, R.r64,
+             R.r32, slot);
+}
+
+// FP32C grids that take the flat step kernel also take the wide spline tiles
 template <int PREC>
 static int64_t enqueue_spline(const Run &R, cudaStream_t s, int slot) {
-  const Params &P = R.P;
-  constexpr int TS = SplineLaunch<PREC>::TS;
-  const unsigned blocks = unsigned((P.Nx - 2 + TS - 1) / TS);
-  launch_pdl(k_spline<PREC>, blocks, unsigned(SplineLaunch<PREC>::NT), 0, s, P, R.r64, R.r32,
-             slot);
+  if constexpr (PREC == BSDE_FP32C) {
+    if (R.P.flat) {
+      launch_spline<PREC, true>(R, s, slot);
+      return 1;
+    }
+  }
+  launch_spline<PREC, false>(R, s, slot);
   return 1;
 }
 

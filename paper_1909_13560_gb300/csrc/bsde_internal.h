@@ -16,7 +16,7 @@ constexpr int kStepTP = 64;      // grid points per CTA in the step kernels
 constexpr int kMaxGroups = 6;    // (j, l-chunk) groups per point
 constexpr int kPartArrays = 7;   // FP32C per-group partial sums: z (S, C, F), y (S, C, F, F err)
 constexpr int kSplineTile = 512;  // unknowns per CTA in the FP64 spline kernel
-constexpr int kSplineTile32 = 256;  // unknowns (and threads) per CTA in the FP32C one
+constexpr int kSplineTile32 = 256;  // threads per CTA in the FP32C one
 constexpr int kSplineChunk = 4;   // unknowns per thread (serial recurrence, FP64)
 constexpr int kSplineHead = 16;   // FP32C: pivots of the spline LU are constant beyond this
 

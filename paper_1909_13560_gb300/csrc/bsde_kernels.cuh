@@ -316,10 +316,12 @@ struct SplineT<BSDE_FP32C> {
 };
 
 // Shared-memory span of a spline tile of TS unknowns: the tile, W on the
-// left and W + 2 on the right.
+// left and W + 2 on the right, and room for the FP32C sums' register windows
+// to read up to kSplineChunkMax - 2 values past the last one they use.
+constexpr int kSplineChunkMax = 8;
 template <int PREC>
 __host__ __device__ constexpr int spline_span(int TS) {
-  return TS + 2 * SplineT<PREC>::W + 2;
+  return TS + 2 * SplineT<PREC>::W + kSplineChunkMax;
 }
 
 // One tile of TS unknowns of the level in `slot`, by the threads tid < nt of
@@ -456,29 +458,100 @@ __device__ __forceinline__ void spline_tile(const Params &P, Ring64 r64, Ring32 
         sg[1][m - base] = gz;
       }
     }
-    for (int m = (a > F0 ? a : F0) + tid; m < rb && tid < nt; m += nt) {
-      T gy = sr[0][m - base], gz = sr[1][m - base], c = T(1);
+    // Each thread takes CP consecutive unknowns and keeps the W + CP values
+    // its sums read in registers, so a value is read from shared memory once
+    // per thread instead of once per sum.  Every unknown's sum keeps its
+    // terms and their order, so the results do not depend on CP or the
+    // tiling.
+    constexpr int CP = (TS + W + 1 + NT - 1) / NT;
+    static_assert(CP <= kSplineChunkMax, "spline chunk wider than the shared-memory span allows");
+    const int c0 = a + tid * CP;
+    {
+      const int lo = a > F0 ? a : F0;
+      if (tid < nt && c0 < rb && c0 + CP > lo) {
+        T wy[W + CP], wz[W + CP];  // r_{c0-W} .. r_{c0+CP-1}
 #pragma unroll
-      for (int q = 1; q <= W; ++q) {
-        c = -c * rho;
-        gy = __fmaf_rn(c, sr[0][m - q - base], gy);
-        gz = __fmaf_rn(c, sr[1][m - q - base], gz);
+        for (int t = 0; t < W + CP; ++t) {
+          wy[t] = sr[0][c0 - W + t - base];
+          wz[t] = sr[1][c0 - W + t - base];
+        }
+        T gy[CP], gz[CP];
+#pragma unroll
+        for (int t = 0; t < CP; ++t) {
+          gy[t] = wy[W + t];
+          gz[t] = wz[W + t];
+        }
+        T c = T(1);
+#pragma unroll
+        for (int q = 1; q <= W; ++q) {
+          c = -c * rho;
+#pragma unroll
+          for (int t = 0; t < CP; ++t) {
+            gy[t] = __fmaf_rn(c, wy[W + t - q], gy[t]);
+            gz[t] = __fmaf_rn(c, wz[W + t - q], gz[t]);
+          }
+        }
+#pragma unroll
+        for (int t = 0; t < CP; ++t) {
+          const int m = c0 + t;
+          if (m >= lo && m < rb) {
+            sg[0][m - base] = gy[t];
+            sg[1][m - base] = gz[t];
+          }
+        }
       }
-      sg[0][m - base] = gy;
-      sg[1][m - base] = gz;
     }
     bar_sync();
     // backward: M of unknowns [a, bx) into sr (r is no longer needed)
-    for (int m = (a > H ? a : H) + tid; m < bx && tid < nt; m += nt) {
-      const int qmax = u - 1 - m < W ? u - 1 - m : W;
-      T my = T(0), mz = T(0), c = rho;
-      for (int q = 0; q <= qmax; ++q) {
-        my = __fmaf_rn(c, sg[0][m + q - base], my);
-        mz = __fmaf_rn(c, sg[1][m + q - base], mz);
-        c = -c * rho;
+    {
+      const int lo = a > H ? a : H;
+      if (tid < nt && c0 < bx && c0 + CP > lo) {
+        T wy[W + CP], wz[W + CP];  // g_{c0} .. g_{c0+CP-1+W}
+#pragma unroll
+        for (int t = 0; t < W + CP; ++t) {
+          wy[t] = sg[0][c0 + t - base];
+          wz[t] = sg[1][c0 + t - base];
+        }
+        T my[CP], mz[CP];
+#pragma unroll
+        for (int t = 0; t < CP; ++t) my[t] = mz[t] = T(0);
+        if (c0 + CP - 1 + W <= u - 1) {
+          // every sum of the chunk has its W + 1 terms
+          T c = rho;
+#pragma unroll
+          for (int q = 0; q <= W; ++q) {
+#pragma unroll
+            for (int t = 0; t < CP; ++t) {
+              my[t] = __fmaf_rn(c, wy[t + q], my[t]);
+              mz[t] = __fmaf_rn(c, wz[t + q], mz[t]);
+            }
+            c = -c * rho;
+          }
+        } else {
+          // near the last unknown the sums stop there
+#pragma unroll
+          for (int t = 0; t < CP; ++t) {
+            const int qmax = u - 1 - (c0 + t) < W ? u - 1 - (c0 + t) : W;
+            T c = rho;
+#pragma unroll
+            for (int q = 0; q <= W; ++q) {
+              if (q <= qmax) {
+                my[t] = __fmaf_rn(c, wy[t + q], my[t]);
+                mz[t] = __fmaf_rn(c, wz[t + q], mz[t]);
+              }
+              c = -c * rho;
+            }
+          }
+        }
+#pragma unroll
+        for (int t = 0; t < CP; ++t) {
+          const int m = c0 + t;
+          if (m >= lo && m < bx) {
+            sr[0][m - base] = my[t];
+            sr[1][m - base] = mz[t];
+          }
+        }
       }
-      sr[0][m - base] = my;
-      sr[1][m - base] = mz;
     }
     bar_sync();
     if (a < H && tid == 0) {
@@ -517,18 +590,21 @@ __device__ __forceinline__ void spline_tile(const Params &P, Ring64 r64, Ring32 
 
 
 // Spline kernel tiles: FP64 runs serial chunks of kSplineChunk unknowns per
-// thread; FP32C one unknown per thread (its sweeps are sums, not chains).
-template <int PREC>
+// thread; FP32C CP consecutive unknowns per thread (its sweeps are sums, not
+// chains), the forward sweep covering the tile and its right halo of W + 1:
+// one unknown per thread on moderate grids (243 + 13 = 256), four on grids
+// that fill the GPU several times over (BIG: 1011 + 13 = 1024).
+template <int PREC, bool BIG = false>
 struct SplineLaunch {
-  static constexpr int TS = PREC == BSDE_FP64 ? kSplineTile : kSplineTile32;
+  static constexpr int TS = PREC == BSDE_FP64 ? kSplineTile : (BIG ? 1011 : 243);
   static constexpr int NT = PREC == BSDE_FP64 ? kSplineTile / kSplineChunk : kSplineTile32;
 };
 
-template <int PREC>
-__global__ void __launch_bounds__(SplineLaunch<PREC>::NT)
+template <int PREC, bool BIG>
+__global__ void __launch_bounds__(SplineLaunch<PREC, BIG>::NT)
     k_spline(const Params P, Ring64 r64, Ring32 r32, int slot) {
   using T = typename SplineT<PREC>::T;
-  constexpr int TS = SplineLaunch<PREC>::TS, NT = SplineLaunch<PREC>::NT;
+  constexpr int TS = SplineLaunch<PREC, BIG>::TS, NT = SplineLaunch<PREC, BIG>::NT;
   constexpr int S = spline_span<PREC>(TS);
   __shared__ T sr[2][S], sg[2][S];
   __shared__ T sid[kInvPivots];
