@@ -758,7 +758,7 @@ def run_batch(args, rank, world, local_rank):
     for _ in range(args.steps):
         bs.close()
         bs = B.BatchSolver(probs, device=dev)
-        bs.set_config(cfg["cluster"], cfg["target_groups"])
+        bs.set_config(cfg["cluster"], cfg["target_groups"], cfg.get("flat_tiles", 0))
         eres = bs.solve()
     torch.cuda.synchronize(dev)
     e_dt = _max_over_ranks(dist, time.perf_counter() - e_t0)
@@ -1361,7 +1361,7 @@ def run_serving(args, rank, world, local_rank):
             records, summary = serve.serve(srv, arrivals)
         _barrier(dist)
         if not args.no_sweep:
-            for rate in (1000.0, 500.0, 250.0, 125.0):
+            for rate in (1500.0, 1000.0, 750.0, 500.0, 250.0):
                 arr = W.config5_arrivals(rate=rate, duration=args.sweep_duration)
                 _, sm = serve.serve(srv, arr)
                 sweep.append({"rate": rate, "requests": sm["requests"],

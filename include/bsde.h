@@ -314,7 +314,12 @@ typedef struct bsde_batch_s bsde_batch_t;
 typedef struct bsde_batch_config {
   int32_t cluster;       /* CTAs that share one problem: 1, 2, 4 or 8            */
   int32_t target_groups; /* thread groups per grid point in the step tiles, 1..6 */
-  int32_t reserved[6];
+  int32_t flat_tiles;    /* step-tile form: 0 = grouped tiles of 64 points x the
+                            groups (partial sums in shared memory, a barrier per
+                            tile); 1 = flat tiles of one point per thread (384
+                            points), each thread running its point's groups in
+                            turn with no barrier                                 */
+  int32_t reserved[5];
 } bsde_batch_config;
 
 /* Workspace for the n problems ps[0..n-1] (rings, tables, descriptors,
@@ -326,17 +331,18 @@ BSDE_API int bsde_batch_workspace_bytes(int n, const bsde_problem *ps, size_t *b
 
 /* Plan the batch on dev_workspace (caller-owned, >= bsde_batch_workspace_bytes,
  * 256-byte aligned): host constants per problem, descriptors and tables copied
- * to the device.  The default configuration is cluster 2, 4 target groups. */
+ * to the device.  The default configuration is cluster 2, 4 target groups,
+ * grouped tiles. */
 BSDE_API int bsde_plan_batch(int n, const bsde_problem *ps, void *dev_workspace,
                              size_t bytes, bsde_batch_t **out);
 
 BSDE_API int bsde_batch_set_config(bsde_batch_t *b, const bsde_batch_config *cfg);
 BSDE_API int bsde_batch_get_config(const bsde_batch_t *b, bsde_batch_config *cfg);
 
-/* Time every candidate configuration (cluster in {1, 2, 4, 8} x target
- * groups in {2, 4, 6}) on this batch with CUDA events on `stream`, keep the
- * fastest and return it in *best (may be NULL).  Solves the batch 2 x 12
- * times; waits for the stream. */
+/* Time every candidate configuration (cluster in {1, 2, 4, 8} x step-tile
+ * form in {grouped with 2, 4 or 6 target groups, flat}) on this batch with
+ * CUDA events on `stream`, keep the fastest and return it in *best (may be
+ * NULL).  Solves the batch 2 x 16 times; waits for the stream. */
 BSDE_API int bsde_batch_autotune(bsde_batch_t *b, void *stream, bsde_batch_config *best);
 
 /* Solve all problems; results (NULL or n host structs, in the order of ps)
@@ -352,9 +358,10 @@ BSDE_API void bsde_batch_free(bsde_batch_t *b);
  * level ring are free (admission by footprint), runs on the next free
  * cluster while others are in flight, and frees its slot and memory when
  * polled.  Problems must be BSDE_FP32C with the closed-form start and a
- * constant forward process (as for batches).  A request
- * gives the same result alone and in any mix (same kernels per tile, same
- * order of operations).  The server's waits for new requests are bounded: a
+ * constant forward process (as for batches).  Requests run flat step tiles
+ * (one point per thread) unless their step_kernel asks for grouped ones; the
+ * two give the same results.  A request gives the same result alone and in
+ * any mix (same kernels per tile, same order of operations).  The server's waits for new requests are bounded: a
  * cluster that finds no request for idle_ms milliseconds stops the whole
  * server (every cluster leaves after its current request).  From then on
  * bsde_server_submit returns BSDE_ETIMEOUT, bsde_server_poll hands back the

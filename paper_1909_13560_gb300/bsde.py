@@ -86,7 +86,7 @@ BSDE2_TERMINAL = {"SIN_SUM": 0, "SPREAD_LOG": 1}
 
 class bsde_batch_config(ctypes.Structure):
     _fields_ = [("cluster", ctypes.c_int32), ("target_groups", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("flat_tiles", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class bsde_result(ctypes.Structure):
@@ -507,11 +507,12 @@ class BatchSolver:
         c = bsde_batch_config()
         _check(load().bsde_batch_get_config(ctypes.c_void_p(self.batch), ctypes.byref(c)),
                "bsde_batch_get_config")
-        return {"cluster": c.cluster, "target_groups": c.target_groups}
+        return {"cluster": c.cluster, "target_groups": c.target_groups,
+                "flat_tiles": c.flat_tiles}
 
-    def set_config(self, cluster: int, target_groups: int) -> None:
+    def set_config(self, cluster: int, target_groups: int, flat_tiles: int = 0) -> None:
         c = bsde_batch_config()
-        c.cluster, c.target_groups = cluster, target_groups
+        c.cluster, c.target_groups, c.flat_tiles = cluster, target_groups, flat_tiles
         _check(load().bsde_batch_set_config(ctypes.c_void_p(self.batch), ctypes.byref(c)),
                "bsde_batch_set_config")
 
@@ -521,7 +522,8 @@ class BatchSolver:
         c = bsde_batch_config()
         _check(load().bsde_batch_autotune(ctypes.c_void_p(self.batch), ctypes.c_void_p(s.cuda_stream),
                                           ctypes.byref(c)), "bsde_batch_autotune")
-        return {"cluster": c.cluster, "target_groups": c.target_groups}
+        return {"cluster": c.cluster, "target_groups": c.target_groups,
+                "flat_tiles": c.flat_tiles}
 
     def solve(self, stream=None, want_results: bool = True):
         import torch

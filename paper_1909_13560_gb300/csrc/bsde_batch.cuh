@@ -77,12 +77,22 @@ __device__ void batch_instance(BatchSmem &sm, unsigned char *ws, Stats *st,
   }
   cl.sync();
 
-  // the backward loop: step tiles, barrier, spline tiles, barrier
-  const int ntiles = int((P.Nx + kStepTP - 1) / kStepTP);
+  // the backward loop: step tiles, barrier, spline tiles, barrier.  Step
+  // tiles are grouped (kStepTP points x G groups of threads, partial sums in
+  // shared memory, a barrier per tile) or flat (one point per thread, every
+  // group in turn, no barrier), as the descriptor says
+  const bool flat = P.flat != 0;
+  const int tw = flat ? nt : kStepTP;
+  const int ntiles = int((P.Nx + tw - 1) / tw);
   for (int n = P.N - P.k; n >= 0; --n) {
-    for (int t = crank; t < ntiles; t += csize) {
-      step_tile32<DRV, true>(P, sm.D.dc32, r32, sm.tab, sm.part, n, t * kStepTP, st);
-      __syncthreads();
+    if (flat) {
+      for (int t = crank; t < ntiles; t += csize)
+        step_tile32f<DRV, true>(P, sm.D.dc32, r32, sm.tab, n, t * tw, st);
+    } else {
+      for (int t = crank; t < ntiles; t += csize) {
+        step_tile32<DRV, true>(P, sm.D.dc32, r32, sm.tab, sm.part, n, t * kStepTP, st);
+        __syncthreads();
+      }
     }
     cl.sync();
     for (int t = crank; t < nst; t += csize) {

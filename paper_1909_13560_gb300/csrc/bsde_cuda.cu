@@ -730,8 +730,9 @@ struct bsde_batch_s {
   std::vector<size_t> off_ptable, off_ringA, off_ringB;
   bsde_batch_config cfg{};
   int desc_groups = 0;  // target_groups the device descriptors were built with
+  int desc_flat = -1;   // and their step-tile form (flat_tiles)
   cudaGraphExec_t graph = nullptr;
-  int graph_cluster = 0, graph_groups = 0;
+  int graph_cluster = 0, graph_groups = 0, graph_flat = -1;
   Stats *host_stats = nullptr;
 };
 
@@ -768,7 +769,8 @@ static int batch_layout(int n, const bsde_problem *ps, BatchLayout &L) {
 }
 
 // Descriptors, pair tables and the largest-first order, copied to the device.
-static int batch_upload(bsde_batch_t *b, int target_groups) {
+// Every problem takes the batch's step-tile form (flat or grouped).
+static int batch_upload(bsde_batch_t *b, int target_groups, int flat) {
   const int n = b->n;
   std::vector<InstDesc> descs(n);
   std::vector<double> work(n);
@@ -779,6 +781,7 @@ static int batch_upload(bsde_batch_t *b, int target_groups) {
     std::memset(&D, 0, sizeof(D));
     fill_params(b->probs[i], D.P);
     build_tables(D.P, nullptr, t32.data(), tp.data(), target_groups, 6);
+    D.P.flat = flat;
     DrvC<double> c64;
     driver_coefs(D.P, c64, D.dc32);
     D.ringA = int64_t(b->off_ringA[i]);
@@ -796,6 +799,7 @@ static int batch_upload(bsde_batch_t *b, int target_groups) {
   BSDE_CUDA_TRY(cudaMemcpy(b->ws + b->off_order, order.data(), sizeof(int) * n,
                            cudaMemcpyHostToDevice));
   b->desc_groups = target_groups;
+  b->desc_flat = flat;
   return BSDE_OK;
 }
 
@@ -832,10 +836,12 @@ static int batch_enqueue(bsde_batch_t *b, cudaStream_t s) {
 }
 
 static int batch_graph(bsde_batch_t *b) {
-  if (b->graph && b->graph_cluster == b->cfg.cluster && b->graph_groups == b->cfg.target_groups)
+  const int flat = b->cfg.flat_tiles;
+  if (b->graph && b->graph_cluster == b->cfg.cluster && b->graph_groups == b->cfg.target_groups &&
+      b->graph_flat == flat)
     return BSDE_OK;
-  if (b->desc_groups != b->cfg.target_groups) {
-    int rc = batch_upload(b, b->cfg.target_groups);
+  if (b->desc_groups != b->cfg.target_groups || b->desc_flat != flat) {
+    int rc = batch_upload(b, b->cfg.target_groups, flat);
     if (rc) return rc;
   }
   if (b->graph) {
@@ -864,12 +870,13 @@ static int batch_graph(bsde_batch_t *b) {
     return fail(BSDE_ECUDA, std::string("batch graph: ") + cudaGetErrorString(e));
   b->graph_cluster = b->cfg.cluster;
   b->graph_groups = b->cfg.target_groups;
+  b->graph_flat = flat;
   return BSDE_OK;
 }
 
 static bool valid_config(const bsde_batch_config &c) {
   return (c.cluster == 1 || c.cluster == 2 || c.cluster == 4 || c.cluster == 8) &&
-         c.target_groups >= 1 && c.target_groups <= 6;
+         c.target_groups >= 1 && c.target_groups <= 6 && (c.flat_tiles == 0 || c.flat_tiles == 1);
 }
 
 }  // namespace bsde
@@ -911,7 +918,8 @@ int bsde_plan_batch(int n, const bsde_problem *ps, void *dev_workspace, size_t b
   b->probs.assign(ps, ps + n);
   b->cfg.cluster = 2;
   b->cfg.target_groups = 4;
-  int rc = batch_upload(b, b->cfg.target_groups);
+  b->cfg.flat_tiles = 0;
+  int rc = batch_upload(b, b->cfg.target_groups, b->cfg.flat_tiles);
   if (rc == BSDE_OK && cudaMallocHost(&b->host_stats, sizeof(Stats) * size_t(n)) != cudaSuccess)
     rc = fail(BSDE_ECUDA, "pinned result buffer");
   if (rc) {
@@ -973,13 +981,17 @@ int bsde_batch_autotune(bsde_batch_t *b, void *stream, bsde_batch_config *best) 
   cudaEvent_t e0, e1;
   BSDE_CUDA_TRY(cudaEventCreate(&e0));
   BSDE_CUDA_TRY(cudaEventCreate(&e1));
+  // the step-tile forms: grouped tiles with 2, 4 or 6 groups of threads per
+  // point, and flat tiles (one point per thread, its groups in turn; one
+  // group per step j)
   const int clusters[4] = {1, 2, 4, 8};
-  const int groups[3] = {2, 4, 6};
+  const int forms[4][2] = {{2, 0}, {4, 0}, {6, 0}, {1, 1}};  // {target_groups, flat_tiles}
   int rc = BSDE_OK;
-  for (int gi = 0; gi < 3 && rc == BSDE_OK; ++gi) {
+  for (int fi = 0; fi < 4 && rc == BSDE_OK; ++fi) {
     for (int ci = 0; ci < 4 && rc == BSDE_OK; ++ci) {
       b->cfg.cluster = clusters[ci];
-      b->cfg.target_groups = groups[gi];
+      b->cfg.target_groups = forms[fi][0];
+      b->cfg.flat_tiles = forms[fi][1];
       rc = batch_graph(b);
       if (rc) break;
       if (cudaGraphLaunch(b->graph, s) != cudaSuccess) { rc = fail(BSDE_ECUDA, "autotune launch"); break; }
@@ -1198,6 +1210,9 @@ int bsde_server_submit(bsde_server_t *s, const bsde_problem *p, int *slot) {
     PairF32 tp[kMaxK * kMaxL];
     build_tables(D.P, nullptr, t32, tp, 4, 6);
     std::memcpy(S.tab, tp, sizeof(PairF32) * size_t(D.P.k) * size_t(D.P.Lp));
+    // flat step tiles unless the request asks for grouped ones (the same
+    // results: the same group split and order of operations)
+    D.P.flat = p->step_kernel == BSDE_STEP_GROUPED ? 0 : 1;
   }
   DrvC<double> c64;
   driver_coefs(D.P, c64, D.dc32);

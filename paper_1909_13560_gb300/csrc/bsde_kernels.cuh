@@ -1286,41 +1286,51 @@ __global__ void __launch_bounds__(kStepTP * kMaxGroups, 3)
 // ---------------------------------------------------------------------------
 constexpr int kFlatTP = 128;  // grid points (threads) per CTA
 
-template <int DRV>
-__global__ void __launch_bounds__(kFlatTP, 8)
-    k_step32f(const Params P, const DrvC<float> dc, Ring32 r32,
-              const __grid_constant__ PairTab32 tab, int n, Stats *st) {
-  wait_predecessor();
-  const int i0 = blockIdx.x * kFlatTP;
+// One flat tile: blockDim.x consecutive points from i0, one per thread, all
+// groups of a point in turn.  `tab` is the pair table (kernel parameters or
+// shared memory: its reads are uniform across the CTA either way).  Needs no
+// barrier, before or after.
+template <int DRV, bool COH>
+__device__ __forceinline__ void step_tile32f(const Params &P, const DrvC<float> &dc, Ring32 r32,
+                                             const PairF32 *tab, int n, int i0, Stats *st) {
   const int ii = i0 + int(threadIdx.x);
   const int last = int(P.Nx - 1);
+  const int tw = int(blockDim.x);
   const bool active = ii <= last;
   float prev_y = 0.f;
-  if (active) prev_y = r32.A[int64_t((n + 1) % P.nslot) * P.Nx + ii].x;
+  if (active) prev_y = ldl<COH>(r32.A + int64_t((n + 1) % P.nslot) * P.Nx + ii).x;
   Sums32 s{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   for (int g = 0; g < P.G; ++g) {
     const int j = g / P.S + 1, lc = g % P.S;
     const int q0 = lc * P.Lg, q1 = q0 + P.Lg < P.Lp ? q0 + P.Lg : P.Lp;
-    // every node cell of every point of the CTA on the grid (points past the
+    // every node cell of every point of the tile on the grid (points past the
     // end take the clamping path, whose cells stay on the grid)
-    const bool interior = i0 + P.smin[j - 1] >= 0 && i0 + kFlatTP + P.smax[j - 1] <= last;
+    const bool interior = i0 + P.smin[j - 1] >= 0 && i0 + tw + P.smax[j - 1] <= last;
     Acc32 acc{make_float2(0.f, 0.f), make_float2(0.f, 0.f), 0.f, 0.f, 0.f};
     const int64_t off = int64_t((n + j) % P.nslot) * P.Nx;
     float tj, et, emt;
     level_time<DRV>(P, n + j, tj, et, emt);
-    const PairF32 *row = tab.e + (j - 1) * P.Lp;
+    const PairF32 *row = tab + (j - 1) * P.Lp;
     if (P.zform && j == 1)
-      pairs32<DRV, true, false, true>(dc, r32, off, row, q0, q1, ii, last, tj, et, emt, acc);
+      pairs32<DRV, true, COH, true>(dc, r32, off, row, q0, q1, ii, last, tj, et, emt, acc);
     else if (interior)
-      pairs32<DRV, false, false>(dc, r32, off, row, q0, q1, ii, last, tj, et, emt, acc);
+      pairs32<DRV, false, COH>(dc, r32, off, row, q0, q1, ii, last, tj, et, emt, acc);
     else
-      pairs32<DRV, true, false>(dc, r32, off, row, q0, q1, ii, last, tj, et, emt, acc);
+      pairs32<DRV, true, COH>(dc, r32, off, row, q0, q1, ii, last, tj, et, emt, acc);
     fold_group(s, acc.S.y, acc.C.y, acc.Fz, acc.Fy, acc.S.x, acc.C.x, acc.FyC);
   }
   int it = 0;
   float d = 0.f;
   if (active) d = finish_point32<DRV>(P, dc, r32.A, n, ii, s, prev_y, it);
   record_picard32(st, active, it, d, P.picard_tol_f);
+}
+
+template <int DRV>
+__global__ void __launch_bounds__(kFlatTP, 8)
+    k_step32f(const Params P, const DrvC<float> dc, Ring32 r32,
+              const __grid_constant__ PairTab32 tab, int n, Stats *st) {
+  wait_predecessor();
+  step_tile32f<DRV, false>(P, dc, r32, tab.e, n, blockIdx.x * kFlatTP, st);
 }
 
 // ---------------------------------------------------------------------------

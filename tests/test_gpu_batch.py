@@ -73,12 +73,13 @@ def test_batch_alone_equals_in_the_mix(B):
         assert r1["y0"] == res[i]["y0"] and r1["z0"] == res[i]["z0"]
 
 
-@pytest.mark.parametrize("cluster,groups", [(1, 4), (4, 4), (8, 2), (2, 6)])
-def test_batch_configs_agree_with_oracle(B, cluster, groups):
+@pytest.mark.parametrize("cluster,groups,flat", [(1, 4, 0), (4, 4, 0), (8, 2, 0), (2, 6, 0),
+                                                 (1, 1, 1), (4, 1, 1), (2, 4, 1)])
+def test_batch_configs_agree_with_oracle(B, cluster, groups, flat):
     probs = _mixed(count=12, seed=3)
     bs = B.BatchSolver(probs)
-    bs.set_config(cluster, groups)
-    assert bs.config() == {"cluster": cluster, "target_groups": groups}
+    bs.set_config(cluster, groups, flat)
+    assert bs.config() == {"cluster": cluster, "target_groups": groups, "flat_tiles": flat}
     res = bs.solve()
     bs.close()
     for p, r in zip(probs, res):
@@ -94,12 +95,30 @@ def test_batch_autotune_picks_a_valid_config(B):
     bs = B.BatchSolver(probs)
     before = bs.solve()
     best = bs.autotune()
-    assert best["cluster"] in (1, 2, 4, 8) and best["target_groups"] in (2, 4, 6)
+    assert best["cluster"] in (1, 2, 4, 8)
+    assert (best["target_groups"], best["flat_tiles"]) in ((2, 0), (4, 0), (6, 0), (1, 1))
     assert bs.config() == best
     after = bs.solve()
     bs.close()
     for a, b in zip(before, after):
         assert abs(a["y0"] - b["y0"]) <= 1e-6 * max(1.0, abs(a["y0"]))
+
+
+@pytest.mark.parametrize("groups", [1, 4, 6])
+def test_batch_flat_tiles_equal_grouped_tiles_bitwise(B, groups):
+    """Flat step tiles (one point per thread, its groups in turn) and grouped
+    ones (groups of threads per point, partial sums folded in shared memory)
+    with the same group split run the same pairs in the same order of
+    operations: bitwise equal results, whatever the cluster size."""
+    probs = _mixed(count=20, seed=13)
+    bs = B.BatchSolver(probs)
+    bs.set_config(2, groups, 0)
+    a = bs.solve()
+    bs.set_config(4, groups, 1)
+    b = bs.solve()
+    bs.close()
+    for x, y in zip(a, b):
+        assert x["y0"] == y["y0"] and x["z0"] == y["z0"] and x["status"] == y["status"]
 
 
 def test_batch_rejects_fp64_problems(B):
