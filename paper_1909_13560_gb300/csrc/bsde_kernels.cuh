@@ -1036,13 +1036,17 @@ struct Acc32 {
 
 // One group's node pairs for point ii, level data loaded directly from
 // global memory (L1/L2).  With CLAMP false every cell must lie on the grid.
-template <int DRV, bool CLAMP, bool COH, bool ZF = false>
+// UNR: pairs unrolled together, so the next pair's loads can be issued
+// before the current pair's arithmetic (2 pays in the single-solve flat
+// kernel, 2% at config3, whose threads have the registers; the grouped tiles
+// and the batch kernel, which would spill, keep 1).
+template <int DRV, bool CLAMP, bool COH, bool ZF = false, int UNR = 1>
 __device__ __forceinline__ void pairs32(const DrvC<float> &dc, Ring32 r, int64_t off,
                                         const PairF32 *row, int q0, int q1, int ii, int last,
                                         float tj, float et, float emt, Acc32 &acc) {
   const float4 *A = r.A + off;
   const float2 *M = r.M + off;
-#pragma unroll 1
+#pragma unroll UNR
   for (int q = q0; q < q1; ++q) {
     const float4 *te = reinterpret_cast<const float4 *>(row + q);
     const float4 e0 = te[0], e3 = te[3], e4 = te[4];
@@ -1289,8 +1293,8 @@ constexpr int kFlatTP = 128;  // grid points (threads) per CTA
 // One flat tile: blockDim.x consecutive points from i0, one per thread, all
 // groups of a point in turn.  `tab` is the pair table (kernel parameters or
 // shared memory: its reads are uniform across the CTA either way).  Needs no
-// barrier, before or after.
-template <int DRV, bool COH>
+// barrier, before or after.  UNR as for pairs32 (the interior pairs).
+template <int DRV, bool COH, int UNR = 1>
 __device__ __forceinline__ void step_tile32f(const Params &P, const DrvC<float> &dc, Ring32 r32,
                                              const PairF32 *tab, int n, int i0, Stats *st) {
   const int ii = i0 + int(threadIdx.x);
@@ -1314,7 +1318,7 @@ __device__ __forceinline__ void step_tile32f(const Params &P, const DrvC<float> 
     if (P.zform && j == 1)
       pairs32<DRV, true, COH, true>(dc, r32, off, row, q0, q1, ii, last, tj, et, emt, acc);
     else if (interior)
-      pairs32<DRV, false, COH>(dc, r32, off, row, q0, q1, ii, last, tj, et, emt, acc);
+      pairs32<DRV, false, COH, false, UNR>(dc, r32, off, row, q0, q1, ii, last, tj, et, emt, acc);
     else
       pairs32<DRV, true, COH>(dc, r32, off, row, q0, q1, ii, last, tj, et, emt, acc);
     fold_group(s, acc.S.y, acc.C.y, acc.Fz, acc.Fy, acc.S.x, acc.C.x, acc.FyC);
@@ -1330,7 +1334,7 @@ __global__ void __launch_bounds__(kFlatTP, 8)
     k_step32f(const Params P, const DrvC<float> dc, Ring32 r32,
               const __grid_constant__ PairTab32 tab, int n, Stats *st) {
   wait_predecessor();
-  step_tile32f<DRV, false>(P, dc, r32, tab.e, n, blockIdx.x * kFlatTP, st);
+  step_tile32f<DRV, false, 2>(P, dc, r32, tab.e, n, blockIdx.x * kFlatTP, st);
 }
 
 // ---------------------------------------------------------------------------
