@@ -359,9 +359,9 @@ BSDE_API void bsde_batch_free(bsde_batch_t *b);
  * cluster while others are in flight, and frees its slot and memory when
  * polled.  Problems must be BSDE_FP32C with the closed-form start and a
  * constant forward process (as for batches).  Requests run flat step tiles
- * (one point per thread) unless their step_kernel asks for grouped ones; the
- * two give the same results.  A request gives the same result alone and in
- * any mix (same kernels per tile, same order of operations).  The server's waits for new requests are bounded: a
+ * (one point per thread; the same results as grouped tiles at the same group
+ * split; step_kernel is not consulted).  A request gives the same result
+ * alone and in any mix (same kernels per tile, same order of operations).  The server's waits for new requests are bounded: a
  * cluster that finds no request for idle_ms milliseconds stops the whole
  * server (every cluster leaves after its current request).  From then on
  * bsde_server_submit returns BSDE_ETIMEOUT, bsde_server_poll hands back the

@@ -26,7 +26,9 @@ struct alignas(16) InstDesc {
 };
 
 constexpr int kBatchThreads = kStepTP * 6;          // up to six groups per point
-constexpr int kBatchSplineTile = kBatchThreads * kSplineChunk;  // 1536 unknowns
+// spline tiles of 1523 unknowns: with the forward sweep's right halo of 13
+// they fill the 384 threads with four consecutive unknowns each
+constexpr int kBatchSplineTile = kBatchThreads * kSplineChunk - 13;
 
 struct alignas(16) BatchSmem {
   InstDesc D;
@@ -51,7 +53,9 @@ __global__ void k_batch_reset(int *queue, Stats *stats, int count) {
   }
 }
 
-template <int DRV>
+// FLAT: the step-tile form (see below), a template parameter so that each
+// form's kernel gets its own register allocation.
+template <int DRV, bool FLAT>
 __device__ void batch_instance(BatchSmem &sm, unsigned char *ws, Stats *st,
                                cg::cluster_group &cl) {
   const Params &P = sm.D.P;
@@ -80,12 +84,11 @@ __device__ void batch_instance(BatchSmem &sm, unsigned char *ws, Stats *st,
   // the backward loop: step tiles, barrier, spline tiles, barrier.  Step
   // tiles are grouped (kStepTP points x G groups of threads, partial sums in
   // shared memory, a barrier per tile) or flat (one point per thread, every
-  // group in turn, no barrier), as the descriptor says
-  const bool flat = P.flat != 0;
-  const int tw = flat ? nt : kStepTP;
+  // group in turn, no barrier)
+  const int tw = FLAT ? nt : kStepTP;
   const int ntiles = int((P.Nx + tw - 1) / tw);
   for (int n = P.N - P.k; n >= 0; --n) {
-    if (flat) {
+    if constexpr (FLAT) {
       for (int t = crank; t < ntiles; t += csize)
         step_tile32f<DRV, true>(P, sm.D.dc32, r32, sm.tab, n, t * tw, st);
     } else {
@@ -110,6 +113,7 @@ __device__ void batch_instance(BatchSmem &sm, unsigned char *ws, Stats *st,
   }
 }
 
+template <bool FLAT>
 __global__ void __launch_bounds__(kBatchThreads, 2)
     k_batch32(const InstDesc *__restrict__ descs, const int *__restrict__ order, int count,
               int *queue, unsigned char *ws, Stats *stats) {
@@ -138,11 +142,11 @@ __global__ void __launch_bounds__(kBatchThreads, 2)
     }
     __syncthreads();
     switch (sm.D.P.driver) {
-      case BSDE_DRIVER_LIN_SIN: batch_instance<BSDE_DRIVER_LIN_SIN>(sm, ws, stats + id, cl); break;
-      case BSDE_DRIVER_BS: batch_instance<BSDE_DRIVER_BS>(sm, ws, stats + id, cl); break;
-      case BSDE_DRIVER_LB: batch_instance<BSDE_DRIVER_LB>(sm, ws, stats + id, cl); break;
-      case BSDE_DRIVER_EX1: batch_instance<BSDE_DRIVER_EX1>(sm, ws, stats + id, cl); break;
-      default: batch_instance<BSDE_DRIVER_EX2>(sm, ws, stats + id, cl); break;
+      case BSDE_DRIVER_LIN_SIN: batch_instance<BSDE_DRIVER_LIN_SIN, FLAT>(sm, ws, stats + id, cl); break;
+      case BSDE_DRIVER_BS: batch_instance<BSDE_DRIVER_BS, FLAT>(sm, ws, stats + id, cl); break;
+      case BSDE_DRIVER_LB: batch_instance<BSDE_DRIVER_LB, FLAT>(sm, ws, stats + id, cl); break;
+      case BSDE_DRIVER_EX1: batch_instance<BSDE_DRIVER_EX1, FLAT>(sm, ws, stats + id, cl); break;
+      default: batch_instance<BSDE_DRIVER_EX2, FLAT>(sm, ws, stats + id, cl); break;
     }
   }
 }

@@ -809,7 +809,8 @@ static int batch_enqueue(bsde_batch_t *b, cudaStream_t s) {
   Stats *stats = reinterpret_cast<Stats *>(b->ws + b->off_stats);
   k_batch_reset<<<(n + 255) / 256, 256, 0, s>>>(queue, stats, n);
   const size_t smem = sizeof(BatchSmem);
-  BSDE_CUDA_TRY(cudaFuncSetAttribute(k_batch32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  auto *kern = b->cfg.flat_tiles ? k_batch32<true> : k_batch32<false>;
+  BSDE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      int(smem)));
   const int cl = b->cfg.cluster;
   cudaLaunchConfig_t lc{};
@@ -825,13 +826,13 @@ static int batch_enqueue(bsde_batch_t *b, cudaStream_t s) {
   lc.numAttrs = 1;
   lc.gridDim = dim3(unsigned(cl), 1, 1);
   int active = 0;
-  BSDE_CUDA_TRY(cudaOccupancyMaxActiveClusters(&active, k_batch32, &lc));
+  BSDE_CUDA_TRY(cudaOccupancyMaxActiveClusters(&active, kern, &lc));
   if (active < 1) return fail(BSDE_ECUDA, "batch kernel: no cluster fits on the device");
   const int clusters = std::min(active, n);
   lc.gridDim = dim3(unsigned(clusters * cl), 1, 1);
   const InstDesc *descs = reinterpret_cast<const InstDesc *>(b->ws + b->off_desc);
   const int *order = reinterpret_cast<const int *>(b->ws + b->off_order);
-  BSDE_CUDA_TRY(cudaLaunchKernelEx(&lc, k_batch32, descs, order, n, queue, b->ws, stats));
+  BSDE_CUDA_TRY(cudaLaunchKernelEx(&lc, kern, descs, order, n, queue, b->ws, stats));
   return BSDE_OK;
 }
 
@@ -1210,9 +1211,9 @@ int bsde_server_submit(bsde_server_t *s, const bsde_problem *p, int *slot) {
     PairF32 tp[kMaxK * kMaxL];
     build_tables(D.P, nullptr, t32, tp, 4, 6);
     std::memcpy(S.tab, tp, sizeof(PairF32) * size_t(D.P.k) * size_t(D.P.Lp));
-    // flat step tiles unless the request asks for grouped ones (the same
-    // results: the same group split and order of operations)
-    D.P.flat = p->step_kernel == BSDE_STEP_GROUPED ? 0 : 1;
+    // the serving kernel runs flat step tiles (bitwise the grouped tiles'
+    // results at the same group split)
+    D.P.flat = 1;
   }
   DrvC<double> c64;
   driver_coefs(D.P, c64, D.dc32);
