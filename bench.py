@@ -562,7 +562,8 @@ def run_ours(args, rank, world, local_rank):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        lv = max(1, args.cpu_levels // (16 if c3 else 1))
+        # about 10 s of oracle work on 16 host threads at either size
+        lv = max(1, args.cpu_levels // (2 if c3 else 1))
         cpu = cpu_baseline(lv, os.cpu_count() or 1, wl)
         one = cpu_baseline(max(1, lv // 8), 1, wl)
         cpu["single_thread"] = {"value": one["value"], "cores": 1, "sample": one["sample"]}
