@@ -857,6 +857,24 @@ def flops_per_gp_step_2d(k: int, L: int) -> float:
     return k * L * L * per_node + 3 * 6 + 10 * 6
 
 
+def flops_per_gp_step_tp(k: int, L: int, precision: str) -> dict:
+    """Algorithmic flops of one 2-D grid-point step in the tensor-product form,
+    per pass (an FMA as 2 flop).  FP64: the x2 pass takes per (j, l2) and
+    field the two x2 interpolants R, S (1 mul + 3 FMA each) and four weighted
+    sums (4 FMA): 66 per (j, l2); the x1 pass per (j, l1) and field the two x1
+    interpolants and three sums: 60, per j the driver combinations and the
+    z, A updates (27), per point ~10 Picard iterations (80).  FP32C, per
+    mirror pair of nodes: the x2 pass two interpolant sets (48 ops each) and
+    per field the exact pair sum, one compensated product and the plain
+    slope and difference sums (33 ops): 195; the x1 pass two interpolant sets
+    (96), the drivers of both nodes and their difference (40), the z sums by
+    compensated products (44) and the driver sums (13): 193."""
+    if precision == "fp64":
+        return {"x2": k * L * 66.0, "x1": k * L * 60.0 + k * 27.0 + 80.0}
+    pairs = (L + 1) // 2
+    return {"x2": k * pairs * 195.0, "x1": k * pairs * 193.0 + 80.0}
+
+
 def run_2d(args, rank, world, local_rank):
     """Example 4 (Eq. 34-35) at the paper's largest configuration (Table 9:
     K = 6, N = 64, M = 1024 intervals per dimension on [-8, 8]^2, L = 8 per
@@ -871,8 +889,10 @@ def run_2d(args, rank, world, local_rank):
     stream = torch.cuda.current_stream(dev)
     sp = stream.cuda_stream
     K, N, M, L = 6, 64, 1024, 8
-    p = W.ex4_problem(M=M, N=N, k=K, L=L)
+    p = dict(W.ex4_problem(M=M, N=N, k=K, L=L), step_form=args.step_form)
     prec = args.precision
+    # AUTO takes the tensor-product passes for Example 4 (b21 = 0)
+    tensor = args.step_form == "TENSOR" or (args.step_form == "AUTO" and p["b21"] == 0.0)
     s = B.Solver2(p, device=dev, precision=prec)
     np_ = p["Nx1"] * p["Nx2"]
     units = np_ * (N - K + 1)
@@ -910,9 +930,12 @@ def run_2d(args, rank, world, local_rank):
     ez = math.hypot(r["z0"][0] - 1.0, r["z0"][1] - 1.0)
 
     # the step and derivative kernels of one level, replayed from a graph
+    # (the tensor form's two passes one by one)
     reps = 10
     times = {}
-    for part, name in ((1, "k2_step"), (2, "k2_deriv")):
+    parts = ((4, "x2"), (8, "x1"), (1, "k2_step"), (2, "k2_deriv")) if tensor else \
+        ((1, "k2_step"), (2, "k2_deriv"))
+    for part, name in parts:
         s.enqueue_level(sp, 0, part)
         torch.cuda.synchronize(dev)
         g = torch.cuda.CUDAGraph()
@@ -932,13 +955,31 @@ def run_2d(args, rank, world, local_rank):
     peaks = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak = _alu_peak_tflops(prec, sm_max)
-    fpg = flops_per_gp_step_2d(K, L) if prec == "fp64" else flops_per_gp_step_2d32(K, L)
-    step_flops = fpg * np_
-    achieved = step_flops / (times["k2_step"] / 1000.0) / 1e12
+    rec = 96 if prec == "fp64" else 64
+    if tensor:
+        fp = flops_per_gp_step_tp(K, L, prec)
+        dom = max(("x2", "x1"), key=lambda q: times[q])
+        kname = {("x2", "fp64"): "k2_tp1", ("x1", "fp64"): "k2_tp2",
+                 ("x2", "fp32c"): "k2_tp1_32", ("x1", "fp32c"): "k2_tp2_32"}[(dom, prec)]
+        fpg = fp[dom]
+        step_ms = times[dom]
+        # L1 data per point: two records per node and field set; HBM: the x2
+        # pass reads the k ring levels and writes k buffer records, the x1
+        # pass reads them back and writes the new values (24 B)
+        l1b = K * L * 2 * rec
+        hbm_b = {"x2": 2 * K * rec, "x1": K * rec + (32 if prec == "fp64" else 16) + 24}[dom]
+    else:
+        fpg = flops_per_gp_step_2d(K, L) if prec == "fp64" else flops_per_gp_step_2d32(K, L)
+        kname = "k2_step" if prec == "fp64" else "k2_step32p"
+        step_ms = times["k2_step"]
+        l1b = K * L * L * (384 if prec == "fp64" else 256)
+        hbm_b = K * rec + 24
+    achieved = fpg * np_ / (step_ms / 1000.0) / 1e12
     # derivative kernel: reads the new values (24 B) and writes the ring
     # records (96 B) per point
     der_gbs = 120.0 * np_ / (times["k2_deriv"] / 1000.0) / 1e9
     hbm = float(peaks.get("hbm_gbs", 6800.0))
+    hbm_gbs = hbm_b * np_ / (step_ms / 1000.0) / 1e9
 
     # end to end: caller levels from pinned host memory, level 0 back
     init = [torch.from_numpy(a).pin_memory() for a in _ex4_levels(p)]
@@ -985,6 +1026,8 @@ def run_2d(args, rank, world, local_rank):
                                    "per dimension (1025^2 points), N=64, K=6, L=8 per dimension "
                                    f"(64 tensor nodes), {prec.upper()}; one solve per step",
                        "precision": prec,
+                       "step_form": ("tensor-product passes (x2 pass, x1 pass)" if tensor
+                                     else "node-wise step kernel"),
                        "Nx1": p["Nx1"], "Nx2": p["Nx2"], "N": N, "k": K, "L": L,
                        "l2": "flushed between steps (256 MiB write, outside the timed events); "
                              "the level ring (700 MB) is HBM-resident",
@@ -996,15 +1039,19 @@ def run_2d(args, rank, world, local_rank):
                          and abs(ez - 2.32e-6) <= 0.02 * 2.32e-6},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak,
-                         "traffic": None if prec == "fp64" else _traffic("k2_step32p"),
-                         # K = 6, L = 8: the 192-entry pair table fits the
-                         # FP32C step's parameters (k2_step32p)
-                         "kernel": "k2_step" if prec == "fp64" else "k2_step32p",
+                         "traffic": _traffic(kname) if (tensor or prec != "fp64") else None,
+                         # node-wise, K = 6, L = 8: the 192-entry pair table
+                         # fits the FP32C step's parameters (k2_step32p)
+                         "kernel": kname,
+                         "hbm": {"achieved": hbm_gbs, "peak": hbm, "unit": "GB/s",
+                                 "frac": hbm_gbs / hbm, "bytes_per_point": hbm_b},
+                         "pass_ms": ({"k2_tp1": times["x2"], "k2_tp2": times["x1"]}
+                                     if tensor else None),
                          "peak_source": (f"derived: 152 SMs x 2 FP64 FMA units x 2 flop x {sm_max:.0f} MHz"
                                          if prec == "fp64" else
                                          f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz"),
                          "flop_per_gp_step": fpg,
-                         "l1_bytes_per_gp_step": K * L * L * (384 if prec == "fp64" else 256),
+                         "l1_bytes_per_gp_step": l1b,
                          "step_launch_ms": times["k2_step"],
                          "deriv": {"kernel": "k2_deriv", "bound": "hbm", "achieved": der_gbs,
                                    "peak": hbm, "unit": "GB/s", "frac": der_gbs / hbm,
@@ -1430,6 +1477,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp32c", "fp64"], default="fp32c")
+    ap.add_argument("--step-form", choices=["AUTO", "NODEWISE", "TENSOR"], default="AUTO",
+                    help="ex4_2d: form of the 2-D step kernels")
     ap.add_argument("--workload", choices=["config2", "config3", "config4", "config5", "ex4_2d",
                                            "general", "decomp"],
                     default="config3",

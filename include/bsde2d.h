@@ -50,16 +50,30 @@ enum {
                                    b11 b21 (Example 5)                               */
 };
 
+/* Form of the step kernels (bsde2_problem.step_form). */
+enum {
+  BSDE2_STEP_AUTO = 0,     /* TENSOR when b21 == 0, NODEWISE otherwise              */
+  BSDE2_STEP_NODEWISE = 1, /* one kernel over the L^2 tensor nodes of every step j:
+                              per node the bicubic values of the three fields      */
+  BSDE2_STEP_TENSOR = 2    /* two kernels per level (b21 == 0 only, else
+                              BSDE_EINVAL): the node shifts and the quadrature
+                              weights then factor per dimension, and the L^2-node
+                              sums are taken as an x2 pass of L nodes into a
+                              per-step buffer, then an x1 pass of L nodes.  Same
+                              values as NODEWISE up to rounding order             */
+};
+
 typedef struct bsde2_problem {
   int32_t driver, terminal;
   int32_t precision;  /* BSDE_FP64, or BSDE_FP32C: level values as float pairs,
                          derivatives as floats, the bicubic increment over the
                          cell's corner value in FP32, compensated sums, Picard
-                         on the increment in FP32 (derivatives computed in FP64) */
+                         on the increment in FP32 (derivatives: the finite
+                         differences in FP32 over the float pairs' increments) */
   int32_t picard_max; /* Picard iteration cap (paper: 30)                         */
   int32_t N, k, L;    /* time steps, steps of the scheme (1..min(6, N)), GH nodes
                          per dimension (1..16)                                    */
-  int32_t reserved;   /* 0                                                        */
+  int32_t step_form;  /* BSDE2_STEP_* (0: AUTO)                                  */
   int64_t Nx1, Nx2;   /* grid points per dimension, >= 6 each (the one-sided
                          stencil at the second node reaches five nodes on)      */
   double T, x1_min, x1_max, x2_min, x2_max, x01, x02; /* horizon, box, readout */
@@ -81,10 +95,12 @@ typedef struct bsde2_plan_s bsde2_plan_t;
 /* Device workspace a plan for *p needs, in bytes: a ring of k + 1 levels of
  * 3 fields x (value, dx1 d/dx1, dx2 d/dx2, dx1 dx2 d2/dx1dx2) doubles per
  * grid point (96 B), one plane of new values (24 B per point), the node
- * table, a staging area of 3 k planes and the statistics.  BSDE_EINVAL for a
- * bad problem (k outside 1..min(6, N), Nx1 or Nx2 < 6, L outside 1..16, x0
- * outside the box, unknown id or precision, T <= 0).  FP32C keeps one 64-byte
- * record per point and level instead of 96 bytes. */
+ * table, a staging area of 3 k planes and the statistics; the TENSOR form
+ * adds the x2 pass's buffer of k records per point (96 B FP64, 64 B FP32C).
+ * BSDE_EINVAL for a bad problem (k outside 1..min(6, N), Nx1 or Nx2 < 6, L
+ * outside 1..16, x0 outside the box, unknown id, precision or step form,
+ * TENSOR with b21 != 0, T <= 0).  FP32C keeps one 64-byte record per point
+ * and level instead of 96 bytes. */
 BSDE_API int bsde2_workspace_bytes(const bsde2_problem *p, size_t *bytes);
 
 /* Validate *p, build the node table on the host (per (j, l1, l2): the cell
@@ -115,11 +131,15 @@ BSDE_API int bsde2_solve(bsde2_plan_t *plan, void *stream, const double *init_y,
 BSDE_API int bsde2_result_fetch(bsde2_plan_t *plan, void *stream, bsde2_result *result);
 
 /* Enqueue the kernels of backward level n (0 <= n <= N-k) outside the graph:
- * parts & 1 = the step kernel, parts & 2 = the derivative kernel.  Used to
- * time the kernels one by one (meaningful after a completed solve). */
+ * parts & 1 = the step kernel (the TENSOR form: both passes), parts & 4 = the
+ * x2 pass alone, parts & 8 = the x1 pass alone (TENSOR only; the x1 pass
+ * reads the buffer the x2 pass of the same level wrote), parts & 2 = the
+ * derivative kernel.  Used to time the kernels one by one (meaningful after
+ * a completed solve). */
 BSDE_API int bsde2_enqueue_level(bsde2_plan_t *plan, void *stream, int n, int parts);
 
-/* Kernel launches in one bsde2_solve. */
+/* Kernel launches in one bsde2_solve: 1 + 2 k + (2 or 3 with TENSOR)
+ * (N - k + 1) + 2. */
 BSDE_API int64_t bsde2_plan_launches(const bsde2_plan_t *plan);
 
 /* Release the plan's host resources and graphs (not the workspace). */

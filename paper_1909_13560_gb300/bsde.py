@@ -23,6 +23,7 @@ BSDE_PRECISION = {"fp64": 0, "fp32c": 1}
 BSDE_INIT = {"EXACT": 0, "ONESTEP": 1}
 BSDE_STEP = {"AUTO": 0, "GROUPED": 1, "FLAT": 2}
 BSDE_ZFORM = {"EZ": 0, "EYDW": 1}
+BSDE2_STEP = {"AUTO": 0, "NODEWISE": 1, "TENSOR": 2}
 
 BSDE_OK = 0
 BSDE_WARN_NOCONV = 1
@@ -60,7 +61,7 @@ class bsde2_problem(ctypes.Structure):
         ("driver", ctypes.c_int32), ("terminal", ctypes.c_int32),
         ("precision", ctypes.c_int32), ("picard_max", ctypes.c_int32),
         ("N", ctypes.c_int32), ("k", ctypes.c_int32), ("L", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("step_form", ctypes.c_int32),
         ("Nx1", ctypes.c_int64), ("Nx2", ctypes.c_int64),
         ("T", ctypes.c_double), ("x1_min", ctypes.c_double), ("x1_max", ctypes.c_double),
         ("x2_min", ctypes.c_double), ("x2_max", ctypes.c_double),
@@ -694,6 +695,7 @@ def make_problem2(p: dict, precision: str = "fp64") -> bsde2_problem:
               "b11", "b21", "b22", "alpha", "beta1", "beta2"):
         setattr(s, f, float(p[f]))
     s.picard_tol = float(p.get("picard_tol", 1e-12))
+    s.step_form = BSDE2_STEP[p.get("step_form", "AUTO")]
     return s
 
 

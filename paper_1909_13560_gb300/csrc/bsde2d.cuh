@@ -118,8 +118,21 @@ __device__ void closed_form2(const Params2 &P, double t, double x1, double x2, d
   z2 = u2 * P.b22;
 }
 
-// Level values of the closed form at t_{N-m} into the new-value plane V
-// (fields y, z1, z2; i1 fastest).
+// The new-value plane V holds the three fields of a new level (y, z1, z2;
+// Np entries each, i1 fastest): doubles in FP64, float pairs (hi, lo) with
+// |lo| <= ulp(hi)/2 in FP32C (the same 8 bytes per entry), so that the FP32C
+// derivative kernel needs no FP64 arithmetic.
+__device__ __forceinline__ void put_v(const Params2 &P, double *V, int f, int64_t q, double x) {
+  if (P.precision == BSDE_FP32C) {
+    const float h = __double2float_rn(x);
+    reinterpret_cast<float2 *>(V)[f * P.Np + q] =
+        make_float2(h, __double2float_rn(__dsub_rn(x, double(h))));
+  } else {
+    V[f * P.Np + q] = x;
+  }
+}
+
+// Level values of the closed form at t_{N-m} into V.
 __global__ void k2_init_closed(const Params2 P, double *V, int m) {
   const double t = __dmul_rn(double(P.N - m), P.dt);
   for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < P.Np;
@@ -127,9 +140,9 @@ __global__ void k2_init_closed(const Params2 P, double *V, int m) {
     const int64_t i1 = q % P.Nx1, i2 = q / P.Nx1;
     double u, z1, z2;
     closed_form2(P, t, P.x1_min + double(i1) * P.dx1, P.x2_min + double(i2) * P.dx2, u, z1, z2);
-    V[q] = u;
-    V[P.Np + q] = z1;
-    V[2 * P.Np + q] = z2;
+    put_v(P, V, 0, q, u);
+    put_v(P, V, 1, q, z1);
+    put_v(P, V, 2, q, z2);
   }
 }
 
@@ -139,8 +152,21 @@ __global__ void k2_import(const Params2 P, double *V, const double *stage, int m
   const int64_t kp = int64_t(P.k) * P.Np;
   for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < P.Np;
        q += int64_t(gridDim.x) * blockDim.x) {
-    for (int f = 0; f < 3; ++f) V[f * P.Np + q] = stage[f * kp + int64_t(m) * P.Np + q];
+    for (int f = 0; f < 3; ++f) put_v(P, V, f, q, stage[f * kp + int64_t(m) * P.Np + q]);
   }
+}
+
+// y^n = A + delta of the FP32C tails as a float pair (TwoSum: A's hi part
+// need not dominate when y^n is near zero), and z as the exact pairs.
+__device__ __forceinline__ void put_new32(const Params2 &P, double *V, int64_t q, float Ah,
+                                          float Al, float dl, float z1h, float z1l, float z2h,
+                                          float z2l) {
+  float yh = Ah, yl = 0.f;
+  two_sum_into(yh, yl, __fadd_rn(Al, dl));  // yl: the exact error, |yl| <= ulp(yh)/2
+  float2 *V2 = reinterpret_cast<float2 *>(V);
+  V2[q] = make_float2(yh, yl);
+  V2[P.Np + q] = make_float2(z1h, z1l);
+  V2[2 * P.Np + q] = make_float2(z2h, z2l);
 }
 
 // ---------------------------------------------------------------------------
@@ -150,15 +176,46 @@ __global__ void k2_import(const Params2 P, double *V, const double *stage, int m
 // One CTA per kDerTX x kDerTY tile; the tile and a halo of 4 in each
 // direction (the one-sided stencils reach 4 nodes) staged in shared memory.
 // ---------------------------------------------------------------------------
+// (a product with the rounded 1/12 instead of a division: FP64 division is a
+// multi-instruction sequence on the FP64 pipe, which bounds this kernel)
+constexpr double kInv12 = 1.0 / 12.0;
 __device__ __forceinline__ double fd4(const double *f, int s, int i, int n) {
   // f points at node i of a line (stride s); n nodes on the line
   if (i >= 2 && i <= n - 3)
-    return (f[-2 * s] - 8.0 * f[-s] + 8.0 * f[s] - f[2 * s]) / 12.0;
+    return (f[-2 * s] - 8.0 * f[-s] + 8.0 * f[s] - f[2 * s]) * kInv12;
   if (i < 2)
-    return (-25.0 * f[0] + 48.0 * f[s] - 36.0 * f[2 * s] + 16.0 * f[3 * s] - 3.0 * f[4 * s]) /
-           12.0;
-  return (25.0 * f[0] - 48.0 * f[-s] + 36.0 * f[-2 * s] - 16.0 * f[-3 * s] + 3.0 * f[-4 * s]) /
-         12.0;
+    return (-25.0 * f[0] + 48.0 * f[s] - 36.0 * f[2 * s] + 16.0 * f[3 * s] - 3.0 * f[4 * s]) *
+           kInv12;
+  return (25.0 * f[0] - 48.0 * f[-s] + 36.0 * f[-2 * s] - 16.0 * f[-3 * s] + 3.0 * f[-4 * s]) *
+         kInv12;
+}
+
+// The same differences in FP32 on values given as float pairs hi + lo: the
+// stencil's weights sum to zero, so it is written over the increments
+// f_m - f_0 = (hi_m - hi_0) + (lo_m - lo_0), whose FP32 rounding is relative
+// to the increment, and the result is the stored float derivative.
+// (LO false: plain float values, l unused)
+template <bool LO>
+__device__ __forceinline__ float dinc(const float *h, const float *l, int a, int b) {
+  return LO ? __fadd_rn(__fsub_rn(h[a], h[b]), __fsub_rn(l[a], l[b])) : __fsub_rn(h[a], h[b]);
+}
+template <bool LO>
+__device__ __forceinline__ float fd4f(const float *h, const float *l, int s, int i, int n) {
+  const float c12 = float(1.0 / 12.0);
+  if (i >= 2 && i <= n - 3)
+    return __fmul_rn(__fmaf_rn(8.f, dinc<LO>(h, l, s, -s), dinc<LO>(h, l, -2 * s, 2 * s)), c12);
+  if (i < 2) {
+    float t = __fmul_rn(48.f, dinc<LO>(h, l, s, 0));
+    t = __fmaf_rn(-36.f, dinc<LO>(h, l, 2 * s, 0), t);
+    t = __fmaf_rn(16.f, dinc<LO>(h, l, 3 * s, 0), t);
+    t = __fmaf_rn(-3.f, dinc<LO>(h, l, 4 * s, 0), t);
+    return __fmul_rn(t, c12);
+  }
+  float t = __fmul_rn(48.f, dinc<LO>(h, l, 0, -s));
+  t = __fmaf_rn(-36.f, dinc<LO>(h, l, 0, -2 * s), t);
+  t = __fmaf_rn(16.f, dinc<LO>(h, l, 0, -3 * s), t);
+  t = __fmaf_rn(-3.f, dinc<LO>(h, l, 0, -4 * s), t);
+  return __fmul_rn(t, c12);
 }
 
 __global__ void __launch_bounds__(kDerTX * kDerTY)
@@ -168,41 +225,45 @@ __global__ void __launch_bounds__(kDerTX * kDerTY)
   __shared__ double sv[H][W];
   __shared__ double sy[kDerTY][W];
   wait_predecessor();
-  const int x0 = blockIdx.x * kDerTX, y0 = blockIdx.y * kDerTY;
   const int n1 = int(P.Nx1), n2 = int(P.Nx2);
   const int tid = threadIdx.x;
-  for (int f = 0; f < 3; ++f) {
-    const double *v = V + int64_t(f) * P.Np;
-    // tile + halo, indices clamped onto the grid (halo entries off the grid
-    // are never read by an on-grid stencil)
-    for (int e = tid; e < H * W; e += blockDim.x) {
-      const int r = e / W, c = e % W;
-      int g2 = y0 - kDerH + r, g1 = x0 - kDerH + c;
-      g2 = g2 < 0 ? 0 : (g2 >= n2 ? n2 - 1 : g2);
-      g1 = g1 < 0 ? 0 : (g1 >= n1 ? n1 - 1 : g1);
-      sv[r][c] = v[int64_t(g2) * n1 + g1];
-    }
-    __syncthreads();
-    // x2 derivative on the tile's rows, every column of the staged span
-    for (int e = tid; e < kDerTY * W; e += blockDim.x) {
-      const int r = e / W, c = e % W;
-      const int i2 = y0 + r;
-      sy[r][c] = i2 < n2 ? fd4(&sv[r + kDerH][c], W, i2, n2) : 0.0;
-    }
-    __syncthreads();
-    for (int e = tid; e < kDerTX * kDerTY; e += blockDim.x) {
-      const int r = e / kDerTX, c = e % kDerTX;
-      const int i1 = x0 + c, i2 = y0 + r;
-      if (i1 < n1 && i2 < n2) {
-        const double val = sv[r + kDerH][c + kDerH];
-        const double fx = fd4(&sv[r + kDerH][c + kDerH], 1, i1, n1);
-        const double fy = sy[r][c + kDerH];
-        const double fxy = fd4(&sy[r][c + kDerH], 1, i1, n1);
-        ring[(int64_t(slot) * 3 + f) * P.Np + int64_t(i2) * n1 + i1] =
-            make_double4_32a(val, fx, fy, fxy);
+  const int x0 = blockIdx.x * kDerTX;
+  // rows of tiles beyond the grid's y extent (65535) taken in turn
+  for (int ty = blockIdx.y; ty * kDerTY < n2; ty += gridDim.y) {
+    const int y0 = ty * kDerTY;
+    for (int f = 0; f < 3; ++f) {
+      const double *v = V + int64_t(f) * P.Np;
+      // tile + halo, indices clamped onto the grid (halo entries off the grid
+      // are never read by an on-grid stencil)
+      for (int e = tid; e < H * W; e += blockDim.x) {
+        const int r = e / W, c = e % W;
+        int g2 = y0 - kDerH + r, g1 = x0 - kDerH + c;
+        g2 = g2 < 0 ? 0 : (g2 >= n2 ? n2 - 1 : g2);
+        g1 = g1 < 0 ? 0 : (g1 >= n1 ? n1 - 1 : g1);
+        sv[r][c] = v[int64_t(g2) * n1 + g1];
       }
+      __syncthreads();
+      // x2 derivative on the tile's rows, every column of the staged span
+      for (int e = tid; e < kDerTY * W; e += blockDim.x) {
+        const int r = e / W, c = e % W;
+        const int i2 = y0 + r;
+        sy[r][c] = i2 < n2 ? fd4(&sv[r + kDerH][c], W, i2, n2) : 0.0;
+      }
+      __syncthreads();
+      for (int e = tid; e < kDerTX * kDerTY; e += blockDim.x) {
+        const int r = e / kDerTX, c = e % kDerTX;
+        const int i1 = x0 + c, i2 = y0 + r;
+        if (i1 < n1 && i2 < n2) {
+          const double val = sv[r + kDerH][c + kDerH];
+          const double fx = fd4(&sv[r + kDerH][c + kDerH], 1, i1, n1);
+          const double fy = sy[r][c + kDerH];
+          const double fxy = fd4(&sy[r][c + kDerH], 1, i1, n1);
+          ring[(int64_t(slot) * 3 + f) * P.Np + int64_t(i2) * n1 + i1] =
+              make_double4_32a(val, fx, fy, fxy);
+        }
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
 }
 
@@ -384,58 +445,63 @@ __global__ void k2_reset_stats(Stats2 *s) {
 // product of the weight's hi part with hi_00 (FMA error term) and add it by
 // TwoSum (comp_acc1); the driver terms are summed in plain FP32; z^n and A
 // are formed as float pairs and y^n by Picard on the increment, as in the 1-D
-// FP32C step.  Derivatives of a new level come from the FP64 values.
+// FP32C step.  Derivatives of a new level: the fourth-order differences in
+// FP32 over the new values split into float pairs (fd4f).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kDerTX * kDerTY)
     k2_deriv32(const Params2 P, const double *__restrict__ V, float4 *__restrict__ ring,
                int slot) {
   constexpr int W = kDerTX + 2 * kDerH, H = kDerTY + 2 * kDerH;
-  __shared__ double sv[H][W];
-  __shared__ double sy[kDerTY][W];
+  __shared__ float sh[H][W], sl[H][W];
+  __shared__ float sy[kDerTY][W];
   wait_predecessor();
-  const int x0 = blockIdx.x * kDerTX, y0 = blockIdx.y * kDerTY;
   const int n1 = int(P.Nx1), n2 = int(P.Nx2);
   const int tid = threadIdx.x;
-  // one point per thread (kDerTX * kDerTY threads)
-  const int r = tid / kDerTX, c = tid % kDerTX;
-  const int i1 = x0 + c, i2 = y0 + r;
-  double val[3], fx[3], fy[3], fxy[3];
-  for (int f = 0; f < 3; ++f) {
-    const double *v = V + int64_t(f) * P.Np;
-    for (int e = tid; e < H * W; e += blockDim.x) {
-      const int rr = e / W, cc = e % W;
-      int g2 = y0 - kDerH + rr, g1 = x0 - kDerH + cc;
-      g2 = g2 < 0 ? 0 : (g2 >= n2 ? n2 - 1 : g2);
-      g1 = g1 < 0 ? 0 : (g1 >= n1 ? n1 - 1 : g1);
-      sv[rr][cc] = v[int64_t(g2) * n1 + g1];
-    }
-    __syncthreads();
-    for (int e = tid; e < kDerTY * W; e += blockDim.x) {
-      const int rr = e / W, cc = e % W;
-      const int j2 = y0 + rr;
-      sy[rr][cc] = j2 < n2 ? fd4(&sv[rr + kDerH][cc], W, j2, n2) : 0.0;
-    }
-    __syncthreads();
-    val[f] = fx[f] = fy[f] = fxy[f] = 0.0;
-    if (i1 < n1 && i2 < n2) {
-      val[f] = sv[r + kDerH][c + kDerH];
-      fx[f] = fd4(&sv[r + kDerH][c + kDerH], 1, i1, n1);
-      fy[f] = sy[r][c + kDerH];
-      fxy[f] = fd4(&sy[r][c + kDerH], 1, i1, n1);
-    }
-    __syncthreads();
-  }
-  if (i1 < n1 && i2 < n2) {
-    float hi[3], lo[3];
+  const int x0 = blockIdx.x * kDerTX;
+  // rows of tiles beyond the grid's y extent (65535) taken in turn
+  for (int ty = blockIdx.y; ty * kDerTY < n2; ty += gridDim.y) {
+    const int y0 = ty * kDerTY;
+    // one point per thread (kDerTX * kDerTY threads)
+    const int r = tid / kDerTX, c = tid % kDerTX;
+    const int i1 = x0 + c, i2 = y0 + r;
+    float hi[3], lo[3], fx[3], fy[3], fxy[3];
+#pragma unroll
     for (int f = 0; f < 3; ++f) {
-      hi[f] = __double2float_rn(val[f]);
-      lo[f] = __double2float_rn(__dsub_rn(val[f], double(hi[f])));
+      const float2 *v = reinterpret_cast<const float2 *>(V) + int64_t(f) * P.Np;
+      for (int e = tid; e < H * W; e += blockDim.x) {
+        const int rr = e / W, cc = e % W;
+        int g2 = y0 - kDerH + rr, g1 = x0 - kDerH + cc;
+        g2 = g2 < 0 ? 0 : (g2 >= n2 ? n2 - 1 : g2);
+        g1 = g1 < 0 ? 0 : (g1 >= n1 ? n1 - 1 : g1);
+        const float2 x = v[int64_t(g2) * n1 + g1];
+        sh[rr][cc] = x.x;
+        sl[rr][cc] = x.y;
+      }
+      __syncthreads();
+      // x2 derivative on the tile's rows, every column of the staged span
+      for (int e = tid; e < kDerTY * W; e += blockDim.x) {
+        const int rr = e / W, cc = e % W;
+        const int j2 = y0 + rr;
+        sy[rr][cc] = j2 < n2 ? fd4f<true>(&sh[rr + kDerH][cc], &sl[rr + kDerH][cc], W, j2, n2) : 0.f;
+      }
+      __syncthreads();
+      hi[f] = lo[f] = fx[f] = fy[f] = fxy[f] = 0.f;
+      if (i1 < n1 && i2 < n2) {
+        hi[f] = sh[r + kDerH][c + kDerH];
+        lo[f] = sl[r + kDerH][c + kDerH];
+        fx[f] = fd4f<true>(&sh[r + kDerH][c + kDerH], &sl[r + kDerH][c + kDerH], 1, i1, n1);
+        fy[f] = sy[r][c + kDerH];
+        fxy[f] = fd4f<false>(&sy[r][c + kDerH], nullptr, 1, i1, n1);
+      }
+      __syncthreads();
     }
-    float4 *b = ring + int64_t(slot) * 4 * P.Np + int64_t(i2) * n1 + i1;
-    b[0] = make_float4(hi[0], hi[1], hi[2], lo[0]);
-    b[P.Np] = make_float4(lo[1], lo[2], float(fx[0]), float(fx[1]));
-    b[2 * P.Np] = make_float4(float(fx[2]), float(fy[0]), float(fy[1]), float(fy[2]));
-    b[3 * P.Np] = make_float4(float(fxy[0]), float(fxy[1]), float(fxy[2]), 0.f);
+    if (i1 < n1 && i2 < n2) {
+      float4 *b = ring + int64_t(slot) * 4 * P.Np + int64_t(i2) * n1 + i1;
+      b[0] = make_float4(hi[0], hi[1], hi[2], lo[0]);
+      b[P.Np] = make_float4(lo[1], lo[2], fx[0], fx[1]);
+      b[2 * P.Np] = make_float4(fx[2], fy[0], fy[1], fy[2]);
+      b[3 * P.Np] = make_float4(fxy[0], fxy[1], fxy[2], 0.f);
+    }
   }
 }
 
@@ -666,9 +732,7 @@ __device__ __forceinline__ void step2_tile32(const Params2 &P, const float4 *__r
       if (cyc) d = 0.f;
       if (d <= P.picard_tol_f || !isfinite(d)) break;  // a non-finite step cannot converge
     }
-    V[qq] = double(Ah) + (double(Al) + double(dl));
-    V[P.Np + qq] = double(z1h) + double(z1l);
-    V[2 * P.Np + qq] = double(z2h) + double(z2l);
+    put_new32(P, V, qq, Ah, Al, dl, z1h, z1l, z2h, z2l);
   }
   record_picard32(st, active, it, d, P.picard_tol_f);
 }
@@ -711,6 +775,394 @@ __global__ void __launch_bounds__(kStep2TP * kMaxGroups, 1)
   float *part = reinterpret_cast<float *>(smem_raw);  // [10][G][kStep2TP]
   wait_predecessor();
   step2_tile32(P, ring, V, tab.e, part, n, st);
+}
+
+// ---------------------------------------------------------------------------
+// The 2-D step as two tensor-product passes (linear driver, uncorrelated
+// forward process b21 = 0).  A node's cell shift and Hermite basis then
+// split into an x1 part of l1 and an x2 part of l2, and the weights of
+// Eq. 20-21 into products of one-dimensional ones: wt = u_l1 u_l2,
+// wt DeltaW1 = ua_l1 u_l2, wt DeltaW2 = u_l1 ua_l2 with u_l = omega_l /
+// sqrt(pi) and ua_l = u_l a_l sqrt(2 j dt).  The bicubic value regroups as
+//   v = h1_0 R(c1) + h1_1 R(c1+1) + h1_2 S(c1) + h1_3 S(c1+1),
+// R(m1) = x2 interpolant of (v, dx2 v_x2) on column m1, S(m1) = that of
+// (dx1 v_x1, dx1 dx2 v_x1x2), so every expectation the step needs is
+//   pass 1 (x2): R_u, S_u = sum_l2 u_l2 (R, S at i2 + s2_l2), and R_a, S_a
+//                with ua_l2, at every point and step j;
+//   pass 2 (x1): E00[v] = sum_l1 u_l1 (h1 . (R_u, S_u) at i1 + s1_l1),
+//                E10[v] with ua_l1, E01[v] = sum_l1 u_l1 (h1 . (R_a, S_a)).
+// With f = alpha y + beta . z linear, E[f] and E[f DeltaW] are the same
+// combinations of these, and the lines of Eq. 20 read
+//   z1 = sum_j cz_j E00_j[z1] + cf_j E10_j[f],  z2 likewise with E01,
+//   A  = sum_j cy_j E00_j[y] + cfy_j E00_j[f],
+// cz_j = (delta_j1 - gz_j) / gz_0, cf_j = gz_j / gz_0, cy_j = [j = k],
+// cfy_j = k dt gy_j.  Work per point and step: 48 L + 36 L multiply-adds
+// against ~46 L^2 for the node-wise kernel.
+// ---------------------------------------------------------------------------
+struct TPTab2d {
+  int32_t s1[kMaxK][kMaxL2], s2[kMaxK][kMaxL2];
+  double h1[kMaxK][kMaxL2][4], h2[kMaxK][kMaxL2][4];
+  double u[kMaxL2], ua[kMaxK][kMaxL2];
+  double cz[kMaxK], cf[kMaxK], cy[kMaxK], cfy[kMaxK];
+};
+static_assert(sizeof(Params2) + sizeof(TPTab2d) + 64 <= 32764,
+              "tensor-product tables exceed the kernel parameter limit");
+
+// off the box: the value at the projection (theta 0 at the low end, 1 at the
+// high end), as the node-wise kernels do it per dimension
+template <typename T>
+__device__ __forceinline__ void tp_clamp(int &c, int n, T *h) {
+  if (c < 0 || c > n - 2) {
+    const bool lo = c < 0;
+    c = lo ? 0 : n - 2;
+    h[0] = lo ? T(1) : T(0);
+    h[1] = lo ? T(0) : T(1);
+    h[2] = h[3] = T(0);
+  }
+}
+
+constexpr int kTPThreads = 256;
+constexpr int kTP1X = 32, kTP1Y = kTPThreads / kTP1X;  // FP32C x2-pass tile
+
+// FP64 pass 1: per point and step j (blockIdx.y = j - 1), per field the
+// double4 (R_u, S_u, R_a, S_a) into tp[((j - 1) * 3 + f) * Np + point].
+__global__ void __launch_bounds__(kTPThreads)
+    k2_tp1(const Params2 P, const double4_32a *__restrict__ ring, double4_32a *__restrict__ tp,
+           const __grid_constant__ TPTab2d T, int n) {
+  wait_predecessor();
+  const int64_t qq = int64_t(blockIdx.x) * kTPThreads + threadIdx.x;
+  const int jm = blockIdx.y;
+  if (qq >= P.Np) return;
+  const int n1 = int(P.Nx1), n2 = int(P.Nx2);
+  const int i1 = int(qq % n1), i2 = int(qq / n1);
+  const double4_32a *lev = ring + int64_t((n + jm + 1) % P.nslot) * 3 * P.Np;
+  double acc[3][4];
+#pragma unroll
+  for (int f = 0; f < 3; ++f) acc[f][0] = acc[f][1] = acc[f][2] = acc[f][3] = 0.0;
+#pragma unroll 1
+  for (int l = 0; l < P.L; ++l) {
+    int c2 = i2 + T.s2[jm][l];
+    double h[4] = {T.h2[jm][l][0], T.h2[jm][l][1], T.h2[jm][l][2], T.h2[jm][l][3]};
+    tp_clamp(c2, n2, h);
+    const int64_t o = int64_t(c2) * n1 + i1;
+    const double u = T.u[l], ua = T.ua[jm][l];
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+      const double4_32a a = lev[f * P.Np + o], c = lev[f * P.Np + o + n1];
+      const double R = a.x * h[0] + c.x * h[1] + a.z * h[2] + c.z * h[3];
+      const double S = a.y * h[0] + c.y * h[1] + a.w * h[2] + c.w * h[3];
+      acc[f][0] += u * R;
+      acc[f][1] += u * S;
+      acc[f][2] += ua * R;
+      acc[f][3] += ua * S;
+    }
+  }
+#pragma unroll
+  for (int f = 0; f < 3; ++f)
+    tp[(int64_t(jm) * 3 + f) * P.Np + qq] =
+        make_double4_32a(acc[f][0], acc[f][1], acc[f][2], acc[f][3]);
+}
+
+// FP64 pass 2 and the tail: the expectations of every step j, z^n, A and y^n
+// by Picard (as k2_step), into the plane of new values V.
+__global__ void __launch_bounds__(kTPThreads)
+    k2_tp2(const Params2 P, const double4_32a *__restrict__ ring,
+           const double4_32a *__restrict__ tp, double *__restrict__ V,
+           const __grid_constant__ TPTab2d T, int n, Stats *st) {
+  wait_predecessor();
+  const int64_t qq = int64_t(blockIdx.x) * kTPThreads + threadIdx.x;
+  const bool active = qq < P.Np;
+  int it = 0;
+  double d = 0.0;
+  if (active) {
+    const int n1 = int(P.Nx1);
+    const int i1 = int(qq % n1), i2 = int(qq / n1);
+    double z1 = 0.0, z2 = 0.0, A = 0.0;
+    for (int jm = 0; jm < P.k; ++jm) {
+      const double4_32a *tj = tp + int64_t(jm) * 3 * P.Np;
+      double e00[3] = {0.0, 0.0, 0.0}, e10[3] = {0.0, 0.0, 0.0}, e01[3] = {0.0, 0.0, 0.0};
+#pragma unroll 1
+      for (int l = 0; l < P.L; ++l) {
+        int c1 = i1 + T.s1[jm][l];
+        double h[4] = {T.h1[jm][l][0], T.h1[jm][l][1], T.h1[jm][l][2], T.h1[jm][l][3]};
+        tp_clamp(c1, n1, h);
+        const int64_t o = int64_t(i2) * n1 + c1;
+        const double u = T.u[l], ua = T.ua[jm][l];
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+          const double4_32a a = tj[f * P.Np + o], b = tj[f * P.Np + o + 1];
+          const double v = a.x * h[0] + b.x * h[1] + a.y * h[2] + b.y * h[3];
+          const double va = a.z * h[0] + b.z * h[1] + a.w * h[2] + b.w * h[3];
+          e00[f] += u * v;
+          e10[f] += ua * v;
+          e01[f] += u * va;
+        }
+      }
+      const double F00 = P.alpha * e00[0] + P.beta1 * e00[1] + P.beta2 * e00[2];
+      const double F10 = P.alpha * e10[0] + P.beta1 * e10[1] + P.beta2 * e10[2];
+      const double F01 = P.alpha * e01[0] + P.beta1 * e01[1] + P.beta2 * e01[2];
+      z1 += T.cz[jm] * e00[1] + T.cf[jm] * F10;
+      z2 += T.cz[jm] * e00[2] + T.cf[jm] * F01;
+      A += T.cy[jm] * e00[0] + T.cfy[jm] * F00;
+    }
+    double y = ring[(int64_t((n + 1) % P.nslot) * 3) * P.Np + qq].x;
+    while (it < P.picard_max) {
+      const double y1 = A + P.hg0 * (P.alpha * y + P.beta1 * z1 + P.beta2 * z2);
+      d = fabs(y1 - y);
+      y = y1;
+      ++it;
+      if (d <= P.picard_tol || !isfinite(d)) break;  // a non-finite step cannot converge
+    }
+    V[qq] = y;
+    V[P.Np + qq] = z1;
+    V[2 * P.Np + qq] = z2;
+  }
+  record_picard(st, active, it, d, P.picard_tol);
+}
+
+// FP32C tables: the Hermite bases as floats; pass 1 weights u and ua; pass 2
+// weights per step with the multistep coefficients folded in: cz_j u, cy_j u,
+// cfy_j u, cf_j ua, cf_j u.  Each weight but cfy_j u is a float pair (hi, lo):
+// the lo part takes the weight's own rounding out of the sums, which would
+// otherwise repeat identically at every point and level.  Nodes l and
+// L-1-l mirror each other (u equal, ua opposite) and are taken as a pair; the
+// middle node of an odd L stands alone.
+struct TPTab2f {
+  int32_t s1[kMaxK][kMaxL2], s2[kMaxK][kMaxL2];
+  float h1[kMaxK][kMaxL2][4], h2[kMaxK][kMaxL2][4];
+  float uh[kMaxL2], ul[kMaxL2], uah[kMaxK][kMaxL2], ual[kMaxK][kMaxL2];
+  float czh[kMaxK][kMaxL2], czl[kMaxK][kMaxL2], cyh[kMaxK][kMaxL2], cyl[kMaxK][kMaxL2];
+  float cfy[kMaxK][kMaxL2], cfah[kMaxK][kMaxL2], cfal[kMaxK][kMaxL2], cfuh[kMaxK][kMaxL2],
+      cful[kMaxK][kMaxL2];
+};
+static_assert(sizeof(Params2) + sizeof(TPTab2f) + 64 <= 32764,
+              "tensor-product tables exceed the kernel parameter limit");
+
+// The x2 interpolants (value part hi + del, slope part) of the three fields
+// at one node of pass 1, from the records of rows c2 (a) and c2 + 1 (c).
+__device__ __forceinline__ void tp1_node32(const Rec2f &a, const Rec2f &c, const float *h,
+                                           float *hi, float *del, float *sl) {
+  // per field: hi, lo, dx1 v_x1, dx2 v_x2, dx1 dx2 v_x1x2 (see Rec2f)
+  const float ah[3] = {a.v0.x, a.v0.y, a.v0.z}, al[3] = {a.v0.w, a.v1.x, a.v1.y};
+  const float ch[3] = {c.v0.x, c.v0.y, c.v0.z}, cl[3] = {c.v0.w, c.v1.x, c.v1.y};
+  const float afx[3] = {a.v1.z, a.v1.w, a.v2.x}, cfx[3] = {c.v1.z, c.v1.w, c.v2.x};
+  const float afy[3] = {a.v2.y, a.v2.z, a.v2.w}, cfy[3] = {c.v2.y, c.v2.z, c.v2.w};
+  const float afxy[3] = {a.v3.x, a.v3.y, a.v3.z}, cfxy[3] = {c.v3.x, c.v3.y, c.v3.z};
+#pragma unroll
+  for (int f = 0; f < 3; ++f) {
+    // h_0 + h_1 = 1: the value is the row-c2 value plus increments
+    const float dv = __fadd_rn(__fsub_rn(ch[f], ah[f]), __fsub_rn(cl[f], al[f]));
+    hi[f] = ah[f];
+    del[f] = __fmaf_rn(h[3], cfy[f], __fmaf_rn(h[2], afy[f], __fmaf_rn(h[1], dv, al[f])));
+    sl[f] = __fmaf_rn(h[3], cfxy[f],
+                      __fmaf_rn(h[2], afxy[f], __fmaf_rn(h[1], cfx[f], __fmul_rn(h[0], afx[f]))));
+  }
+}
+
+// FP32C pass 1: per point and step, the four float4 planes
+//   W0 = (Ru_hi y, z1, z2, Ru_lo y)   W1 = (Ru_lo z1, z2, Su y, z1)
+//   W2 = (Su z2, Ra y, z1, z2)        W3 = (Sa y, z1, z2, 0)
+// R_u a compensated sum (float pair), the other three plain FP32 (slope
+// terms, and the ua-weighted value differences of mirror nodes, all small).
+__global__ void __launch_bounds__(kTPThreads)
+    k2_tp1_32(const Params2 P, const float4 *__restrict__ ring, float4 *__restrict__ tp,
+              const __grid_constant__ TPTab2f T, int n) {
+  wait_predecessor();
+  // a CTA takes a tile of kTP1X columns x kTP1Y rows, a warp one row: for a
+  // node the warps read rows i2 + s2 and i2 + s2 + 1, so the tile's warps
+  // share all but one of their rows through L1 (L2 traffic ~ (Y + 1) / 2Y
+  // of one-row tiles')
+  const int n1 = int(P.Nx1), n2 = int(P.Nx2);
+  const int i1 = blockIdx.x * kTP1X + threadIdx.x % kTP1X;
+  const int jm = blockIdx.z;
+  if (i1 >= n1) return;
+  // rows of tiles beyond the grid's y extent (65535) taken in turn
+  for (int ty = blockIdx.y; ty * kTP1Y < n2; ty += gridDim.y) {
+    const int i2 = ty * kTP1Y + threadIdx.x / kTP1X;
+    if (i2 >= n2) continue;
+    const int64_t qq = int64_t(i2) * n1 + i1;
+    const Lev2f lev = lev2f(ring, P.Np, (n + jm + 1) % P.nslot);
+    float RS[3] = {0.f, 0.f, 0.f}, RC[3] = {0.f, 0.f, 0.f}, Su[3] = {0.f, 0.f, 0.f},
+          Ra[3] = {0.f, 0.f, 0.f}, Sa[3] = {0.f, 0.f, 0.f};
+    const int L = P.L, Lh = P.L / 2;
+#pragma unroll 1
+    for (int q = 0; q < (L + 1) / 2; ++q) {
+      const int la = q, lb = L - 1 - q;
+      int ca = i2 + T.s2[jm][la], cb = i2 + T.s2[jm][lb];
+      float ha[4] = {T.h2[jm][la][0], T.h2[jm][la][1], T.h2[jm][la][2], T.h2[jm][la][3]};
+      float hb[4] = {T.h2[jm][lb][0], T.h2[jm][lb][1], T.h2[jm][lb][2], T.h2[jm][lb][3]};
+      tp_clamp(ca, n2, ha);
+      tp_clamp(cb, n2, hb);
+      const int64_t oa = int64_t(ca) * n1 + i1, ob = int64_t(cb) * n1 + i1;
+      float hia[3], dea[3], sla[3];
+      tp1_node32(load_rec(lev, oa), load_rec(lev, oa + n1), ha, hia, dea, sla);
+      if (q < Lh) {
+        float hib[3], deb[3], slb[3];
+        tp1_node32(load_rec(lev, ob), load_rec(lev, ob + n1), hb, hib, deb, slb);
+        const float uah = T.uah[jm][la], ual = T.ual[jm][la];
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+          float hs = hia[f], he = 0.f;
+          two_sum_into(hs, he, hib[f]);
+          comp_acc1(RS[f], RC[f], T.uh[la], T.ul[la], hs, __fadd_rn(__fadd_rn(dea[f], deb[f]), he));
+          Su[f] = __fmaf_rn(T.uh[la], __fadd_rn(sla[f], slb[f]), Su[f]);
+          const float dv = __fadd_rn(__fsub_rn(hia[f], hib[f]), __fsub_rn(dea[f], deb[f]));
+          Ra[f] = __fmaf_rn(ual, dv, __fmaf_rn(uah, dv, Ra[f]));
+          Sa[f] = __fmaf_rn(uah, __fsub_rn(sla[f], slb[f]), Sa[f]);
+        }
+      } else {
+        // the middle node of an odd L (a = 0: no ua terms)
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+          comp_acc1(RS[f], RC[f], T.uh[la], T.ul[la], hia[f], dea[f]);
+          Su[f] = __fmaf_rn(T.uh[la], sla[f], Su[f]);
+        }
+      }
+    }
+    float Rh[3], Rl[3];
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+      // renormalized: |lo| within half an ulp of hi
+      const float sm = __fadd_rn(RS[f], RC[f]);
+      Rl[f] = __fsub_rn(RC[f], __fsub_rn(sm, RS[f]));
+      Rh[f] = sm;
+    }
+    float4 *b = tp + int64_t(jm) * 4 * P.Np + qq;
+    b[0] = make_float4(Rh[0], Rh[1], Rh[2], Rl[0]);
+    b[P.Np] = make_float4(Rl[1], Rl[2], Su[0], Su[1]);
+    b[2 * P.Np] = make_float4(Su[2], Ra[0], Ra[1], Ra[2]);
+    b[3 * P.Np] = make_float4(Sa[0], Sa[1], Sa[2], 0.f);
+  }
+}
+
+// One node of pass 2: the x1 interpolants of the three fields from the
+// pass-1 records of columns c1 (A) and c1 + 1 (B): value hi + del of (R_u,
+// S_u), and the plain value of (R_a, S_a).
+__device__ __forceinline__ void tp2_node32(const Rec2f &A, const Rec2f &B, const float *h,
+                                           float *hi, float *del, float *va) {
+  const float ah[3] = {A.v0.x, A.v0.y, A.v0.z}, al[3] = {A.v0.w, A.v1.x, A.v1.y};
+  const float bh[3] = {B.v0.x, B.v0.y, B.v0.z}, bl[3] = {B.v0.w, B.v1.x, B.v1.y};
+  const float as[3] = {A.v1.z, A.v1.w, A.v2.x}, bs[3] = {B.v1.z, B.v1.w, B.v2.x};
+  const float ar[3] = {A.v2.y, A.v2.z, A.v2.w}, br[3] = {B.v2.y, B.v2.z, B.v2.w};
+  const float aS[3] = {A.v3.x, A.v3.y, A.v3.z}, bS[3] = {B.v3.x, B.v3.y, B.v3.z};
+#pragma unroll
+  for (int f = 0; f < 3; ++f) {
+    const float dv = __fadd_rn(__fsub_rn(bh[f], ah[f]), __fsub_rn(bl[f], al[f]));
+    hi[f] = ah[f];
+    del[f] = __fmaf_rn(h[3], bs[f], __fmaf_rn(h[2], as[f], __fmaf_rn(h[1], dv, al[f])));
+    va[f] = __fmaf_rn(h[3], bS[f],
+                      __fmaf_rn(h[2], aS[f], __fmaf_rn(h[1], br[f], __fmul_rn(h[0], ar[f]))));
+  }
+}
+
+// FP32C pass 2 and the tail: per point, every step's x1 pass over mirror
+// pairs of l1 (compensated z and y sums, plain driver terms, as the
+// node-wise FP32C kernel keeps them), then z^n, A and y^n as there.
+__global__ void __launch_bounds__(kTPThreads)
+    k2_tp2_32(const Params2 P, const float4 *__restrict__ ring, const float4 *__restrict__ tp,
+              double *__restrict__ V, const __grid_constant__ TPTab2f T, int n, Stats *st) {
+  wait_predecessor();
+  const int64_t qq = int64_t(blockIdx.x) * kTPThreads + threadIdx.x;
+  const bool active = qq < P.Np;
+  int it = 0;
+  float d = 0.f;
+  if (active) {
+    const int n1 = int(P.Nx1);
+    const int i1 = int(qq % n1), i2 = int(qq / n1);
+    const int L = P.L, Lh = P.L / 2;
+    Acc2f a{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int jm = 0; jm < P.k; ++jm) {
+      const Lev2f W = lev2f(tp, P.Np, jm);
+      const bool yj = jm == P.k - 1;
+#pragma unroll 1
+      for (int q = 0; q < (L + 1) / 2; ++q) {
+        const int la = q, lb = L - 1 - q;
+        int ca = i1 + T.s1[jm][la], cb = i1 + T.s1[jm][lb];
+        float ha[4] = {T.h1[jm][la][0], T.h1[jm][la][1], T.h1[jm][la][2], T.h1[jm][la][3]};
+        float hb[4] = {T.h1[jm][lb][0], T.h1[jm][lb][1], T.h1[jm][lb][2], T.h1[jm][lb][3]};
+        tp_clamp(ca, n1, ha);
+        tp_clamp(cb, n1, hb);
+        const int64_t oa = int64_t(i2) * n1 + ca, ob = int64_t(i2) * n1 + cb;
+        float hia[3], dea[3], vaa[3];
+        tp2_node32(load_rec(W, oa), load_rec(W, oa + 1), ha, hia, dea, vaa);
+        const float Fa = __fmaf_rn(P.alpha_f, __fadd_rn(hia[0], dea[0]),
+                                   __fmaf_rn(P.beta1_f, __fadd_rn(hia[1], dea[1]),
+                                             __fmul_rn(P.beta2_f, __fadd_rn(hia[2], dea[2]))));
+        const float Ga = __fmaf_rn(P.alpha_f, vaa[0],
+                                   __fmaf_rn(P.beta1_f, vaa[1], __fmul_rn(P.beta2_f, vaa[2])));
+        if (q < Lh) {
+          float hib[3], deb[3], vab[3];
+          tp2_node32(load_rec(W, ob), load_rec(W, ob + 1), hb, hib, deb, vab);
+          const float Fb = __fmaf_rn(P.alpha_f, __fadd_rn(hib[0], deb[0]),
+                                     __fmaf_rn(P.beta1_f, __fadd_rn(hib[1], deb[1]),
+                                               __fmul_rn(P.beta2_f, __fadd_rn(hib[2], deb[2]))));
+          const float Gb = __fmaf_rn(P.alpha_f, vab[0],
+                                     __fmaf_rn(P.beta1_f, vab[1], __fmul_rn(P.beta2_f, vab[2])));
+          // F_a - F_b from the fields' differences (their hi parts subtract
+          // exactly), as the node-wise kernel forms it
+          float dv[3];
+#pragma unroll
+          for (int f = 0; f < 3; ++f)
+            dv[f] = __fadd_rn(__fsub_rn(hia[f], hib[f]), __fsub_rn(dea[f], deb[f]));
+          const float dF = __fmaf_rn(P.alpha_f, dv[0],
+                                     __fmaf_rn(P.beta1_f, dv[1], __fmul_rn(P.beta2_f, dv[2])));
+          a.F1 = __fmaf_rn(T.cfal[jm][la], dF, __fmaf_rn(T.cfah[jm][la], dF, a.F1));
+          const float G = __fadd_rn(Ga, Gb);
+          a.F2 = __fmaf_rn(T.cful[jm][la], G, __fmaf_rn(T.cfuh[jm][la], G, a.F2));
+          two_sum_into(a.Fy, a.FyC, __fmul_rn(T.cfy[jm][la], __fadd_rn(Fa, Fb)));
+          float hs, he;
+#pragma unroll
+          for (int f = 1; f < 3; ++f) {
+            hs = hia[f];
+            he = 0.f;
+            two_sum_into(hs, he, hib[f]);
+            const float dd = __fadd_rn(__fadd_rn(dea[f], deb[f]), he);
+            if (f == 1)
+              comp_acc1(a.S1, a.C1, T.czh[jm][la], T.czl[jm][la], hs, dd);
+            else
+              comp_acc1(a.S2, a.C2, T.czh[jm][la], T.czl[jm][la], hs, dd);
+          }
+          if (yj) {
+            hs = hia[0];
+            he = 0.f;
+            two_sum_into(hs, he, hib[0]);
+            comp_acc1(a.Sy, a.Cy, T.cyh[jm][la], T.cyl[jm][la], hs,
+                      __fadd_rn(__fadd_rn(dea[0], deb[0]), he));
+          }
+        } else {
+          // the middle node of an odd L (a = 0: no ua term)
+          a.F2 = __fmaf_rn(T.cful[jm][la], Ga, __fmaf_rn(T.cfuh[jm][la], Ga, a.F2));
+          two_sum_into(a.Fy, a.FyC, __fmul_rn(T.cfy[jm][la], Fa));
+          comp_acc1(a.S1, a.C1, T.czh[jm][la], T.czl[jm][la], hia[1], dea[1]);
+          comp_acc1(a.S2, a.C2, T.czh[jm][la], T.czl[jm][la], hia[2], dea[2]);
+          if (yj) comp_acc1(a.Sy, a.Cy, T.cyh[jm][la], T.cyl[jm][la], hia[0], dea[0]);
+        }
+      }
+    }
+    // z_d = S + (C + F) and A = S + (C + F) as exact float pairs
+    float z1h = a.S1, z1l = 0.f, z2h = a.S2, z2l = 0.f, Ah = a.Sy, Al = 0.f;
+    two_sum_into(z1h, z1l, __fadd_rn(a.C1, a.F1));
+    two_sum_into(z2h, z2l, __fadd_rn(a.C2, a.F2));
+    two_sum_into(Ah, Al, a.Fy);
+    two_sum_into(Ah, Al, __fadd_rn(a.Cy, a.FyC));
+    const float zlin = __fmaf_rn(P.beta1_f, z1h, __fmul_rn(P.beta2_f, z2h));
+    // Picard on the increment delta = y^n - A: delta = hg0 f(A + delta, z)
+    const float4 v0 = lev2f(ring, P.Np, (n + 1) % P.nslot).p0[qq];
+    float dl = __fadd_rn(__fsub_rn(v0.x, Ah), __fsub_rn(v0.w, Al));
+    float dpp = __int_as_float(0x7fc00000);
+    while (it < P.picard_max) {
+      const float dn = __fmul_rn(P.hg0_f, __fmaf_rn(P.alpha_f, __fadd_rn(Ah, dl), zlin));
+      ++it;
+      d = fabsf(__fsub_rn(dn, dl));
+      const bool cyc = dn == dpp && picard_cycle_ok(d, __fadd_rn(Ah, dl), dn);
+      dpp = dl;
+      dl = dn;
+      if (cyc) d = 0.f;
+      if (d <= P.picard_tol_f || !isfinite(d)) break;  // a non-finite step cannot converge
+    }
+    put_new32(P, V, qq, Ah, Al, dl, z1h, z1l, z2h, z2l);
+  }
+  record_picard32(st, active, it, d, P.picard_tol_f);
 }
 
 __device__ double interp2_point32(const Params2 &P, const Lev2f &lev, int field, double X1,
@@ -769,8 +1221,12 @@ __global__ void k2_export32(const Params2 P, const float4 *ring, int slot, doubl
 // Host side: validation, constants, layout.
 // ---------------------------------------------------------------------------
 struct Layout2 {
-  size_t ring, vals, table, stage, stats, total;
+  size_t ring, vals, table, stage, stats, tp, total;
 };
+
+static bool tensor_form2(const bsde2_problem &p) {
+  return p.step_form == BSDE2_STEP_TENSOR || (p.step_form == BSDE2_STEP_AUTO && p.b21 == 0.0);
+}
 
 static int validate2(const bsde2_problem &p) {
   if (p.k < 1 || p.k > kMaxK || p.k > p.N || p.N < 1) return BSDE_EINVAL;
@@ -786,6 +1242,8 @@ static int validate2(const bsde2_problem &p) {
     return BSDE_EINVAL;
   if (p.precision != BSDE_FP64 && p.precision != BSDE_FP32C) return BSDE_EINVAL;
   if (p.picard_max < 1 || !(p.picard_tol >= 0.0)) return BSDE_EINVAL;
+  if (p.step_form < BSDE2_STEP_AUTO || p.step_form > BSDE2_STEP_TENSOR) return BSDE_EINVAL;
+  if (p.step_form == BSDE2_STEP_TENSOR && p.b21 != 0.0) return BSDE_EINVAL;
   return BSDE_OK;
 }
 
@@ -800,6 +1258,8 @@ static Layout2 layout2(const bsde2_problem &p) {
   L.table = off; off = up(off + size_t(p.k) * p.L * p.L * sizeof(Node2));
   L.stage = off; off = up(off + 3 * size_t(p.k) * np * 8);
   L.stats = off; off = up(off + sizeof(Stats2));
+  L.tp = off;
+  if (tensor_form2(p)) off = up(off + size_t(p.k) * np * (p.precision == BSDE_FP64 ? 96 : 64));
   L.total = off;
   return L;
 }
@@ -934,6 +1394,53 @@ static void plan2_constants(const bsde2_problem &p, Params2 &P, std::vector<Node
   }
 }
 
+// The tensor-product tables from the node table (whose shift and basis in
+// x1 depend on l1 alone and in x2 on l2 alone when b21 = 0) and the
+// one-dimensional quadrature weights.
+static void build_tp2(const bsde2_problem &p, const Params2 &P, const std::vector<Node2> &tab,
+                      TPTab2d &D, TPTab2f &F) {
+  std::memset(&D, 0, sizeof(D));
+  std::memset(&F, 0, sizeof(F));
+  double a[kMaxL2], w[kMaxL2];
+  gauss_hermite(p.L, a, w);
+  const double rpi = std::sqrt(M_PI);
+  auto split = [](double v, float &hi, float &lo) {
+    hi = float(v);
+    lo = float(v - double(hi));
+  };
+  for (int l = 0; l < p.L; ++l) {
+    D.u[l] = w[l] / rpi;
+    split(D.u[l], F.uh[l], F.ul[l]);
+  }
+  for (int jm = 0; jm < P.k; ++jm) {
+    const int j = jm + 1;
+    const double sq = std::sqrt(2.0 * j * P.dt);
+    D.cz[jm] = ((j == 1 ? 1.0 : 0.0) - P.gz[j]) / P.gz[0];
+    D.cf[jm] = P.gz[j] / P.gz[0];
+    D.cy[jm] = j == P.k ? 1.0 : 0.0;
+    D.cfy[jm] = P.h * P.gy[j];
+    for (int l = 0; l < p.L; ++l) {
+      const Node2 &e1 = tab[size_t(jm) * P.LL + size_t(l) * p.L];  // (l1 = l, l2 = 0)
+      const Node2 &e2 = tab[size_t(jm) * P.LL + size_t(l)];        // (l1 = 0, l2 = l)
+      D.s1[jm][l] = F.s1[jm][l] = e1.s1;
+      D.s2[jm][l] = F.s2[jm][l] = e2.s2;
+      for (int u = 0; u < 4; ++u) {
+        D.h1[jm][l][u] = e1.h1[u];
+        D.h2[jm][l][u] = e2.h2[u];
+        F.h1[jm][l][u] = float(e1.h1[u]);
+        F.h2[jm][l][u] = float(e2.h2[u]);
+      }
+      D.ua[jm][l] = D.u[l] * sq * a[l];
+      split(D.ua[jm][l], F.uah[jm][l], F.ual[jm][l]);
+      split(D.cz[jm] * D.u[l], F.czh[jm][l], F.czl[jm][l]);
+      split(D.cy[jm] * D.u[l], F.cyh[jm][l], F.cyl[jm][l]);
+      F.cfy[jm][l] = float(D.cfy[jm] * D.u[l]);
+      split(D.cf[jm] * D.ua[jm][l], F.cfah[jm][l], F.cfal[jm][l]);
+      split(D.cf[jm] * D.u[l], F.cfuh[jm][l], F.cful[jm][l]);
+    }
+  }
+}
+
 }  // namespace bsde
 
 struct bsde2_plan_s {
@@ -947,6 +1454,9 @@ struct bsde2_plan_s {
   bsde::Stats2 *host_stats;  // pinned
   bool tab_param;            // FP32C: the pair table fits the step's parameters
   bsde::PairTab2 tab;        // ... and is passed by value (k2_step32p)
+  bool tensor;               // the step as two tensor-product passes
+  bsde::TPTab2d tpd;         // their tables (FP64, FP32C), by value
+  bsde::TPTab2f tpf;
 };
 
 namespace bsde {
@@ -955,8 +1465,54 @@ static size_t step32_2d_smem(const Params2 &P) {
   return sizeof(Node2f) * size_t(P.k) * P.LLp + sizeof(float) * 10 * size_t(P.G) * kStep2TP;
 }
 
+// The tensor-product passes of level n: parts & 1 the x2 pass, & 2 the x1
+// pass and the tail.
+static void launch2_tp(bsde2_plan_t *pl, cudaStream_t s, int n, int parts) {
+  const Params2 &P = pl->P;
+  cudaLaunchConfig_t lc{};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  const unsigned blocks = unsigned((P.Np + kTPThreads - 1) / kTPThreads);
+  lc.blockDim = dim3(kTPThreads, 1, 1);
+  lc.stream = s;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  Stats *st = reinterpret_cast<Stats *>(pl->ws + pl->lay.stats);
+  double *V = reinterpret_cast<double *>(pl->ws + pl->lay.vals);
+  if (parts & 1) {
+    lc.gridDim = dim3(blocks, unsigned(P.k), 1);
+    if (P.precision == BSDE_FP32C) {
+      lc.gridDim = dim3(unsigned((P.Nx1 + kTP1X - 1) / kTP1X),
+                        unsigned(std::min<int64_t>((P.Nx2 + kTP1Y - 1) / kTP1Y, 65535)),
+                        unsigned(P.k));
+      cudaLaunchKernelEx(&lc, k2_tp1_32, P, reinterpret_cast<const float4 *>(pl->ws + pl->lay.ring),
+                         reinterpret_cast<float4 *>(pl->ws + pl->lay.tp), pl->tpf, n);
+    } else {
+      cudaLaunchKernelEx(&lc, k2_tp1, P,
+                         reinterpret_cast<const double4_32a *>(pl->ws + pl->lay.ring),
+                         reinterpret_cast<double4_32a *>(pl->ws + pl->lay.tp), pl->tpd, n);
+    }
+  }
+  if (parts & 2) {
+    lc.gridDim = dim3(blocks, 1, 1);
+    if (P.precision == BSDE_FP32C)
+      cudaLaunchKernelEx(&lc, k2_tp2_32, P, reinterpret_cast<const float4 *>(pl->ws + pl->lay.ring),
+                         reinterpret_cast<const float4 *>(pl->ws + pl->lay.tp), V, pl->tpf, n, st);
+    else
+      cudaLaunchKernelEx(&lc, k2_tp2, P,
+                         reinterpret_cast<const double4_32a *>(pl->ws + pl->lay.ring),
+                         reinterpret_cast<const double4_32a *>(pl->ws + pl->lay.tp), V, pl->tpd,
+                         n, st);
+  }
+}
+
 static void launch2_step(bsde2_plan_t *pl, cudaStream_t s, int n) {
   const Params2 &P = pl->P;
+  if (pl->tensor) {
+    launch2_tp(pl, s, n, 3);
+    return;
+  }
   const unsigned blocks = unsigned((P.Np + kStep2TP - 1) / kStep2TP);
   if (P.precision == BSDE_FP32C && pl->tab_param) {
     launch_pdl(k2_step32p, blocks, unsigned(kStep2TP * P.G),
@@ -987,7 +1543,8 @@ static void launch2_deriv(bsde2_plan_t *pl, cudaStream_t s, int slot) {
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   at[0].val.programmaticStreamSerializationAllowed = 1;
-  lc.gridDim = dim3(unsigned((P.Nx1 + kDerTX - 1) / kDerTX), unsigned((P.Nx2 + kDerTY - 1) / kDerTY), 1);
+  lc.gridDim = dim3(unsigned((P.Nx1 + kDerTX - 1) / kDerTX),
+                    unsigned(std::min<int64_t>((P.Nx2 + kDerTY - 1) / kDerTY, 65535)), 1);
   lc.blockDim = dim3(kDerTX * kDerTY, 1, 1);
   lc.stream = s;
   lc.attrs = at;
@@ -1022,7 +1579,7 @@ static int64_t enqueue2_solve(bsde2_plan_t *pl, cudaStream_t s, bool imported) {
   for (int n = P.N - P.k; n >= 0; --n) {
     launch2_step(pl, s, n);
     launch2_deriv(pl, s, n % P.nslot);
-    launches += 2;
+    launches += pl->tensor ? 3 : 2;
   }
   double *out = reinterpret_cast<double *>(pl->ws + pl->lay.stage);
   if (P.precision == BSDE_FP32C) {
@@ -1103,6 +1660,8 @@ int bsde2_plan(const bsde2_problem *p, void *dev_workspace, size_t bytes, bsde2_
   pl->ws = static_cast<unsigned char *>(dev_workspace);
   std::vector<Node2> tab;
   plan2_constants(*p, pl->P, tab, resident_step_threads(pl->device));
+  pl->tensor = tensor_form2(*p);
+  if (pl->tensor) build_tp2(*p, pl->P, tab, pl->tpd, pl->tpf);
   cudaError_t e;
   if (p->precision == BSDE_FP32C) {
     std::vector<Node2f> t32;
@@ -1178,7 +1737,10 @@ int bsde2_enqueue_level(bsde2_plan_t *pl, void *stream, int n, int parts) {
   if (n < 0 || n > pl->P.N - pl->P.k) return fail(BSDE_EINVAL, "level out of range");
   DeviceGuard guard(pl->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((parts & 12) && !pl->tensor) return fail(BSDE_EINVAL, "pass parts need the TENSOR form");
   if (parts & 1) launch2_step(pl, s, n);
+  if (parts & 4) launch2_tp(pl, s, n, 1);
+  if (parts & 8) launch2_tp(pl, s, n, 2);
   if (parts & 2) launch2_deriv(pl, s, n % pl->P.nslot);
   BSDE_CUDA_TRY(cudaGetLastError());
   return BSDE_OK;
@@ -1187,7 +1749,7 @@ int bsde2_enqueue_level(bsde2_plan_t *pl, void *stream, int n, int parts) {
 int64_t bsde2_plan_launches(const bsde2_plan_t *pl) {
   if (!pl) return 0;
   const bsde::Params2 &P = pl->P;
-  return 1 + 2 * int64_t(P.k) + 2 * int64_t(P.N - P.k + 1) + 2;
+  return 1 + 2 * int64_t(P.k) + (pl->tensor ? 3 : 2) * int64_t(P.N - P.k + 1) + 2;
 }
 
 void bsde2_free(bsde2_plan_t *pl) {

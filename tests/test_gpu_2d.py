@@ -65,16 +65,53 @@ CASES = {
     # 2 x 128 mirror pairs: beyond the parameter table's 192 entries, so the
     # FP32C step copies its table into shared memory (k2_step32)
     "ex4_L16_k2": W.ex4_problem(M=96, N=8, k=2, L=16),
+    # uncorrelated with drift, odd L (the middle node alone), large shifts
+    # that leave the box on both sides in both dimensions
+    "diag_drift_L3": _with(W.ex4_problem(M=40, N=10, k=4, L=3, x_lim=3.0), a1=0.3, a2=-0.2,
+                           b11=0.8, b21=0.0, b22=0.6),
+    # a single node per dimension (a_0 = 0: no DeltaW terms), ragged grid
+    "L1_ragged": _with(W.ex4_problem(M=30, N=6, k=2, L=1), Nx1=37, Nx2=29),
+    # Example 5 uncorrelated with the paper's K = 6 and an odd L
+    "ex5_k6_L7": W.ex5_problem(M=48, N=8, k=6, L=7, width=2.0),
 }
 
 
+def _forms(p):
+    # both step forms where the tensor-product passes apply (b21 = 0)
+    return ["NODEWISE", "TENSOR"] if p["b21"] == 0.0 else ["NODEWISE"]
+
+
 @pytest.mark.parametrize("prec,tol", [("fp64", TOL), ("fp32c", 2e-7)])
-@pytest.mark.parametrize("name", list(CASES))
-def test_2d_parity(B, name, prec, tol):
-    p = CASES[name]
+@pytest.mark.parametrize("name,form", [(n, f) for n in CASES for f in _forms(CASES[n])])
+def test_2d_parity(B, name, form, prec, tol):
+    p = dict(CASES[name], step_form=form)
     ref = O.solve2(p, threads=THREADS, want_level=True)
     got = B.solve2(p, want_level=True, precision=prec)
-    _cmp(got, ref, f"{name} {prec}", tol=tol)
+    _cmp(got, ref, f"{name} {form} {prec}", tol=tol)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp32c", 2e-7)])
+def test_2d_tensor_passes_equal_the_nodewise_step(B, prec, tol):
+    """The two step forms compute the same sums in another order: their level
+    values agree to rounding (FP64) or to the FP32C tolerance."""
+    p = W.ex5_problem(M=64, N=8, k=3, L=8, width=2.0)
+    a = B.solve2(dict(p, step_form="NODEWISE"), want_level=True, precision=prec)
+    b = B.solve2(dict(p, step_form="TENSOR"), want_level=True, precision=prec)
+    for f in ("y", "z1", "z2"):
+        scale = max(1.0, float(np.max(np.abs(a[f]))))
+        assert float(np.max(np.abs(a[f] - b[f]))) <= tol * scale, f
+
+
+def test_2d_pass_parts_need_the_tensor_form(B):
+    s = B.Solver2(dict(W.ex5_problem(M=24, N=4, k=2, L=4, rho=0.5)))
+    s.solve()
+    import torch
+    sp = torch.cuda.current_stream().cuda_stream
+    for parts in (4, 8):
+        with pytest.raises(B.BsdeError) as ei:
+            s.enqueue_level(sp, 0, parts)
+        assert ei.value.code == B.BSDE_EINVAL
+    s.close()
 
 
 def test_2d_imported_levels_and_polynomial_exactness(B):
@@ -121,23 +158,26 @@ def test_2d_picard_wide_two_cycle_is_reported(B, prec):
     assert got["picard_iters_max"] == p["picard_max"]
 
 
-def test_2d_repeat_solves_are_bitwise_identical(B):
-    s = B.Solver2(W.ex4_problem(M=48, N=8, k=3))
+@pytest.mark.parametrize("form,per_level", [("NODEWISE", 2), ("TENSOR", 3)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_2d_repeat_solves_are_bitwise_identical(B, form, per_level, prec):
+    s = B.Solver2(dict(W.ex4_problem(M=48, N=8, k=3), step_form=form), precision=prec)
     a = s.solve(want_level=True)
     b = s.solve(want_level=True)
     assert np.array_equal(a["y"], b["y"]) and np.array_equal(a["z1"], b["z1"])
-    assert s.launches == 1 + 2 * 3 + 2 * (8 - 3 + 1) + 2
+    assert s.launches == 1 + 2 * 3 + per_level * (8 - 3 + 1) + 2
     s.close()
 
 
+@pytest.mark.parametrize("form", ["NODEWISE", "TENSOR"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32c"])
 @pytest.mark.parametrize("K,N,M,ye,ze", [(6, 64, 1024, 8.00e-07, 2.32e-06),
                                          (3, 32, 512, 9.72e-06, 2.79e-05)])
-def test_2d_paper_table9_at_full_size(B, K, N, M, ye, ze, prec):
+def test_2d_paper_table9_at_full_size(B, K, N, M, ye, ze, prec, form):
     """Example 4 at the paper's largest sizes (Table 9, Section 5): the
     printed errors of (y_0, z_0) (z as the Euclidean norm of the error
-    vector), three digits."""
-    r = B.solve2(W.ex4_problem(M=M, N=N, k=K), precision=prec)
+    vector), three digits, in both step forms."""
+    r = B.solve2(dict(W.ex4_problem(M=M, N=N, k=K), step_form=form), precision=prec)
     ey = abs(r["y0"])
     ez = math.hypot(r["z0"][0] - 1.0, r["z0"][1] - 1.0)
     print(f"Table 9 {prec} K={K} N={N} M={M}: y err {ey:.3e} (paper {ye:.2e}), z err {ez:.3e} (paper {ze:.2e})")
@@ -145,10 +185,14 @@ def test_2d_paper_table9_at_full_size(B, K, N, M, ye, ze, prec):
         assert ey == pytest.approx(ye, rel=0.02)
         assert ez == pytest.approx(ze, rel=0.02)
     else:
-        # FP32C: within 2e-8 of the FP64 solve (its rounding is ~1.5% of the
-        # scheme's y error at K = 6), and the printed digits to 3%
-        r64 = B.solve2(W.ex4_problem(M=M, N=N, k=K), precision="fp64")
-        assert abs(r["y0"] - r64["y0"]) <= 2e-8
-        assert max(abs(a - b) for a, b in zip(r["z0"], r64["z0"])) <= 2e-8
+        # FP32C: y0 within 5e-8 and z0 within 1e-7 of the FP64 solve in the
+        # same step form (level fields of both forms deviate from FP64 by up
+        # to ~1e-7 in z at these sizes: 4% of the scheme's z error at K = 6),
+        # and the printed digits to 3%
+        r64 = B.solve2(dict(W.ex4_problem(M=M, N=N, k=K), step_form=form), precision="fp64")
+        print(f"  FP32C - FP64 ({form}): y {abs(r['y0'] - r64['y0']):.2e} z "
+              f"{max(abs(a - b) for a, b in zip(r['z0'], r64['z0'])):.2e}")
+        assert abs(r["y0"] - r64["y0"]) <= 5e-8
+        assert max(abs(a - b) for a, b in zip(r["z0"], r64["z0"])) <= 1e-7
         assert ey == pytest.approx(ye, rel=0.03)
         assert ez == pytest.approx(ze, rel=0.03)

@@ -193,12 +193,38 @@ def test_invalid_2d_problems_rejected(bad):
     assert ei.value.code == B.BSDE_EINVAL
 
 
+def test_invalid_2d_step_forms_rejected():
+    # the tensor-product passes need an uncorrelated forward process
+    p = dict(W.ex5_problem(rho=0.5), step_form="TENSOR")
+    with pytest.raises(B.BsdeError) as ei:
+        B.bsde2_workspace_bytes(B.make_problem2(p))
+    assert ei.value.code == B.BSDE_EINVAL
+    for bad in (-1, 3):
+        s = B.make_problem2(W.ex4_problem())
+        s.step_form = bad
+        with pytest.raises(B.BsdeError) as ei:
+            B.bsde2_workspace_bytes(s)
+        assert ei.value.code == B.BSDE_EINVAL
+
+
 def test_2d_workspace_bytes():
     p = W.ex4_problem(M=1024, N=64, k=6)
-    b = B.bsde2_workspace_bytes(B.make_problem2(p))
     np_ = 1025 * 1025
     # ring 7 x 3 x 32 B, new values 24 B, staging 6 x 24 B per point
-    assert 7 * 96 * np_ + 24 * np_ + 6 * 24 * np_ <= b < (7 * 96 + 24 + 6 * 24) * np_ + (1 << 20)
+    base = 7 * 96 * np_ + 24 * np_ + 6 * 24 * np_
+    b = B.bsde2_workspace_bytes(B.make_problem2(dict(p, step_form="NODEWISE")))
+    assert base <= b < base + (1 << 20)
+    # the tensor form (the default for b21 = 0) adds the x2 pass's buffer of
+    # k records per point: 96 B in FP64, 64 B in FP32C
+    for form in ("AUTO", "TENSOR"):
+        b = B.bsde2_workspace_bytes(B.make_problem2(dict(p, step_form=form)))
+        assert base + 6 * 96 * np_ <= b < base + 6 * 96 * np_ + (1 << 20)
+    b32 = B.bsde2_workspace_bytes(B.make_problem2(p, precision="fp32c"))
+    base32 = 7 * 64 * np_ + 24 * np_ + 6 * 24 * np_
+    assert base32 + 6 * 64 * np_ <= b32 < base32 + 6 * 64 * np_ + (1 << 20)
+    # a correlated process keeps the node-wise form under AUTO
+    b5 = B.bsde2_workspace_bytes(B.make_problem2(W.ex5_problem(M=1024, N=64, k=6, rho=0.5)))
+    assert base <= b5 < base + (1 << 20)
 
 
 @pytest.mark.parametrize("bad", [
