@@ -75,13 +75,6 @@ def _peaks():
         return {}
 
 
-def _alu_peak_tflops(precision: str, sm_mhz: float) -> float:
-    """FP32: 152 SMs x 128 lanes x 2 flop per FMA; FP64: 152 SMs x 2 FMA units
-    x 2 (GB300 unit counts), at the given SM clock."""
-    lanes = 128 if precision == "fp32c" else 2
-    return 152 * lanes * 2 * sm_mhz * 1e6 / 1e12
-
-
 class ClockSampler:
     """nvidia-smi clock/throttle samples while the timed region runs."""
 
@@ -953,8 +946,8 @@ def run_2d(args, rank, world, local_rank):
         times[name] = e0.elapsed_time(e1) / reps
         del g
     peaks = _peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = _alu_peak_tflops(prec, sm_max)
+    pk = measured_peaks(dev)
+    peak = pk["fp64_tflops"] if prec == "fp64" else pk["fp32_tflops"]
     rec = 96 if prec == "fp64" else 64
     if tensor:
         fp = flops_per_gp_step_tp(K, L, prec)
@@ -975,9 +968,10 @@ def run_2d(args, rank, world, local_rank):
         l1b = K * L * L * (384 if prec == "fp64" else 256)
         hbm_b = K * rec + 24
     achieved = fpg * np_ / (step_ms / 1000.0) / 1e12
-    # derivative kernel: reads the new values (24 B) and writes the ring
-    # records (96 B) per point
-    der_gbs = 120.0 * np_ / (times["k2_deriv"] / 1000.0) / 1e9
+    # derivative kernel: reads the new values (24 B: doubles, or float pairs
+    # in FP32C) and writes the ring records (96 B FP64, 64 B FP32C) per point
+    der_b = 24 + rec
+    der_gbs = der_b * np_ / (times["k2_deriv"] / 1000.0) / 1e9
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     hbm_gbs = hbm_b * np_ / (step_ms / 1000.0) / 1e9
 
@@ -1047,16 +1041,18 @@ def run_2d(args, rank, world, local_rank):
                                  "frac": hbm_gbs / hbm, "bytes_per_point": hbm_b},
                          "pass_ms": ({"k2_tp1": times["x2"], "k2_tp2": times["x1"]}
                                      if tensor else None),
-                         "peak_source": (f"derived: 152 SMs x 2 FP64 FMA units x 2 flop x {sm_max:.0f} MHz"
-                                         if prec == "fp64" else
-                                         f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz"),
+                         "peak_source": "measured in this run: bsde_fma_probe, "
+                                        + ("FP64 FMA" if prec == "fp64" else
+                                           "FP32 FMA (better of scalar and packed FP32x2)")
+                                        + " (of measured)",
                          "flop_per_gp_step": fpg,
                          "l1_bytes_per_gp_step": l1b,
                          "step_launch_ms": times["k2_step"],
-                         "deriv": {"kernel": "k2_deriv", "bound": "hbm", "achieved": der_gbs,
+                         "deriv": {"kernel": "k2_deriv" if prec == "fp64" else "k2_deriv32",
+                                   "bound": "hbm", "achieved": der_gbs,
                                    "peak": hbm, "unit": "GB/s", "frac": der_gbs / hbm,
                                    "launch_ms": times["k2_deriv"],
-                                   "bytes_per_point": 120}},
+                                   "bytes_per_point": der_b}},
             "e2e": {"value": world * units * args.steps / e_dt, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": s.launches * args.steps,
@@ -1190,9 +1186,8 @@ def run_general(args, rank, world, local_rank):
         rows.append({"name": name, "y0": r.y0, "z0": r.z0, "exact_y0": u, "exact_z0": z,
                      "err_y0_vs_exact": abs(r.y0 - u), "err_z0_vs_exact": abs(r.z0 - z),
                      "step_launch_us": 1000.0 * avg, "launches": s.launches})
-    peaks = _peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = _alu_peak_tflops(prec, sm_max)
+    pk = measured_peaks(dev)
+    peak = pk["fp64_tflops"] if prec == "fp64" else pk["fp32_tflops"]
     achieved = kern_flops / (kern_ms / 1000.0) / 1e12
 
     # end to end: caller levels from pinned host memory, level 0 and the
@@ -1252,9 +1247,10 @@ def run_general(args, rank, world, local_rank):
                          "bound": "alu", "achieved": achieved,
                          "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          "traffic": None,
-                         "peak_source": (f"derived: 152 SMs x 2 FP64 FMA units x 2 flop x {sm_max:.0f} MHz"
-                                         if prec == "fp64" else
-                                         f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz"),
+                         "peak_source": "measured in this run: bsde_fma_probe, "
+                                        + ("FP64 FMA" if prec == "fp64" else
+                                           "FP32 FMA (better of scalar and packed FP32x2)")
+                                        + " (of measured)",
                          "flop_per_gp_step": {n: (flops_per_gp_step_general if prec == "fp64"
                                                   else flops_per_gp_step_general32)(W.levels_K(p), p["L"])
                                               for n, p in probs.items()}},
