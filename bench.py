@@ -50,6 +50,19 @@ def flops_per_gp_step(k: int, L: int) -> float:
     return k * L * FLOP_NODE + 2 * L + 4 * k + 12
 
 
+# The per-node count of the method's arithmetic used for the rooflines of the
+# 1-D step kernels: per node the y and z spline values (8 each), the driver
+# (4-8) and the quadrature sums (6-10), about 30, and 42 once the sums carry
+# their compensation (the FP32C kernels); per point ~3 per step j for z and
+# ~6 per Picard iteration.  The narrower count above (23 per node: the
+# Black-Scholes driver, plain sums) is reported beside it.
+FLOP_NODE_PLAIN, FLOP_NODE_COMP = 30, 42
+
+
+def flops_per_gp_step_method(k: int, L: int, compensated: bool, picard_iters: int) -> float:
+    return k * L * (FLOP_NODE_COMP if compensated else FLOP_NODE_PLAIN) + 3 * k + 6 * picard_iters
+
+
 def _env_int(name, default):
     try:
         return int(os.environ.get(name, default))
@@ -459,7 +472,10 @@ def run_ours(args, rank, world, local_rank):
     # captured in a CUDA graph, so the host's launch overhead does not starve
     # the device; the graph is replayed on the timing stream between events.
     reps = 20
+    fp64 = args.precision == "fp64"
+    iters = {r["k"]: max(1, int(r["picard_iters_max"])) for r in rows}
     kern_ms, kern_flops, kern_l2, step_us, levels_total = 0.0, 0.0, 0.0, {}, 0
+    kern_flops_min = 0.0
     for k, p, s in zip(ks, probs, solvers):
         B.bsde_enqueue_level(s.plan, sp, 0, 1)
         torch.cuda.synchronize(dev)
@@ -480,13 +496,14 @@ def run_ours(args, rank, world, local_rank):
         nlev = p["N"] - k + 1
         levels_total += nlev
         kern_ms += avg * nlev
-        kern_flops += flops_per_gp_step(k, p["L"]) * p["Nx"] * nlev
+        kern_flops += flops_per_gp_step_method(k, p["L"], not fp64, iters[k]) * p["Nx"] * nlev
+        kern_flops_min += flops_per_gp_step(k, p["L"]) * p["Nx"] * nlev
         kern_l2 += L2_BYTES_NODE * p["Nx"] * k * p["L"] * nlev
         del graph
     pk = measured_peaks(dev)
-    fp64 = args.precision == "fp64"
     peak = pk["fp64_tflops"] if fp64 else pk["fp32_tflops"]
     achieved = kern_flops / (kern_ms / 1000.0) / 1e12
+    achieved_min = kern_flops_min / (kern_ms / 1000.0) / 1e12
     # the FP32C step kernel reads, per point and node, the value record
     # (16 B) and the second derivatives (8 B) of its cell's left node from L2
     # (the right node's are the next lane's, an L1 hit): its L2 -> SM rate
@@ -601,7 +618,20 @@ def run_ours(args, rank, world, local_rank):
                                          + ("FP64 FMA" if fp64 else
                                             "FP32 FMA (better of scalar and packed FP32x2)")
                                          + " (of measured)"),
-                         "flop_per_gp_step": {str(k): flops_per_gp_step(k, 16) for k in ks},
+                         "flop_per_gp_step": {str(k): flops_per_gp_step_method(k, 16, not fp64,
+                                                                               iters[k])
+                                              for k in ks},
+                         "flop_count": (f"{FLOP_NODE_COMP if not fp64 else FLOP_NODE_PLAIN} per "
+                                        "node (spline values, driver, "
+                                        + ("compensated " if not fp64 else "") +
+                                        "sums), 3 per step j, 6 per Picard iteration "
+                                        "(the solve's maximum count)"),
+                         "minimal": {"flop_per_gp_step": {str(k): flops_per_gp_step(k, 16)
+                                                          for k in ks},
+                                     "achieved": achieved_min, "frac": achieved_min / peak,
+                                     "flop_count": "23 per node (two spline values, the "
+                                                   "Black-Scholes driver, three plain sums), "
+                                                   "2L + 4k + 12 per point"},
                          "avg_launch_ms": kern_ms / levels_total,
                          "step_launch_us": step_us,
                          "l2": l2},
@@ -775,7 +805,12 @@ def run_batch(args, rank, world, local_rank):
                          f"({cu} grid-point steps, {cdt:.1f} s)"}
     if rank == 0:
         pk = measured_peaks(dev)
-        achieved = flops_per_step / (ms_max / args.steps / 1000.0) / 1e12
+        achieved_min = flops_per_step / (ms_max / args.steps / 1000.0) / 1e12
+        # the method's count (compensated sums) with each instance's Picard count
+        flops_method = sum(flops_per_gp_step_method(p["k"], p["L"], True,
+                                                    max(1, int(r["picard_iters_max"]))) * u
+                           for p, u, r in zip(probs, units, res32))
+        achieved = flops_method / (ms_max / args.steps / 1000.0) / 1e12
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
@@ -806,6 +841,12 @@ def run_batch(args, rank, world, local_rank):
             "roofline": {"kernel": "k_batch32", "bound": "alu", "achieved": achieved,
                          "peak": pk["fp32_tflops"], "unit": "TFLOP/s",
                          "frac": achieved / pk["fp32_tflops"], "traffic": None,
+                         "flop_count": f"{FLOP_NODE_COMP} per node (compensated sums), 3 per "
+                                       "step j, 6 per Picard iteration; whole batch over the "
+                                       "step time",
+                         "minimal": {"achieved": achieved_min,
+                                     "frac": achieved_min / pk["fp32_tflops"],
+                                     "flop_count": "23 per node, 2L + 4k + 12 per point"},
                          "peak_source": "measured in this run: bsde_fma_probe, FP32 FMA (of "
                                         "measured)"},
             "peaks": pk,
