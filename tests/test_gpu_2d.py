@@ -114,11 +114,13 @@ def test_2d_pass_parts_need_the_tensor_form(B):
     s.close()
 
 
-def test_2d_imported_levels_and_polynomial_exactness(B):
+@pytest.mark.parametrize("b21", [0.25, 0.0])
+def test_2d_imported_levels_and_polynomial_exactness(B, b21):
     """Caller levels through host memory: a quadratic terminal with f = 0 and
-    a correlated forward process, exact to rounding inside the box (as in the
+    a drifting forward process, correlated (the node-wise step) or not (the
+    tensor-product passes), exact to rounding inside the box (as in the
     oracle's pin), and equal to the oracle everywhere."""
-    a1, a2, b11, b21, b22 = 0.2, -0.3, 0.7, 0.25, 0.5
+    a1, a2, b11, b22 = 0.2, -0.3, 0.7, 0.5
     p = _with(W.ex4_problem(M=64, N=8, k=3), alpha=0.0, beta1=0.0, beta2=0.0, a1=a1, a2=a2,
               b11=b11, b21=b21, b22=b22)
     x1 = np.linspace(p["x1_min"], p["x1_max"], p["Nx1"])
