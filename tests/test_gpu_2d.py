@@ -102,6 +102,20 @@ def test_2d_tensor_passes_equal_the_nodewise_step(B, prec, tol):
         assert float(np.max(np.abs(a[f] - b[f]))) <= tol * scale, f
 
 
+@pytest.mark.parametrize("form", ["NODEWISE", "TENSOR"])
+@pytest.mark.parametrize("prec,tol", [("fp64", TOL), ("fp32c", 2e-7)])
+def test_2d_tall_grid_beyond_the_launch_y_limit(B, form, prec, tol):
+    """Nx2 = 600001 rows: the derivative kernels' and the x2 pass's tile rows
+    (8 per CTA) exceed the 65535 CTAs of a launch's y extent, so their CTAs
+    take several tile rows each.  Six columns over [-0.5, 0.5] keep the x1
+    spacing (0.2) in the range the FP32C increments are made for."""
+    p = _with(W.ex4_problem(M=5, N=2, k=1, L=2), Nx1=6, Nx2=600001, x1_min=-0.5, x1_max=0.5,
+              step_form=form)
+    ref = O.solve2(p, threads=THREADS, want_level=True)
+    got = B.solve2(p, want_level=True, precision=prec)
+    _cmp(got, ref, f"tall {form} {prec}", tol=tol)
+
+
 def test_2d_pass_parts_need_the_tensor_form(B):
     s = B.Solver2(dict(W.ex5_problem(M=24, N=4, k=2, L=4, rho=0.5)))
     s.solve()
