@@ -690,6 +690,10 @@ def run_batch(args, rank, world, local_rank):
     stream = torch.cuda.current_stream(dev)
     sp = stream.cuda_stream
     probs = W.config4()
+    # --instances n: the first n instances (a small case for profiling; the
+    # workload is all 4096)
+    n_inst = len(probs) if args.instances <= 0 else min(args.instances, len(probs))
+    probs = probs[:n_inst]
     units = [W.gp_steps(p) for p in probs]
     units_per_step = sum(units)
     flops_per_step = sum(flops_per_gp_step(p["k"], p["L"]) * u for p, u in zip(probs, units))
@@ -721,8 +725,9 @@ def run_batch(args, rank, world, local_rank):
     res32 = bs.solve()
 
     gold = _golden4()
-    if gold is None or len(gold) != len(probs):
+    if gold is None or len(gold) != len(W.config4()):
         raise RuntimeError("tests/golden/config4_oracle.json is missing or stale")
+    gold = gold[:len(probs)]
     g32 = [gate(r["y0"], r["z0"], *g, "fp32c") for r, g in zip(res32, gold)]
 
     # the plain FP64 per-instance form: one plan per instance, its solves
@@ -816,7 +821,9 @@ def run_batch(args, rank, world, local_rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": "config4: 4096 Black-Scholes calls, seed 13560, K~U[70,130], "
+            "config": {"workload": ("config4: 4096 Black-Scholes calls" if n_inst == 4096 else
+                                    f"config4 (first {n_inst} of its 4096 Black-Scholes calls)")
+                                   + ", seed 13560, K~U[70,130], "
                                    "sigma~U[.1,.5], T~U[.25,2], r~U[0,.05], Nx in 2^10..2^14, "
                                    "N in 32..256, k~U{1..6}, L=16; FP32C, one persistent launch",
                        "instances": len(probs), "batch_config": cfg, "plan_s": plan_s,
@@ -1549,6 +1556,9 @@ def main():
                     help="config4: skip the FP64 per-instance comparison")
     ap.add_argument("--fp64-steps", type=int, default=2,
                     help="config4: timed steps of the FP64 per-instance arm (~7 s each)")
+    ap.add_argument("--instances", type=int, default=0,
+                    help="config4: only the first n instances (a small case for profiling; "
+                         "0 = all 4096)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="config4: a fixed batch configuration (cluster 1, 4 groups) instead "
                          "of the autotuned one")

@@ -307,8 +307,22 @@ void build_tables(Params &P, NodeF64 *t64, NodeF32 *t32, PairF32 *tp, int target
   }
   const double rpi = 1.0 / std::sqrt(M_PI);
   const double c6 = P.dx * P.dx / 6.0;
+  P.c6 = c6;
+  P.c6_f = float(c6);
+  P.xmin_f[0] = float(P.x_min);
+  P.xmin_f[1] = float(P.x_min - double(P.xmin_f[0]));
+  P.dx_f[0] = float(P.dx);
+  P.dx_f[1] = float(P.dx - double(P.dx_f[0]));
   for (int j = 1; j <= P.k; ++j) {
     const double sq = std::sqrt(2.0 * j * P.dt);
+    {
+      const double g[4] = {P.a_x * double(j) * P.dt * P.inv_dx, P.a_1 * double(j) * P.dt * P.inv_dx,
+                           P.b_x * sq * P.inv_dx, P.b_1 * sq * P.inv_dx};
+      for (int q = 0; q < 4; ++q) {
+        P.gen_f[j - 1][2 * q] = float(g[q]);
+        P.gen_f[j - 1][2 * q + 1] = float(g[q] - double(P.gen_f[j - 1][2 * q]));
+      }
+    }
     int smin = 0x7fffffff, smax = -0x7fffffff;
     for (int l = 0; l < P.L; ++l) {
       const double dW = sq * a[l];

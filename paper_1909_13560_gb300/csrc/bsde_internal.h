@@ -105,6 +105,16 @@ struct Params {
                     // a divide; it may move a node that lands within rounding
                     // of a grid node to the neighbouring cell, where the spline
                     // has the same value to rounding)
+  double c6;        // dx^2 / 6 (the spline's curvature weight scale)
+  float c6_f;       // float(c6)
+  // general forward path: per step j the node offset in cells,
+  // o = A_j(x) + B_j(x) a_l, as affine functions of the point's x:
+  // A_j = a0 + a1 x = a(x) j dt / dx, B_j = b0 + b1 x = b(x) sqrt(2 j dt) / dx,
+  // formed once on the host; the FP32C kernel takes them as float pairs
+  // gen_f[j - 1] = (a0, a1, b0, b1) x (hi, lo) and the point's x from the
+  // float pairs xmin_f, dx_f, so it forms its offsets without FP64
+  float gen_f[kMaxK][8];
+  float xmin_f[2], dx_f[2];
   double invd[kInvPivots];
   // work split of the step kernels: S l-chunks of Lg nodes per j, G = k S
   // groups per point; shift range per j (for the clamp-free fast path)

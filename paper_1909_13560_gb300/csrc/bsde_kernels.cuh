@@ -731,7 +731,11 @@ __global__ void __launch_bounds__(kStepTP * kMaxGroups)
   if (ii <= last) {
     const double4_32a *lev = ring + int64_t((n + j) % P.nslot) * P.Nx;
     const double tj = (n + j) * P.dt;
-    const double et = exp(tj * tj), emt = exp(-tj * tj);
+    double et = 0.0, emt = 0.0;  // Example 2's driver only
+    if constexpr (DRV == BSDE_DRIVER_EX2) {
+      et = exp(tj * tj);
+      emt = exp(-tj * tj);
+    }
     const NodeF64 *row = tab + (j - 1) * P.L;
     const bool interior = i0 + P.smin[j - 1] >= 0 && i0 + kStepTP + P.smax[j - 1] <= last;
     const bool yj = j == P.ky, zf = P.zform && j == 1;
@@ -806,12 +810,16 @@ __global__ void __launch_bounds__(kStepTP * kMaxGroups)
   if (ii <= last) {
     const double4_32a *lev = ring + int64_t((n + j) % P.nslot) * P.Nx;
     const double tj = __dmul_rn(double(n + j), P.dt);
-    const double et = exp(tj * tj), emt = exp(-tj * tj);
+    double et = 0.0, emt = 0.0;
+    if constexpr (DRV == BSDE_DRIVER_EX2) {
+      et = exp(tj * tj);
+      emt = exp(-tj * tj);
+    }
     const NodeF64 *row = tab + (j - 1) * P.L;
     const bool yj = j == P.ky, zf = P.zform && j == 1;
     const double ax = P.a_x + P.a_1 * xi, bx = P.b_x + P.b_1 * xi;
     const double drift = ax * double(j) * P.dt;
-    const double c6 = P.dx * P.dx / 6.0;
+    const double c6 = P.c6;
 #pragma unroll 2
     for (int l = l0; l < l1; ++l) {
       const NodeF64 &e = row[l];
@@ -1342,16 +1350,26 @@ __global__ void __launch_bounds__(kFlatTP, 8)
 // computed per point.  Node q of a pair sits at the offset
 // o = A_j + B_j a_q cells from its grid point (node L-1-q at A_j - B_j a_q),
 // A_j = a(x_i) j dt / dx and B_j = b(x_i) sqrt(2 j dt) / dx formed once per
-// thread in FP64 and split into float pairs, a_q a float pair, so the offset
-// is a float pair accurate to ~1e-10 cells (a plain float would lose 1e-3
-// cells at offsets of thousands of cells); its floor is the cell shift and
-// the remainder theta.  The spline value, the pair arithmetic, the
+// thread as float pairs from the plan's affine coefficients and x_i (itself
+// a float pair; pair_affine, no FP64), a_q a float pair, so the offset is a
+// float pair accurate to ~1e-9 cells (a plain float would lose 1e-3 cells at
+// offsets of thousands of cells); its floor is the cell shift and the
+// remainder theta.  The spline value, the pair arithmetic, the
 // compensated sums and the Picard tail are those of k_step32, with the
 // driver reading the node's position.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void split_pair(double v, float &h, float &l) {
-  h = __double2float_rn(v);
-  l = __double2float_rn(__dsub_rn(v, double(h)));
+// c0 + c1 x for float pairs c0, c1, x, as a float pair to ~2^-44 relative:
+// the exact product of the hi parts (FMA error term) and the exact sum of
+// the large terms (TwoSum), the small cross terms in FP32.
+__device__ __forceinline__ void pair_affine(float c0h, float c0l, float c1h, float c1l, float xh,
+                                            float xl, float &h, float &l) {
+  const float p = __fmul_rn(c1h, xh);
+  const float pl = __fmaf_rn(c1h, xl, __fmaf_rn(c1l, xh, __fmaf_rn(c1h, xh, -p)));
+  const float s = __fadd_rn(c0h, p);
+  const float bp = __fsub_rn(s, c0h);
+  const float err = __fadd_rn(__fsub_rn(c0h, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+  h = s;
+  l = __fadd_rn(err, __fadd_rn(c0l, pl));
 }
 
 // o = A + s B a (s = +1 or -1) as a float pair; the cell shift (floor) and
@@ -1411,12 +1429,15 @@ __global__ void __launch_bounds__(kStepTP * kMaxGroups, 3)
       float tj, et, emt;
       level_time<DRV>(P, n + w.j, tj, et, emt);
       const PairF32 *row = tab + (w.j - 1) * P.Lp;
-      const double xi = P.x_min + double(ii) * P.dx;
+      // x_i = x_min + i dx as a float pair (i < 2^24 is exact in FP32)
+      float xh, xl;
+      pair_affine(P.xmin_f[0], P.xmin_f[1], P.dx_f[0], P.dx_f[1], float(ii), 0.f, xh, xl);
+      const float *gf = P.gen_f[w.j - 1];
       float Ah, Al, Bh, Bl;
-      split_pair((P.a_x + P.a_1 * xi) * double(w.j) * P.dt * P.inv_dx, Ah, Al);
-      split_pair((P.b_x + P.b_1 * xi) * sqrt(2.0 * double(w.j) * P.dt) * P.inv_dx, Bh, Bl);
-      const float xf = float(xi), dxf = float(P.dx);
-      const float c6 = float(P.dx * P.dx / 6.0);
+      pair_affine(gf[0], gf[1], gf[2], gf[3], xh, xl, Ah, Al);
+      pair_affine(gf[4], gf[5], gf[6], gf[7], xh, xl, Bh, Bl);
+      const float xf = __fadd_rn(xh, xl), dxf = P.dx_f[0];
+      const float c6 = P.c6_f;
 #pragma unroll 1
       for (int q = w.q0; q < w.q1; ++q) {
         const float4 *te = reinterpret_cast<const float4 *>(row + q);
