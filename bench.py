@@ -332,7 +332,8 @@ def run_reference(args, rank, world):
     value = tot / args.steps
     probs = _single_problems(wl)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
-            "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+            "n_gpus": world, "devices": "host cores only (rank 0)",
+            "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 * wall / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": _workload_text(wl, [k for k, _ in probs]),
