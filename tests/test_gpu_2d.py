@@ -73,6 +73,9 @@ CASES = {
     "L1_ragged": _with(W.ex4_problem(M=30, N=6, k=2, L=1), Nx1=37, Nx2=29),
     # Example 5 uncorrelated with the paper's K = 6 and an odd L
     "ex5_k6_L7": W.ex5_problem(M=48, N=8, k=6, L=7, width=2.0),
+    # a degenerate forward process: X2 drifts but does not diffuse (b22 = 0),
+    # so every x2 node of a step shares one cell and z2 = 0
+    "degenerate_b22": _with(W.ex4_problem(M=40, N=8, k=3, L=4, x_lim=4.0), a2=0.25, b22=0.0),
 }
 
 

@@ -24,13 +24,14 @@ def B():
     return bsde
 
 
-def _mixed(count=40, seed=7):
+def _mixed(count=42, seed=7):
     """Uneven problems: the config4 recipe at smaller sizes, plus
-    lending/borrowing calls and the paper's two nonlinear examples."""
+    lending/borrowing calls, the paper's two nonlinear examples and the
+    linear sin problem (all five drivers)."""
     rng = np.random.default_rng(seed)
     out = []
     for i in range(count):
-        kind = i % 5
+        kind = i % 6
         k = int(rng.integers(1, 7))
         N = int(8 << int(rng.integers(0, 3)))
         k = min(k, N)
@@ -45,8 +46,10 @@ def _mixed(count=40, seed=7):
                                       Nx=Nx, N=N, k=k, L=16, driver="LB"))
         elif kind == 3:
             out.append(W.ex1_problem(Nx=Nx, N=N, k=k, L=12, x_lim=8.0))
-        else:
+        elif kind == 4:
             out.append(W.ex2_problem(Nx=Nx, N=N, k=k, L=12, x_lim=8.0))
+        else:
+            out.append(W.sin_problem(Nx=Nx, N=N, k=k, L=8))
     return out
 
 
