@@ -94,3 +94,17 @@ def test_stored_config4_values_match_the_instances():
                if math.isfinite(y) and abs(y - u) <= 1e-2 * max(1.0, abs(u))
                and abs(z - zz) <= 1e-2 * max(1.0, abs(zz)))
     assert conv == 3185
+
+
+def test_roofline_flop_counts():
+    # the method's count: 42 flop per node with compensated sums (30 plain),
+    # 3 per step j, 6 per Picard iteration
+    assert bench.flops_per_gp_step_method(2, 16, True, 4) == 42 * 32 + 6 + 24
+    assert bench.flops_per_gp_step_method(4, 16, False, 5) == 30 * 64 + 12 + 30
+    # the narrower count: 23 per node, 2L + 4k + 12 per point
+    assert bench.flops_per_gp_step(2, 16) == 23 * 32 + 32 + 8 + 12
+    # the 2-D tensor-product passes, per point and level
+    fp = bench.flops_per_gp_step_tp(6, 8, "fp64")
+    assert fp == {"x2": 6 * 8 * 66.0, "x1": 6 * 8 * 60.0 + 6 * 27.0 + 80.0}
+    f32 = bench.flops_per_gp_step_tp(6, 8, "fp32c")
+    assert f32["x2"] == 6 * 4 * 195.0 and f32["x1"] == 6 * 4 * 193.0 + 80.0
