@@ -390,7 +390,8 @@ def run_ours(args, rank, world, local_rank):
     # the flat FP32C step kernel (no shared-memory partial sums, no barrier,
     # uniform table reads; bitwise the grouped kernel's results) then beats
     # the grouped one that the library picks for a 65536-point grid alone
-    flat2 = (wl == "config2" and args.precision == "fp32c" and not args.sequential)
+    flat2 = (wl == "config2" and args.precision == "fp32c"
+             and (not args.sequential or args.step_kernel == "FLAT"))
     if flat2:
         probs = [dict(p, step_kernel="FLAT") for p in probs]
     solvers = [B.Solver(p, args.precision, device=dev) for p in probs]
@@ -608,8 +609,10 @@ def run_ours(args, rank, world, local_rank):
                                  "<= 18 MB per solve, L2-resident within a solve by design")),
                        "step_kernel": ("FP64" if fp64 else
                                        "flat FP32C (chosen by the library for this grid)" if c3
-                                       else "flat FP32C (step_kernel = FLAT: the concurrent "
-                                            "solves fill the GPU together)" if flat2
+                                       else ("flat FP32C (step_kernel = FLAT, asked for with "
+                                             "--step-kernel)" if args.sequential else
+                                             "flat FP32C (step_kernel = FLAT: the concurrent "
+                                             "solves fill the GPU together)") if flat2
                                        else "grouped FP32C (chosen by the library for this grid)"),
                        "schedule": ("the step's solves one after another on one stream"
                                     if args.sequential else
@@ -1570,6 +1573,9 @@ def main():
                     help="config4: skip the FP64 per-instance comparison")
     ap.add_argument("--fp64-steps", type=int, default=2,
                     help="config4: timed steps of the FP64 per-instance arm (~7 s each)")
+    ap.add_argument("--step-kernel", choices=["AUTO", "FLAT"], default="AUTO",
+                    help="config2 FP32C: FLAT also with --sequential (the concurrent default "
+                         "takes it anyway)")
     ap.add_argument("--instances", type=int, default=0,
                     help="config4: only the first n instances (a small case for profiling; "
                          "0 = all 4096)")
