@@ -168,25 +168,35 @@ static void launch_step_any(bsde_plan_t *pl, const Run &R, cudaStream_t s, int n
   }
 }
 
-template <int PREC, bool BIG>
+template <int PREC>
 static void launch_spline(const Run &R, cudaStream_t s, int slot) {
   const Params &P = R.P;
-  constexpr int TS = SplineLaunch<PREC, BIG>::TS;
+  constexpr int TS = SplineLaunch<PREC>::TS;
   const unsigned blocks = unsigned((P.Nx - 2 + TS - 1) / TS);
-  launch_pdl(k_spline<PREC, BIG>, blocks, unsigned(SplineLaunch<PREC, BIG>::NT), 0, s, P, R.r64,
-             R.r32, slot);
+  launch_pdl(k_spline<PREC>, blocks, unsigned(SplineLaunch<PREC>::NT), 0, s, P, R.r64, R.r32,
+             slot);
 }
 
-// FP32C grids that take the flat step kernel also take the wide spline tiles
+// The spline of a single solve.  FP32C: on grids that fill the GPU twice
+// over the wide tiles (fewer CTAs, which leave room to other solves' work
+// running beside them), else the warp-tiled kernel (CTA 0 the first tile,
+// then 104 unknowns per warp, 4 warps per CTA); both give the same M
+// bitwise.  FP64: the tiled kernel.
 template <int PREC>
 static int64_t enqueue_spline(const Run &R, cudaStream_t s, int slot) {
   if constexpr (PREC == BSDE_FP32C) {
-    if (R.P.flat) {
-      launch_spline<PREC, true>(R, s, slot);
+    if (R.P.wide_spline) {
+      launch_spline<PREC>(R, s, slot);
       return 1;
     }
+    const int64_t u = R.P.Nx - 2;
+    const int64_t nw = u > kSplHeadTS ? (u - kSplHeadTS + kSplWarpOut - 1) / kSplWarpOut : 0;
+    const int per = kSplWarpThreads / 32;
+    launch_pdl(k_spline32w, unsigned(1 + (nw + per - 1) / per), unsigned(kSplWarpThreads), 0, s,
+               R.P, R.r32, slot);
+  } else {
+    launch_spline<PREC>(R, s, slot);
   }
-  launch_spline<PREC, false>(R, s, slot);
   return 1;
 }
 

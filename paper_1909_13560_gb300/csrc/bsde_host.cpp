@@ -272,9 +272,10 @@ static void work_split(Params &P, int target_groups, int max_groups, long reside
   P.G = P.k * S;
   // automatic: a grid whose points alone fill the resident threads twice
   // takes the flat kernel (same split, same order of operations)
-  if (P.flat < 0)
-    P.flat = P.precision == BSDE_FP32C && resident_threads > 0 &&
-             long(P.Nx) >= 2 * resident_threads;
+  const bool big = P.precision == BSDE_FP32C && resident_threads > 0 &&
+                   long(P.Nx) >= 2 * resident_threads;
+  if (P.flat < 0) P.flat = big;
+  P.wide_spline = big;
 }
 
 // Node tables.  On the uniform grid with a constant-coefficient forward

@@ -16,7 +16,6 @@ constexpr int kStepTP = 64;      // grid points per CTA in the step kernels
 constexpr int kMaxGroups = 6;    // (j, l-chunk) groups per point
 constexpr int kPartArrays = 7;   // FP32C per-group partial sums: z (S, C, F), y (S, C, F, F err)
 constexpr int kSplineTile = 512;  // unknowns per CTA in the FP64 spline kernel
-constexpr int kSplineTile32 = 256;  // threads per CTA in the FP32C one
 constexpr int kSplineChunk = 4;   // unknowns per thread (serial recurrence, FP64)
 constexpr int kSplineHead = 16;   // FP32C: pivots of the spline LU are constant beyond this
 
@@ -119,6 +118,8 @@ struct Params {
   // work split of the step kernels: S l-chunks of Lg nodes per j, G = k S
   // groups per point; shift range per j (for the clamp-free fast path)
   int32_t S, Lg, G, Lp;  // Lp = ceil(L/2) pairs; in FP32C the chunks hold Lg pairs
+  int32_t wide_spline;   // FP32C: the spline's wide tiles (grids that fill the GPU
+                         // twice over, whatever step kernel was asked for)
   int32_t flat;          // FP32C constant-shift step: one thread runs all G groups of
                          // its point (k_step32f), for grids of at least two waves
   int32_t smin[kMaxK], smax[kMaxK];

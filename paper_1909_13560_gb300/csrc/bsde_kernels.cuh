@@ -589,28 +589,159 @@ __device__ __forceinline__ void spline_tile(const Params &P, Ring64 r64, Ring32 
 }
 
 
-// Spline kernel tiles: FP64 runs serial chunks of kSplineChunk unknowns per
-// thread; FP32C CP consecutive unknowns per thread (its sweeps are sums, not
-// chains), the forward sweep covering the tile and its right halo of W + 1:
-// one unknown per thread on moderate grids (243 + 13 = 256), four on grids
-// that fill the GPU several times over (BIG: 1011 + 13 = 1024).
-template <int PREC, bool BIG = false>
+// The tiled spline kernel: FP64 runs tiles of kSplineTile unknowns, serial
+// chunks of kSplineChunk unknowns per thread; FP32C tiles of 1011 unknowns,
+// four consecutive unknowns per thread (its sweeps are sums, not chains),
+// the forward sweep covering the tile and its right halo of W + 1 (1024).
+// FP32C takes these wide tiles on grids that fill the GPU twice over; on
+// smaller grids single solves run the warp-tiled k_spline32w below, and
+// batches and the server run spline_tile inside their persistent kernels.
+template <int PREC>
 struct SplineLaunch {
-  static constexpr int TS = PREC == BSDE_FP64 ? kSplineTile : (BIG ? 1011 : 243);
-  static constexpr int NT = PREC == BSDE_FP64 ? kSplineTile / kSplineChunk : kSplineTile32;
+  static constexpr int TS = PREC == BSDE_FP64 ? kSplineTile : 1011;
+  static constexpr int NT = PREC == BSDE_FP64 ? kSplineTile / kSplineChunk : 256;
 };
 
-template <int PREC, bool BIG>
-__global__ void __launch_bounds__(SplineLaunch<PREC, BIG>::NT)
+template <int PREC>
+__global__ void __launch_bounds__(SplineLaunch<PREC>::NT)
     k_spline(const Params P, Ring64 r64, Ring32 r32, int slot) {
   using T = typename SplineT<PREC>::T;
-  constexpr int TS = SplineLaunch<PREC, BIG>::TS, NT = SplineLaunch<PREC, BIG>::NT;
+  constexpr int TS = SplineLaunch<PREC>::TS, NT = SplineLaunch<PREC>::NT;
   constexpr int S = spline_span<PREC>(TS);
   __shared__ T sr[2][S], sg[2][S];
   __shared__ T sid[kInvPivots];
   if (threadIdx.x < kInvPivots) sid[threadIdx.x] = T(P.invd[threadIdx.x]);
   wait_predecessor();
   spline_tile<PREC, TS, false, NT>(P, r64, r32, slot, blockIdx.x, blockDim.x, sr, sg, sid);
+}
+
+// ---------------------------------------------------------------------------
+// The FP32C spline of a single solve, warp-tiled.  Beyond the first tile the
+// sweeps are the 13-term sums of spline_tile, evaluated without shared memory
+// or block barriers: a warp holds 128 consecutive unknowns, 4 per lane (r
+// from the lane's own level records), and takes the 12 values each sum needs
+// from the neighbouring lanes by shuffles.  It outputs the 104 unknowns whose
+// forward sums have their left terms and whose backward sums their right ones
+// inside the warp (the first and last 12 are its halo).  Each sum keeps the
+// terms, weights and order of spline_tile, so the second derivatives are
+// bitwise those of the tiled kernel.  CTA 0 runs the first tile (unknowns
+// 0..242: the exact serial head, node 0) with spline_tile itself.
+// ---------------------------------------------------------------------------
+constexpr int kSplWarpCP = 4;                                      // unknowns per lane
+constexpr int kSplWarpOut = 32 * kSplWarpCP - 2 * SplineT<BSDE_FP32C>::W;  // 104
+constexpr int kSplHeadTS = 243;                                    // CTA 0's tile
+constexpr int kSplWarpThreads = 128;
+
+__global__ void __launch_bounds__(kSplWarpThreads)
+    k_spline32w(const Params P, Ring32 r32, int slot) {
+  constexpr int W = SplineT<BSDE_FP32C>::W, CP = kSplWarpCP;
+  __shared__ float sr[2][spline_span<BSDE_FP32C>(kSplHeadTS)];
+  __shared__ float sg[2][spline_span<BSDE_FP32C>(kSplHeadTS)];
+  __shared__ float sid[kInvPivots];
+  const int u = int(P.Nx - 2);
+  if (blockIdx.x == 0) {  // uniform over the CTA
+    if (threadIdx.x < kInvPivots) sid[threadIdx.x] = float(P.invd[threadIdx.x]);
+    wait_predecessor();
+    spline_tile<BSDE_FP32C, kSplHeadTS, false, kSplWarpThreads>(
+        P, Ring64{nullptr}, r32, slot, 0, blockDim.x, sr, sg, sid);
+    return;
+  }
+  wait_predecessor();
+  const int lane = threadIdx.x & 31;
+  const int wg = (blockIdx.x - 1) * (kSplWarpThreads / 32) + (threadIdx.x >> 5);
+  const int s0 = kSplHeadTS + wg * kSplWarpOut;  // first output unknown
+  if (s0 >= u) return;                           // uniform over the warp
+  const int64_t off = int64_t(slot) * P.Nx;
+  const int m0 = s0 - W + lane * CP;             // the lane's unknowns m0 .. m0 + 3
+  const float inv6 = float(P.inv_dx2_6);
+  const float rho = float(P.invd[kSplineHead]);
+  // r_m from the (hi, lo) pairs of nodes m, m + 1, m + 2 (as spline_tile)
+  float ry[CP], rz[CP];
+  {
+    float4 v[CP + 2];
+#pragma unroll
+    for (int q = 0; q < CP + 2; ++q)
+      v[q] = m0 + q <= u + 1 ? r32.A[off + m0 + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float dy[CP + 1], dz[CP + 1];
+#pragma unroll
+    for (int q = 0; q < CP + 1; ++q) {
+      dy[q] = __fadd_rn(__fsub_rn(v[q + 1].x, v[q].x), __fsub_rn(v[q + 1].z, v[q].z));
+      dz[q] = __fadd_rn(__fsub_rn(v[q + 1].y, v[q].y), __fsub_rn(v[q + 1].w, v[q].w));
+    }
+#pragma unroll
+    for (int q = 0; q < CP; ++q) {
+      const bool in = m0 + q < u;
+      ry[q] = in ? __fmul_rn(inv6, __fsub_rn(dy[q + 1], dy[q])) : 0.f;
+      rz[q] = in ? __fmul_rn(inv6, __fsub_rn(dz[q + 1], dz[q])) : 0.f;
+    }
+  }
+  // forward: g_m = sum_q (-rho)^q r_{m-q}; the window r_{m0-W} .. r_{m0+3}
+  // from lanes lane-3 .. lane (lanes 0..2 hold the halo: their g is unused)
+  float gy[CP], gz[CP];
+  {
+    float wy[W + CP], wz[W + CP];
+#pragma unroll
+    for (int d = 1; d <= W / CP; ++d) {
+#pragma unroll
+      for (int t = 0; t < CP; ++t) {
+        wy[W - d * CP + t] = __shfl_up_sync(0xffffffffu, ry[t], d);
+        wz[W - d * CP + t] = __shfl_up_sync(0xffffffffu, rz[t], d);
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < CP; ++t) {
+      wy[W + t] = ry[t];
+      wz[W + t] = rz[t];
+      gy[t] = wy[W + t];
+      gz[t] = wz[W + t];
+    }
+    float c = 1.f;
+#pragma unroll
+    for (int q = 1; q <= W; ++q) {
+      c = -c * rho;
+#pragma unroll
+      for (int t = 0; t < CP; ++t) {
+        gy[t] = __fmaf_rn(c, wy[W + t - q], gy[t]);
+        gz[t] = __fmaf_rn(c, wz[W + t - q], gz[t]);
+      }
+    }
+  }
+  // backward: M_m = sum_q rho (-rho)^q g_{m+q}, stopping at the last
+  // unknown; the window g_{m0} .. g_{m0+3+W} from lanes lane .. lane+3
+  // (lanes 29..31 hold the halo: their M is not written)
+  float wy[W + CP], wz[W + CP];
+#pragma unroll
+  for (int t = 0; t < CP; ++t) {
+    wy[t] = gy[t];
+    wz[t] = gz[t];
+  }
+#pragma unroll
+  for (int d = 1; d <= W / CP; ++d) {
+#pragma unroll
+    for (int t = 0; t < CP; ++t) {
+      wy[d * CP + t] = __shfl_down_sync(0xffffffffu, gy[t], d);
+      wz[d * CP + t] = __shfl_down_sync(0xffffffffu, gz[t], d);
+    }
+  }
+  const int e = s0 + kSplWarpOut < u ? s0 + kSplWarpOut : u;  // outputs [s0, e)
+#pragma unroll
+  for (int t = 0; t < CP; ++t) {
+    const int m = m0 + t;
+    if (m < s0 || m >= e) continue;
+    const int qmax = u - 1 - m < W ? u - 1 - m : W;
+    float my = 0.f, mz = 0.f, c = rho;
+#pragma unroll
+    for (int q = 0; q <= W; ++q) {
+      if (q <= qmax) {
+        my = __fmaf_rn(c, wy[t + q], my);
+        mz = __fmaf_rn(c, wz[t + q], mz);
+      }
+      c = -c * rho;
+    }
+    r32.M[off + m + 1] = make_float2(my, mz);  // M of node m + 1
+  }
+  // natural end condition at the last node
+  if (lane == 0 && u - 1 >= s0 && u - 1 < e) r32.M[off + u + 1] = make_float2(0.f, 0.f);
 }
 
 // ---------------------------------------------------------------------------
