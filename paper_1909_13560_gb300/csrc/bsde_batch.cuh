@@ -26,19 +26,32 @@ struct alignas(16) InstDesc {
 };
 
 constexpr int kBatchThreads = kStepTP * 6;          // up to six groups per point
-// spline tiles of 1523 unknowns: with the forward sweep's right halo of 13
-// they fill the 384 threads with four consecutive unknowns each
-constexpr int kBatchSplineTile = kBatchThreads * kSplineChunk - 13;
 
+// The spline of a level runs as in a single solve's warp-tiled kernel: the
+// cluster's first CTA takes the first tile (the exact serial head; shared
+// memory below), and every warp of the cluster takes warp tiles in turn.
 struct alignas(16) BatchSmem {
   InstDesc D;
   PairF32 tab[kMaxK * (kMaxL / 2)];
   float part[kPartArrays * kMaxGroups * kStepTP];
-  float sr[2][spline_span<BSDE_FP32C>(kBatchSplineTile)];
-  float sg[2][spline_span<BSDE_FP32C>(kBatchSplineTile)];
+  float sr[2][spline_span<BSDE_FP32C>(kSplHeadTS)];
+  float sg[2][spline_span<BSDE_FP32C>(kSplHeadTS)];
   float sid[kInvPivots];
   int inst;
 };
+
+// The spline of the level in `slot` by the cluster's CTAs (every thread of
+// every CTA calls it; the caller separates it from the step phases by a
+// cluster barrier).
+__device__ __forceinline__ void batch_spline(BatchSmem &sm, const Params &P, Ring32 r32,
+                                             int slot, int crank, int csize) {
+  if (crank == 0)  // uniform over the CTA: the first tile holds CTA barriers
+    spline_tile<BSDE_FP32C, kSplHeadTS, true, kBatchThreads>(P, Ring64{nullptr}, r32, slot, 0,
+                                                              blockDim.x, sm.sr, sm.sg, sm.sid);
+  const int wpc = int(blockDim.x) / 32, nw = spline_warp_tiles(P.Nx);
+  for (int wt = crank * wpc + int(threadIdx.x >> 5); wt < nw; wt += csize * wpc)
+    spline_warp_tile<true>(P, r32, slot, wt);
+}
 
 __global__ void k_batch_reset(int *queue, Stats *stats, int count) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -71,13 +84,9 @@ __device__ void batch_instance(BatchSmem &sm, unsigned char *ws, Stats *st,
     for (int64_t i = int64_t(crank) * nt + tid; i < P.Nx; i += int64_t(csize) * nt)
       init_point<BSDE_FP32C>(P, r64, r32, m, i);
   cl.sync();
-  const int nst = int((P.Nx - 2 + kBatchSplineTile - 1) / kBatchSplineTile);
   for (int m = 0; m < P.k; ++m) {
-    for (int t = crank; t < nst; t += csize) {
-      spline_tile<BSDE_FP32C, kBatchSplineTile, true, kBatchThreads>(
-          P, r64, r32, (P.N - m) % P.nslot, t, nt, sm.sr, sm.sg, sm.sid);
-      __syncthreads();
-    }
+    batch_spline(sm, P, r32, (P.N - m) % P.nslot, crank, csize);
+    __syncthreads();  // CTA 0's shared-memory tile is reused by the next level
   }
   cl.sync();
 
@@ -98,11 +107,7 @@ __device__ void batch_instance(BatchSmem &sm, unsigned char *ws, Stats *st,
       }
     }
     cl.sync();
-    for (int t = crank; t < nst; t += csize) {
-      spline_tile<BSDE_FP32C, kBatchSplineTile, true, kBatchThreads>(
-          P, r64, r32, n % P.nslot, t, nt, sm.sr, sm.sg, sm.sid);
-      __syncthreads();
-    }
+    batch_spline(sm, P, r32, n % P.nslot, crank, csize);
     cl.sync();
   }
   if (crank == 0 && tid == 0) {

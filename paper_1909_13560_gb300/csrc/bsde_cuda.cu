@@ -189,8 +189,7 @@ static int64_t enqueue_spline(const Run &R, cudaStream_t s, int slot) {
       launch_spline<PREC>(R, s, slot);
       return 1;
     }
-    const int64_t u = R.P.Nx - 2;
-    const int64_t nw = u > kSplHeadTS ? (u - kSplHeadTS + kSplWarpOut - 1) / kSplWarpOut : 0;
+    const int64_t nw = spline_warp_tiles(R.P.Nx);
     const int per = kSplWarpThreads / 32;
     launch_pdl(k_spline32w, unsigned(1 + (nw + per - 1) / per), unsigned(kSplWarpThreads), 0, s,
                R.P, R.r32, slot);

@@ -632,24 +632,16 @@ constexpr int kSplWarpOut = 32 * kSplWarpCP - 2 * SplineT<BSDE_FP32C>::W;  // 10
 constexpr int kSplHeadTS = 243;                                    // CTA 0's tile
 constexpr int kSplWarpThreads = 128;
 
-__global__ void __launch_bounds__(kSplWarpThreads)
-    k_spline32w(const Params P, Ring32 r32, int slot) {
+// One warp tile of the level in `slot`: output unknowns [s0, s0 + 104) with
+// s0 = kSplHeadTS + 104 wt (unknowns below kSplHeadTS are the first tile's).
+// Called by all 32 lanes of a warp; COH: level loads through L2 (the batch
+// kernels, whose levels other SMs write within the launch).
+template <bool COH>
+__device__ __forceinline__ void spline_warp_tile(const Params &P, Ring32 r32, int slot, int wt) {
   constexpr int W = SplineT<BSDE_FP32C>::W, CP = kSplWarpCP;
-  __shared__ float sr[2][spline_span<BSDE_FP32C>(kSplHeadTS)];
-  __shared__ float sg[2][spline_span<BSDE_FP32C>(kSplHeadTS)];
-  __shared__ float sid[kInvPivots];
   const int u = int(P.Nx - 2);
-  if (blockIdx.x == 0) {  // uniform over the CTA
-    if (threadIdx.x < kInvPivots) sid[threadIdx.x] = float(P.invd[threadIdx.x]);
-    wait_predecessor();
-    spline_tile<BSDE_FP32C, kSplHeadTS, false, kSplWarpThreads>(
-        P, Ring64{nullptr}, r32, slot, 0, blockDim.x, sr, sg, sid);
-    return;
-  }
-  wait_predecessor();
   const int lane = threadIdx.x & 31;
-  const int wg = (blockIdx.x - 1) * (kSplWarpThreads / 32) + (threadIdx.x >> 5);
-  const int s0 = kSplHeadTS + wg * kSplWarpOut;  // first output unknown
+  const int s0 = kSplHeadTS + wt * kSplWarpOut;  // first output unknown
   if (s0 >= u) return;                           // uniform over the warp
   const int64_t off = int64_t(slot) * P.Nx;
   const int m0 = s0 - W + lane * CP;             // the lane's unknowns m0 .. m0 + 3
@@ -661,7 +653,7 @@ __global__ void __launch_bounds__(kSplWarpThreads)
     float4 v[CP + 2];
 #pragma unroll
     for (int q = 0; q < CP + 2; ++q)
-      v[q] = m0 + q <= u + 1 ? r32.A[off + m0 + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+      v[q] = m0 + q <= u + 1 ? ldl<COH>(r32.A + off + m0 + q) : make_float4(0.f, 0.f, 0.f, 0.f);
     float dy[CP + 1], dz[CP + 1];
 #pragma unroll
     for (int q = 0; q < CP + 1; ++q) {
@@ -742,6 +734,29 @@ __global__ void __launch_bounds__(kSplWarpThreads)
   }
   // natural end condition at the last node
   if (lane == 0 && u - 1 >= s0 && u - 1 < e) r32.M[off + u + 1] = make_float2(0.f, 0.f);
+}
+
+// Warp tiles of a level: ceil((u - kSplHeadTS) / 104) for u = Nx - 2 unknowns.
+__host__ __device__ inline int spline_warp_tiles(int64_t Nx) {
+  const int64_t u = Nx - 2;
+  return u > kSplHeadTS ? int((u - kSplHeadTS + kSplWarpOut - 1) / kSplWarpOut) : 0;
+}
+
+__global__ void __launch_bounds__(kSplWarpThreads)
+    k_spline32w(const Params P, Ring32 r32, int slot) {
+  __shared__ float sr[2][spline_span<BSDE_FP32C>(kSplHeadTS)];
+  __shared__ float sg[2][spline_span<BSDE_FP32C>(kSplHeadTS)];
+  __shared__ float sid[kInvPivots];
+  if (blockIdx.x == 0) {  // uniform over the CTA
+    if (threadIdx.x < kInvPivots) sid[threadIdx.x] = float(P.invd[threadIdx.x]);
+    wait_predecessor();
+    spline_tile<BSDE_FP32C, kSplHeadTS, false, kSplWarpThreads>(
+        P, Ring64{nullptr}, r32, slot, 0, blockDim.x, sr, sg, sid);
+    return;
+  }
+  wait_predecessor();
+  spline_warp_tile<false>(P, r32, slot,
+                          (blockIdx.x - 1) * (kSplWarpThreads / 32) + (threadIdx.x >> 5));
 }
 
 // ---------------------------------------------------------------------------
