@@ -719,7 +719,8 @@ def run_batch(args, rank, world, local_rank):
     plan_s = time.perf_counter() - t0
     # the batch configuration by timing (bsde_batch_autotune, outside the timed
     # region) unless a fixed one is asked for
-    cfg = (bs.set_config(1, 4) or bs.config()) if args.no_autotune else bs.autotune()
+    fixed = (1, 4, 0) if args.no_autotune else args.batch_config
+    cfg = (bs.set_config(*fixed) or bs.config()) if fixed else bs.autotune()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     for _ in range(args.warmup):
         flush.zero_()
@@ -1582,6 +1583,10 @@ def main():
     ap.add_argument("--no-autotune", action="store_true",
                     help="config4: a fixed batch configuration (cluster 1, 4 groups) instead "
                          "of the autotuned one")
+    ap.add_argument("--batch-config", default=None,
+                    type=lambda v: tuple(int(t) for t in v.split(",")),
+                    help="config4: a fixed batch configuration 'cluster,groups,flat' "
+                         "(e.g. 1,1,1) instead of the autotuned one")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
