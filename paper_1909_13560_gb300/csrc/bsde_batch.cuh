@@ -42,16 +42,15 @@ struct alignas(16) BatchSmem {
 
 // The spline of the level in `slot` by the cluster's CTAs (every thread of
 // every CTA calls it; the caller separates it from the step phases by a
-// cluster barrier).  COH: level loads through L2 (see batch_instance).
-template <bool COH>
+// cluster barrier).
 __device__ __forceinline__ void batch_spline(BatchSmem &sm, const Params &P, Ring32 r32,
                                              int slot, int crank, int csize) {
   if (crank == 0)  // uniform over the CTA: the first tile holds CTA barriers
-    spline_tile<BSDE_FP32C, kSplHeadTS, COH, kBatchThreads>(P, Ring64{nullptr}, r32, slot, 0,
-                                                             blockDim.x, sm.sr, sm.sg, sm.sid);
+    spline_tile<BSDE_FP32C, kSplHeadTS, kBatchThreads>(P, Ring64{nullptr}, r32, slot, 0,
+                                                        blockDim.x, sm.sr, sm.sg, sm.sid);
   const int wpc = int(blockDim.x) / 32, nw = spline_warp_tiles(P.Nx);
   for (int wt = crank * wpc + int(threadIdx.x >> 5); wt < nw; wt += csize * wpc)
-    spline_warp_tile<COH>(P, r32, slot, wt);
+    spline_warp_tile(P, r32, slot, wt);
 }
 
 __global__ void k_batch_reset(int *queue, Stats *stats, int count) {
@@ -68,15 +67,12 @@ __global__ void k_batch_reset(int *queue, Stats *stats, int count) {
 }
 
 // FLAT: the step-tile form (see below), a template parameter so that each
-// form's kernel gets its own register allocation.  COH: level loads through
-// L2 (ld.global.cg), needed when the cluster's other CTAs, on other SMs,
-// write the ring slots this CTA reads within the launch; a 1-CTA cluster
-// reads only what its own threads wrote before a barrier, so its loads may
-// go through L1 (where a node's right-end record is the neighbouring lane's
-// left-end record).  Every instance of a batch has a ring region of its own,
-// so no other SM touches those lines within the launch.  The server reuses
-// pool memory across requests and keeps COH.
-template <int DRV, bool FLAT, bool COH>
+// form's kernel gets its own register allocation.  Level loads go through L1
+// (ldl): the ring slots a CTA reads were written by the cluster's CTAs before
+// the cluster barrier that ends the previous phase, whose release/acquire
+// semantics make them visible to those loads.  A node's right-end record is
+// the neighbouring lane's left-end record, so the loads hit L1.
+template <int DRV, bool FLAT>
 __device__ void batch_instance(BatchSmem &sm, unsigned char *ws, Stats *st,
                                cg::cluster_group &cl) {
   const Params &P = sm.D.P;
@@ -93,7 +89,7 @@ __device__ void batch_instance(BatchSmem &sm, unsigned char *ws, Stats *st,
       init_point<BSDE_FP32C>(P, r64, r32, m, i);
   cl.sync();
   for (int m = 0; m < P.k; ++m) {
-    batch_spline<COH>(sm, P, r32, (P.N - m) % P.nslot, crank, csize);
+    batch_spline(sm, P, r32, (P.N - m) % P.nslot, crank, csize);
     __syncthreads();  // CTA 0's shared-memory tile is reused by the next level
   }
   cl.sync();
@@ -107,26 +103,26 @@ __device__ void batch_instance(BatchSmem &sm, unsigned char *ws, Stats *st,
   for (int n = P.N - P.k; n >= 0; --n) {
     if constexpr (FLAT) {
       for (int t = crank; t < ntiles; t += csize)
-        step_tile32f<DRV, COH>(P, sm.D.dc32, r32, sm.tab, n, t * tw, st);
+        step_tile32f<DRV>(P, sm.D.dc32, r32, sm.tab, n, t * tw, st);
     } else {
       for (int t = crank; t < ntiles; t += csize) {
-        step_tile32<DRV, COH>(P, sm.D.dc32, r32, sm.tab, sm.part, n, t * kStepTP, st);
+        step_tile32<DRV>(P, sm.D.dc32, r32, sm.tab, sm.part, n, t * kStepTP, st);
         __syncthreads();
       }
     }
     cl.sync();
-    batch_spline<COH>(sm, P, r32, n % P.nslot, crank, csize);
+    batch_spline(sm, P, r32, n % P.nslot, crank, csize);
     cl.sync();
   }
   if (crank == 0 && tid == 0) {
     double ay, az;
-    readout_values<BSDE_FP32C, COH>(P, r64, r32, 0, ay, az);
+    readout_values<BSDE_FP32C>(P, r64, r32, 0, ay, az);
     st->y0 = ay;
     st->z0 = az;
   }
 }
 
-template <bool FLAT, bool COH>
+template <bool FLAT>
 __global__ void __launch_bounds__(kBatchThreads, 2)
     k_batch32(const InstDesc *__restrict__ descs, const int *__restrict__ order, int count,
               int *queue, unsigned char *ws, Stats *stats) {
@@ -155,11 +151,11 @@ __global__ void __launch_bounds__(kBatchThreads, 2)
     }
     __syncthreads();
     switch (sm.D.P.driver) {
-      case BSDE_DRIVER_LIN_SIN: batch_instance<BSDE_DRIVER_LIN_SIN, FLAT, COH>(sm, ws, stats + id, cl); break;
-      case BSDE_DRIVER_BS: batch_instance<BSDE_DRIVER_BS, FLAT, COH>(sm, ws, stats + id, cl); break;
-      case BSDE_DRIVER_LB: batch_instance<BSDE_DRIVER_LB, FLAT, COH>(sm, ws, stats + id, cl); break;
-      case BSDE_DRIVER_EX1: batch_instance<BSDE_DRIVER_EX1, FLAT, COH>(sm, ws, stats + id, cl); break;
-      default: batch_instance<BSDE_DRIVER_EX2, FLAT, COH>(sm, ws, stats + id, cl); break;
+      case BSDE_DRIVER_LIN_SIN: batch_instance<BSDE_DRIVER_LIN_SIN, FLAT>(sm, ws, stats + id, cl); break;
+      case BSDE_DRIVER_BS: batch_instance<BSDE_DRIVER_BS, FLAT>(sm, ws, stats + id, cl); break;
+      case BSDE_DRIVER_LB: batch_instance<BSDE_DRIVER_LB, FLAT>(sm, ws, stats + id, cl); break;
+      case BSDE_DRIVER_EX1: batch_instance<BSDE_DRIVER_EX1, FLAT>(sm, ws, stats + id, cl); break;
+      default: batch_instance<BSDE_DRIVER_EX2, FLAT>(sm, ws, stats + id, cl); break;
     }
   }
 }

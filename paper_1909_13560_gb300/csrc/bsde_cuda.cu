@@ -818,10 +818,7 @@ static int batch_enqueue(bsde_batch_t *b, cudaStream_t s) {
   Stats *stats = reinterpret_cast<Stats *>(b->ws + b->off_stats);
   k_batch_reset<<<(n + 255) / 256, 256, 0, s>>>(queue, stats, n);
   const size_t smem = sizeof(BatchSmem);
-  // a 1-CTA cluster's level loads may go through L1 (batch_instance)
-  const bool coh = b->cfg.cluster > 1;
-  auto *kern = b->cfg.flat_tiles ? (coh ? k_batch32<true, true> : k_batch32<true, false>)
-                                 : (coh ? k_batch32<false, true> : k_batch32<false, false>);
+  auto *kern = b->cfg.flat_tiles ? k_batch32<true> : k_batch32<false>;
   BSDE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      int(smem)));
   const int cl = b->cfg.cluster;

@@ -173,16 +173,16 @@ __device__ __forceinline__ void split_store(float4 *A, int64_t i, double y, doub
   A[i] = make_float4(yh, zh, yl, zl);
 }
 
-// Level loads.  Within one launch of the per-level kernels the levels they
-// read are constant, so any cache path is fine; the persistent batch kernel
-// rewrites ring slots between levels from other SMs, so there (COH = true)
-// the loads go to L2 (ld.global.cg), which the cluster barrier makes current.
-template <bool COH, typename T>
+// Level loads: plain loads through L1.  Within one launch of the per-level
+// kernels the levels they read are constant.  The persistent batch and
+// serving kernels rewrite ring slots between levels from other SMs of a
+// cluster; the cluster barrier between those phases (barrier.cluster.arrive
+// with release and barrier.cluster.wait with acquire semantics, at cluster
+// scope) orders the writes before the next phase's loads, so these loads see
+// them without bypassing L1.
+template <typename T>
 __device__ __forceinline__ T ldl(const T *p) {
-  if constexpr (COH)
-    return __ldcg(p);
-  else
-    return *p;
+  return *p;
 }
 
 // Programmatic dependent launch: a kernel launched with programmatic stream
@@ -332,7 +332,7 @@ __host__ __device__ constexpr int spline_span(int TS) {
 // Unknown m is M_{m+1}; the tile is unknowns [a, b), the forward sweep runs
 // over [a, rb) and the backward one over [a, min(b + 1, u)) (one more on the
 // right: FP32C cell b needs M_{b+1}).
-template <int PREC, int TS, bool COH, int NT>
+template <int PREC, int TS, int NT>
 __device__ __forceinline__ void spline_tile(const Params &P, Ring64 r64, Ring32 r32, int slot,
                                             int tile, int nt,
                                             typename SplineT<PREC>::T (*sr)[spline_span<PREC>(TS)],
@@ -364,7 +364,7 @@ __device__ __forceinline__ void spline_tile(const Params &P, Ring64 r64, Ring32 
         double vy[RC + 2], vz[RC + 2];
 #pragma unroll
         for (int q = 0; q < RC + 2; ++q) {
-          const double4_32a v = m0 + q < rb + 2 ? ldl<COH>(r64.ring + off + m0 + q)
+          const double4_32a v = m0 + q < rb + 2 ? ldl(r64.ring + off + m0 + q)
                                                 : make_double4_32a(0.0, 0.0, 0.0, 0.0);
           vy[q] = v.x;
           vz[q] = v.z;
@@ -382,7 +382,7 @@ __device__ __forceinline__ void spline_tile(const Params &P, Ring64 r64, Ring32 
         float4 v[RC + 2];
 #pragma unroll
         for (int q = 0; q < RC + 2; ++q)
-          v[q] = m0 + q < rb + 2 ? ldl<COH>(r32.A + off + m0 + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+          v[q] = m0 + q < rb + 2 ? ldl(r32.A + off + m0 + q) : make_float4(0.f, 0.f, 0.f, 0.f);
         const float inv6 = float(P.inv_dx2_6);
         float dy[RC + 1], dz[RC + 1];
 #pragma unroll
@@ -612,7 +612,7 @@ __global__ void __launch_bounds__(SplineLaunch<PREC>::NT)
   __shared__ T sid[kInvPivots];
   if (threadIdx.x < kInvPivots) sid[threadIdx.x] = T(P.invd[threadIdx.x]);
   wait_predecessor();
-  spline_tile<PREC, TS, false, NT>(P, r64, r32, slot, blockIdx.x, blockDim.x, sr, sg, sid);
+  spline_tile<PREC, TS, NT>(P, r64, r32, slot, blockIdx.x, blockDim.x, sr, sg, sid);
 }
 
 // ---------------------------------------------------------------------------
@@ -634,9 +634,7 @@ constexpr int kSplWarpThreads = 128;
 
 // One warp tile of the level in `slot`: output unknowns [s0, s0 + 104) with
 // s0 = kSplHeadTS + 104 wt (unknowns below kSplHeadTS are the first tile's).
-// Called by all 32 lanes of a warp; COH: level loads through L2 (the batch
-// kernels, whose levels other SMs write within the launch).
-template <bool COH>
+// Called by all 32 lanes of a warp.
 __device__ __forceinline__ void spline_warp_tile(const Params &P, Ring32 r32, int slot, int wt) {
   constexpr int W = SplineT<BSDE_FP32C>::W, CP = kSplWarpCP;
   const int u = int(P.Nx - 2);
@@ -653,7 +651,7 @@ __device__ __forceinline__ void spline_warp_tile(const Params &P, Ring32 r32, in
     float4 v[CP + 2];
 #pragma unroll
     for (int q = 0; q < CP + 2; ++q)
-      v[q] = m0 + q <= u + 1 ? ldl<COH>(r32.A + off + m0 + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+      v[q] = m0 + q <= u + 1 ? ldl(r32.A + off + m0 + q) : make_float4(0.f, 0.f, 0.f, 0.f);
     float dy[CP + 1], dz[CP + 1];
 #pragma unroll
     for (int q = 0; q < CP + 1; ++q) {
@@ -750,12 +748,12 @@ __global__ void __launch_bounds__(kSplWarpThreads)
   if (blockIdx.x == 0) {  // uniform over the CTA
     if (threadIdx.x < kInvPivots) sid[threadIdx.x] = float(P.invd[threadIdx.x]);
     wait_predecessor();
-    spline_tile<BSDE_FP32C, kSplHeadTS, false, kSplWarpThreads>(
+    spline_tile<BSDE_FP32C, kSplHeadTS, kSplWarpThreads>(
         P, Ring64{nullptr}, r32, slot, 0, blockDim.x, sr, sg, sid);
     return;
   }
   wait_predecessor();
-  spline_warp_tile<false>(P, r32, slot,
+  spline_warp_tile(P, r32, slot,
                           (blockIdx.x - 1) * (kSplWarpThreads / 32) + (threadIdx.x >> 5));
 }
 
@@ -1194,7 +1192,7 @@ struct Acc32 {
 // before the current pair's arithmetic (2 pays in the single-solve flat
 // kernel, 2% at config3, whose threads have the registers; the grouped tiles
 // and the batch kernel, which would spill, keep 1).
-template <int DRV, bool CLAMP, bool COH, bool ZF = false, int UNR = 1>
+template <int DRV, bool CLAMP, bool ZF = false, int UNR = 1>
 __device__ __forceinline__ void pairs32(const DrvC<float> &dc, Ring32 r, int64_t off,
                                         const PairF32 *row, int q0, int q1, int ii, int last,
                                         float tj, float et, float emt, Acc32 &acc) {
@@ -1211,10 +1209,10 @@ __device__ __forceinline__ void pairs32(const DrvC<float> &dc, Ring32 r, int64_t
     // the cell's right end (a clamped node sits on an end node with zero
     // weights, so its right end is the node itself)
     const int ca1 = CLAMP && ca == last ? ca : ca + 1, cb1 = CLAMP && cb == last ? cb : cb + 1;
-    const float4 aa0 = ldl<COH>(A + ca), aa1 = ldl<COH>(A + ca1), ba0 = ldl<COH>(A + cb),
-                 ba1 = ldl<COH>(A + cb1);
-    const float2 ma0 = ldl<COH>(M + ca), ma1 = ldl<COH>(M + ca1), mb0 = ldl<COH>(M + cb),
-                 mb1 = ldl<COH>(M + cb1);
+    const float4 aa0 = ldl(A + ca), aa1 = ldl(A + ca1), ba0 = ldl(A + cb),
+                 ba1 = ldl(A + cb1);
+    const float2 ma0 = ldl(M + ca), ma1 = ldl(M + ca1), mb0 = ldl(M + cb),
+                 mb1 = ldl(M + cb1);
     pair_math<DRV, ZF>(dc, tj, et, emt, e0, e1, e2, e3, e4, aa0, aa1, ma0, ma1, ba0, ba1, mb0,
                        mb1, acc.S, acc.C, acc.Fz, acc.Fy, acc.FyC);
   }
@@ -1344,7 +1342,7 @@ __device__ __forceinline__ float finish_point32(const Params &P, const DrvC<floa
   return d;
 }
 
-template <int DRV, bool COH>
+template <int DRV>
 __device__ __forceinline__ void finish_points32(const Params &P, const DrvC<float> &dc,
                                                 float4 *__restrict__ ringA, const float *part,
                                                 int G, int n, int i0, Stats *st, float prev_y) {
@@ -1371,7 +1369,7 @@ __device__ __forceinline__ void finish_points32(const Params &P, const DrvC<floa
 // or in the kernel's parameters) and `part` is in shared memory.  Thread tp of group g accumulates the pairs of group g for
 // point i0 + tp; threads of groups g >= G idle.  The caller separates
 // consecutive tiles by a barrier (part is reused).
-template <int DRV, bool COH>
+template <int DRV>
 __device__ __forceinline__ void step_tile32(const Params &P, const DrvC<float> &dc, Ring32 r32,
                                             const PairF32 *tab, float *part, int n, int i0,
                                             Stats *st) {
@@ -1381,7 +1379,7 @@ __device__ __forceinline__ void step_tile32(const Params &P, const DrvC<float> &
   // the Picard start y^{n+1} of the points this thread finishes, loaded early
   float prev_y = 0.f;
   if (threadIdx.x < kStepTP && i0 + int(threadIdx.x) <= last)
-    prev_y = ldl<COH>(r32.A + int64_t((n + 1) % P.nslot) * P.Nx + i0 + threadIdx.x).x;
+    prev_y = ldl(r32.A + int64_t((n + 1) % P.nslot) * P.Nx + i0 + threadIdx.x).x;
   if (g < G) {
     const Group32 w = group32(P, g, i0);
     Acc32 acc{make_float2(0.f, 0.f), make_float2(0.f, 0.f), 0.f, 0.f, 0.f};
@@ -1390,16 +1388,16 @@ __device__ __forceinline__ void step_tile32(const Params &P, const DrvC<float> &
     level_time<DRV>(P, n + w.j, tj, et, emt);
     const PairF32 *row = tab + (w.j - 1) * P.Lp;
     if (P.zform && w.j == 1)  // the E[y DeltaW] z form (clamping always on)
-      pairs32<DRV, true, COH, true>(dc, r32, off, row, w.q0, w.q1, i0 + tp, last, tj, et, emt,
+      pairs32<DRV, true, true>(dc, r32, off, row, w.q0, w.q1, i0 + tp, last, tj, et, emt,
                                     acc);
     else if (w.interior)
-      pairs32<DRV, false, COH>(dc, r32, off, row, w.q0, w.q1, i0 + tp, last, tj, et, emt, acc);
+      pairs32<DRV, false>(dc, r32, off, row, w.q0, w.q1, i0 + tp, last, tj, et, emt, acc);
     else  // cells clamp onto the grid, so points past the end are harmless
-      pairs32<DRV, true, COH>(dc, r32, off, row, w.q0, w.q1, i0 + tp, last, tj, et, emt, acc);
+      pairs32<DRV, true>(dc, r32, off, row, w.q0, w.q1, i0 + tp, last, tj, et, emt, acc);
     store_partials(part, G, g, tp, acc);
   }
   __syncthreads();
-  finish_points32<DRV, COH>(P, dc, r32.A, part, G, n, i0, st, prev_y);
+  finish_points32<DRV>(P, dc, r32.A, part, G, n, i0, st, prev_y);
 }
 
 
@@ -1430,7 +1428,7 @@ __global__ void __launch_bounds__(kStepTP * kMaxGroups, 3)
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float *part = reinterpret_cast<float *>(smem_raw);  // [kPartArrays][G][kStepTP]
   wait_predecessor();
-  step_tile32<DRV, false>(P, dc, r32, tab.e, part, n, blockIdx.x * kStepTP, st);
+  step_tile32<DRV>(P, dc, r32, tab.e, part, n, blockIdx.x * kStepTP, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -1448,7 +1446,7 @@ constexpr int kFlatTP = 128;  // grid points (threads) per CTA
 // groups of a point in turn.  `tab` is the pair table (kernel parameters or
 // shared memory: its reads are uniform across the CTA either way).  Needs no
 // barrier, before or after.  UNR as for pairs32 (the interior pairs).
-template <int DRV, bool COH, int UNR = 1>
+template <int DRV, int UNR = 1>
 __device__ __forceinline__ void step_tile32f(const Params &P, const DrvC<float> &dc, Ring32 r32,
                                              const PairF32 *tab, int n, int i0, Stats *st) {
   const int ii = i0 + int(threadIdx.x);
@@ -1456,7 +1454,7 @@ __device__ __forceinline__ void step_tile32f(const Params &P, const DrvC<float> 
   const int tw = int(blockDim.x);
   const bool active = ii <= last;
   float prev_y = 0.f;
-  if (active) prev_y = ldl<COH>(r32.A + int64_t((n + 1) % P.nslot) * P.Nx + ii).x;
+  if (active) prev_y = ldl(r32.A + int64_t((n + 1) % P.nslot) * P.Nx + ii).x;
   Sums32 s{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   for (int g = 0; g < P.G; ++g) {
     const int j = g / P.S + 1, lc = g % P.S;
@@ -1470,11 +1468,11 @@ __device__ __forceinline__ void step_tile32f(const Params &P, const DrvC<float> 
     level_time<DRV>(P, n + j, tj, et, emt);
     const PairF32 *row = tab + (j - 1) * P.Lp;
     if (P.zform && j == 1)
-      pairs32<DRV, true, COH, true>(dc, r32, off, row, q0, q1, ii, last, tj, et, emt, acc);
+      pairs32<DRV, true, true>(dc, r32, off, row, q0, q1, ii, last, tj, et, emt, acc);
     else if (interior)
-      pairs32<DRV, false, COH, false, UNR>(dc, r32, off, row, q0, q1, ii, last, tj, et, emt, acc);
+      pairs32<DRV, false, false, UNR>(dc, r32, off, row, q0, q1, ii, last, tj, et, emt, acc);
     else
-      pairs32<DRV, true, COH>(dc, r32, off, row, q0, q1, ii, last, tj, et, emt, acc);
+      pairs32<DRV, true>(dc, r32, off, row, q0, q1, ii, last, tj, et, emt, acc);
     fold_group(s, acc.S.y, acc.C.y, acc.Fz, acc.Fy, acc.S.x, acc.C.x, acc.FyC);
   }
   int it = 0;
@@ -1488,7 +1486,7 @@ __global__ void __launch_bounds__(kFlatTP, 8)
     k_step32f(const Params P, const DrvC<float> dc, Ring32 r32,
               const __grid_constant__ PairTab32 tab, int n, Stats *st) {
   wait_predecessor();
-  step_tile32f<DRV, false, 2>(P, dc, r32, tab.e, n, blockIdx.x * kFlatTP, st);
+  step_tile32f<DRV, 2>(P, dc, r32, tab.e, n, blockIdx.x * kFlatTP, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -1629,7 +1627,7 @@ __global__ void __launch_bounds__(kStepTP * kMaxGroups, 3)
     store_partials(part, G, g, tp, acc);
   }
   __syncthreads();
-  finish_points32<DRV, false>(P, dc, r32.A, part, G, n, i0, st, prev_y);
+  finish_points32<DRV>(P, dc, r32.A, part, G, n, i0, st, prev_y);
 }
 
 // ---------------------------------------------------------------------------
@@ -1707,7 +1705,7 @@ __global__ void __launch_bounds__(256) k_fma_probe(int iters, double *sink) {
 // ---------------------------------------------------------------------------
 // S4: readout of y^0, z^0 at x0 by the spline (Section 3.1 step 3).
 // ---------------------------------------------------------------------------
-template <int PREC, bool COH = false>
+template <int PREC>
 __device__ void readout_values(const Params &P, Ring64 r64, Ring32 r32, int slot, double &ay,
                                double &az) {
   const int64_t off = int64_t(slot) * P.Nx;
@@ -1727,10 +1725,10 @@ __device__ void readout_values(const Params &P, Ring64 r64, Ring32 r32, int slot
   }
   for (int q = 0; q < 2; ++q) {
     if constexpr (PREC == BSDE_FP64) {
-      const double4_32a a = ldl<COH>(r64.ring + off + c + q);
+      const double4_32a a = ldl(r64.ring + off + c + q);
       v[0][q] = a.x; M[0][q] = a.y; v[1][q] = a.z; M[1][q] = a.w;
     } else {
-      const float4 a = ldl<COH>(r32.A + off + c + q);
+      const float4 a = ldl(r32.A + off + c + q);
       v[0][q] = double(a.x) + double(a.z);
       v[1][q] = double(a.y) + double(a.w);
     }
@@ -1744,7 +1742,7 @@ __device__ void readout_values(const Params &P, Ring64 r64, Ring32 r32, int slot
   } else {
     // curvature part kappa (P + theta Q), P and Q formed in FP32 from the
     // nodes' second derivatives as the step kernels form them
-    const float2 m0 = ldl<COH>(r32.M + off + c), m1 = ldl<COH>(r32.M + off + c + 1);
+    const float2 m0 = ldl(r32.M + off + c), m1 = ldl(r32.M + off + c + 1);
     const float Py = __fmaf_rn(2.f, m0.x, m1.x), Pz = __fmaf_rn(2.f, m0.y, m1.y);
     const float Qy = __fsub_rn(m1.x, m0.x), Qz = __fsub_rn(m1.y, m0.y);
     const double ka = -c6 * th * om;

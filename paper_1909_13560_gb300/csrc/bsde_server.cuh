@@ -119,11 +119,11 @@ __global__ void __launch_bounds__(kBatchThreads, 2)
     __syncthreads();
     cl.sync();
     switch (sm.D.P.driver) {
-      case BSDE_DRIVER_LIN_SIN: batch_instance<BSDE_DRIVER_LIN_SIN, true, true>(sm, pool, st, cl); break;
-      case BSDE_DRIVER_BS: batch_instance<BSDE_DRIVER_BS, true, true>(sm, pool, st, cl); break;
-      case BSDE_DRIVER_LB: batch_instance<BSDE_DRIVER_LB, true, true>(sm, pool, st, cl); break;
-      case BSDE_DRIVER_EX1: batch_instance<BSDE_DRIVER_EX1, true, true>(sm, pool, st, cl); break;
-      default: batch_instance<BSDE_DRIVER_EX2, true, true>(sm, pool, st, cl); break;
+      case BSDE_DRIVER_LIN_SIN: batch_instance<BSDE_DRIVER_LIN_SIN, true>(sm, pool, st, cl); break;
+      case BSDE_DRIVER_BS: batch_instance<BSDE_DRIVER_BS, true>(sm, pool, st, cl); break;
+      case BSDE_DRIVER_LB: batch_instance<BSDE_DRIVER_LB, true>(sm, pool, st, cl); break;
+      case BSDE_DRIVER_EX1: batch_instance<BSDE_DRIVER_EX1, true>(sm, pool, st, cl); break;
+      default: batch_instance<BSDE_DRIVER_EX2, true>(sm, pool, st, cl); break;
     }
     // batch_instance ends with the readout by rank 0 after the last barrier;
     // wait for the Picard statistics of every CTA, then publish

@@ -124,6 +124,24 @@ def test_batch_flat_tiles_equal_grouped_tiles_bitwise(B, groups):
         assert x["y0"] == y["y0"] and x["z0"] == y["z0"] and x["status"] == y["status"]
 
 
+@pytest.mark.parametrize("cluster", [2, 4, 8])
+def test_batch_cluster_sizes_equal_bitwise(B, cluster):
+    """The CTAs of a cluster share an instance's level phases; a cluster size
+    changes which SM computes which tile, never a result: bitwise equal to
+    1-CTA clusters at the same group split."""
+    probs = _mixed(count=20, seed=29)
+    bs = B.BatchSolver(probs)
+    bs.set_config(1, 1, 1)
+    a = bs.solve()
+    bs.set_config(cluster, 1, 1)
+    b = bs.solve()
+    b2 = bs.solve()
+    bs.close()
+    for x, y, y2 in zip(a, b, b2):
+        assert x["y0"] == y["y0"] and x["z0"] == y["z0"] and x["status"] == y["status"]
+        assert y["y0"] == y2["y0"] and y["z0"] == y2["z0"]
+
+
 def test_batch_rejects_fp64_problems(B):
     with pytest.raises(B.BsdeError) as ei:
         B.bsde_batch_workspace_bytes([W.sin_problem()], "fp64")

@@ -49,10 +49,13 @@ def _wait_all(srv, n, timeout=60.0):
     return got
 
 
-def test_results_alone_equal_in_the_mix(B):
+@pytest.mark.parametrize("cluster", [1, 8])
+def test_results_alone_equal_in_the_mix(B, cluster):
+    """Alone or in a mix, on any cluster, in pool memory that other requests
+    used before: the same result, bitwise."""
     reqs = _requests()
     srv = B.Server(slots=64, pool_bytes=1 << 30)
-    srv.start(cluster=1, idle_ms=20000)
+    srv.start(cluster=cluster, idle_ms=20000)
     try:
         slots = [srv.submit(p) for p in reqs]
         assert all(s is not None for s in slots)
