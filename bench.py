@@ -866,6 +866,11 @@ def run_batch(args, rank, world, local_rank):
             "roofline": {"kernel": "k_batch32", "bound": "alu", "achieved": achieved,
                          "peak": pk["fp32_tflops"], "unit": "TFLOP/s",
                          "frac": achieved / pk["fp32_tflops"], "traffic": None,
+                         "traffic_note": "one launch runs the whole batch (about 0.5 s), too "
+                                         "long for a multi-pass capture; the DRAM bytes of "
+                                         "512-instance launches (profiles/k_batch32_config4.md) "
+                                         "do not scale by instance count, since how many rings "
+                                         "stay in L2 depends on how many run at once",
                          "flop_count": f"{FLOP_NODE_COMP} per node (compensated sums), 3 per "
                                        "step j, 6 per Picard iteration; whole batch over the "
                                        "step time",
@@ -1313,6 +1318,11 @@ def run_general(args, rank, world, local_rank):
                          "bound": "alu", "achieved": achieved,
                          "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          "traffic": None,
+                         "traffic_note": ("the step launches of the two problems differ; one "
+                                          "captured Vasicek launch read 3.16 MB "
+                                          "(profiles/k_step32_gen_general.md), its input "
+                                          "levels once") if prec != "fp64" else
+                                         "no DRAM capture of the FP64 general kernel",
                          "peak_source": "measured in this run: bsde_fma_probe, "
                                         + ("FP64 FMA" if prec == "fp64" else
                                            "FP32 FMA (better of scalar and packed FP32x2)")
