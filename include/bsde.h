@@ -316,8 +316,9 @@ typedef struct bsde_batch_config {
   int32_t target_groups; /* thread groups per grid point in the step tiles, 1..6 */
   int32_t flat_tiles;    /* step-tile form: 0 = grouped tiles of 64 points x the
                             groups (partial sums in shared memory, a barrier per
-                            tile); 1 = flat tiles of one point per thread (384
-                            points), each thread running its point's groups in
+                            tile; CTAs of 384 threads, 2 per SM); 1 = flat
+                            tiles of one point per thread (CTAs of 256 points, 3
+                            per SM), each thread running its point's groups in
                             turn with no barrier                                 */
   int32_t reserved[5];
 } bsde_batch_config;

@@ -25,7 +25,10 @@ struct alignas(16) InstDesc {
   int64_t pad;
 };
 
-constexpr int kBatchThreads = kStepTP * 6;          // up to six groups per point
+constexpr int kBatchThreads = kStepTP * 6;  // grouped tiles: up to six groups per point
+// flat tiles (one point per thread): 256-point tiles divide the power-of-two
+// grids of a batch evenly, and three such CTAs fit an SM
+constexpr int kBatchFlatThreads = 256;
 
 // The spline of a level runs as in a single solve's warp-tiled kernel: the
 // cluster's first CTA takes the first tile (the exact serial head; shared
@@ -42,12 +45,13 @@ struct alignas(16) BatchSmem {
 
 // The spline of the level in `slot` by the cluster's CTAs (every thread of
 // every CTA calls it; the caller separates it from the step phases by a
-// cluster barrier).
+// cluster barrier).  NT: the first tile's thread count (<= blockDim.x).
+template <int NT>
 __device__ __forceinline__ void batch_spline(BatchSmem &sm, const Params &P, Ring32 r32,
                                              int slot, int crank, int csize) {
   if (crank == 0)  // uniform over the CTA: the first tile holds CTA barriers
-    spline_tile<BSDE_FP32C, kSplHeadTS, kBatchThreads>(P, Ring64{nullptr}, r32, slot, 0,
-                                                        blockDim.x, sm.sr, sm.sg, sm.sid);
+    spline_tile<BSDE_FP32C, kSplHeadTS, NT>(P, Ring64{nullptr}, r32, slot, 0, blockDim.x, sm.sr,
+                                            sm.sg, sm.sid);
   const int wpc = int(blockDim.x) / 32, nw = spline_warp_tiles(P.Nx);
   for (int wt = crank * wpc + int(threadIdx.x >> 5); wt < nw; wt += csize * wpc)
     spline_warp_tile(P, r32, slot, wt);
@@ -78,6 +82,7 @@ __device__ void batch_instance(BatchSmem &sm, unsigned char *ws, Stats *st,
   const Params &P = sm.D.P;
   const int crank = int(cl.block_rank()), csize = int(cl.num_blocks());
   const int tid = threadIdx.x, nt = blockDim.x;
+  constexpr int kNT = FLAT ? kBatchFlatThreads : kBatchThreads;  // blockDim.x >= kNT
   float4 *ringA = reinterpret_cast<float4 *>(ws + sm.D.ringA);
 
   Ring64 r64{nullptr};
@@ -89,7 +94,7 @@ __device__ void batch_instance(BatchSmem &sm, unsigned char *ws, Stats *st,
       init_point<BSDE_FP32C>(P, r64, r32, m, i);
   cl.sync();
   for (int m = 0; m < P.k; ++m) {
-    batch_spline(sm, P, r32, (P.N - m) % P.nslot, crank, csize);
+    batch_spline<kNT>(sm, P, r32, (P.N - m) % P.nslot, crank, csize);
     __syncthreads();  // CTA 0's shared-memory tile is reused by the next level
   }
   cl.sync();
@@ -111,7 +116,7 @@ __device__ void batch_instance(BatchSmem &sm, unsigned char *ws, Stats *st,
       }
     }
     cl.sync();
-    batch_spline(sm, P, r32, n % P.nslot, crank, csize);
+    batch_spline<kNT>(sm, P, r32, n % P.nslot, crank, csize);
     cl.sync();
   }
   if (crank == 0 && tid == 0) {
@@ -123,7 +128,7 @@ __device__ void batch_instance(BatchSmem &sm, unsigned char *ws, Stats *st,
 }
 
 template <bool FLAT>
-__global__ void __launch_bounds__(kBatchThreads, 2)
+__global__ void __launch_bounds__(FLAT ? kBatchFlatThreads : kBatchThreads, FLAT ? 3 : 2)
     k_batch32(const InstDesc *__restrict__ descs, const int *__restrict__ order, int count,
               int *queue, unsigned char *ws, Stats *stats) {
   extern __shared__ __align__(128) unsigned char smem_raw[];

@@ -828,7 +828,7 @@ static int batch_enqueue(bsde_batch_t *b, cudaStream_t s) {
   attr[0].val.clusterDim.x = unsigned(cl);
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
-  lc.blockDim = dim3(kBatchThreads, 1, 1);
+  lc.blockDim = dim3(b->cfg.flat_tiles ? kBatchFlatThreads : kBatchThreads, 1, 1);
   lc.dynamicSmemBytes = smem;
   lc.stream = s;
   lc.attrs = attr;
@@ -1178,7 +1178,7 @@ int bsde_server_start(bsde_server_t *s, void *stream, int cluster, int idle_ms) 
   attr[0].val.clusterDim.x = unsigned(cluster);
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
-  lc.blockDim = dim3(kBatchThreads, 1, 1);
+  lc.blockDim = dim3(kBatchFlatThreads, 1, 1);  // requests run flat step tiles
   lc.dynamicSmemBytes = smem;
   lc.stream = st;
   lc.attrs = attr;

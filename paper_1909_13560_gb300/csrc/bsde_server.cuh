@@ -54,7 +54,7 @@ __device__ __forceinline__ void st_release_sys(uint32_t *p, uint32_t v) {
   asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__global__ void __launch_bounds__(kBatchThreads, 2)
+__global__ void __launch_bounds__(kBatchFlatThreads, 3)
     k_server32(ServerCtl *ctl, ServerSlot *slots, ServerDev *dev, Stats *dstats,
                unsigned char *pool, unsigned long long idle_ns) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
