@@ -753,8 +753,7 @@ __global__ void __launch_bounds__(kSplWarpThreads)
     return;
   }
   wait_predecessor();
-  spline_warp_tile(P, r32, slot,
-                          (blockIdx.x - 1) * (kSplWarpThreads / 32) + (threadIdx.x >> 5));
+  spline_warp_tile(P, r32, slot, (blockIdx.x - 1) * (kSplWarpThreads / 32) + (threadIdx.x >> 5));
 }
 
 // ---------------------------------------------------------------------------
@@ -1209,10 +1208,8 @@ __device__ __forceinline__ void pairs32(const DrvC<float> &dc, Ring32 r, int64_t
     // the cell's right end (a clamped node sits on an end node with zero
     // weights, so its right end is the node itself)
     const int ca1 = CLAMP && ca == last ? ca : ca + 1, cb1 = CLAMP && cb == last ? cb : cb + 1;
-    const float4 aa0 = ldl(A + ca), aa1 = ldl(A + ca1), ba0 = ldl(A + cb),
-                 ba1 = ldl(A + cb1);
-    const float2 ma0 = ldl(M + ca), ma1 = ldl(M + ca1), mb0 = ldl(M + cb),
-                 mb1 = ldl(M + cb1);
+    const float4 aa0 = ldl(A + ca), aa1 = ldl(A + ca1), ba0 = ldl(A + cb), ba1 = ldl(A + cb1);
+    const float2 ma0 = ldl(M + ca), ma1 = ldl(M + ca1), mb0 = ldl(M + cb), mb1 = ldl(M + cb1);
     pair_math<DRV, ZF>(dc, tj, et, emt, e0, e1, e2, e3, e4, aa0, aa1, ma0, ma1, ba0, ba1, mb0,
                        mb1, acc.S, acc.C, acc.Fz, acc.Fy, acc.FyC);
   }
@@ -1366,9 +1363,10 @@ __device__ __forceinline__ void finish_points32(const Params &P, const DrvC<floa
 
 // One tile of kStepTP points of level n with direct loads, called by every
 // thread of the CTA; `tab` is the pair table of the problem (in shared memory
-// or in the kernel's parameters) and `part` is in shared memory.  Thread tp of group g accumulates the pairs of group g for
-// point i0 + tp; threads of groups g >= G idle.  The caller separates
-// consecutive tiles by a barrier (part is reused).
+// or in the kernel's parameters) and `part` is in shared memory.  Thread tp
+// of group g accumulates the pairs of group g for point i0 + tp; threads of
+// groups g >= G idle.  The caller separates consecutive tiles by a barrier
+// (part is reused).
 template <int DRV>
 __device__ __forceinline__ void step_tile32(const Params &P, const DrvC<float> &dc, Ring32 r32,
                                             const PairF32 *tab, float *part, int n, int i0,
@@ -1388,8 +1386,7 @@ __device__ __forceinline__ void step_tile32(const Params &P, const DrvC<float> &
     level_time<DRV>(P, n + w.j, tj, et, emt);
     const PairF32 *row = tab + (w.j - 1) * P.Lp;
     if (P.zform && w.j == 1)  // the E[y DeltaW] z form (clamping always on)
-      pairs32<DRV, true, true>(dc, r32, off, row, w.q0, w.q1, i0 + tp, last, tj, et, emt,
-                                    acc);
+      pairs32<DRV, true, true>(dc, r32, off, row, w.q0, w.q1, i0 + tp, last, tj, et, emt, acc);
     else if (w.interior)
       pairs32<DRV, false>(dc, r32, off, row, w.q0, w.q1, i0 + tp, last, tj, et, emt, acc);
     else  // cells clamp onto the grid, so points past the end are harmless
