@@ -39,7 +39,7 @@ static int fail(int code, const std::string &msg) {
 class DeviceGuard {
  public:
   explicit DeviceGuard(int dev) {
-    cudaGetDevice(&prev_);
+    if (cudaGetDevice(&prev_) != cudaSuccess) prev_ = dev;  // then nothing to restore
     if (prev_ != dev) cudaSetDevice(dev);
     dev_ = dev;
   }
@@ -383,12 +383,14 @@ int bsde_plan(const bsde_problem *p, void *dev_workspace, size_t bytes, bsde_pla
     return fail(BSDE_ENOSPC, "workspace smaller than bsde_workspace_bytes()");
   if (reinterpret_cast<uintptr_t>(dev_workspace) % 256)
     return fail(BSDE_EINVAL, "workspace must be 256-byte aligned");
+  int device = 0;
+  BSDE_CUDA_TRY(cudaGetDevice(&device));
   bsde_plan_t *pl = new (std::nothrow) bsde_plan_t();
   if (!pl) return fail(BSDE_ENOMEM, "plan allocation");
   pl->prob = *p;
   pl->P = P;
   pl->lay = lay;
-  cudaGetDevice(&pl->device);
+  pl->device = device;
   pl->ws = static_cast<unsigned char *>(dev_workspace);
   pl->ws_bytes = bytes;
   driver_coefs(P, pl->dc64, pl->dc32);
@@ -912,10 +914,12 @@ int bsde_plan_batch(int n, const bsde_problem *ps, void *dev_workspace, size_t b
     return fail(BSDE_ENOSPC, "workspace smaller than bsde_batch_workspace_bytes()");
   if (reinterpret_cast<uintptr_t>(dev_workspace) % 256)
     return fail(BSDE_EINVAL, "workspace must be 256-byte aligned");
+  int device = 0;
+  BSDE_CUDA_TRY(cudaGetDevice(&device));
   bsde_batch_t *b = new (std::nothrow) bsde_batch_t();
   if (!b) return fail(BSDE_ENOMEM, "batch allocation");
   b->n = n;
-  cudaGetDevice(&b->device);
+  b->device = device;
   b->ws = static_cast<unsigned char *>(dev_workspace);
   b->ws_bytes = bytes;
   b->off_desc = L.off_desc;
@@ -1121,10 +1125,12 @@ int bsde_server_create(void *dev_workspace, size_t bytes, int slots, size_t pool
   if (!dev_workspace || bytes < need) return fail(BSDE_ENOSPC, "server workspace too small");
   if (reinterpret_cast<uintptr_t>(dev_workspace) % 256)
     return fail(BSDE_EINVAL, "workspace must be 256-byte aligned");
+  int device = 0;
+  BSDE_CUDA_TRY(cudaGetDevice(&device));
   bsde_server_t *s = new (std::nothrow) bsde_server_t();
   if (!s) return fail(BSDE_ENOMEM, "server allocation");
   auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
-  cudaGetDevice(&s->device);
+  s->device = device;
   s->nslots = slots;
   s->ws = static_cast<unsigned char *>(dev_workspace);
   s->ws_bytes = bytes;
