@@ -108,3 +108,21 @@ def test_roofline_flop_counts():
     assert fp == {"x2": 6 * 8 * 66.0, "x1": 6 * 8 * 60.0 + 6 * 27.0 + 80.0}
     f32 = bench.flops_per_gp_step_tp(6, 8, "fp32c")
     assert f32["x2"] == 6 * 4 * 195.0 and f32["x1"] == 6 * 4 * 193.0 + 80.0
+
+
+@pytest.mark.parametrize("kernel", ["k_step32f_config3", "k_step32f_config2", "k_step32_config2",
+                                    "k2_tp1_32", "k2_tp2_32", "k2_tp1", "k2_tp2", "k2_step32p"])
+def test_roofline_traffic_entries(kernel):
+    """Every kernel whose DRAM traffic the bench line reports has an entry in
+    the committed traffic table, positive, with the profile summary it came
+    from."""
+    t = bench._traffic(kernel)
+    assert t is not None and t > 0
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    with open(os.path.join(root, "profiles", "dram_traffic.json")) as fh:
+        entry = json.load(fh)[kernel]
+    assert entry["workload"]
+    refs = [w for w in entry["note"].replace(",", " ").replace(")", " ").split()
+            if w.endswith(".md")]
+    assert refs and all(os.path.exists(os.path.join(root, "profiles", r)) for r in refs)
+    assert bench._traffic("no_such_kernel") is None
